@@ -1,0 +1,305 @@
+"""Pins for the FP64 oracle: facts fixed by the paper or by mathematics,
+independent of the oracle's own formulas (CPU only)."""
+
+import math
+import os
+
+import numpy as np
+import pytest
+
+from oracle import fast_hals as fh
+from oracle import mlp, nnls, objective as ob, pl_nmf, tile_model as tm
+from paper_1904_07935_b300 import synth
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+EPS = 1e-16
+
+
+def _golden(name):
+    with open(os.path.join(GOLDEN, name)) as f:
+        rows = [ln.split(None, 2) for ln in f if ln.strip() and not ln.startswith("#")]
+    return {r[0]: float(r[1]) for r in rows}
+
+
+def _dense(V, D, K0, seed):
+    return synth.planted_dense(V, D, K0, seed).A.astype(np.float64)
+
+
+# --- Sec. 3.3: the tiled reorder performs the same operations -----------------
+
+@pytest.mark.parametrize("K,T", [(7, 1), (7, 2), (7, 3), (7, 5), (7, 7), (16, 16),
+                                 (20, 3), (20, 16), (33, 8)])
+def test_reorder_identity(K, T):
+    """Alg. 2 (three phases) equals Alg. 1 (sequential k loop) to rounding,
+    for T dividing K, T not dividing K, T = 1 and T = K."""
+    A = _dense(45, 38, 5, 7)
+    W0, H0 = synth.init_factors(21 + K, 45, 38, K)
+    W = fh.normalize_init(W0)
+    H = H0.astype(np.float64)
+    tr = {}
+    W1, H1 = fh.iteration(A, W, H, EPS, trace=tr)
+    Hp = pl_nmf.update_h(tr["R"], tr["S"], H, T, EPS)
+    Wp = pl_nmf.update_w(tr["P"], tr["Q"], W, T, EPS)
+    assert np.max(np.abs(Hp - H1)) <= 1e-12 * np.max(np.abs(H1))
+    assert np.max(np.abs(Wp - W1)) <= 1e-12 * np.max(np.abs(W1))
+
+
+def test_reorder_identity_sparse_with_empty_rows():
+    sp = synth.sparse_termdoc(400, 150, 3, mean_terms=15)
+    assert np.any(np.diff(sp.A.row_ptr) == 0)          # Zipf tail words never drawn
+    W0, H0 = synth.init_factors(4, 400, 150, 12)
+    W = fh.normalize_init(W0)
+    tr = {}
+    W1, H1 = fh.iteration(sp.A, W, H0, EPS, trace=tr)
+    for T in (4, 5):
+        assert np.allclose(pl_nmf.update_w(tr["P"], tr["Q"], W, T, EPS), W1, rtol=0, atol=1e-13)
+        assert np.allclose(pl_nmf.update_h(tr["R"], tr["S"], H0, T, EPS), H1, rtol=0,
+                           atol=1e-12 * np.abs(H1).max())
+    # an empty row of A has P = 0, so every entry is clamped to eps before the
+    # column is normalised: all empty rows share the column's minimum value
+    empty = np.where(np.diff(sp.A.row_ptr) == 0)[0]
+    assert np.all(W1[empty] == W1[empty[0]][None, :])
+    assert np.all(W1[empty[0]] == W1.min(axis=0))
+
+
+# --- monotone objective --------------------------------------------------------
+
+def test_objective_non_increasing():
+    """With unit-norm W columns each coordinate step is an exact minimiser, so
+    the objective never increases (up to rounding) after the first iteration."""
+    A = _dense(80, 60, 6, 3)
+    W0, H0 = synth.init_factors(8, 80, 60, 9)
+    W, H = fh.normalize_init(W0), H0.astype(np.float64)
+    fs = []
+    for _ in range(60):
+        W, H = fh.iteration(A, W, H, EPS)
+        fs.append(ob.frob2_direct(A, W, H))
+    for a, b in zip(fs, fs[1:]):
+        assert b <= a * (1 + 1e-12)
+    assert fs[-1] < 0.5 * fs[0]
+
+
+def test_non_negativity_and_unit_columns():
+    sp = synth.sparse_termdoc(300, 120, 5, mean_terms=12)
+    W0, H0 = synth.init_factors(6, 300, 120, 10)
+    W, H, _ = fh.run(sp.A, W0, H0, 5)
+    # H is clamped at eps; W is clamped at eps and then divided by its column
+    # norm, so it stays strictly positive
+    assert H.min() >= EPS and W.min() > 0
+    assert np.allclose(np.linalg.norm(W, axis=0), 1.0, atol=1e-14)
+
+
+# --- K = 1: clamped power iteration --------------------------------------------
+
+def test_k1_one_step_closed_form():
+    """K = 1, unit w: h <- max(eps, A^T w), w <- normalise(max(eps, A h))."""
+    A = _dense(40, 30, 3, 2)
+    W0, H0 = synth.init_factors(3, 40, 30, 1)
+    w = W0[:, 0].astype(np.float64)
+    w /= math.sqrt(float(np.dot(w, w)))
+    h1 = np.maximum(EPS, A.T @ w)
+    g = np.maximum(EPS, A @ h1)
+    w1 = g / math.sqrt(float(np.dot(g, g)))
+    W, H = fh.iteration(A, w[:, None].copy(), H0.astype(np.float64), EPS)
+    assert np.allclose(H[0], h1, rtol=1e-12, atol=0)
+    assert np.allclose(W[:, 0], w1, rtol=1e-12, atol=0)
+
+
+def test_k1_limit_is_perron_vector():
+    """The K = 1 iteration is a power iteration on A A^T: w -> u1, h -> s1 v1,
+    objective -> ||A||^2 - s1^2 (LAPACK SVD)."""
+    A = _dense(40, 30, 3, 2)
+    W0, H0 = synth.init_factors(3, 40, 30, 1)
+    W, H, _ = fh.run(A, W0, H0, 200)
+    U, s, Vt = np.linalg.svd(A)
+    u1 = np.abs(U[:, 0])
+    assert np.max(np.abs(W[:, 0] - u1)) < 1e-10
+    assert np.max(np.abs(H[0] - s[0] * np.abs(Vt[0]))) < 1e-10 * s[0]
+    f_expected = float(np.sum(A * A)) - s[0] ** 2
+    assert abs(ob.frob2_direct(A, W, H) - f_expected) <= 1e-10 * float(np.sum(A * A))
+
+
+# --- planted exact recovery ----------------------------------------------------
+
+def test_planted_separable_recovery():
+    rng = np.random.default_rng(0)
+    V, D, K = 12, 10, 3
+    W0 = np.zeros((V, K))
+    for v in range(V):
+        W0[v, v % K] = 0.5 + rng.random()
+    # H0 holds an identity block and zeros, so the exact NMF is unique up to
+    # permutation and scaling of the columns of W
+    H0 = (0.5 + rng.random((K, D))) * (rng.random((K, D)) < 0.5)
+    H0[:, :K] = np.eye(K)
+    A = W0 @ H0
+    Wi, Hi = synth.init_factors(11, V, D, K)
+    W, H, _ = fh.run(A, Wi, Hi, 600)
+    assert ob.relative_error(A, W, H, direct=True) < 1e-8
+    # factors match up to permutation and scale: each recovered column is
+    # proportional to one planted column
+    Wn = W0 / np.linalg.norm(W0, axis=0)
+    C = np.abs(W.T @ Wn)
+    assert np.allclose(np.sort(C.max(axis=1)), 1.0, atol=1e-8)
+    assert sorted(C.argmax(axis=1).tolist()) == [0, 1, 2]
+
+
+# --- KKT -----------------------------------------------------------------------
+
+def test_kkt_residual_decays():
+    A = _dense(64, 48, 4, 13)
+    W0, H0 = synth.init_factors(14, 64, 48, 4)
+    W, H = fh.normalize_init(W0), H0.astype(np.float64)
+
+    def kkt(W, H):
+        gW = W @ (H @ H.T) - A @ H.T
+        gH = (W.T @ W) @ H - W.T @ A
+        return math.hypot(np.linalg.norm(np.minimum(W - EPS, gW)),
+                          np.linalg.norm(np.minimum(H - EPS, gH)))
+
+    W, H = fh.iteration(A, W, H, EPS)
+    k0 = kkt(W, H)
+    for _ in range(1500):
+        W, H = fh.iteration(A, W, H, EPS)
+    assert kkt(W, H) < 1e-4 * k0
+
+
+# --- Eq. 2 directly vs the trace identity -------------------------------------
+
+def test_trace_identity_dense_and_sparse():
+    A = _dense(50, 40, 5, 17)
+    W0, H0 = synth.init_factors(18, 50, 40, 6)
+    W, H, _ = fh.run(A, W0, H0, 3)
+    a, b = ob.frob2_direct(A, W, H), ob.frob2_trace(A, W, H)
+    assert abs(a - b) <= 1e-10 * a
+    sp = synth.sparse_termdoc(500, 200, 19, mean_terms=25)
+    W0, H0 = synth.init_factors(20, 500, 200, 8)
+    W, H, _ = fh.run(sp.A, W0, H0, 3)
+    a, b = ob.frob2_direct(sp.A, W, H), ob.frob2_trace(sp.A, W, H)
+    assert abs(a - b) <= 1e-10 * a
+    # ||A||_F^2 = D for column-normalised tf-idf
+    assert abs(ob.norm2_A(sp.A) - 200) < 1e-4
+
+
+# --- fixed-W H subproblem ------------------------------------------------------
+
+def test_fixed_w_sweeps_reach_nnls_optimum():
+    rng = np.random.default_rng(5)
+    V, K = 30, 6
+    W = np.abs(rng.normal(size=(V, K)))
+    W /= np.linalg.norm(W, axis=0)
+    docs = np.abs(rng.normal(size=(V, 5))) * (rng.random((V, 5)) < 0.5)
+    Rt = docs.T @ W
+    S = W.T @ W
+    H, sweeps = nnls.hals_sweeps(Rt, S, np.full((K, 5), 0.5), EPS, tol=1e-14)
+    for j in range(5):
+        x_lh = nnls.nnls_lawson_hanson(W, docs[:, j])
+        x_bf = nnls.nnls_bruteforce(W, docs[:, j])
+        assert np.allclose(x_lh, x_bf, atol=1e-10)
+        assert np.allclose(H[:, j], x_bf, atol=1e-9)
+
+
+# --- warm-start network: analytic gradients vs central differences ------------
+
+def test_mlp_gradients_finite_difference():
+    rng = np.random.default_rng(1)
+    sizes = [(7, 9), (9, 9), (9, 5)]
+    params = []
+    for (i, o) in sizes:
+        params += [rng.normal(scale=0.5, size=(i, o)), rng.normal(scale=0.1, size=o)]
+    x = rng.normal(size=(4, 7))
+    t = np.abs(rng.normal(size=(4, 5)))
+    y, cache = mlp.forward(params, x)
+    grads = mlp.backward(params, cache, y, t)
+    h = 1e-6
+    for pi, p in enumerate(params):
+        flat = p.reshape(-1)
+        for j in range(0, flat.size, max(1, flat.size // 7)):
+            old = flat[j]
+            flat[j] = old + h
+            lp = mlp.loss(params, x, t)
+            flat[j] = old - h
+            lm = mlp.loss(params, x, t)
+            flat[j] = old
+            num = (lp - lm) / (2 * h)
+            ana = grads[pi].reshape(-1)[j]
+            assert abs(num - ana) <= 1e-7 * max(1.0, abs(ana)) + 1e-9
+
+
+def test_mlp_activation_closed_forms():
+    # GELU(0) = 0, GELU(x) -> x for large x, softplus(0) = ln 2, threshold branch.
+    assert mlp.gelu(np.array(0.0)) == 0.0
+    assert abs(mlp.gelu(np.array(10.0)) - 10.0) < 1e-12
+    assert abs(mlp.gelu(np.array(1.0)) - 0.8413447460685429) < 1e-15   # Phi(1) = 0.84134...
+    assert abs(mlp.softplus(np.array(0.0)) - math.log(2.0)) < 1e-15
+    assert mlp.softplus(np.array(25.0)) == 25.0
+
+
+def test_adam_first_step_is_sign_times_lr():
+    # With bias correction the first Adam step is lr * g / (|g| + eps').
+    p = [np.array([1.0, -2.0, 3.0])]
+    g = [np.array([0.5, -4.0, 1e-3])]
+    out, m, v = mlp.adam_step(p, g, [np.zeros(3)], [np.zeros(3)], 1, lr=0.1)
+    assert np.allclose(out[0], p[0] - 0.1 * g[0] / (np.abs(g[0]) + 1e-8), atol=1e-15)
+
+
+# --- the paper's printed model numbers (Sec. 5) --------------------------------
+
+def test_paper_worked_numbers():
+    g = _golden("paper_worked_numbers.txt")
+    C = tm.CACHE_35MB_WORDS
+    assert tm.fast_hals_w_loop(11314, 160) == g["w_loop_words_V11314_K160"]
+    assert math.floor(tm.vol(11314, 160, 15, C)) == g["plnmf_vol_V11314_K160_T15"]
+    for K, key in ((80, "tile_K80"), (160, "tile_K160"), (240, "tile_K240")):
+        # the paper prints the values truncated to two decimals
+        assert math.floor(tm.tile_size_printed(K, C) * 100) / 100 == pytest.approx(g[key], abs=1e-9)
+        # the exact stationary point of Eq. 9 rounds to the same tile sizes
+        assert abs(tm.tile_size_stationary(K, C) - g[key]) < 0.02
+    ratio = tm.fast_hals_w_loop(11314, 160) / tm.vol(11314, 160, 15, C)
+    assert round(ratio, 1) == g["reduction_factor"]
+
+
+# --- planted mistakes: each pin above catches a plausible oracle bug ----------
+
+def test_pins_catch_planted_mistakes(monkeypatch):
+    A = _dense(40, 30, 3, 2)
+    W0, H0 = synth.init_factors(3, 40, 30, 5)
+
+    # (1) Jacobi instead of Gauss-Seidel in the H loop -> reorder pin fails.
+    def jacobi_h(R, S, H, eps=EPS):
+        H = np.array(H, dtype=np.float64)
+        return np.maximum(eps, H + R.T - S.T @ H)
+    W = fh.normalize_init(W0)
+    tr = {}
+    monkeypatch.setattr(fh, "update_h", jacobi_h)
+    W1, H1 = fh.iteration(A, W, H0, EPS, trace=tr)
+    monkeypatch.undo()
+    Hp = pl_nmf.update_h(tr["R"], tr["S"], H0, 2, EPS)
+    assert np.max(np.abs(Hp - H1)) > 1e-6
+
+    # (2) sign error on P in the W loop -> monotone pin fails.
+    def bad_w(P, Q, W, eps=EPS):
+        W = np.array(W, dtype=np.float64)
+        for k in range(W.shape[1]):
+            W[:, k] = np.maximum(eps, W[:, k] * Q[k, k] - P[:, k] - W @ Q[:, k])
+            W[:, k] /= np.linalg.norm(W[:, k])
+        return W
+    monkeypatch.setattr(fh, "update_w", bad_w)
+    W, H = fh.normalize_init(W0), H0.astype(np.float64)
+    fs = []
+    for _ in range(6):
+        W, H = fh.iteration(A, W, H, EPS)
+        fs.append(ob.frob2_direct(A, W, H))
+    monkeypatch.undo()
+    assert any(b > a * (1 + 1e-12) for a, b in zip(fs, fs[1:])) or fs[-1] > fs[0] * 0.9
+
+    # (3) dropped normalisation -> K = 1 closed form fails.
+    def unnormalised_w(P, Q, W, eps=EPS):
+        W = np.array(W, dtype=np.float64)
+        for k in range(W.shape[1]):
+            W[:, k] = np.maximum(eps, W[:, k] * Q[k, k] + P[:, k] - W @ Q[:, k])
+        return W
+    monkeypatch.setattr(fh, "update_w", unnormalised_w)
+    w = fh.normalize_init(W0[:, :1])
+    Wb, _ = fh.iteration(A, w, H0[:1].astype(np.float64), EPS)
+    monkeypatch.undo()
+    assert abs(np.linalg.norm(Wb[:, 0]) - 1.0) > 1e-3
