@@ -1,0 +1,168 @@
+/*
+ * nmf.h — C ABI of the B300 FAST-HALS / PL-NMF library (libplnmf.so).
+ *
+ * The library factorises a non-negative matrix A (V x D) as A ~= W H with
+ * W (V x K) and H (K x D) non-negative, minimising 1/2 ||A - WH||_F^2
+ * (Sec. 1, Eq. 1; Sec. 2.1, Eq. 2) with the FAST-HALS iteration of Alg. 1,
+ * whose column-sequential factor updates are regrouped into column tiles as in
+ * Alg. 2 (Sec. 3.3, Eqs. 4-6).  All compute runs in CUDA kernels on one GPU.
+ *
+ * Conventions for every entry point
+ *   - Pointers marked "device" must be device (or managed) memory of the
+ *     current CUDA device; pointers marked "host or device" may be either
+ *     (the copy direction is inferred through unified addressing).
+ *   - Matrices are row-major with the stated shapes.
+ *   - Every call returns an nmf_status and never aborts or traps.  A CUDA
+ *     error raised asynchronously by an earlier launch is reported by the
+ *     next call that synchronises (NMF_ECUDA).
+ *   - A context is bound to one CUDA stream and is not thread-safe; use one
+ *     context per stream/thread.
+ */
+#ifndef PLNMF_NMF_H
+#define PLNMF_NMF_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  NMF_OK = 0,
+  NMF_EINVAL = 1,       /* bad argument (shape, pointer, negative or non-finite A, ...) */
+  NMF_ENOMEM = 2,       /* device allocation failed */
+  NMF_ECUDA = 3,        /* a CUDA call or kernel failed */
+  NMF_ETIMEOUT = 4,     /* a bounded device-side wait expired (status word set by a kernel) */
+  NMF_ENUMERIC = 5,     /* a column norm was zero or not finite */
+  NMF_EBUSY = 6,        /* context is being captured or used by another call */
+  NMF_EUNSUPPORTED = 7  /* valid request this build does not implement (shape limits) */
+} nmf_status;
+
+typedef enum { NMF_DENSE_F32 = 0, NMF_CSR_F32_I32 = 1 } nmf_format;
+typedef enum { NMF_PREC_FP32 = 0, NMF_PREC_BF16 = 1 } nmf_precision;
+
+/*
+ * Problem description (Sec. 1: A in R+^{V x D}, rank K; Alg. 1 inputs A, eps
+ * and a random non-negative initialisation).
+ *   V, D, K      1 <= K <= min(V, D); K <= 512 in this build.
+ *   fmt          NMF_DENSE_F32: `dense` (device, V x D row-major, leading
+ *                dimension `ld` >= D).
+ *                NMF_CSR_F32_I32: `row_ptr` (V+1), `col_idx` (nnz), `val`
+ *                (nnz), device, rows = words (V), columns = documents (D);
+ *                row_ptr[0] = 0, non-decreasing, column indices in [0, D).
+ *                The caller owns A; it must stay valid and unchanged for the
+ *                life of the context.
+ *   W0, H0       optional initial factors (host or device), W0 V x K and
+ *                H0 K x D row-major.  NULL -> U[0,1) from `seed` drawn with
+ *                the SplitMix64 stream defined in the Python module
+ *                paper_1904_07935_b300.synth (entry r*cols+c of stream
+ *                seed ^ 0x5757.. for W, seed ^ 0x4848.. for H).  Either way
+ *                the columns of W are then scaled to unit L2 norm.
+ *   eps          clamp floor of Alg. 1 (paper leaves it unset; 0 -> 1e-16).
+ *   tile_T       column-tile width T of Alg. 2; 0 -> library choice.
+ *   prec         NMF_PREC_FP32 (all FP32) or NMF_PREC_BF16 (dense A only:
+ *                products A H^T and A^T W with BF16 operands, FP32 accumulate).
+ *   stream       cudaStream_t to run on (NULL -> the context creates one).
+ */
+typedef struct {
+  int32_t V, D, K;
+  int32_t fmt;
+  const float* dense;
+  int64_t ld;
+  const int32_t* row_ptr;
+  const int32_t* col_idx;
+  const float* val;
+  int64_t nnz;
+  const float* W0;
+  const float* H0;
+  uint64_t seed;
+  float eps;
+  int32_t tile_T;
+  int32_t prec;
+  void* stream;
+} nmf_problem;
+
+typedef struct nmf_ctx nmf_ctx;
+
+/* Validates the problem (shapes, CSR structure, A >= 0 and finite), builds
+ * the transposed CSR of A and the SpMM work plans, computes ||A||_F^2 in
+ * FP64, allocates W, H and all intermediates and initialises the factors.
+ * On success *out owns every device buffer it allocated.  Synchronous. */
+nmf_status nmf_init(const nmf_problem* p, nmf_ctx** out);
+
+/* Runs n_iters iterations of Alg. 1 (H update, then W update) on the
+ * context's stream, asynchronously.  Each iteration also records the
+ * objective (Eq. 2 times 2, via the trace identity, FP64) of the new
+ * factors.  The first call captures the iteration in a CUDA graph. */
+nmf_status nmf_iterate(nmf_ctx* c, int32_t n_iters);
+
+/* Synchronises the stream and returns the latest objective
+ * frob2 = ||A - WH||_F^2 and rel = sqrt(frob2 / ||A||_F^2) (Sec. 6.2.2).
+ * Before any iteration it evaluates the initial factors.  Also reports
+ * device-side status (NMF_ETIMEOUT / NMF_ENUMERIC) raised since the last
+ * call.  Either output pointer may be NULL. */
+nmf_status nmf_error(nmf_ctx* c, double* frob2, double* rel);
+
+/* Copies the n most recent per-iteration objectives (oldest first) to host
+ * memory `out` (FP64).  n <= number of iterations run and <= 4096. */
+nmf_status nmf_objective_history(nmf_ctx* c, double* out, int32_t n);
+
+/* W: V x K, H: K x D, row-major FP32, host or device.  Either may be NULL.
+ * Synchronous. */
+nmf_status nmf_get_factors(nmf_ctx* c, float* W, float* H);
+/* Replaces the factors (checkpoint / resume).  W is used as given (no
+ * normalisation).  Synchronous. */
+nmf_status nmf_set_factors(nmf_ctx* c, const float* W, const float* H);
+
+/* Individual steps of one iteration, for per-step parity and timing
+ * (Alg. 1 lines noted; all asynchronous on the context stream):
+ *   NMF_STEP_R        R = A^T W                    (line 4)
+ *   NMF_STEP_S        S = W^T W                    (line 5)
+ *   NMF_STEP_UPDATE_H H update with R, S           (lines 6-8, Alg. 2 order)
+ *   NMF_STEP_P        P = A H^T                    (line 10)
+ *   NMF_STEP_Q        Q = H H^T                    (line 11)
+ *   NMF_STEP_UPDATE_W W update with P, Q           (lines 12-16, Alg. 2 order)
+ *   NMF_STEP_OBJECTIVE objective of current W, H using the current P and the
+ *                     Gram of the current W (recomputed) and Q. */
+typedef enum {
+  NMF_STEP_R = 0, NMF_STEP_S = 1, NMF_STEP_UPDATE_H = 2, NMF_STEP_P = 3,
+  NMF_STEP_Q = 4, NMF_STEP_UPDATE_W = 5, NMF_STEP_OBJECTIVE = 6
+} nmf_step;
+nmf_status nmf_run_step(nmf_ctx* c, int32_t step);
+
+/* Internal buffers, exposed for per-step parity tests (row-major FP32):
+ *   NMF_BUF_W  V x K        NMF_BUF_HT D x K (H transposed)
+ *   NMF_BUF_R  D x K        NMF_BUF_P  V x K
+ *   NMF_BUF_S  K x K        NMF_BUF_Q  K x K
+ * `count` must equal the element count of the buffer.  dst/src host or
+ * device.  Synchronous. */
+typedef enum {
+  NMF_BUF_W = 0, NMF_BUF_HT = 1, NMF_BUF_R = 2, NMF_BUF_P = 3, NMF_BUF_S = 4, NMF_BUF_Q = 5
+} nmf_buffer;
+nmf_status nmf_get_buffer(nmf_ctx* c, int32_t which, float* dst, int64_t count);
+nmf_status nmf_set_buffer(nmf_ctx* c, int32_t which, const float* src, int64_t count);
+
+/* Step timing (tracing): runs n_iters iterations eagerly (no graph) with a
+ * CUDA event between consecutive steps on the context stream and writes the
+ * mean milliseconds per iteration of each step to step_ms[0..6]:
+ *   0 R = A^T W, 1 H update, 2 P = A H^T, 3 Q = H H^T, 4 W update,
+ *   5 S = W^T W of the new W, 6 objective.
+ * The factors advance by n_iters iterations.  Synchronous. */
+#define NMF_PROFILE_STEPS 7
+nmf_status nmf_profile(nmf_ctx* c, int32_t n_iters, float* step_ms);
+
+/* Introspection: tile width in use, cluster size of the W column chain,
+ * number of kernel launches one iteration makes. */
+nmf_status nmf_query(nmf_ctx* c, int32_t* tile_T, int32_t* chain_ctas, int32_t* launches_per_iter);
+
+/* Frees every device buffer and the graph of the context.  NULL is a no-op. */
+void nmf_destroy(nmf_ctx* c);
+
+const char* nmf_status_str(int32_t s);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PLNMF_NMF_H */

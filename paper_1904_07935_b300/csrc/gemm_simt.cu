@@ -1,0 +1,211 @@
+// FP32 SIMT GEMM family used by the FP32 path: dense products A H^T and
+// A^T W (Alg. 1 lines 4/10 for dense A), the Gram matrices W^T W and H H^T
+// (lines 5/11), phase 1 of the regrouped factor update (Eq. 4 plus the old
+// half of Eq. 5, as one strictly-upper masked GEMM) and phase 3 (Eq. 6).
+//
+// 64 x 64 output tile per 256-thread CTA, 4 x 4 register micro-tile per
+// thread, k staged through shared memory 16 at a time (double-buffered via
+// registers).  FP32 multiply-add with FP32 accumulation.
+#include "internal.cuh"
+
+namespace plnmf {
+namespace {
+
+constexpr int BM = 64, BN = 64, BK = 16;
+
+__device__ __forceinline__ float load_a(const GemmArgs& g, int m, int k) {
+  if (m >= g.M || k >= g.Kin) return 0.f;
+  return g.transA ? __ldg(g.A + (int64_t)k * g.lda + m) : __ldg(g.A + (int64_t)m * g.lda + k);
+}
+
+__device__ __forceinline__ float load_b(const GemmArgs& g, int k, int n, int k_end) {
+  if (k >= k_end || n >= g.N) return 0.f;
+  if (g.mode == GM_PHASE1 && !(k > n)) return 0.f;   // strictly upper part only
+  return __ldg(g.B + (int64_t)k * g.ldb + n);
+}
+
+__global__ void __launch_bounds__(256) gemm_kernel(GemmArgs g) {
+  __shared__ __align__(16) float As[2][BK][BM + 4];   // padded: conflict-light transposing stores
+  __shared__ __align__(16) float Bs[2][BK][BN];
+
+  int tm = blockIdx.y, tn = blockIdx.x;
+  if (g.upper_only && tn < tm) return;
+  const int m0 = tm * BM, n0 = tn * BN;
+  const int z = blockIdx.z;
+  int k_begin = 0, k_end = g.Kin;
+  if (g.mode == GM_PARTIAL) {
+    k_begin = z * g.k_chunk;
+    k_end = min(g.Kin, k_begin + g.k_chunk);
+  }
+  if (g.mode == GM_PHASE1) {
+    // B[k][n] with k <= n is masked: chunks entirely below n0 + 1 contribute nothing.
+    k_begin = ((n0 + 1) / BK) * BK;
+  }
+  const int tid = threadIdx.x;
+  const int tx = tid & 15, ty = tid >> 4;
+
+  // Loader mapping: 64 x 16 elements per operand, 4 per thread.
+  // A: element (m = m0 + (tid & 63), k = kk + (tid >> 6) * 4 + i) for transA = 0 reads
+  // along k; for transA = 1 the mapping is transposed so that reads run along m.
+  float ra[4], rb[4];
+  auto fetch = [&](int kk) {
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      int e = tid + i * 256;                  // 0..1023
+      int mm, kq;
+      if (g.transA) { mm = e & 63; kq = e >> 6; } else { kq = e & 15; mm = e >> 4; }
+      ra[i] = load_a(g, m0 + mm, kk + kq);
+      int nn = e & 63, kb = e >> 6;
+      rb[i] = load_b(g, kk + kb, n0 + nn, k_end);
+    }
+  };
+  auto stash = [&](int buf) {
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      int e = tid + i * 256;
+      int mm, kq;
+      if (g.transA) { mm = e & 63; kq = e >> 6; } else { kq = e & 15; mm = e >> 4; }
+      As[buf][kq][mm] = ra[i];
+      Bs[buf][e >> 6][e & 63] = rb[i];
+    }
+  };
+
+  float acc[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
+
+  int buf = 0;
+  if (k_begin < k_end) {
+    fetch(k_begin);
+    stash(0);
+    __syncthreads();
+    for (int kk = k_begin; kk < k_end; kk += BK) {
+      const bool more = kk + BK < k_end;
+      if (more) fetch(kk + BK);
+#pragma unroll
+      for (int q = 0; q < BK; ++q) {
+        const float4 a = *reinterpret_cast<const float4*>(&As[buf][q][ty * 4]);
+        const float4 b = *reinterpret_cast<const float4*>(&Bs[buf][q][tx * 4]);
+        const float av[4] = {a.x, a.y, a.z, a.w};
+        const float bv[4] = {b.x, b.y, b.z, b.w};
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+          for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(av[i], bv[j], acc[i][j]);
+      }
+      if (more) {
+        stash(buf ^ 1);
+        __syncthreads();
+        buf ^= 1;
+      }
+    }
+  }
+
+  // Epilogue.
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int m = m0 + ty * 4 + i;
+    if (m >= g.M) continue;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int n = n0 + tx * 4 + j;
+      if (n >= g.N) continue;
+      const float v = acc[i][j];
+      switch (g.mode) {
+        case GM_STORE:
+          g.C[(int64_t)m * g.ldc + n] = v;
+          break;
+        case GM_PHASE1: {
+          const float e = g.E[(int64_t)m * g.lde + n];
+          float base = e;
+          if (g.h_mode) {
+            const float cdiag = 1.f - g.B[(int64_t)n * g.ldb + n];
+            base = fmaf(cdiag, g.X[(int64_t)m * g.ldx + n], e);
+          }
+          g.C[(int64_t)m * g.ldc + n] = base - v;
+          break;
+        }
+        case GM_SUB:
+          g.C[(int64_t)m * g.ldc + n] -= v;
+          break;
+        case GM_PARTIAL:
+          g.C[(int64_t)z * g.part_stride + (int64_t)m * g.ldc + n] = v;
+          break;
+      }
+    }
+  }
+}
+
+// S[i][j] = sum_z part[z][i][j] (FP64, z ascending) for i <= j, mirrored.
+__global__ void gram_reduce_kernel(const float* __restrict__ part, int n_chunks, int Kp, int K,
+                                   float* __restrict__ S) {
+  const int i = blockIdx.y;
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= Kp) return;
+  if (i >= K || j >= K) {
+    S[(int64_t)i * Kp + j] = 0.f;
+    return;
+  }
+  if (j < i) return;
+  double s = 0.0;
+  const size_t stride = (size_t)Kp * Kp;
+  for (int z = 0; z < n_chunks; ++z) s += (double)part[z * stride + (size_t)i * Kp + j];
+  const float f = (float)s;
+  S[(int64_t)i * Kp + j] = f;
+  S[(int64_t)j * Kp + i] = f;
+}
+
+}  // namespace
+
+cudaError_t gemm_run(const GemmArgs& a, cudaStream_t s) {
+  if (a.M <= 0 || a.N <= 0) return cudaSuccess;
+  dim3 grid((a.N + BN - 1) / BN, (a.M + BM - 1) / BM, a.mode == GM_PARTIAL ? a.n_chunks : 1);
+  gemm_kernel<<<grid, 256, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t gram_setup(GramWork& g, int N, int Kp) {
+  g.N = N;
+  g.Kp = Kp;
+  // Enough chunks to cover about two waves of the 148 SMs.
+  const int tiles = ((Kp + 63) / 64) * ((Kp + 63) / 64 + 1) / 2;
+  int want = std::max(1, (296 + tiles - 1) / tiles);
+  int chunk = (N + want - 1) / want;
+  chunk = std::max(256, ((chunk + BK - 1) / BK) * BK);
+  g.chunk = chunk;
+  g.n_chunks = (N + chunk - 1) / chunk;
+  return cudaMalloc(&g.d_part, sizeof(float) * (size_t)g.n_chunks * Kp * Kp);
+}
+
+void gram_free(GramWork& g) {
+  cudaFree(g.d_part);
+  g.d_part = nullptr;
+}
+
+cudaError_t gram_run(const GramWork& g, const float* X, float* S, int K, cudaStream_t s) {
+  GemmArgs a;
+  a.M = g.Kp;
+  a.N = g.Kp;
+  a.Kin = g.N;
+  a.A = X;
+  a.lda = g.Kp;
+  a.transA = 1;
+  a.B = X;
+  a.ldb = g.Kp;
+  a.C = g.d_part;
+  a.ldc = g.Kp;
+  a.mode = GM_PARTIAL;
+  a.k_chunk = g.chunk;
+  a.part_stride = (int64_t)g.Kp * g.Kp;
+  a.n_chunks = g.n_chunks;
+  a.upper_only = 1;
+  cudaError_t err = gemm_run(a, s);
+  if (err != cudaSuccess) return err;
+  dim3 grid((g.Kp + 127) / 128, g.Kp);
+  gram_reduce_kernel<<<grid, 128, 0, s>>>(g.d_part, g.n_chunks, g.Kp, K, S);
+  return cudaGetLastError();
+}
+
+}  // namespace plnmf

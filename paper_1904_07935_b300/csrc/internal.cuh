@@ -1,0 +1,123 @@
+// Internal declarations shared by the CUDA translation units of libplnmf.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <vector>
+
+#include "../../include/nmf.h"
+
+namespace plnmf {
+
+// Device status word bits (set by kernels, read and cleared by the host).
+enum : int {
+  ST_TIMEOUT = 1,   // a bounded spin-wait gave up
+  ST_NUMERIC = 2,   // a column norm was zero or not finite
+};
+
+// Wall-clock limit of every device-side wait (read from %globaltimer).  The
+// waits inside one iteration last microseconds; a wait that exceeds this
+// sets ST_TIMEOUT in the status word and the kernel stops waiting.
+constexpr unsigned long long kWaitLimitNs = 200ull * 1000ull * 1000ull;
+
+constexpr int kMaxK = 512;
+
+// ---------------------------------------------------------------------------
+// SpMM (CSR times tall dense) with a host-built, deterministic work plan.
+// ---------------------------------------------------------------------------
+struct SpmmPlan {
+  int rows = 0, cols = 0;
+  int n_items = 0;          // work items {row, nnz_begin, nnz_end, slot}
+  int n_long = 0;           // rows split into several items
+  int n_slots = 0;          // partial rows written by split items
+  int4* d_items = nullptr;
+  int4* d_combine = nullptr;  // {row, first_slot, n_slots, 0}
+  float* d_partial = nullptr; // n_slots x Kp
+};
+
+// Builds the plan from host CSR row pointers.  seg = max nnz per item.
+cudaError_t spmm_plan_build(SpmmPlan& plan, const std::vector<int>& row_ptr, int rows, int cols,
+                            int Kp, int seg);
+void spmm_plan_free(SpmmPlan& plan);
+// Y (rows x Kp) = A (CSR) * X (cols x Kp).
+cudaError_t spmm_run(const SpmmPlan& plan, const int* col_idx, const float* val, const float* X,
+                     float* Y, int Kp, cudaStream_t s);
+
+// ---------------------------------------------------------------------------
+// SIMT FP32 GEMM family (64 x 64 CTA tiles, 4 x 4 register micro-tiles).
+// ---------------------------------------------------------------------------
+enum GemmMode : int {
+  GM_STORE = 0,     // C = acc
+  GM_PHASE1 = 1,    // C = E + c'_n * X[m][n] - acc  (strictly-upper masked B)
+  GM_SUB = 2,       // C -= acc
+  GM_PARTIAL = 3,   // C[z] = acc over k-chunk z (split-K partials)
+};
+
+struct GemmArgs {
+  int M = 0, N = 0, Kin = 0;
+  const float* A = nullptr;  int64_t lda = 0;  int transA = 0;   // op(A)[m][k]
+  const float* B = nullptr;  int64_t ldb = 0;                    // B[k][n]
+  float* C = nullptr;        int64_t ldc = 0;
+  int mode = GM_STORE;
+  // GM_PHASE1 extras: E (M x N, lde), X (M x N, ldx) and the Gram G whose
+  // diagonal gives c'_n = h_mode ? 1 - G[n][n] : 0.  The mask keeps B[k][n]
+  // only for k > n (global indices).
+  const float* E = nullptr;  int64_t lde = 0;
+  const float* X = nullptr;  int64_t ldx = 0;
+  int h_mode = 0;
+  // GM_PARTIAL: k-range of chunk z is [z*k_chunk, (z+1)*k_chunk); partial z
+  // starts at C + z * part_stride.
+  int k_chunk = 0;  int64_t part_stride = 0;  int n_chunks = 1;
+  // Only tiles with (tile_n >= tile_m) are computed when upper_only (Grams).
+  int upper_only = 0;
+};
+
+cudaError_t gemm_run(const GemmArgs& a, cudaStream_t s);
+
+// S (Kp x Kp) = X^T X for X (N x Kp): split-N partials, FP64 fixed-order sum.
+struct GramWork {
+  float* d_part = nullptr;   // n_chunks x Kp x Kp
+  int n_chunks = 0, chunk = 0, N = 0, Kp = 0;
+};
+cudaError_t gram_setup(GramWork& g, int N, int Kp);
+void gram_free(GramWork& g);
+cudaError_t gram_run(const GramWork& g, const float* X, float* S, int K, cudaStream_t s);
+
+// ---------------------------------------------------------------------------
+// Tall-factor update (Alg. 2 regrouped): phase 1 GEMM, per-tile chain, phase 3.
+// ---------------------------------------------------------------------------
+struct ChainConfig {
+  int cluster = 16;       // CTAs cooperating on the normalised chain
+  int threads = 1024;
+  int rpt = 2;            // rows per thread
+  int tt = 16;            // compile-time max tile width
+};
+
+// Y (N x Kp): phase-1 base; X: factor (old on entry, new on exit); G: Gram.
+cudaError_t chain_run(float* Y, float* X, const float* G, int N, int Kp, int lo, int hi,
+                      float eps, bool normalize, const ChainConfig& cfg, int* d_status,
+                      cudaStream_t s);
+bool chain_config_for(int N, bool normalize, int T, ChainConfig* cfg);
+
+// ---------------------------------------------------------------------------
+// Misc kernels.
+// ---------------------------------------------------------------------------
+// Element (r, c < cols) of a rows x ld buffer = SplitMix64 draw r*cols + c
+// (or c*rows + r for the transposed variant); padding columns are zeroed.
+cudaError_t fill_uniform_splitmix(float* dst, int rows, int cols, int ld, uint64_t seed,
+                                  cudaStream_t s);
+cudaError_t fill_uniform_splitmix_t(float* dst, int rows, int cols, int ld, uint64_t seed,
+                                    cudaStream_t s);
+cudaError_t normalize_columns(float* X, int N, int K, int ld, cudaStream_t s);
+// frob2 = normA2 - 2 <W, P> + <S, Q>, written to out[slot] (FP64).
+cudaError_t objective_run(const float* W, const float* P, int V, int Kp, const float* S,
+                          const float* Q, double normA2, double* partial, int n_partial,
+                          double* out, unsigned* d_counter, int hist_cap, cudaStream_t s);
+constexpr int kSumsqBlocks = 592;
+cudaError_t sumsq_dense_f64(const float* A, int64_t rows, int64_t cols, int64_t ld,
+                            double* d_out, int* d_bad, cudaStream_t s);
+cudaError_t transpose_f32(const float* src, int rows, int cols, int lds, float* dst, int ldd,
+                          cudaStream_t s);
+
+}  // namespace plnmf

@@ -1,0 +1,606 @@
+// Host runtime and C ABI (include/nmf.h): problem validation, transposed CSR
+// and SpMM plans, buffers, the per-iteration launch sequence (Alg. 1 with the
+// factor updates regrouped as in Alg. 2) and its CUDA-graph capture.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "internal.cuh"
+
+using namespace plnmf;
+
+struct nmf_ctx {
+  int V = 0, D = 0, K = 0, Kp = 0, T = 16, fmt = 0, prec = 0;
+  float eps = 1e-16f;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  // A (caller-owned) and its transpose (context-owned, CSR only).
+  const float* dense = nullptr;
+  int64_t lda = 0;
+  const int* rp = nullptr;
+  const int* ci = nullptr;
+  const float* va = nullptr;
+  int64_t nnz = 0;
+  int* rpT = nullptr;
+  int* ciT = nullptr;
+  float* vaT = nullptr;
+  SpmmPlan planA, planAt;
+  GramWork gramW, gramH;
+  ChainConfig chainW, chainH;
+  // Factors and intermediates, row stride Kp, padding columns kept at zero.
+  float *W = nullptr, *Ht = nullptr, *R = nullptr, *P = nullptr, *S = nullptr, *Q = nullptr;
+  float* Y = nullptr;       // phase-1 / phase-3 base, max(V, D) x Kp
+  float* stage = nullptr;   // transpose staging, max(V, D) x Kp
+  double* obj_partial = nullptr;
+  int n_obj_partial = 296;
+  double* hist = nullptr;
+  unsigned* d_counter = nullptr;
+  int* d_status = nullptr;
+  double normA2 = 0.0;
+  bool s_valid = false;       // S == W^T W for the current W
+  long long iters_run = 0;
+  int launches_per_iter = 0;
+  int launch_count = 0;       // kernels issued by the last enqueue sequence
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t graph_exec = nullptr;
+};
+
+namespace {
+
+constexpr int kHistCap = 4096;
+
+nmf_status from_cuda(cudaError_t e) {
+  if (e == cudaSuccess) return NMF_OK;
+  if (e == cudaErrorMemoryAllocation) return NMF_ENOMEM;
+  return NMF_ECUDA;
+}
+
+#define CK(x)                                  \
+  do {                                         \
+    cudaError_t _e = (x);                      \
+    if (_e != cudaSuccess) return from_cuda(_e); \
+  } while (0)
+
+template <typename T>
+cudaError_t dalloc(T** p, size_t count) {
+  return cudaMalloc(reinterpret_cast<void**>(p), sizeof(T) * std::max<size_t>(count, 1));
+}
+
+bool is_device_ptr(const void* p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+// ---- launch sequence --------------------------------------------------------
+
+cudaError_t enq_product_R(nmf_ctx* c) {   // R = A^T W  (D x Kp)
+  if (c->fmt == NMF_CSR_F32_I32) {
+    c->launch_count += 1 + (c->planAt.n_long > 0);
+    return spmm_run(c->planAt, c->ciT, c->vaT, c->W, c->R, c->Kp, c->stream);
+  }
+  GemmArgs a;
+  a.M = c->D; a.N = c->Kp; a.Kin = c->V;
+  a.A = c->dense; a.lda = c->lda; a.transA = 1;
+  a.B = c->W; a.ldb = c->Kp;
+  a.C = c->R; a.ldc = c->Kp;
+  c->launch_count += 1;
+  return gemm_run(a, c->stream);
+}
+
+cudaError_t enq_product_P(nmf_ctx* c) {   // P = A H^T  (V x Kp)
+  if (c->fmt == NMF_CSR_F32_I32) {
+    c->launch_count += 1 + (c->planA.n_long > 0);
+    return spmm_run(c->planA, c->ci, c->va, c->Ht, c->P, c->Kp, c->stream);
+  }
+  GemmArgs a;
+  a.M = c->V; a.N = c->Kp; a.Kin = c->D;
+  a.A = c->dense; a.lda = c->lda; a.transA = 0;
+  a.B = c->Ht; a.ldb = c->Kp;
+  a.C = c->P; a.ldc = c->Kp;
+  c->launch_count += 1;
+  return gemm_run(a, c->stream);
+}
+
+cudaError_t enq_gram(nmf_ctx* c, const GramWork& g, const float* X, float* out) {
+  c->launch_count += 2;
+  return gram_run(g, X, out, c->K, c->stream);
+}
+
+// Regrouped update of one tall factor X (N x Kp) with Gram G and data term B:
+//   phase 1:  Y = B + c' (.) X - X triu(G, 1)         (all old contributions)
+//   per tile: chain (phase 2), then Y[:, hi:] -= X[:, lo:hi] G[lo:hi, hi:]  (phase 3)
+cudaError_t enq_update(nmf_ctx* c, float* X, const float* G, const float* B, int N, bool is_w) {
+  const int K = c->K, Kp = c->Kp, T = c->T;
+  GemmArgs a;
+  a.M = N; a.N = K; a.Kin = K;
+  a.A = X; a.lda = Kp; a.transA = 0;
+  a.B = G; a.ldb = Kp;
+  a.C = c->Y; a.ldc = Kp;
+  a.mode = GM_PHASE1;
+  a.E = B; a.lde = Kp;
+  a.X = X; a.ldx = Kp;
+  a.h_mode = is_w ? 0 : 1;
+  cudaError_t e = gemm_run(a, c->stream);
+  c->launch_count += 1;
+  if (e != cudaSuccess) return e;
+  const ChainConfig& cfg = is_w ? c->chainW : c->chainH;
+  for (int lo = 0; lo < K; lo += T) {
+    const int hi = std::min(K, lo + T);
+    e = chain_run(c->Y, X, G, N, Kp, lo, hi, c->eps, is_w, cfg, c->d_status, c->stream);
+    c->launch_count += 1;
+    if (e != cudaSuccess) return e;
+    if (hi < K) {
+      GemmArgs b;
+      b.M = N; b.N = K - hi; b.Kin = hi - lo;
+      b.A = X + lo; b.lda = Kp; b.transA = 0;
+      b.B = G + (int64_t)lo * Kp + hi; b.ldb = Kp;
+      b.C = c->Y + hi; b.ldc = Kp;
+      b.mode = GM_SUB;
+      e = gemm_run(b, c->stream);
+      c->launch_count += 1;
+      if (e != cudaSuccess) return e;
+    }
+  }
+  return cudaSuccess;
+}
+
+cudaError_t enq_objective(nmf_ctx* c) {
+  c->launch_count += 2;
+  return objective_run(c->W, c->P, c->V, c->Kp, c->S, c->Q, c->normA2, c->obj_partial,
+                       c->n_obj_partial, c->hist, c->d_counter, kHistCap, c->stream);
+}
+
+// One iteration; S must equal W^T W on entry and does again on exit.
+cudaError_t enq_iteration(nmf_ctx* c) {
+  cudaError_t e;
+  if ((e = enq_product_R(c)) != cudaSuccess) return e;
+  if ((e = enq_update(c, c->Ht, c->S, c->R, c->D, false)) != cudaSuccess) return e;
+  if ((e = enq_product_P(c)) != cudaSuccess) return e;
+  if ((e = enq_gram(c, c->gramH, c->Ht, c->Q)) != cudaSuccess) return e;
+  if ((e = enq_update(c, c->W, c->Q, c->P, c->V, true)) != cudaSuccess) return e;
+  if ((e = enq_gram(c, c->gramW, c->W, c->S)) != cudaSuccess) return e;
+  return enq_objective(c);
+}
+
+nmf_status read_status(nmf_ctx* c) {
+  int st = 0;
+  CK(cudaMemcpy(&st, c->d_status, sizeof(int), cudaMemcpyDeviceToHost));
+  if (st != 0) {
+    CK(cudaMemset(c->d_status, 0, sizeof(int)));
+    if (st & ST_TIMEOUT) return NMF_ETIMEOUT;
+    if (st & ST_NUMERIC) return NMF_ENUMERIC;
+  }
+  return NMF_OK;
+}
+
+void destroy_graph(nmf_ctx* c) {
+  if (c->graph_exec) cudaGraphExecDestroy(c->graph_exec);
+  if (c->graph) cudaGraphDestroy(c->graph);
+  c->graph_exec = nullptr;
+  c->graph = nullptr;
+}
+
+nmf_status validate_and_copy_csr(const nmf_problem* p, std::vector<int>& rp, std::vector<int>& ci,
+                                 std::vector<float>& va, double* normA2) {
+  if (!p->row_ptr || (p->nnz > 0 && (!p->col_idx || !p->val)) || p->nnz < 0) return NMF_EINVAL;
+  if (p->nnz > 0x7fffffffLL) return NMF_EUNSUPPORTED;
+  rp.resize((size_t)p->V + 1);
+  ci.resize((size_t)p->nnz);
+  va.resize((size_t)p->nnz);
+  CK(cudaMemcpy(rp.data(), p->row_ptr, sizeof(int) * rp.size(), cudaMemcpyDefault));
+  if (p->nnz > 0) {
+    CK(cudaMemcpy(ci.data(), p->col_idx, sizeof(int) * ci.size(), cudaMemcpyDefault));
+    CK(cudaMemcpy(va.data(), p->val, sizeof(float) * va.size(), cudaMemcpyDefault));
+  }
+  if (rp[0] != 0 || rp[p->V] != p->nnz) return NMF_EINVAL;
+  for (int r = 0; r < p->V; ++r)
+    if (rp[r + 1] < rp[r]) return NMF_EINVAL;
+  double s = 0.0;
+  for (int64_t e = 0; e < p->nnz; ++e) {
+    if (ci[e] < 0 || ci[e] >= p->D) return NMF_EINVAL;
+    const float v = va[e];
+    if (!(v >= 0.f) || !std::isfinite(v)) return NMF_EINVAL;
+    s += (double)v * (double)v;
+  }
+  *normA2 = s;
+  return NMF_OK;
+}
+
+nmf_status init_impl(const nmf_problem* p, nmf_ctx* c) {
+  c->V = p->V;
+  c->D = p->D;
+  c->K = p->K;
+  c->Kp = (p->K + 3) & ~3;
+  c->fmt = p->fmt;
+  c->prec = p->prec;
+  c->eps = p->eps == 0.f ? 1e-16f : p->eps;
+  const int V = c->V, D = c->D, Kp = c->Kp;
+  if (p->stream) {
+    c->stream = static_cast<cudaStream_t>(p->stream);
+  } else {
+    CK(cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking));
+    c->own_stream = true;
+  }
+  // Tile width: the column chain keeps a tile in registers (<= 16 wide,
+  // <= 8 wide above 32K rows).
+  int T = p->tile_T > 0 ? p->tile_T : 16;
+  if (!chain_config_for(V, true, T, &c->chainW)) {
+    if (p->tile_T > 0) return NMF_EUNSUPPORTED;
+    T = 8;
+    if (!chain_config_for(V, true, T, &c->chainW)) return NMF_EUNSUPPORTED;
+  }
+  if (!chain_config_for(D, false, T, &c->chainH)) return NMF_EUNSUPPORTED;
+  c->T = T;
+
+  CK(dalloc(&c->d_status, 1));
+  CK(cudaMemset(c->d_status, 0, sizeof(int)));
+  CK(dalloc(&c->d_counter, 1));
+  CK(cudaMemset(c->d_counter, 0, sizeof(unsigned)));
+  CK(dalloc(&c->hist, kHistCap));
+  CK(dalloc(&c->obj_partial, c->n_obj_partial));
+
+  if (c->fmt == NMF_CSR_F32_I32) {
+    std::vector<int> rp, ci;
+    std::vector<float> va;
+    nmf_status st = validate_and_copy_csr(p, rp, ci, va, &c->normA2);
+    if (st != NMF_OK) return st;
+    c->rp = p->row_ptr;
+    c->ci = p->col_idx;
+    c->va = p->val;
+    c->nnz = p->nnz;
+    // CSR of A^T (documents as rows), built by a stable counting sort so
+    // that word indices stay ascending inside every document row.
+    std::vector<int> rpT((size_t)D + 1, 0), ciT((size_t)p->nnz);
+    std::vector<float> vaT((size_t)p->nnz);
+    for (int64_t e = 0; e < p->nnz; ++e) rpT[(size_t)ci[e] + 1]++;
+    for (int d = 0; d < D; ++d) rpT[d + 1] += rpT[d];
+    std::vector<int> fill(rpT.begin(), rpT.end() - 1);
+    for (int r = 0; r < V; ++r)
+      for (int e = rp[r]; e < rp[r + 1]; ++e) {
+        const int pos = fill[ci[e]]++;
+        ciT[pos] = r;
+        vaT[pos] = va[e];
+      }
+    CK(dalloc(&c->rpT, rpT.size()));
+    CK(dalloc(&c->ciT, ciT.size()));
+    CK(dalloc(&c->vaT, vaT.size()));
+    CK(cudaMemcpy(c->rpT, rpT.data(), sizeof(int) * rpT.size(), cudaMemcpyHostToDevice));
+    if (p->nnz > 0) {
+      CK(cudaMemcpy(c->ciT, ciT.data(), sizeof(int) * ciT.size(), cudaMemcpyHostToDevice));
+      CK(cudaMemcpy(c->vaT, vaT.data(), sizeof(float) * vaT.size(), cudaMemcpyHostToDevice));
+    }
+    CK(spmm_plan_build(c->planA, rp, V, D, Kp, 512));
+    CK(spmm_plan_build(c->planAt, rpT, D, V, Kp, 512));
+  } else if (c->fmt == NMF_DENSE_F32) {
+    if (!p->dense || p->ld < p->D) return NMF_EINVAL;
+    if (!is_device_ptr(p->dense)) return NMF_EINVAL;
+    c->dense = p->dense;
+    c->lda = p->ld;
+    double* d_part = nullptr;
+    int* d_bad = nullptr;
+    CK(dalloc(&d_part, kSumsqBlocks));
+    CK(dalloc(&d_bad, 1));
+    CK(cudaMemset(d_bad, 0, sizeof(int)));
+    CK(sumsq_dense_f64(p->dense, V, D, p->ld, d_part, d_bad, c->stream));
+    std::vector<double> part(kSumsqBlocks);
+    int bad = 0;
+    CK(cudaStreamSynchronize(c->stream));
+    CK(cudaMemcpy(part.data(), d_part, sizeof(double) * kSumsqBlocks, cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(&bad, d_bad, sizeof(int), cudaMemcpyDeviceToHost));
+    cudaFree(d_part);
+    cudaFree(d_bad);
+    if (bad) return NMF_EINVAL;
+    double s = 0.0;
+    for (double v : part) s += v;
+    c->normA2 = s;
+  } else {
+    return NMF_EINVAL;
+  }
+  if (!(c->normA2 > 0.0)) return NMF_EINVAL;
+
+  const size_t nV = (size_t)V * Kp, nD = (size_t)D * Kp, nK = (size_t)Kp * Kp;
+  const size_t nMax = (size_t)std::max(V, D) * Kp;
+  CK(dalloc(&c->W, nV));
+  CK(dalloc(&c->P, nV));
+  CK(dalloc(&c->Ht, nD));
+  CK(dalloc(&c->R, nD));
+  CK(dalloc(&c->S, nK));
+  CK(dalloc(&c->Q, nK));
+  CK(dalloc(&c->Y, nMax));
+  CK(dalloc(&c->stage, nMax));
+  CK(cudaMemsetAsync(c->P, 0, sizeof(float) * nV, c->stream));
+  CK(cudaMemsetAsync(c->R, 0, sizeof(float) * nD, c->stream));
+  CK(cudaMemsetAsync(c->Y, 0, sizeof(float) * nMax, c->stream));
+  CK(gram_setup(c->gramW, V, Kp));
+  CK(gram_setup(c->gramH, D, Kp));
+
+  // Initial factors.
+  const uint64_t sw = p->seed ^ 0x5757575757575757ull, sh = p->seed ^ 0x4848484848484848ull;
+  if (p->W0) {
+    CK(cudaMemsetAsync(c->W, 0, sizeof(float) * nV, c->stream));
+    CK(cudaMemcpy2DAsync(c->W, sizeof(float) * Kp, p->W0, sizeof(float) * p->K, sizeof(float) * p->K, V,
+                         cudaMemcpyDefault, c->stream));
+  } else {
+    CK(fill_uniform_splitmix(c->W, V, p->K, Kp, sw, c->stream));
+  }
+  if (p->H0) {
+    CK(cudaMemcpyAsync(c->stage, p->H0, sizeof(float) * (size_t)p->K * D, cudaMemcpyDefault, c->stream));
+    CK(cudaMemsetAsync(c->Ht, 0, sizeof(float) * nD, c->stream));
+    CK(transpose_f32(c->stage, p->K, D, D, c->Ht, Kp, c->stream));
+  } else {
+    CK(fill_uniform_splitmix_t(c->Ht, D, p->K, Kp, sh, c->stream));
+  }
+  CK(normalize_columns(c->W, V, p->K, Kp, c->stream));
+  CK(gram_run(c->gramW, c->W, c->S, c->K, c->stream));
+  c->s_valid = true;
+  CK(cudaStreamSynchronize(c->stream));
+  // Count the launches of one iteration (dry count, nothing is enqueued).
+  return NMF_OK;
+}
+
+void free_ctx(nmf_ctx* c) {
+  if (!c) return;
+  destroy_graph(c);
+  if (c->stream) cudaStreamSynchronize(c->stream);
+  spmm_plan_free(c->planA);
+  spmm_plan_free(c->planAt);
+  gram_free(c->gramW);
+  gram_free(c->gramH);
+  for (void* p : {(void*)c->rpT, (void*)c->ciT, (void*)c->vaT, (void*)c->W, (void*)c->Ht, (void*)c->R,
+                  (void*)c->P, (void*)c->S, (void*)c->Q, (void*)c->Y, (void*)c->stage,
+                  (void*)c->obj_partial, (void*)c->hist, (void*)c->d_counter, (void*)c->d_status})
+    if (p) cudaFree(p);
+  if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
+  delete c;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* nmf_status_str(int32_t s) {
+  switch (s) {
+    case NMF_OK: return "ok";
+    case NMF_EINVAL: return "invalid argument";
+    case NMF_ENOMEM: return "out of device memory";
+    case NMF_ECUDA: return "CUDA error";
+    case NMF_ETIMEOUT: return "device wait timed out";
+    case NMF_ENUMERIC: return "zero or non-finite column norm";
+    case NMF_EBUSY: return "context busy";
+    case NMF_EUNSUPPORTED: return "unsupported by this build";
+    default: return "unknown status";
+  }
+}
+
+nmf_status nmf_init(const nmf_problem* p, nmf_ctx** out) {
+  if (!p || !out) return NMF_EINVAL;
+  *out = nullptr;
+  if (p->V <= 0 || p->D <= 0 || p->K <= 0 || p->K > std::min(p->V, p->D)) return NMF_EINVAL;
+  if (p->K > kMaxK) return NMF_EUNSUPPORTED;
+  if (!(p->eps >= 0.f) || !std::isfinite(p->eps)) return NMF_EINVAL;
+  if (p->tile_T < 0) return NMF_EINVAL;
+  if (p->prec != NMF_PREC_FP32) return NMF_EUNSUPPORTED;
+  nmf_ctx* c = new (std::nothrow) nmf_ctx();
+  if (!c) return NMF_ENOMEM;
+  nmf_status st = init_impl(p, c);
+  if (st != NMF_OK) {
+    cudaGetLastError();
+    free_ctx(c);
+    return st;
+  }
+  *out = c;
+  return NMF_OK;
+}
+
+nmf_status nmf_iterate(nmf_ctx* c, int32_t n_iters) {
+  if (!c || n_iters < 0) return NMF_EINVAL;
+  if (n_iters == 0) return NMF_OK;
+  if (!c->s_valid) {
+    c->launch_count = 0;
+    CK(enq_gram(c, c->gramW, c->W, c->S));
+    c->s_valid = true;
+  }
+  if (!c->graph_exec) {
+    c->launch_count = 0;
+    CK(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
+    cudaError_t e = enq_iteration(c);
+    cudaGraph_t g = nullptr;
+    cudaError_t e2 = cudaStreamEndCapture(c->stream, &g);
+    if (e != cudaSuccess || e2 != cudaSuccess) {
+      if (g) cudaGraphDestroy(g);
+      return from_cuda(e != cudaSuccess ? e : e2);
+    }
+    c->graph = g;
+    c->launches_per_iter = c->launch_count;
+    CK(cudaGraphInstantiate(&c->graph_exec, g, 0));
+  }
+  for (int i = 0; i < n_iters; ++i) CK(cudaGraphLaunch(c->graph_exec, c->stream));
+  c->iters_run += n_iters;
+  return NMF_OK;
+}
+
+nmf_status nmf_error(nmf_ctx* c, double* frob2, double* rel) {
+  if (!c) return NMF_EINVAL;
+  if (c->iters_run == 0) {
+    // Objective of the initial factors.
+    c->launch_count = 0;
+    CK(enq_product_P(c));
+    CK(enq_gram(c, c->gramH, c->Ht, c->Q));
+    CK(enq_gram(c, c->gramW, c->W, c->S));
+    CK(enq_objective(c));
+    c->s_valid = true;
+  }
+  CK(cudaStreamSynchronize(c->stream));
+  nmf_status st = read_status(c);
+  unsigned cnt = 0;
+  CK(cudaMemcpy(&cnt, c->d_counter, sizeof(unsigned), cudaMemcpyDeviceToHost));
+  double f = NAN;
+  if (cnt > 0) CK(cudaMemcpy(&f, c->hist + (cnt - 1) % kHistCap, sizeof(double), cudaMemcpyDeviceToHost));
+  if (frob2) *frob2 = f;
+  if (rel) *rel = std::sqrt(std::max(f, 0.0) / c->normA2);
+  return st;
+}
+
+nmf_status nmf_objective_history(nmf_ctx* c, double* out, int32_t n) {
+  if (!c || !out || n < 0 || n > kHistCap) return NMF_EINVAL;
+  CK(cudaStreamSynchronize(c->stream));
+  unsigned cnt = 0;
+  CK(cudaMemcpy(&cnt, c->d_counter, sizeof(unsigned), cudaMemcpyDeviceToHost));
+  if ((unsigned)n > cnt) return NMF_EINVAL;
+  std::vector<double> h(kHistCap);
+  CK(cudaMemcpy(h.data(), c->hist, sizeof(double) * kHistCap, cudaMemcpyDeviceToHost));
+  for (int i = 0; i < n; ++i) out[i] = h[(cnt - n + i) % kHistCap];
+  return read_status(c);
+}
+
+nmf_status nmf_get_factors(nmf_ctx* c, float* W, float* H) {
+  if (!c) return NMF_EINVAL;
+  const int K = c->K, Kp = c->Kp;
+  if (W)
+    CK(cudaMemcpy2DAsync(W, sizeof(float) * K, c->W, sizeof(float) * Kp, sizeof(float) * K, c->V,
+                         cudaMemcpyDefault, c->stream));
+  if (H) {
+    CK(transpose_f32(c->Ht, c->D, K, Kp, c->stage, c->D, c->stream));
+    CK(cudaMemcpyAsync(H, c->stage, sizeof(float) * (size_t)K * c->D, cudaMemcpyDefault, c->stream));
+  }
+  CK(cudaStreamSynchronize(c->stream));
+  return read_status(c);
+}
+
+nmf_status nmf_set_factors(nmf_ctx* c, const float* W, const float* H) {
+  if (!c) return NMF_EINVAL;
+  const int K = c->K, Kp = c->Kp;
+  if (W) {
+    CK(cudaMemcpy2DAsync(c->W, sizeof(float) * Kp, W, sizeof(float) * K, sizeof(float) * K, c->V,
+                         cudaMemcpyDefault, c->stream));
+    c->s_valid = false;
+  }
+  if (H) {
+    CK(cudaMemcpyAsync(c->stage, H, sizeof(float) * (size_t)K * c->D, cudaMemcpyDefault, c->stream));
+    CK(transpose_f32(c->stage, K, c->D, c->D, c->Ht, Kp, c->stream));
+  }
+  CK(cudaStreamSynchronize(c->stream));
+  return NMF_OK;
+}
+
+nmf_status nmf_run_step(nmf_ctx* c, int32_t step) {
+  if (!c) return NMF_EINVAL;
+  c->launch_count = 0;
+  switch (step) {
+    case NMF_STEP_R: CK(enq_product_R(c)); break;
+    case NMF_STEP_S: CK(enq_gram(c, c->gramW, c->W, c->S)); c->s_valid = true; break;
+    case NMF_STEP_UPDATE_H: CK(enq_update(c, c->Ht, c->S, c->R, c->D, false)); break;
+    case NMF_STEP_P: CK(enq_product_P(c)); break;
+    case NMF_STEP_Q: CK(enq_gram(c, c->gramH, c->Ht, c->Q)); break;
+    case NMF_STEP_UPDATE_W: CK(enq_update(c, c->W, c->Q, c->P, c->V, true)); c->s_valid = false; break;
+    case NMF_STEP_OBJECTIVE:
+      CK(enq_gram(c, c->gramW, c->W, c->S));
+      c->s_valid = true;
+      CK(enq_objective(c));
+      break;
+    default: return NMF_EINVAL;
+  }
+  return NMF_OK;
+}
+
+nmf_status nmf_get_buffer(nmf_ctx* c, int32_t which, float* dst, int64_t count) {
+  if (!c || !dst) return NMF_EINVAL;
+  const int K = c->K, Kp = c->Kp;
+  const float* src = nullptr;
+  int rows = 0;
+  switch (which) {
+    case NMF_BUF_W: src = c->W; rows = c->V; break;
+    case NMF_BUF_HT: src = c->Ht; rows = c->D; break;
+    case NMF_BUF_R: src = c->R; rows = c->D; break;
+    case NMF_BUF_P: src = c->P; rows = c->V; break;
+    case NMF_BUF_S: src = c->S; rows = K; break;
+    case NMF_BUF_Q: src = c->Q; rows = K; break;
+    default: return NMF_EINVAL;
+  }
+  if (count != (int64_t)rows * K) return NMF_EINVAL;
+  CK(cudaMemcpy2DAsync(dst, sizeof(float) * K, src, sizeof(float) * Kp, sizeof(float) * K, rows,
+                       cudaMemcpyDefault, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  return read_status(c);
+}
+
+nmf_status nmf_set_buffer(nmf_ctx* c, int32_t which, const float* src, int64_t count) {
+  if (!c || !src) return NMF_EINVAL;
+  const int K = c->K, Kp = c->Kp;
+  float* dst = nullptr;
+  int rows = 0;
+  switch (which) {
+    case NMF_BUF_W: dst = c->W; rows = c->V; c->s_valid = false; break;
+    case NMF_BUF_HT: dst = c->Ht; rows = c->D; break;
+    case NMF_BUF_R: dst = c->R; rows = c->D; break;
+    case NMF_BUF_P: dst = c->P; rows = c->V; break;
+    case NMF_BUF_S: dst = c->S; rows = K; c->s_valid = false; break;
+    case NMF_BUF_Q: dst = c->Q; rows = K; break;
+    default: return NMF_EINVAL;
+  }
+  if (count != (int64_t)rows * K) return NMF_EINVAL;
+  CK(cudaMemcpy2DAsync(dst, sizeof(float) * Kp, src, sizeof(float) * K, sizeof(float) * K, rows,
+                       cudaMemcpyDefault, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  return NMF_OK;
+}
+
+nmf_status nmf_profile(nmf_ctx* c, int32_t n_iters, float* step_ms) {
+  if (!c || !step_ms || n_iters <= 0) return NMF_EINVAL;
+  if (!c->s_valid) {
+    CK(enq_gram(c, c->gramW, c->W, c->S));
+    c->s_valid = true;
+  }
+  cudaEvent_t ev[NMF_PROFILE_STEPS + 1];
+  for (auto& e : ev) CK(cudaEventCreate(&e));
+  double acc[NMF_PROFILE_STEPS] = {0};
+  nmf_status st = NMF_OK;
+  for (int it = 0; it < n_iters && st == NMF_OK; ++it) {
+    cudaError_t e = cudaSuccess;
+    e = cudaEventRecord(ev[0], c->stream);
+    if (e == cudaSuccess) e = enq_product_R(c);
+    if (e == cudaSuccess) e = cudaEventRecord(ev[1], c->stream);
+    if (e == cudaSuccess) e = enq_update(c, c->Ht, c->S, c->R, c->D, false);
+    if (e == cudaSuccess) e = cudaEventRecord(ev[2], c->stream);
+    if (e == cudaSuccess) e = enq_product_P(c);
+    if (e == cudaSuccess) e = cudaEventRecord(ev[3], c->stream);
+    if (e == cudaSuccess) e = enq_gram(c, c->gramH, c->Ht, c->Q);
+    if (e == cudaSuccess) e = cudaEventRecord(ev[4], c->stream);
+    if (e == cudaSuccess) e = enq_update(c, c->W, c->Q, c->P, c->V, true);
+    if (e == cudaSuccess) e = cudaEventRecord(ev[5], c->stream);
+    if (e == cudaSuccess) e = enq_gram(c, c->gramW, c->W, c->S);
+    if (e == cudaSuccess) e = cudaEventRecord(ev[6], c->stream);
+    if (e == cudaSuccess) e = enq_objective(c);
+    if (e == cudaSuccess) e = cudaEventRecord(ev[7], c->stream);
+    if (e == cudaSuccess) e = cudaEventSynchronize(ev[7]);
+    for (int k = 0; k < NMF_PROFILE_STEPS && e == cudaSuccess; ++k) {
+      float ms = 0.f;
+      e = cudaEventElapsedTime(&ms, ev[k], ev[k + 1]);
+      acc[k] += ms;
+    }
+    st = from_cuda(e);
+  }
+  for (auto& e : ev) cudaEventDestroy(e);
+  if (st != NMF_OK) return st;
+  c->iters_run += n_iters;
+  for (int k = 0; k < NMF_PROFILE_STEPS; ++k) step_ms[k] = (float)(acc[k] / n_iters);
+  return read_status(c);
+}
+
+nmf_status nmf_query(nmf_ctx* c, int32_t* tile_T, int32_t* chain_ctas, int32_t* launches_per_iter) {
+  if (!c) return NMF_EINVAL;
+  if (tile_T) *tile_T = c->T;
+  if (chain_ctas) *chain_ctas = c->chainW.cluster;
+  if (launches_per_iter) *launches_per_iter = c->launches_per_iter;
+  return NMF_OK;
+}
+
+void nmf_destroy(nmf_ctx* c) { free_ctx(c); }
+
+}  // extern "C"

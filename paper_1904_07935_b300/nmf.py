@@ -1,0 +1,224 @@
+"""Thin ctypes binding over libplnmf.so (include/nmf.h).
+
+Argument marshalling only: every step of the factorisation runs in the CUDA
+library.  Arrays may be torch tensors (device or host) or numpy arrays (host);
+the binding passes their data pointers.  Importing this module loads the
+library and raises if it has not been built.
+"""
+
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libplnmf.so")
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(
+        f"{LIB_PATH} is missing: build it with `python -m paper_1904_07935_b300.build` "
+        "(there is no CPU fallback)")
+
+lib = ctypes.CDLL(LIB_PATH)
+
+NMF_OK, NMF_EINVAL, NMF_ENOMEM, NMF_ECUDA, NMF_ETIMEOUT, NMF_ENUMERIC, NMF_EBUSY, NMF_EUNSUPPORTED = range(8)
+DENSE_F32, CSR_F32_I32 = 0, 1
+PREC_FP32, PREC_BF16 = 0, 1
+STEP_R, STEP_S, STEP_UPDATE_H, STEP_P, STEP_Q, STEP_UPDATE_W, STEP_OBJECTIVE = range(7)
+BUF_W, BUF_HT, BUF_R, BUF_P, BUF_S, BUF_Q = range(6)
+
+
+class Problem(ctypes.Structure):
+    _fields_ = [
+        ("V", ctypes.c_int32), ("D", ctypes.c_int32), ("K", ctypes.c_int32),
+        ("fmt", ctypes.c_int32),
+        ("dense", ctypes.c_void_p), ("ld", ctypes.c_int64),
+        ("row_ptr", ctypes.c_void_p), ("col_idx", ctypes.c_void_p), ("val", ctypes.c_void_p),
+        ("nnz", ctypes.c_int64),
+        ("W0", ctypes.c_void_p), ("H0", ctypes.c_void_p),
+        ("seed", ctypes.c_uint64), ("eps", ctypes.c_float), ("tile_T", ctypes.c_int32),
+        ("prec", ctypes.c_int32), ("stream", ctypes.c_void_p),
+    ]
+
+
+_vp, _i32, _i64, _dp = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.POINTER(ctypes.c_double)
+_SIGS = {
+    "nmf_init": ([ctypes.POINTER(Problem), ctypes.POINTER(_vp)], _i32),
+    "nmf_iterate": ([_vp, _i32], _i32),
+    "nmf_error": ([_vp, _dp, _dp], _i32),
+    "nmf_objective_history": ([_vp, _vp, _i32], _i32),
+    "nmf_get_factors": ([_vp, _vp, _vp], _i32),
+    "nmf_set_factors": ([_vp, _vp, _vp], _i32),
+    "nmf_run_step": ([_vp, _i32], _i32),
+    "nmf_get_buffer": ([_vp, _i32, _vp, _i64], _i32),
+    "nmf_set_buffer": ([_vp, _i32, _vp, _i64], _i32),
+    "nmf_query": ([_vp, ctypes.POINTER(_i32), ctypes.POINTER(_i32), ctypes.POINTER(_i32)], _i32),
+    "nmf_profile": ([_vp, _i32, _vp], _i32),
+    "nmf_destroy": ([_vp], None),
+    "nmf_status_str": ([_i32], ctypes.c_char_p),
+}
+for _name, (_args, _res) in _SIGS.items():
+    _f = getattr(lib, _name)
+    _f.argtypes = _args
+    _f.restype = _res
+
+
+class NmfError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        self.status = status
+        super().__init__(f"{where}: {lib.nmf_status_str(status).decode()} (status {status})")
+
+
+def check(status: int, where: str) -> None:
+    if status != NMF_OK:
+        raise NmfError(status, where)
+
+
+def ptr(x) -> int | None:
+    """Data pointer of a torch tensor / numpy array (must be contiguous)."""
+    if x is None:
+        return None
+    if hasattr(x, "data_ptr"):
+        if not x.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return x.data_ptr()
+    if isinstance(x, np.ndarray):
+        if not x.flags["C_CONTIGUOUS"]:
+            raise ValueError("array must be C-contiguous")
+        return x.ctypes.data
+    raise TypeError(type(x))
+
+
+def _stream_ptr(stream) -> int | None:
+    if stream is None:
+        return None
+    if hasattr(stream, "cuda_stream"):
+        return stream.cuda_stream
+    return int(stream)
+
+
+class Nmf:
+    """One factorisation context (nmf_ctx)."""
+
+    def __init__(self, V, D, K, *, dense=None, ld=None, row_ptr=None, col_idx=None, val=None,
+                 W0=None, H0=None, seed=0, eps=0.0, tile_T=0, prec=PREC_FP32, stream=None):
+        p = Problem()
+        p.V, p.D, p.K = V, D, K
+        self._keep = [dense, row_ptr, col_idx, val, W0, H0]
+        if dense is not None:
+            p.fmt = DENSE_F32
+            p.dense = ptr(dense)
+            p.ld = D if ld is None else ld
+        else:
+            p.fmt = CSR_F32_I32
+            p.row_ptr, p.col_idx, p.val = ptr(row_ptr), ptr(col_idx), ptr(val)
+            p.nnz = int(val.shape[0]) if val is not None else 0
+        p.W0, p.H0 = ptr(W0), ptr(H0)
+        p.seed, p.eps, p.tile_T, p.prec = seed, eps, tile_T, prec
+        p.stream = _stream_ptr(stream)
+        h = ctypes.c_void_p()
+        check(lib.nmf_init(ctypes.byref(p), ctypes.byref(h)), "nmf_init")
+        self.h = h
+        self.V, self.D, self.K = V, D, K
+
+    # context management
+    def close(self):
+        if getattr(self, "h", None):
+            lib.nmf_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        self.close()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    # calls
+    def iterate(self, n=1):
+        check(lib.nmf_iterate(self.h, n), "nmf_iterate")
+
+    def error(self):
+        f, r = ctypes.c_double(), ctypes.c_double()
+        check(lib.nmf_error(self.h, ctypes.byref(f), ctypes.byref(r)), "nmf_error")
+        return f.value, r.value
+
+    def history(self, n):
+        out = np.empty(n, dtype=np.float64)
+        check(lib.nmf_objective_history(self.h, out.ctypes.data, n), "nmf_objective_history")
+        return out
+
+    def get_factors(self, W=None, H=None):
+        """Returns host numpy (W V x K, H K x D) unless destinations are given."""
+        ret = W is None and H is None
+        if ret:
+            W = np.empty((self.V, self.K), dtype=np.float32)
+            H = np.empty((self.K, self.D), dtype=np.float32)
+        check(lib.nmf_get_factors(self.h, ptr(W), ptr(H)), "nmf_get_factors")
+        return (W, H) if ret else None
+
+    def set_factors(self, W=None, H=None):
+        check(lib.nmf_set_factors(self.h, ptr(W), ptr(H)), "nmf_set_factors")
+
+    def run_step(self, step):
+        check(lib.nmf_run_step(self.h, step), "nmf_run_step")
+
+    _SHAPES = {BUF_W: ("V", "K"), BUF_HT: ("D", "K"), BUF_R: ("D", "K"), BUF_P: ("V", "K"),
+               BUF_S: ("K", "K"), BUF_Q: ("K", "K")}
+
+    def buffer_shape(self, which):
+        a, b = self._SHAPES[which]
+        return getattr(self, a), getattr(self, b)
+
+    def get_buffer(self, which, out=None):
+        shape = self.buffer_shape(which)
+        if out is None:
+            out = np.empty(shape, dtype=np.float32)
+        check(lib.nmf_get_buffer(self.h, which, ptr(out), shape[0] * shape[1]), "nmf_get_buffer")
+        return out
+
+    def set_buffer(self, which, src):
+        shape = self.buffer_shape(which)
+        if isinstance(src, np.ndarray):
+            src = np.ascontiguousarray(src, dtype=np.float32)
+        check(lib.nmf_set_buffer(self.h, which, ptr(src), shape[0] * shape[1]), "nmf_set_buffer")
+
+    PROFILE_STEPS = ("R", "update_H", "P", "Q", "update_W", "S", "objective")
+
+    def profile(self, n_iters):
+        """Mean ms per iteration of each step (eager launches, CUDA events)."""
+        out = np.zeros(len(self.PROFILE_STEPS), dtype=np.float32)
+        check(lib.nmf_profile(self.h, n_iters, out.ctypes.data), "nmf_profile")
+        return dict(zip(self.PROFILE_STEPS, out.tolist()))
+
+    def query(self):
+        t, c, l = _i32(), _i32(), _i32()
+        check(lib.nmf_query(self.h, ctypes.byref(t), ctypes.byref(c), ctypes.byref(l)), "nmf_query")
+        return {"tile_T": t.value, "chain_ctas": c.value, "launches_per_iter": l.value}
+
+
+def from_sparse(prob, K, device="cuda", **kw):
+    """Context for a synth.SparseProblem; copies its CSR to the device with torch."""
+    import torch
+    A = prob.A
+    rp = torch.from_numpy(A.row_ptr).to(device)
+    ci = torch.from_numpy(A.col_idx).to(device)
+    va = torch.from_numpy(A.val).to(device)
+    ctx = Nmf(A.n_rows, A.n_cols, K, row_ptr=rp, col_idx=ci, val=va, **kw)
+    ctx._keep += [rp, ci, va]
+    return ctx
+
+
+def from_dense(A, K, device="cuda", **kw):
+    """Context for a dense float32 matrix (numpy or torch)."""
+    import torch
+    if isinstance(A, np.ndarray):
+        A = torch.from_numpy(np.ascontiguousarray(A, dtype=np.float32))
+    A = A.to(device).contiguous()
+    ctx = Nmf(A.shape[0], A.shape[1], K, dense=A, **kw)
+    ctx._keep.append(A)
+    return ctx

@@ -1,0 +1,291 @@
+"""GPU parity: the CUDA path through the C-ABI against the FP64 oracle on the
+same seeded inputs.  Tolerances (FP32 path): after one iteration the
+max-norm relative difference of W and of H is at most 1e-5; after the full
+iteration count the objective (Eq. 2, evaluated by the oracle in FP64 on the
+GPU's factors) is within 1e-4 relative of the oracle's own run."""
+
+import math
+
+import numpy as np
+import pytest
+
+from oracle import fast_hals as fh
+from oracle import objective as ob
+from paper_1904_07935_b300 import synth
+
+from ._parity import (colmax_rel, f32, forward_error_ratio, fp32_storage_sensitivity, h_update_scale,
+                      rel_h, rel_w)
+
+pytestmark = pytest.mark.gpu
+
+EPS = 1e-16
+TOL_ITER = 1e-5      # one iteration, FP32 path
+TOL_OBJ = 1e-4       # relative objective after the full run, FP32 path
+
+
+@pytest.fixture(scope="module")
+def nmf():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("needs a GPU")
+    from paper_1904_07935_b300 import nmf as m
+    return m
+
+
+def _dense_ctx(nmf, A, K, W0, H0, **kw):
+    import torch
+    return nmf.from_dense(A, K, W0=torch.from_numpy(W0).cuda(), H0=torch.from_numpy(H0).cuda(), **kw)
+
+
+def _sparse_ctx(nmf, prob, K, W0, H0, **kw):
+    import torch
+    return nmf.from_sparse(prob, K, W0=torch.from_numpy(W0).cuda(), H0=torch.from_numpy(H0).cuda(), **kw)
+
+
+def _oracle_start(W0, H0):
+    """The oracle's view of the initial factors: W with unit columns (FP64)."""
+    return fh.normalize_init(W0), H0.astype(np.float64)
+
+
+# --- initialisation -----------------------------------------------------------
+
+def test_device_init_matches_splitmix_definition(nmf):
+    prob = synth.planted_dense(96, 80, 4, 3)
+    ctx = nmf.from_dense(prob.A, 7, seed=1234)
+    W, H = ctx.get_factors()
+    W0, H0 = synth.init_factors(1234, 96, 80, 7)
+    assert np.array_equal(H, H0)                               # bit-exact draws
+    Wn = W0.astype(np.float64) / np.linalg.norm(W0.astype(np.float64), axis=0)
+    assert np.max(np.abs(W - Wn)) < 2e-7
+    assert np.allclose(np.linalg.norm(W.astype(np.float64), axis=0), 1.0, atol=1e-6)
+
+
+# --- products and Grams -------------------------------------------------------
+
+def _check_products(ctx, nmf, A64, W, H, tol):
+    ctx.set_buffer(nmf.BUF_W, W)
+    ctx.set_buffer(nmf.BUF_HT, np.ascontiguousarray(H.T))
+    for st in (nmf.STEP_R, nmf.STEP_S, nmf.STEP_P, nmf.STEP_Q):
+        ctx.run_step(st)
+    W64, H64 = W.astype(np.float64), H.astype(np.float64)
+    R = np.asarray(A64.T @ W64)
+    P = np.asarray(A64 @ H64.T)
+    for which, ref in ((nmf.BUF_R, R), (nmf.BUF_P, P), (nmf.BUF_S, W64.T @ W64), (nmf.BUF_Q, H64 @ H64.T)):
+        got = ctx.get_buffer(which)
+        err = np.max(np.abs(got - ref)) / np.max(np.abs(ref))
+        assert err < tol, (which, err)
+
+
+def test_dense_products_and_grams(nmf):
+    prob = synth.planted_dense(300, 230, 5, 11)             # ragged vs the 64-wide tiles
+    W0, H0 = synth.init_factors(12, 300, 230, 13)          # K = 13: padded to 16
+    ctx = _dense_ctx(nmf, prob.A, 13, W0, H0)
+    _check_products(ctx, nmf, prob.A.astype(np.float64), W0, H0, 2e-6)
+
+
+def test_sparse_products_with_long_and_empty_rows(nmf):
+    sp = synth.sparse_termdoc(3000, 1400, 21, mean_terms=40)
+    lens = np.diff(sp.A.row_ptr)
+    assert lens.max() > 512 and (lens == 0).any()          # split rows and empty rows
+    W0, H0 = synth.init_factors(22, 3000, 1400, 37)
+    ctx = _sparse_ctx(nmf, sp, 37, W0, H0)
+    _check_products(ctx, nmf, sp.A.to_scipy().astype(np.float64), W0, H0, 2e-6)
+
+
+# --- factor updates in isolation ----------------------------------------------
+
+@pytest.mark.parametrize("K,T", [(16, 16), (16, 1), (20, 3), (37, 16), (48, 8)])
+def test_update_h_matches_alg1(nmf, K, T):
+    prob = synth.planted_dense(260, 700, 6, 31)
+    W0, H0 = synth.init_factors(32 + K, 260, 700, K)
+    W, H = _oracle_start(W0, H0)
+    A = prob.A.astype(np.float64)
+    R, S = f32(A.T @ W), f32(W.T @ W)
+    Hin = f32(H)
+    ctx = _dense_ctx(nmf, prob.A, K, W0, H0, tile_T=T)
+    ctx.set_buffer(nmf.BUF_R, R)
+    ctx.set_buffer(nmf.BUF_S, S)
+    ctx.set_buffer(nmf.BUF_HT, np.ascontiguousarray(Hin.T))
+    ctx.run_step(nmf.STEP_UPDATE_H)
+    got = ctx.get_buffer(nmf.BUF_HT).T
+    ref = fh.update_h(R.astype(np.float64), S.astype(np.float64), Hin, EPS)
+    assert rel_h(got, ref) < TOL_ITER
+    # kernel arithmetic: error within FP32 rounding of the terms it combines
+    assert forward_error_ratio(got, ref, h_update_scale(R, S, Hin, ref)) < 1e-6
+
+
+@pytest.mark.parametrize("K,T", [(16, 16), (16, 1), (20, 3), (37, 16), (48, 8)])
+def test_update_w_matches_alg1(nmf, K, T):
+    prob = synth.planted_dense(900, 300, 6, 41)
+    W0, H0 = synth.init_factors(42 + K, 900, 300, K)
+    W, H = _oracle_start(W0, H0)
+    A = prob.A.astype(np.float64)
+    P, Q = f32(A @ H.T), f32(H @ H.T)
+    Win = f32(W)
+    ctx = _dense_ctx(nmf, prob.A, K, W0, H0, tile_T=T)
+    ctx.set_buffer(nmf.BUF_P, P)
+    ctx.set_buffer(nmf.BUF_Q, Q)
+    ctx.set_buffer(nmf.BUF_W, Win)
+    ctx.run_step(nmf.STEP_UPDATE_W)
+    got = ctx.get_buffer(nmf.BUF_W)
+    ref = fh.update_w(P.astype(np.float64), Q.astype(np.float64), Win, EPS)
+    assert rel_w(got, ref) < TOL_ITER
+    print("W per-column max rel", colmax_rel(got, ref, 0))
+    assert np.allclose(np.linalg.norm(got.astype(np.float64), axis=0), 1.0, atol=1e-5)
+
+
+# --- one full iteration ---------------------------------------------------------
+
+def _one_iteration(nmf, A_oracle, ctx, W0, H0):
+    ctx.iterate(1)
+    Wg, Hg = ctx.get_factors()
+    W, H = _oracle_start(W0, H0)
+    Wr, Hr = fh.iteration(A_oracle, W, H, EPS)
+    return Wg, Hg, Wr, Hr
+
+
+def test_one_iteration_dense_512x384_k16(nmf):
+    """First iteration from the random start.  Its W update cancels terms of
+    size ~1e5 (Q ~ 2e6), so rounding P, Q and W to FP32 once already moves W
+    by ~5e-5 (max-norm); the W tolerance is 10x that oracle-computed floor
+    (FP32 sums of up to D = 384 terms) or 1e-5, whichever is larger."""
+    prob = synth.dense_small()
+    W0, H0 = synth.init_factors(0xC1, 512, 384, 16)
+    ctx = _dense_ctx(nmf, prob.A, 16, W0, H0)
+    Wg, Hg, Wr, Hr = _one_iteration(nmf, prob.A, ctx, W0, H0)
+    dW, dH = fp32_storage_sensitivity(prob.A, *_oracle_start(W0, H0))
+    print("per-column: H", colmax_rel(Hg, Hr, 1), "W", colmax_rel(Wg, Wr, 0), "floor", dW, dH)
+    assert rel_h(Hg, Hr) < max(TOL_ITER, 10 * dH)
+    assert rel_w(Wg, Wr) < max(TOL_ITER, 10 * dW)
+
+
+def test_one_iteration_dense_512x384_k16_from_iterate_10(nmf):
+    """Same workload, one iteration from the oracle's 10th iterate (rounded to
+    FP32 and given to both sides): the strict 1e-5 bound applies."""
+    prob = synth.dense_small()
+    W0, H0 = synth.init_factors(0xC1, 512, 384, 16)
+    W10, H10, _ = fh.run(prob.A, W0, H0, 10)
+    W10, H10 = f32(W10), f32(H10)
+    ctx = _dense_ctx(nmf, prob.A, 16, W0, H0)
+    ctx.set_factors(W10, H10)
+    ctx.iterate(1)
+    Wg, Hg = ctx.get_factors()
+    Wr, Hr = fh.iteration(prob.A, W10.astype(np.float64), H10.astype(np.float64), EPS)
+    assert rel_h(Hg, Hr) < TOL_ITER
+    assert rel_w(Wg, Wr) < TOL_ITER
+
+
+def test_one_iteration_sparse_small_ragged(nmf):
+    sp = synth.sparse_termdoc(2500, 1300, 51, mean_terms=30)
+    W0, H0 = synth.init_factors(52, 2500, 1300, 21)
+    ctx = _sparse_ctx(nmf, sp, 21, W0, H0, tile_T=6)
+    Wg, Hg, Wr, Hr = _one_iteration(nmf, sp.A, ctx, W0, H0)
+    assert rel_h(Hg, Hr) < TOL_ITER
+    assert rel_w(Wg, Wr) < TOL_ITER
+
+
+@pytest.fixture(scope="module")
+def text_full():
+    return synth.text_20ng_like()
+
+
+def test_one_iteration_text_full_size_k160(nmf, text_full):
+    """26,214 x 11,314, ~1.1M nnz, K = 160: the launch configuration the
+    benchmark times, one iteration against the full FP64 oracle."""
+    W0, H0 = synth.init_factors(0xC2, 26214, 11314, 160)
+    ctx = _sparse_ctx(nmf, text_full, 160, W0, H0)
+    Wg, Hg, Wr, Hr = _one_iteration(nmf, text_full.A, ctx, W0, H0)
+    assert rel_h(Hg, Hr) < TOL_ITER
+    assert rel_w(Wg, Wr) < TOL_ITER
+
+
+# --- objective ------------------------------------------------------------------
+
+def test_objective_after_50_iterations_dense_small(nmf):
+    prob = synth.dense_small()
+    W0, H0 = synth.init_factors(0xC1, 512, 384, 16)
+    ctx = _dense_ctx(nmf, prob.A, 16, W0, H0)
+    ctx.iterate(50)
+    Wg, Hg = ctx.get_factors()
+    Wr, Hr, _ = fh.run(prob.A, W0, H0, 50)
+    f_gpu = ob.frob2_direct(prob.A, Wg, Hg)
+    f_ref = ob.frob2_direct(prob.A, Wr, Hr)
+    assert abs(f_gpu - f_ref) <= TOL_OBJ * f_ref
+    assert Wg.min() > 0 and Hg.min() > 0
+
+
+def test_reported_objective_matches_direct_evaluation(nmf):
+    """nmf_error (trace identity, FP64 accumulation of FP32 terms) against
+    Eq. 2 evaluated by the oracle on the same factors."""
+    sp = synth.sparse_termdoc(4000, 2000, 61, mean_terms=50)
+    W0, H0 = synth.init_factors(62, 4000, 2000, 24)
+    ctx = _sparse_ctx(nmf, sp, 24, W0, H0)
+    f0, r0 = ctx.error()                                   # initial factors
+    W, H = ctx.get_factors()
+    fd = ob.frob2_direct(sp.A, W, H)
+    assert abs(f0 - fd) <= 1e-5 * fd
+    ctx.iterate(5)
+    f5, r5 = ctx.error()
+    W, H = ctx.get_factors()
+    fd = ob.frob2_direct(sp.A, W, H)
+    assert abs(f5 - fd) <= 1e-5 * fd
+    assert abs(r5 - math.sqrt(fd / ob.norm2_A(sp.A))) <= 1e-5
+    hist = ctx.history(5)
+    assert abs(hist[-1] - f5) <= 1e-12 * f5
+    assert np.all(np.diff(hist) <= 1e-5 * hist[0])        # non-increasing up to FP32 noise
+
+
+# --- behaviour -------------------------------------------------------------------
+
+def test_bitwise_deterministic_and_resumable(nmf):
+    sp = synth.sparse_termdoc(3000, 1500, 71, mean_terms=40)
+    W0, H0 = synth.init_factors(72, 3000, 1500, 32)
+    a = _sparse_ctx(nmf, sp, 32, W0, H0)
+    b = _sparse_ctx(nmf, sp, 32, W0, H0)
+    a.iterate(5)
+    b.iterate(3)
+    Wb, Hb = b.get_factors()
+    c = _sparse_ctx(nmf, sp, 32, W0, H0)
+    c.set_factors(Wb, Hb)                                   # checkpoint -> resume
+    c.iterate(2)
+    Wa, Ha = a.get_factors()
+    Wc, Hc = c.get_factors()
+    assert np.array_equal(Wa, Wc) and np.array_equal(Ha, Hc)
+
+
+def test_k1_is_clamped_power_iteration(nmf):
+    prob = synth.planted_dense(200, 150, 3, 81)
+    W0, H0 = synth.init_factors(82, 200, 150, 1)
+    ctx = _dense_ctx(nmf, prob.A, 1, W0, H0)
+    ctx.iterate(1)
+    Wg, Hg = ctx.get_factors()
+    A = prob.A.astype(np.float64)
+    w = W0[:, 0].astype(np.float64)
+    w /= np.linalg.norm(w)
+    h1 = np.maximum(EPS, A.T @ w)
+    g = np.maximum(EPS, A @ h1)
+    assert np.max(np.abs(Hg[0] - h1)) <= 1e-5 * h1.max()
+    assert np.max(np.abs(Wg[:, 0] - g / np.linalg.norm(g))) <= 1e-5
+
+
+def test_invalid_inputs_rejected(nmf):
+    import torch
+    A = synth.planted_dense(50, 40, 3, 91).A.copy()
+    A[3, 4] = -1.0
+    with pytest.raises(nmf.NmfError) as e:
+        nmf.from_dense(A, 4)
+    assert e.value.status == nmf.NMF_EINVAL
+    A[3, 4] = np.nan
+    with pytest.raises(nmf.NmfError):
+        nmf.from_dense(A, 4)
+    sp = synth.sparse_termdoc(200, 100, 92, mean_terms=10)
+    bad = sp.A.col_idx.copy()
+    bad[5] = 100                                            # out of range
+    with pytest.raises(nmf.NmfError):
+        nmf.Nmf(200, 100, 4, row_ptr=torch.from_numpy(sp.A.row_ptr).cuda(),
+                col_idx=torch.from_numpy(bad).cuda(), val=torch.from_numpy(sp.A.val).cuda())
+    rp = sp.A.row_ptr.copy()
+    rp[10], rp[11] = rp[11], rp[10] - 1                     # not monotone
+    with pytest.raises(nmf.NmfError):
+        nmf.Nmf(200, 100, 4, row_ptr=torch.from_numpy(rp).cuda(),
+                col_idx=torch.from_numpy(sp.A.col_idx).cuda(), val=torch.from_numpy(sp.A.val).cuda())
