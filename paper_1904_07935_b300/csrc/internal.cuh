@@ -89,16 +89,22 @@ cudaError_t gram_run(const GramWork& g, const float* X, float* S, int K, cudaStr
 // ---------------------------------------------------------------------------
 struct ChainConfig {
   int cluster = 16;       // CTAs cooperating on the normalised chain
-  int threads = 1024;
-  int rpt = 2;            // rows per thread
-  int tt = 16;            // compile-time max tile width
+  int threads = 256;
+  int rpt = 1;            // rows per thread
+  int tt = 16;            // widest tile the configuration was sized for
 };
+constexpr int kMaxChainTile = 16;
 
 // Y (N x Kp): phase-1 base; X: factor (old on entry, new on exit); G: Gram.
 cudaError_t chain_run(float* Y, float* X, const float* G, int N, int Kp, int lo, int hi,
                       float eps, bool normalize, const ChainConfig& cfg, int* d_status,
                       cudaStream_t s);
 bool chain_config_for(int N, bool normalize, int T, ChainConfig* cfg);
+
+// Whole H update in one launch (rows independent): X (N x Kp) old -> new in
+// place, B = R, G = S.
+cudaError_t h_update_run(float* X, const float* B, const float* G, int N, int K, int Kp, float eps,
+                         cudaStream_t s);
 
 // ---------------------------------------------------------------------------
 // Misc kernels.
@@ -110,7 +116,9 @@ cudaError_t fill_uniform_splitmix(float* dst, int rows, int cols, int ld, uint64
 cudaError_t fill_uniform_splitmix_t(float* dst, int rows, int cols, int ld, uint64_t seed,
                                     cudaStream_t s);
 cudaError_t normalize_columns(float* X, int N, int K, int ld, cudaStream_t s);
-// frob2 = normA2 - 2 <W, P> + <S, Q>, written to out[slot] (FP64).
+// frob2 = normA2 - 2 <W, P> + <S, Q>, appended to the history ring.  The
+// dot products use compensated FP32 arithmetic (Dot2) per thread and FP64
+// across threads; `partial` holds 2 * n_partial doubles.
 cudaError_t objective_run(const float* W, const float* P, int V, int Kp, const float* S,
                           const float* Q, double normA2, double* partial, int n_partial,
                           double* out, unsigned* d_counter, int hist_cap, cudaStream_t s);

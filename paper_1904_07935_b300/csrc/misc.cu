@@ -73,28 +73,57 @@ __global__ void normalize_columns_kernel(float* X, int N, int K, int ld) {
 
 constexpr int kObjThreads = 256;
 
-// partial[b] = sum over this block's grid-stride share of W[i] * P[i] (FP64).
-__global__ void dot_partial_kernel(const float* __restrict__ a, const float* __restrict__ b, long long n,
-                                   double* __restrict__ partial) {
-  double s = 0.0;
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
-       i += (long long)gridDim.x * blockDim.x)
-    s += (double)a[i] * (double)b[i];
-  const double t = block_sum_d<kObjThreads>(s);
-  if (threadIdx.x == 0) partial[blockIdx.x] = t;
+// Error-free transformations (Knuth TwoSum; TwoProduct through fma) and the
+// compensated dot product Dot2 of Ogita, Rump & Oishi, "Accurate sum and dot
+// product", SIAM J. Sci. Comput. 26(6), 2005: the result is as accurate as if
+// computed in twice the working precision, without FP64 arithmetic.
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = a + b;
+  const float z = s - a;
+  e = (a - (s - z)) + (b - z);
 }
 
-// frob2 = normA2 - 2 sum(partial) + <S, Q>; appended to the history ring.
-__global__ void objective_final_kernel(const double* __restrict__ partial, int n_partial,
-                                       const float* __restrict__ S, const float* __restrict__ Q, int Kp,
-                                       double normA2, double* __restrict__ hist, unsigned* counter,
-                                       int hist_cap) {
-  double wp = 0.0;
-  for (int i = threadIdx.x; i < n_partial; i += blockDim.x) wp += partial[i];
+struct Dot2 {
+  float p = 0.f, c = 0.f;     // running sum and accumulated error terms
+  __device__ __forceinline__ void add(float a, float b) {
+    const float h = a * b;
+    const float r = fmaf(a, b, -h);       // exact: a * b = h + r
+    float s, q;
+    two_sum(p, h, s, q);
+    p = s;
+    c += q + r;
+  }
+  __device__ __forceinline__ double value() const { return (double)p + (double)c; }
+};
+
+// partial[b] = <a, b> over this block's grid-stride share of [0, n1), and
+// partial[nb + b] the same for <c, d> over [0, n2).
+__global__ void dot_partial_kernel(const float* __restrict__ a, const float* __restrict__ b, long long n1,
+                                   const float* __restrict__ c, const float* __restrict__ d, long long n2,
+                                   double* __restrict__ partial) {
+  Dot2 s1, s2;
+  const long long step = (long long)gridDim.x * blockDim.x;
+  const long long i0 = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  for (long long i = i0; i < n1; i += step) s1.add(a[i], b[i]);
+  for (long long i = i0; i < n2; i += step) s2.add(c[i], d[i]);
+  const double t1 = block_sum_d<kObjThreads>(s1.value());
+  const double t2 = block_sum_d<kObjThreads>(s2.value());
+  if (threadIdx.x == 0) {
+    partial[blockIdx.x] = t1;
+    partial[gridDim.x + blockIdx.x] = t2;
+  }
+}
+
+// frob2 = normA2 - 2 sum(partial[0..n)) + sum(partial[n..2n)); appended to
+// the history ring.
+__global__ void objective_final_kernel(const double* __restrict__ partial, int n_partial, double normA2,
+                                       double* __restrict__ hist, unsigned* counter, int hist_cap) {
+  double wp = 0.0, sq = 0.0;
+  for (int i = threadIdx.x; i < n_partial; i += blockDim.x) {
+    wp += partial[i];
+    sq += partial[n_partial + i];
+  }
   wp = block_sum_d<kObjThreads>(wp);
-  double sq = 0.0;
-  const int n = Kp * Kp;
-  for (int i = threadIdx.x; i < n; i += blockDim.x) sq += (double)S[i] * (double)Q[i];
   sq = block_sum_d<kObjThreads>(sq);
   if (threadIdx.x == 0) {
     const unsigned it = *counter;
@@ -166,11 +195,11 @@ cudaError_t normalize_columns(float* X, int N, int K, int ld, cudaStream_t s) {
 cudaError_t objective_run(const float* W, const float* P, int V, int Kp, const float* S, const float* Q,
                           double normA2, double* partial, int n_partial, double* out, unsigned* d_counter,
                           int hist_cap, cudaStream_t s) {
-  dot_partial_kernel<<<n_partial, kObjThreads, 0, s>>>(W, P, (long long)V * Kp, partial);
+  dot_partial_kernel<<<n_partial, kObjThreads, 0, s>>>(W, P, (long long)V * Kp, S, Q, (long long)Kp * Kp,
+                                                      partial);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  objective_final_kernel<<<1, kObjThreads, 0, s>>>(partial, n_partial, S, Q, Kp, normA2, out, d_counter,
-                                                   hist_cap);
+  objective_final_kernel<<<1, kObjThreads, 0, s>>>(partial, n_partial, normA2, out, d_counter, hist_cap);
   return cudaGetLastError();
 }
 

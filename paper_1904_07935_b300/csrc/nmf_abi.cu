@@ -117,6 +117,11 @@ cudaError_t enq_gram(nmf_ctx* c, const GramWork& g, const float* X, float* out) 
 //   per tile: chain (phase 2), then Y[:, hi:] -= X[:, lo:hi] G[lo:hi, hi:]  (phase 3)
 cudaError_t enq_update(nmf_ctx* c, float* X, const float* G, const float* B, int N, bool is_w) {
   const int K = c->K, Kp = c->Kp, T = c->T;
+  if (!is_w) {
+    // H: rows are independent, the whole regrouped update is one kernel.
+    c->launch_count += 1;
+    return h_update_run(X, B, G, N, K, Kp, c->eps, c->stream);
+  }
   GemmArgs a;
   a.M = N; a.N = K; a.Kin = K;
   a.A = X; a.lda = Kp; a.transA = 0;
@@ -243,7 +248,7 @@ nmf_status init_impl(const nmf_problem* p, nmf_ctx* c) {
   CK(dalloc(&c->d_counter, 1));
   CK(cudaMemset(c->d_counter, 0, sizeof(unsigned)));
   CK(dalloc(&c->hist, kHistCap));
-  CK(dalloc(&c->obj_partial, c->n_obj_partial));
+  CK(dalloc(&c->obj_partial, 2 * c->n_obj_partial));
 
   if (c->fmt == NMF_CSR_F32_I32) {
     std::vector<int> rp, ci;
