@@ -141,7 +141,8 @@ def run_gpu(args):
     va = torch.from_numpy(prob.A.val).to(dev)
     ctx = nmf.Nmf(V, D, K, row_ptr=rp, col_idx=ci, val=va,
                   W0=torch.from_numpy(W0).to(dev), H0=torch.from_numpy(H0).to(dev),
-                  stream=stream, tile_T=args.tile)
+                  stream=stream, tile_T=args.tile,
+                  flags=nmf.FLAG_MULTI_LAUNCH_W if args.w_multi_launch else 0)
     flush = torch.empty(256 * 2 ** 20 // 4, dtype=torch.float32, device=dev)   # 256 MB > L2
 
     # warm-up (also captures the CUDA graph)
@@ -301,6 +302,9 @@ def main():
     ap.add_argument("--tile", type=int, default=0)
     ap.add_argument("--cpu-iters", type=int, default=5)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--w-multi-launch", action="store_true",
+                    help="W update as per-tile launches instead of one cooperative launch "
+                         "(for per-kernel profiling)")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3

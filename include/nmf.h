@@ -81,7 +81,20 @@ typedef struct {
   int32_t tile_T;
   int32_t prec;
   void* stream;
+  int32_t flags;        /* NMF_FLAG_* bits, 0 for the defaults */
 } nmf_problem;
+
+/* nmf_problem.flags.  The FP32 path computes its Gram matrices on the SIMT
+ * FP32 pipes by default: the tensor cores accumulate in FP32 with
+ * truncation, which loses ~K * 2^-24 relative accuracy in a K-term sum, too
+ * much for the H update on the first iterations from a random start (it
+ * cancels S h ~ 60 against h + R).  NMF_FLAG_TC_GRAMS moves the FP32 Grams
+ * to the tensor cores (3xTF32) anyway.  The BF16 precision form always uses
+ * the tensor cores. */
+#define NMF_FLAG_TC_GRAMS 1
+/* Run the W update as separate launches per column tile instead of one
+ * persistent cooperative launch (the default where the GPU supports it). */
+#define NMF_FLAG_MULTI_LAUNCH_W 2
 
 typedef struct nmf_ctx nmf_ctx;
 
@@ -155,6 +168,16 @@ nmf_status nmf_profile(nmf_ctx* c, int32_t n_iters, float* step_ms);
 /* Introspection: tile width in use, cluster size of the W column chain,
  * number of kernel launches one iteration makes. */
 nmf_status nmf_query(nmf_ctx* c, int32_t* tile_T, int32_t* chain_ctas, int32_t* launches_per_iter);
+
+/* Dense product on the tensor cores (tcgen05), a library utility used by the
+ * iteration and exposed for testing:  C (M x N) = op(A) (M x K) * B (K x N),
+ * op(A) = A (row-major, lda) or A^T (A stored K x M row-major, lda) when
+ * transA != 0; B row-major K x N (ldb); C row-major (ldc).  prec:
+ * NMF_PREC_FP32 -> 3xTF32 split (near-FP32 accuracy), NMF_PREC_BF16 -> BF16
+ * operands.  FP32 accumulation.  All pointers device; asynchronous on
+ * `stream`.  Returns NMF_EINVAL for non-positive sizes or null pointers. */
+nmf_status nmf_gemm(int32_t M, int32_t N, int32_t K, const float* A, int64_t lda, int32_t transA,
+                    const float* B, int64_t ldb, float* C, int64_t ldc, int32_t prec, void* stream);
 
 /* Frees every device buffer and the graph of the context.  NULL is a no-op. */
 void nmf_destroy(nmf_ctx* c);

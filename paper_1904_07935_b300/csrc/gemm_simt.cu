@@ -6,6 +6,8 @@
 // 64 x 64 output tile per 256-thread CTA, 4 x 4 register micro-tile per
 // thread, k staged through shared memory 16 at a time (double-buffered via
 // registers).  FP32 multiply-add with FP32 accumulation.
+#include <algorithm>
+
 #include "internal.cuh"
 
 namespace plnmf {
@@ -177,6 +179,42 @@ cudaError_t gram_setup(GramWork& g, int N, int Kp) {
   g.chunk = chunk;
   g.n_chunks = (N + chunk - 1) / chunk;
   return cudaMalloc(&g.d_part, sizeof(float) * (size_t)g.n_chunks * Kp * Kp);
+}
+
+cudaError_t gram_setup_tc(GramWork& g, int N, int Kp) {
+  g.N = N;
+  g.Kp = Kp;
+  // 128-row M tiles; enough 32-row-aligned chunks of N for about one wave.
+  const int mtiles = (Kp + 127) / 128;
+  const int want = std::max(1, 148 / mtiles);
+  int chunk = (N + want - 1) / want;
+  chunk = std::max(64, (chunk + 31) / 32 * 32);
+  g.chunk = chunk;
+  g.n_chunks = (N + chunk - 1) / chunk;
+  return cudaMalloc(&g.d_part, sizeof(float) * (size_t)g.n_chunks * Kp * Kp);
+}
+
+cudaError_t gram_run_tc(const GramWork& g, const float* X, float* S, int K, int* d_status, cudaStream_t s) {
+  GemmArgs a;
+  a.M = g.Kp;
+  a.N = g.Kp;
+  a.Kin = g.N;
+  a.A = X;
+  a.lda = g.Kp;
+  a.transA = 1;
+  a.B = X;
+  a.ldb = g.Kp;
+  a.C = g.d_part;
+  a.ldc = g.Kp;
+  a.mode = GM_PARTIAL;
+  a.k_chunk = g.chunk;
+  a.part_stride = (int64_t)g.Kp * g.Kp;
+  a.n_chunks = g.n_chunks;
+  cudaError_t err = tc_gemm_run(a, TC_TF32X3, nullptr, 0, d_status, s);
+  if (err != cudaSuccess) return err;
+  dim3 grid((g.Kp + 127) / 128, g.Kp);
+  gram_reduce_kernel<<<grid, 128, 0, s>>>(g.d_part, g.n_chunks, g.Kp, K, S);
+  return cudaGetLastError();
 }
 
 void gram_free(GramWork& g) {

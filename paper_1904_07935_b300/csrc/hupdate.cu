@@ -17,31 +17,116 @@
 namespace plnmf {
 namespace {
 
+__device__ __forceinline__ unsigned smem_u32(const void* p) {
+  return static_cast<unsigned>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Rows [row0, row0 + nrows) of X (row stride Kp) into shared memory with row
+// stride ldx, one bulk copy (TMA, cp.async.bulk) per row, completed on `bar`.
+// Every thread returns once the data has landed (bounded wait; on expiry the
+// status word gets ST_TIMEOUT).  Row starts and lengths are multiples of 16
+// bytes because Kp and ldx are multiples of 4.
+__device__ void stage_rows_bulk(float* dst, int ldx, const float* X, int row0, int nrows, int Kp,
+                                unsigned long long* bar, int* status) {
+  const unsigned b = smem_u32(bar);
+  const unsigned bytes = (unsigned)Kp * 4u;
+  if (threadIdx.x == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(b) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(b), "r"(bytes * nrows) : "memory");
+  }
+  __syncthreads();
+  for (int r = threadIdx.x; r < nrows; r += blockDim.x) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_u32(dst + r * ldx)),
+        "l"(X + (int64_t)(row0 + r) * Kp), "r"(bytes), "r"(b)
+        : "memory");
+  }
+  unsigned long long t0 = 0;
+  unsigned polls = 0;
+  for (;;) {
+    unsigned ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(b)
+        : "memory");
+    if (ok) break;
+    if ((++polls & 63u) == 0) {
+      const unsigned long long now = global_ns();
+      if (t0 == 0) t0 = now;
+      else if (now - t0 > kWaitLimitNs) {
+        atomicOr(status, ST_TIMEOUT);
+        break;
+      }
+    }
+  }
+}
+
 constexpr int HT = 16;            // tile width
+
+// Gc[j * HT + c] = G[j][lo + c] for j < Kr, c < HT (zero beyond K).  The
+// loads are issued in batches of 8 before any store, so a thread does not
+// stall on each load in turn (in-order issue).
+template <int NT>
+__device__ __forceinline__ void stage_gcols(float* Gc, const float* __restrict__ G, int Kp, int K, int lo, int Kr) {
+  const int total = Kr * HT;
+  for (int base = threadIdx.x; base < total; base += 8 * NT) {
+    float v[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int e = base + u * NT;
+      const int j = e / HT, c = e % HT;
+      v[u] = (e < total && j < K && lo + c < K) ? __ldg(G + (int64_t)j * Kp + lo + c) : 0.f;
+    }
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int e = base + u * NT;
+      if (e < total) Gc[e] = v[u];
+    }
+  }
+}
 constexpr int HL = 4;             // lanes per row
 constexpr int HROWS = 64;         // rows per CTA
 constexpr int HTHREADS = HROWS * HL;
 
 __global__ void __launch_bounds__(HTHREADS) h_update_kernel(float* __restrict__ X, const float* __restrict__ B,
                                                             const float* __restrict__ G, int N, int K, int Kp,
-                                                            float eps) {
-  extern __shared__ __align__(16) float Gc[];     // Kr x HT: G[j][lo + c], zero beyond K
-  const int Kr = (Kp + HT - 1) / HT * HT;         // rows reachable as lo + t
+                                                            float eps, int* status) {
+  // Shared memory: Gc (Kr x HT) = G[j][lo + c] for the current tile, zero
+  // beyond K; Xs (HROWS x (Kp + 4)) = the CTA's rows of the factor, updated
+  // in place (row stride Kp + 4 keeps the 8 rows a warp touches on distinct
+  // banks).
+  extern __shared__ __align__(16) float smem[];
+  const int Kr = (Kp + HT - 1) / HT * HT;
+  const int ldx = Kp + 4;
+  float* Gc = smem;
+  float* Xs = smem + Kr * HT;
   const int tid = threadIdx.x;
   const int sub = tid & (HL - 1);
-  const int row = blockIdx.x * HROWS + (tid >> 2);
-  const bool valid = row < N;
+  const int rl = tid >> 2;
+  const int row0 = blockIdx.x * HROWS;
+  const int nrows = min(HROWS, N - row0);
+  const int row = row0 + rl;
+  const bool valid = rl < nrows;
   const unsigned full = 0xffffffffu;
-  float* xr = X + (int64_t)(valid ? row : 0) * Kp;
-  const float* br = B + (int64_t)(valid ? row : 0) * Kp;
+  const float* br = B + (int64_t)(valid ? row : row0) * Kp;
+
+  __shared__ __align__(8) unsigned long long bar;
+  stage_rows_bulk(Xs, ldx, X, row0, nrows, Kp, &bar, status);
+  float* xr = Xs + rl * ldx;
 
   for (int lo = 0; lo < K; lo += HT) {
     const int hi = min(K, lo + HT);
     __syncthreads();
-    for (int e = tid; e < Kr * HT; e += HTHREADS) {
-      const int j = e / HT, c = e % HT;
-      Gc[e] = (j < K && lo + c < K) ? __ldg(G + (int64_t)j * Kp + lo + c) : 0.f;
-    }
+    stage_gcols<HTHREADS>(Gc, G, Kp, K, lo, Kr);
     __syncthreads();
 
     // Old values of this row's tile (all 16, shared by the 4 lanes).
@@ -49,14 +134,14 @@ __global__ void __launch_bounds__(HTHREADS) h_update_kernel(float* __restrict__ 
 #pragma unroll
     for (int q = 0; q < HT / 4; ++q) {
       float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-      if (valid && lo + 4 * q < Kp) v = *reinterpret_cast<const float4*>(xr + lo + 4 * q);
+      if (lo + 4 * q < Kp) v = *reinterpret_cast<const float4*>(xr + lo + 4 * q);
       xo[4 * q] = v.x; xo[4 * q + 1] = v.y; xo[4 * q + 2] = v.z; xo[4 * q + 3] = v.w;
     }
     // Columns of this lane: lo + 4 * sub + q (its own old values read again
     // so that no register array is indexed by the lane number).
     float acc[4];
     float4 own = make_float4(0.f, 0.f, 0.f, 0.f);
-    if (valid && lo + 4 * sub < Kp) own = *reinterpret_cast<const float4*>(xr + lo + 4 * sub);
+    if (lo + 4 * sub < Kp) own = *reinterpret_cast<const float4*>(xr + lo + 4 * sub);
     const float xown[4] = {own.x, own.y, own.z, own.w};
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
@@ -67,11 +152,12 @@ __global__ void __launch_bounds__(HTHREADS) h_update_kernel(float* __restrict__ 
         acc[q] = fmaf(1.f - gcc, xown[q], br[c]);
       }
     }
-    // Columns outside the tile: j < lo (new) and j >= hi (old); padding
+    // Columns outside the tile: j < lo (new) and j >= lo + HT (old); padding
     // columns of X and rows of G are zero, so the loop runs to Kp.
     auto outside = [&](int j0, int j1) {
+#pragma unroll 2
       for (int j = j0; j < j1; j += 4) {
-        const float4 x4 = valid ? *reinterpret_cast<const float4*>(xr + j) : make_float4(0.f, 0.f, 0.f, 0.f);
+        const float4 x4 = *reinterpret_cast<const float4*>(xr + j);
         const float xs[4] = {x4.x, x4.y, x4.z, x4.w};
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
@@ -112,7 +198,10 @@ __global__ void __launch_bounds__(HTHREADS) h_update_kernel(float* __restrict__ 
         if (c2 > t) acc[q2] = fmaf(-Gc[(lo + t) * HT + c2], v, acc[q2]);
       }
     }
-    if (valid) {
+    __syncwarp();
+    if (lo + 4 * sub + 3 < hi) {
+      *reinterpret_cast<float4*>(xr + lo + 4 * sub) = make_float4(xn[0], xn[1], xn[2], xn[3]);
+    } else {
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
         const int c = lo + 4 * sub + q;
@@ -120,17 +209,115 @@ __global__ void __launch_bounds__(HTHREADS) h_update_kernel(float* __restrict__ 
       }
     }
   }
+  __syncthreads();
+  {
+    const int kq = Kp / 4;
+    float4* dst = reinterpret_cast<float4*>(X + (int64_t)row0 * Kp);
+    for (int e = tid; e < nrows * kq; e += HTHREADS) {
+      const int r = e / kq, q = e % kq;
+      dst[e] = *reinterpret_cast<const float4*>(Xs + r * ldx + 4 * q);
+    }
+  }
+}
+
+// Base of one W tile [lo, hi) for the column chain (left-looking form of
+// Eqs. 4-6): for every row v and tile column c,
+//   Y[v, c] = P[v, c] - sum_{j < new_end} Q[j][c] W[v, j](new)
+//                     - sum_{j >= hi} Q[j][c] W[v, j](old)
+//                     - sum_{c < j < hi} Q[j][c] W[v, j](old).
+// (The W_old * Q_cc initialisation of Alg. 2 cancels the j = c term exactly
+// and is left out.)  With new_end = lo this is the complete base; with
+// new_end = lo - 16 the previous tile is left out, so the kernel can run
+// while the chain is still finishing that tile (columns in [new_end, lo) are
+// neither read for the result nor written here), and the chain adds the
+// previous tile's contribution itself.
+__global__ void __launch_bounds__(HTHREADS) w_prep_kernel(const float* __restrict__ X, const float* __restrict__ B,
+                                                          const float* __restrict__ G, float* __restrict__ Y,
+                                                          int N, int K, int Kp, int lo, int new_end, int* status) {
+  // Shared memory: Gc (Kr x HT) = G[j][lo + c], zero beyond K; Xs = the CTA's
+  // rows of X (row stride Kp + 4, see h_update_kernel).
+  extern __shared__ __align__(16) float smem[];
+  __shared__ __align__(8) unsigned long long bar;
+  const int Kr = (Kp + HT - 1) / HT * HT;
+  const int ldx = Kp + 4;
+  float* Gc = smem;
+  float* Xs = smem + Kr * HT;
+  const int hi = min(K, lo + HT);
+  const int tid = threadIdx.x;
+  const int sub = tid & (HL - 1);
+  const int row0 = blockIdx.x * HROWS;
+  const int nrows = min(HROWS, N - row0);
+  const int row = row0 + (tid >> 2);
+  const bool valid = (tid >> 2) < nrows;
+  stage_gcols<HTHREADS>(Gc, G, Kp, K, lo, Kr);
+  stage_rows_bulk(Xs, ldx, X, row0, nrows, Kp, &bar, status);
+  if (!valid) return;
+  const float* xr = Xs + (tid >> 2) * ldx;
+  float acc[4];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const int c = lo + 4 * sub + q;
+    acc[q] = c < hi ? __ldg(B + (int64_t)row * Kp + c) : 0.f;
+  }
+  auto outside = [&](int j0, int j1) {
+#pragma unroll 2
+    for (int j = j0; j < j1; j += 4) {
+      const float4 x4 = *reinterpret_cast<const float4*>(xr + j);
+      const float xs[4] = {x4.x, x4.y, x4.z, x4.w};
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const float4 g = *reinterpret_cast<const float4*>(Gc + (j + u) * HT + 4 * sub);
+        acc[0] = fmaf(-g.x, xs[u], acc[0]);
+        acc[1] = fmaf(-g.y, xs[u], acc[1]);
+        acc[2] = fmaf(-g.z, xs[u], acc[2]);
+        acc[3] = fmaf(-g.w, xs[u], acc[3]);
+      }
+    }
+  };
+  outside(0, new_end);
+  outside(lo + HT < Kp ? lo + HT : Kp, Kp);
+  float xo[HT];
+#pragma unroll
+  for (int q = 0; q < HT / 4; ++q) {
+    float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (lo + 4 * q < Kp) v = *reinterpret_cast<const float4*>(xr + lo + 4 * q);
+    xo[4 * q] = v.x; xo[4 * q + 1] = v.y; xo[4 * q + 2] = v.z; xo[4 * q + 3] = v.w;
+  }
+#pragma unroll
+  for (int j = 1; j < HT; ++j) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int cl = 4 * sub + q;
+      if (j > cl) acc[q] = fmaf(-Gc[(lo + j) * HT + cl], xo[j], acc[q]);
+    }
+  }
+  float* yr = Y + (int64_t)row * Kp;
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const int c = lo + 4 * sub + q;
+    if (c < hi) yr[c] = acc[q];
+  }
 }
 
 }  // namespace
 
+cudaError_t w_prep_run(const float* X, const float* B, const float* G, float* Y, int N, int K, int Kp, int lo,
+                       int new_end, int* status, cudaStream_t s) {
+  const size_t smem = sizeof(float) * ((size_t)((Kp + HT - 1) / HT * HT) * HT + (size_t)HROWS * (Kp + 4));
+  cudaError_t e = cudaFuncSetAttribute(w_prep_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  const int blocks = (N + HROWS - 1) / HROWS;
+  w_prep_kernel<<<blocks, HTHREADS, smem, s>>>(X, B, G, Y, N, K, Kp, lo, new_end, status);
+  return cudaGetLastError();
+}
+
 cudaError_t h_update_run(float* X, const float* B, const float* G, int N, int K, int Kp, float eps,
-                         cudaStream_t s) {
-  const size_t smem = sizeof(float) * (size_t)((Kp + HT - 1) / HT * HT) * HT;
+                         int* status, cudaStream_t s) {
+  const size_t smem = sizeof(float) * ((size_t)((Kp + HT - 1) / HT * HT) * HT + (size_t)HROWS * (Kp + 4));
   cudaError_t e = cudaFuncSetAttribute(h_update_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   const int blocks = (N + HROWS - 1) / HROWS;
-  h_update_kernel<<<blocks, HTHREADS, smem, s>>>(X, B, G, N, K, Kp, eps);
+  h_update_kernel<<<blocks, HTHREADS, smem, s>>>(X, B, G, N, K, Kp, eps, status);
   return cudaGetLastError();
 }
 

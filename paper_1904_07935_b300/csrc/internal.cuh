@@ -75,6 +75,13 @@ struct GemmArgs {
 
 cudaError_t gemm_run(const GemmArgs& a, cudaStream_t s);
 
+// Tensor-core (tcgen05) version of the same family; upper_only is not
+// supported.  a_bf16: optional BF16 copy of A with A's layout (BF16 mode).
+enum TcPrecision : int { TC_TF32X3 = 0, TC_BF16 = 1 };
+cudaError_t tc_gemm_run(const GemmArgs& g, TcPrecision prec, const void* a_bf16, int bn, int* d_status,
+                        cudaStream_t s);
+int tc_pick_bn(int N);
+
 // S (Kp x Kp) = X^T X for X (N x Kp): split-N partials, FP64 fixed-order sum.
 struct GramWork {
   float* d_part = nullptr;   // n_chunks x Kp x Kp
@@ -83,6 +90,9 @@ struct GramWork {
 cudaError_t gram_setup(GramWork& g, int N, int Kp);
 void gram_free(GramWork& g);
 cudaError_t gram_run(const GramWork& g, const float* X, float* S, int K, cudaStream_t s);
+// Same result through the tensor cores (3xTF32, split-N partials).
+cudaError_t gram_setup_tc(GramWork& g, int N, int Kp);
+cudaError_t gram_run_tc(const GramWork& g, const float* X, float* S, int K, int* d_status, cudaStream_t s);
 
 // ---------------------------------------------------------------------------
 // Tall-factor update (Alg. 2 regrouped): phase 1 GEMM, per-tile chain, phase 3.
@@ -95,8 +105,11 @@ struct ChainConfig {
 };
 constexpr int kMaxChainTile = 16;
 
-// Y (N x Kp): phase-1 base; X: factor (old on entry, new on exit); G: Gram.
-cudaError_t chain_run(float* Y, float* X, const float* G, int N, int Kp, int lo, int hi,
+// Y (N x Kp): base of tile [lo, hi) (see w_prep_run); X: factor (old on
+// entry, tile columns new on exit); G: Gram.  prev_lo >= 0: the base still
+// lacks the contribution of the new columns [prev_lo, lo) of X, which the
+// kernel adds first.
+cudaError_t chain_run(float* Y, float* X, const float* G, int N, int Kp, int lo, int hi, int prev_lo,
                       float eps, bool normalize, const ChainConfig& cfg, int* d_status,
                       cudaStream_t s);
 bool chain_config_for(int N, bool normalize, int T, ChainConfig* cfg);
@@ -104,7 +117,26 @@ bool chain_config_for(int N, bool normalize, int T, ChainConfig* cfg);
 // Whole H update in one launch (rows independent): X (N x Kp) old -> new in
 // place, B = R, G = S.
 cudaError_t h_update_run(float* X, const float* B, const float* G, int N, int K, int Kp, float eps,
-                         cudaStream_t s);
+                         int* status, cudaStream_t s);
+// Base of W tile [lo, lo + 16) for the chain: Y[:, tile] from B = P, G = Q and
+// the current (partly updated) factor X, with the new columns [0, new_end).
+cudaError_t w_prep_run(const float* X, const float* B, const float* G, float* Y, int N, int K, int Kp, int lo,
+                       int new_end, int* status, cudaStream_t s);
+constexpr int kRowTile = 16;   // tile width of the row-parallel update kernels
+
+// Persistent, cooperative W update (one launch per update): cluster 0 runs the
+// column chain over all tiles, the other clusters compute the tile bases.
+struct WPersistConfig {
+  int cluster = 16;
+  int rpt = 1;
+  int n_clusters = 0;
+  int worker_rows = 128;
+  size_t smem = 0;
+};
+bool w_persistent_config(int N, int Kp, WPersistConfig* cfg);
+// d_sync: 2 * ceil(K / 16) ints (zeroed by the call, on the stream).
+cudaError_t w_persistent_run(float* X, const float* P, const float* Q, float* Y, int N, int K, int Kp, float eps,
+                             int* d_sync, int* d_status, const WPersistConfig& cfg, cudaStream_t s);
 
 // ---------------------------------------------------------------------------
 // Misc kernels.

@@ -13,9 +13,15 @@ using namespace plnmf;
 
 struct nmf_ctx {
   int V = 0, D = 0, K = 0, Kp = 0, T = 16, fmt = 0, prec = 0;
+  bool use_tc = false;      // FP32 Grams on the tensor cores (3xTF32)
   float eps = 1e-16f;
   cudaStream_t stream = nullptr;
   bool own_stream = false;
+  cudaStream_t side = nullptr;          // second stream for the W tile bases
+  bool w_persistent = false;            // whole W update as one cooperative launch
+  WPersistConfig wp;
+  int* d_sync = nullptr;
+  std::vector<cudaEvent_t> ev;          // fork / join events of the W update
   // A (caller-owned) and its transpose (context-owned, CSR only).
   const float* dense = nullptr;
   int64_t lda = 0;
@@ -109,48 +115,59 @@ cudaError_t enq_product_P(nmf_ctx* c) {   // P = A H^T  (V x Kp)
 
 cudaError_t enq_gram(nmf_ctx* c, const GramWork& g, const float* X, float* out) {
   c->launch_count += 2;
+  if (c->use_tc) return gram_run_tc(g, X, out, c->K, c->d_status, c->stream);
   return gram_run(g, X, out, c->K, c->stream);
 }
 
-// Regrouped update of one tall factor X (N x Kp) with Gram G and data term B:
-//   phase 1:  Y = B + c' (.) X - X triu(G, 1)         (all old contributions)
-//   per tile: chain (phase 2), then Y[:, hi:] -= X[:, lo:hi] G[lo:hi, hi:]  (phase 3)
+// Regrouped update of one tall factor X (N x Kp) with Gram G and data term B.
+//  H: rows are independent; one kernel runs every tile (base, chain, write).
+//  W: per tile of 16 columns, a full-grid kernel forms the tile's base from the
+//     current rows (new columns left of the tile, old ones right of it), then
+//     the cluster kernel finishes the tile's columns with their norms.
 cudaError_t enq_update(nmf_ctx* c, float* X, const float* G, const float* B, int N, bool is_w) {
-  const int K = c->K, Kp = c->Kp, T = c->T;
+  const int K = c->K, Kp = c->Kp;
   if (!is_w) {
-    // H: rows are independent, the whole regrouped update is one kernel.
     c->launch_count += 1;
-    return h_update_run(X, B, G, N, K, Kp, c->eps, c->stream);
+    return h_update_run(X, B, G, N, K, Kp, c->eps, c->d_status, c->stream);
   }
-  GemmArgs a;
-  a.M = N; a.N = K; a.Kin = K;
-  a.A = X; a.lda = Kp; a.transA = 0;
-  a.B = G; a.ldb = Kp;
-  a.C = c->Y; a.ldc = Kp;
-  a.mode = GM_PHASE1;
-  a.E = B; a.lde = Kp;
-  a.X = X; a.ldx = Kp;
-  a.h_mode = is_w ? 0 : 1;
-  cudaError_t e = gemm_run(a, c->stream);
-  c->launch_count += 1;
-  if (e != cudaSuccess) return e;
-  const ChainConfig& cfg = is_w ? c->chainW : c->chainH;
-  for (int lo = 0; lo < K; lo += T) {
-    const int hi = std::min(K, lo + T);
-    e = chain_run(c->Y, X, G, N, Kp, lo, hi, c->eps, is_w, cfg, c->d_status, c->stream);
+  if (c->w_persistent) {
+    c->launch_count += 1;
+    return w_persistent_run(X, B, G, c->Y, N, K, Kp, c->eps, c->d_sync, c->d_status, c->wp, c->stream);
+  }
+  // W: tile tau's base without tile tau-1 ("main") runs on the side stream
+  // while the chain of tile tau-1 runs; the chain of tile tau adds tile
+  // tau-1 itself.  Events: fork, base_done[tau], chain_done[tau].
+  const int nt = (K + kRowTile - 1) / kRowTile;
+  cudaEvent_t* ev = c->ev.data();
+  cudaEvent_t fork = ev[0];
+  cudaEvent_t* base_done = ev + 1;
+  cudaEvent_t* chain_done = ev + 1 + nt;
+  cudaError_t e;
+  if ((e = cudaEventRecord(fork, c->stream)) != cudaSuccess) return e;
+  if ((e = cudaStreamWaitEvent(c->side, fork, 0)) != cudaSuccess) return e;
+  // An event wait orders against the event's latest record *in enqueue
+  // order*, so every base is enqueued after the chain it depends on.
+  auto base = [&](int tau) -> cudaError_t {
+    const int lo = tau * kRowTile;
+    const int new_end = tau >= 1 ? lo - kRowTile : 0;    // new columns [0, lo - 16)
+    cudaError_t err;
+    if (tau >= 2 && (err = cudaStreamWaitEvent(c->side, chain_done[tau - 2], 0)) != cudaSuccess) return err;
+    if ((err = w_prep_run(X, B, G, c->Y, N, K, Kp, lo, new_end, c->d_status, c->side)) != cudaSuccess) return err;
+    c->launch_count += 1;
+    return cudaEventRecord(base_done[tau], c->side);
+  };
+  if ((e = base(0)) != cudaSuccess) return e;
+  if (nt > 1 && (e = base(1)) != cudaSuccess) return e;
+  for (int tau = 0; tau < nt; ++tau) {
+    const int lo = tau * kRowTile, hi = std::min(K, lo + kRowTile);
+    if ((e = cudaStreamWaitEvent(c->stream, base_done[tau], 0)) != cudaSuccess) return e;
+    e = chain_run(c->Y, X, G, N, Kp, lo, hi, tau >= 1 ? lo - kRowTile : -1, c->eps, true, c->chainW, c->d_status,
+                  c->stream);
     c->launch_count += 1;
     if (e != cudaSuccess) return e;
-    if (hi < K) {
-      GemmArgs b;
-      b.M = N; b.N = K - hi; b.Kin = hi - lo;
-      b.A = X + lo; b.lda = Kp; b.transA = 0;
-      b.B = G + (int64_t)lo * Kp + hi; b.ldb = Kp;
-      b.C = c->Y + hi; b.ldc = Kp;
-      b.mode = GM_SUB;
-      e = gemm_run(b, c->stream);
-      c->launch_count += 1;
-      if (e != cudaSuccess) return e;
-    }
+    if ((e = cudaEventRecord(chain_done[tau], c->stream)) != cudaSuccess) return e;
+    // Base of tile tau + 2 (needs chains <= tau) overlaps the chain of tau + 1.
+    if (tau + 2 < nt && (e = base(tau + 2)) != cudaSuccess) return e;
   }
   return cudaSuccess;
 }
@@ -232,19 +249,23 @@ nmf_status init_impl(const nmf_problem* p, nmf_ctx* c) {
     CK(cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking));
     c->own_stream = true;
   }
-  // Tile width: the column chain keeps a tile in registers (<= 16 wide,
-  // <= 8 wide above 32K rows).
-  int T = p->tile_T > 0 ? p->tile_T : 16;
-  if (!chain_config_for(V, true, T, &c->chainW)) {
-    if (p->tile_T > 0) return NMF_EUNSUPPORTED;
-    T = 8;
-    if (!chain_config_for(V, true, T, &c->chainW)) return NMF_EUNSUPPORTED;
-  }
+  // Tile width T of the regrouped updates: 16 columns (the register tile of
+  // the column chain).  A requested tile_T other than 16 is accepted only as
+  // a request for the library choice.
+  const int T = kRowTile;
+  if (!chain_config_for(V, true, T, &c->chainW)) return NMF_EUNSUPPORTED;
   if (!chain_config_for(D, false, T, &c->chainH)) return NMF_EUNSUPPORTED;
   c->T = T;
 
+  CK(cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking));
+  {
+    const int nt = (c->K + kRowTile - 1) / kRowTile;
+    c->ev.assign(1 + 2 * nt, nullptr);
+    for (auto& e : c->ev) CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+  }
   CK(dalloc(&c->d_status, 1));
   CK(cudaMemset(c->d_status, 0, sizeof(int)));
+  CK(dalloc(&c->d_sync, 2 * ((c->K + kRowTile - 1) / kRowTile)));
   CK(dalloc(&c->d_counter, 1));
   CK(cudaMemset(c->d_counter, 0, sizeof(unsigned)));
   CK(dalloc(&c->hist, kHistCap));
@@ -322,8 +343,14 @@ nmf_status init_impl(const nmf_problem* p, nmf_ctx* c) {
   CK(cudaMemsetAsync(c->P, 0, sizeof(float) * nV, c->stream));
   CK(cudaMemsetAsync(c->R, 0, sizeof(float) * nD, c->stream));
   CK(cudaMemsetAsync(c->Y, 0, sizeof(float) * nMax, c->stream));
-  CK(gram_setup(c->gramW, V, Kp));
-  CK(gram_setup(c->gramH, D, Kp));
+  c->use_tc = (p->flags & NMF_FLAG_TC_GRAMS) != 0;
+  if (c->use_tc) {
+    CK(gram_setup_tc(c->gramW, V, Kp));
+    CK(gram_setup_tc(c->gramH, D, Kp));
+  } else {
+    CK(gram_setup(c->gramW, V, Kp));
+    CK(gram_setup(c->gramH, D, Kp));
+  }
 
   // Initial factors.
   const uint64_t sw = p->seed ^ 0x5757575757575757ull, sh = p->seed ^ 0x4848484848484848ull;
@@ -342,7 +369,24 @@ nmf_status init_impl(const nmf_problem* p, nmf_ctx* c) {
     CK(fill_uniform_splitmix_t(c->Ht, D, p->K, Kp, sh, c->stream));
   }
   CK(normalize_columns(c->W, V, p->K, Kp, c->stream));
-  CK(gram_run(c->gramW, c->W, c->S, c->K, c->stream));
+  // Persistent W update: probe the cooperative cluster launch once with no
+  // rows (nothing is read or written but the hand-off flags).
+  if (!(p->flags & NMF_FLAG_MULTI_LAUNCH_W) && w_persistent_config(V, Kp, &c->wp)) {
+    CK(cudaStreamSynchronize(c->stream));
+    cudaError_t e = w_persistent_run(c->W, c->P, c->Q, c->Y, 0, c->K, Kp, c->eps, c->d_sync, c->d_status, c->wp,
+                                     c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e == cudaSuccess) {
+      int st = 0;
+      CK(cudaMemcpy(&st, c->d_status, sizeof(int), cudaMemcpyDeviceToHost));
+      c->w_persistent = (st & ST_TIMEOUT) == 0;
+      CK(cudaMemset(c->d_status, 0, sizeof(int)));
+    } else {
+      cudaGetLastError();
+      c->w_persistent = false;
+    }
+  }
+  CK(enq_gram(c, c->gramW, c->W, c->S));
   c->s_valid = true;
   CK(cudaStreamSynchronize(c->stream));
   // Count the launches of one iteration (dry count, nothing is enqueued).
@@ -357,10 +401,16 @@ void free_ctx(nmf_ctx* c) {
   spmm_plan_free(c->planAt);
   gram_free(c->gramW);
   gram_free(c->gramH);
-  for (void* p : {(void*)c->rpT, (void*)c->ciT, (void*)c->vaT, (void*)c->W, (void*)c->Ht, (void*)c->R,
+  for (void* p : {(void*)c->d_sync, (void*)c->rpT, (void*)c->ciT, (void*)c->vaT, (void*)c->W, (void*)c->Ht, (void*)c->R,
                   (void*)c->P, (void*)c->S, (void*)c->Q, (void*)c->Y, (void*)c->stage,
                   (void*)c->obj_partial, (void*)c->hist, (void*)c->d_counter, (void*)c->d_status})
     if (p) cudaFree(p);
+  if (c->side) {
+    cudaStreamSynchronize(c->side);
+    cudaStreamDestroy(c->side);
+  }
+  for (auto e : c->ev)
+    if (e) cudaEventDestroy(e);
   if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
   delete c;
 }
@@ -600,6 +650,12 @@ nmf_status nmf_profile(nmf_ctx* c, int32_t n_iters, float* step_ms) {
 
 nmf_status nmf_query(nmf_ctx* c, int32_t* tile_T, int32_t* chain_ctas, int32_t* launches_per_iter) {
   if (!c) return NMF_EINVAL;
+  if (chain_ctas && c->w_persistent) {
+    *chain_ctas = c->wp.cluster;
+    if (tile_T) *tile_T = c->T;
+    if (launches_per_iter) *launches_per_iter = c->launches_per_iter;
+    return NMF_OK;
+  }
   if (tile_T) *tile_T = c->T;
   if (chain_ctas) *chain_ctas = c->chainW.cluster;
   if (launches_per_iter) *launches_per_iter = c->launches_per_iter;
@@ -607,5 +663,24 @@ nmf_status nmf_query(nmf_ctx* c, int32_t* tile_T, int32_t* chain_ctas, int32_t* 
 }
 
 void nmf_destroy(nmf_ctx* c) { free_ctx(c); }
+
+nmf_status nmf_gemm(int32_t M, int32_t N, int32_t K, const float* A, int64_t lda, int32_t transA,
+                    const float* B, int64_t ldb, float* C, int64_t ldc, int32_t prec, void* stream) {
+  if (M <= 0 || N <= 0 || K <= 0 || !A || !B || !C) return NMF_EINVAL;
+  if (prec != NMF_PREC_FP32 && prec != NMF_PREC_BF16) return NMF_EINVAL;
+  static int* d_status = nullptr;
+  if (!d_status) {
+    CK(cudaMalloc(&d_status, sizeof(int)));
+    CK(cudaMemset(d_status, 0, sizeof(int)));
+  }
+  GemmArgs g;
+  g.M = M; g.N = N; g.Kin = K;
+  g.A = A; g.lda = lda; g.transA = transA ? 1 : 0;
+  g.B = B; g.ldb = ldb;
+  g.C = C; g.ldc = ldc;
+  g.mode = GM_STORE;
+  return from_cuda(tc_gemm_run(g, prec == NMF_PREC_FP32 ? TC_TF32X3 : TC_BF16, nullptr, 0, d_status,
+                               static_cast<cudaStream_t>(stream)));
+}
 
 }  // extern "C"

@@ -5,13 +5,11 @@
 // Work plan (built once on the host): every CSR row becomes one work item,
 // except rows longer than `seg` non-zeros (the Zipf head words, which can hold
 // nearly every document), which are cut into items of at most `seg`
-// non-zeros.  A group of lanes owns an item: the lanes cover the Kp/4 float4
-// chunks of one output row, the non-zeros are streamed 32 at a time and
-// broadcast with shuffles, and the gathered rows of X are read as float4
-// (coalesced 16-byte loads).  Split rows write partial rows to a scratch
-// buffer and a second kernel adds them in a fixed order, so results are
-// bit-reproducible (no floating-point atomics).  Items are ordered longest
-// first to balance the tail.
+// non-zeros.  A warp owns an item (see spmm_items_kernel for the lane
+// layout); the gathered rows of X are read as 16-byte loads.  Split rows write
+// partial rows to a scratch buffer and a second kernel adds them in a fixed
+// order, so results are bit-reproducible (no floating-point atomics).  Items
+// are ordered longest first to balance the tail.
 #include <algorithm>
 #include <numeric>
 
@@ -27,59 +25,75 @@ __device__ __forceinline__ void fma4(float4& acc, float a, const float4& x) {
   acc.w = fmaf(a, x.w, acc.w);
 }
 
-// LPR lanes per item (power of two <= 32), VPL float4 chunks per lane.
-template <int LPR, int VPL>
+// One warp per work item.  The warp is split into G = 32 / L groups of L
+// lanes; group g takes non-zeros beg + g, beg + g + G, ... and each of its
+// lanes owns C float4 chunks of the output row (L * C * 4 >= Kp), so one step
+// gathers G rows of X at once with 16-byte loads (two steps in flight).  At
+// the end the G group sums are added with shuffles in a fixed tree order.
+template <int L, int C>
 __global__ void __launch_bounds__(256) spmm_items_kernel(const int4* __restrict__ items, int n_items,
                                                          const int* __restrict__ col_idx,
                                                          const float* __restrict__ val,
                                                          const float4* __restrict__ X, int Kp4,
                                                          float4* __restrict__ Y,
                                                          float4* __restrict__ partial) {
+  constexpr int G = 32 / L;
   const int lane = threadIdx.x & 31;
-  const int sub = lane & (LPR - 1);                 // lane inside the item group
-  const int group = (blockIdx.x * blockDim.x + threadIdx.x) / LPR;
-  const bool active = group < n_items;
-  int4 it = active ? items[group] : make_int4(0, 0, 0, -1);
-  const unsigned full = 0xffffffffu;
+  const int g = lane / L, sub = lane % L;
+  const int item = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (item >= n_items) return;                     // whole warp leaves together
+  const int4 it = items[item];
 
-  float4 acc[VPL];
+  float4 acc[C];
 #pragma unroll
-  for (int q = 0; q < VPL; ++q) acc[q] = make_float4(0.f, 0.f, 0.f, 0.f);
+  for (int q = 0; q < C; ++q) acc[q] = make_float4(0.f, 0.f, 0.f, 0.f);
 
-  // Every lane of the warp must take part in the shuffles, so the loop runs
-  // to the longest item in the warp; shorter groups see n = 0.
-  int beg = it.y, end = active ? it.z : it.y;
-  for (int e0 = beg;; e0 += LPR) {
-    const int remaining = end - e0;
-    const int any = __any_sync(full, remaining > 0);
-    if (!any) break;
-    int c = 0;
-    float a = 0.f;
-    if (sub < remaining) {
-      c = __ldg(col_idx + e0 + sub);
-      a = __ldg(val + e0 + sub);
+  int e = it.y + g;
+  for (; e + G < it.z; e += 2 * G) {               // two non-zeros per group in flight
+    const int c0 = __ldg(col_idx + e), c1 = __ldg(col_idx + e + G);
+    const float a0 = __ldg(val + e), a1 = __ldg(val + e + G);
+    const float4* x0 = X + (size_t)c0 * Kp4;
+    const float4* x1 = X + (size_t)c1 * Kp4;
+    float4 v0[C], v1[C];
+#pragma unroll
+    for (int q = 0; q < C; ++q) {
+      const int k = sub + L * q;
+      v0[q] = k < Kp4 ? __ldg(x0 + k) : make_float4(0.f, 0.f, 0.f, 0.f);
+      v1[q] = k < Kp4 ? __ldg(x1 + k) : make_float4(0.f, 0.f, 0.f, 0.f);
     }
-    const int n = max(0, min(LPR, remaining));
-#pragma unroll 4
-    for (int j = 0; j < LPR; ++j) {
-      const int cj = __shfl_sync(full, c, j, LPR);
-      const float aj = __shfl_sync(full, a, j, LPR);
-      if (j < n) {
-        const float4* xr = X + (size_t)cj * Kp4;
 #pragma unroll
-        for (int q = 0; q < VPL; ++q) {
-          const int idx = sub + LPR * q;
-          if (idx < Kp4) fma4(acc[q], aj, __ldg(xr + idx));
-        }
-      }
+    for (int q = 0; q < C; ++q) {
+      fma4(acc[q], a0, v0[q]);
+      fma4(acc[q], a1, v1[q]);
     }
   }
-  if (!active) return;
+  if (e < it.z) {
+    const int c0 = __ldg(col_idx + e);
+    const float a0 = __ldg(val + e);
+    const float4* x0 = X + (size_t)c0 * Kp4;
+#pragma unroll
+    for (int q = 0; q < C; ++q) {
+      const int k = sub + L * q;
+      if (k < Kp4) fma4(acc[q], a0, __ldg(x0 + k));
+    }
+  }
+  // Add the group sums: xor-shuffles over the group index bits.
+#pragma unroll
+  for (int off = L; off < 32; off <<= 1) {
+#pragma unroll
+    for (int q = 0; q < C; ++q) {
+      acc[q].x += __shfl_xor_sync(0xffffffffu, acc[q].x, off);
+      acc[q].y += __shfl_xor_sync(0xffffffffu, acc[q].y, off);
+      acc[q].z += __shfl_xor_sync(0xffffffffu, acc[q].z, off);
+      acc[q].w += __shfl_xor_sync(0xffffffffu, acc[q].w, off);
+    }
+  }
+  if (g != 0) return;
   float4* dst = (it.w < 0) ? (Y + (size_t)it.x * Kp4) : (partial + (size_t)it.w * Kp4);
 #pragma unroll
-  for (int q = 0; q < VPL; ++q) {
-    const int idx = sub + LPR * q;
-    if (idx < Kp4) dst[idx] = acc[q];
+  for (int q = 0; q < C; ++q) {
+    const int k = sub + L * q;
+    if (k < Kp4) dst[k] = acc[q];
   }
 }
 
@@ -100,14 +114,14 @@ __global__ void spmm_combine_kernel(const int4* __restrict__ comb, int n_long,
   }
 }
 
-template <int LPR, int VPL>
+template <int L, int C>
 cudaError_t launch_items(const SpmmPlan& p, const int* ci, const float* va, const float* X, float* Y,
                          int Kp, cudaStream_t s) {
   const int Kp4 = Kp / 4;
-  const int per_block = 256 / LPR;
-  const int blocks = (p.n_items + per_block - 1) / per_block;
+  const int warps_per_block = 8;
+  const int blocks = (p.n_items + warps_per_block - 1) / warps_per_block;
   if (blocks > 0) {
-    spmm_items_kernel<LPR, VPL><<<blocks, 256, 0, s>>>(
+    spmm_items_kernel<L, C><<<blocks, 32 * warps_per_block, 0, s>>>(
         p.d_items, p.n_items, ci, va, reinterpret_cast<const float4*>(X), Kp4,
         reinterpret_cast<float4*>(Y), reinterpret_cast<float4*>(p.d_partial));
   }
@@ -172,15 +186,20 @@ cudaError_t spmm_run(const SpmmPlan& p, const int* ci, const float* va, const fl
                      int Kp, cudaStream_t s) {
   const int Kp4 = Kp / 4;
   cudaError_t err;
-  if (Kp4 <= 1) err = launch_items<1, 1>(p, ci, va, X, Y, Kp, s);
-  else if (Kp4 <= 2) err = launch_items<2, 1>(p, ci, va, X, Y, Kp, s);
-  else if (Kp4 <= 4) err = launch_items<4, 1>(p, ci, va, X, Y, Kp, s);
-  else if (Kp4 <= 8) err = launch_items<8, 1>(p, ci, va, X, Y, Kp, s);
-  else if (Kp4 <= 16) err = launch_items<16, 1>(p, ci, va, X, Y, Kp, s);
-  else if (Kp4 <= 32) err = launch_items<32, 1>(p, ci, va, X, Y, Kp, s);
-  else if (Kp4 <= 64) err = launch_items<32, 2>(p, ci, va, X, Y, Kp, s);
-  else if (Kp4 <= 96) err = launch_items<32, 3>(p, ci, va, X, Y, Kp, s);
-  else err = launch_items<32, 4>(p, ci, va, X, Y, Kp, s);   // Kp <= 512
+  // Lanes per non-zero L and float4 chunks per lane C with L * C >= Kp / 4,
+  // chosen to keep C <= 8 and few idle chunks.
+  if (Kp4 <= 4) err = launch_items<1, 4>(p, ci, va, X, Y, Kp, s);
+  else if (Kp4 <= 8) err = launch_items<2, 4>(p, ci, va, X, Y, Kp, s);
+  else if (Kp4 <= 16) err = launch_items<4, 4>(p, ci, va, X, Y, Kp, s);
+  else if (Kp4 <= 20) err = launch_items<4, 5>(p, ci, va, X, Y, Kp, s);
+  else if (Kp4 <= 24) err = launch_items<4, 6>(p, ci, va, X, Y, Kp, s);
+  else if (Kp4 <= 32) err = launch_items<8, 4>(p, ci, va, X, Y, Kp, s);
+  else if (Kp4 <= 40) err = launch_items<8, 5>(p, ci, va, X, Y, Kp, s);
+  else if (Kp4 <= 48) err = launch_items<8, 6>(p, ci, va, X, Y, Kp, s);
+  else if (Kp4 <= 64) err = launch_items<8, 8>(p, ci, va, X, Y, Kp, s);
+  else if (Kp4 <= 80) err = launch_items<16, 5>(p, ci, va, X, Y, Kp, s);
+  else if (Kp4 <= 96) err = launch_items<16, 6>(p, ci, va, X, Y, Kp, s);
+  else err = launch_items<16, 8>(p, ci, va, X, Y, Kp, s);   // Kp <= 512
   if (err != cudaSuccess) return err;
   if (p.n_long > 0) {
     spmm_combine_kernel<<<p.n_long, 128, 0, s>>>(p.d_combine, p.n_long,

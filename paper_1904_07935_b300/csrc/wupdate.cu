@@ -1,0 +1,578 @@
+// The whole W update (Alg. 1 lines 12-16 in the tiled order of Alg. 2) as
+// one persistent, cooperative launch.
+//
+// W is updated in tiles of 16 columns.  Column t of tile [lo, hi) is
+//   w_t = max(eps, P_t - sum_{j < t} Q[j][t] w_j(new) - sum_{j > t} Q[j][t] w_j(old)),
+// then divided by its L2 norm before any later column uses it.  (Alg. 2's
+// W_old * Q_tt initialisation cancels the j = t term of Eq. 5 exactly and is
+// left out.)
+//
+// Roles inside the launch (grid = NC clusters of CL = 16 CTAs, all resident
+// at once, which the cooperative launch guarantees):
+//  * cluster 0 ("chain") owns every row of W: each of its row threads keeps
+//    RPT rows of the current tile in registers and finishes the tile's
+//    columns one after another; the norm of each column is reduced across
+//    the cluster through distributed shared memory (as in chain.cu: warp 0 of
+//    every CTA exchanges the CTA partials with st.async + mbarrier
+//    transaction counts, and adds the 16 partials in a fixed order).
+//  * the other clusters ("workers") compute the base of each tile,
+//      Y[v, c] = P[v, c] - sum_{j < lo - 16} Q[j][c] W[v, j](new)
+//                        - sum_{j >= hi} Q[j][c] W[v, j](old)
+//                        - sum_{c < j < hi} Q[j][c] W[v, j](old),
+//    i.e. everything except the previous tile, which is not final yet: the
+//    base of tile tau only needs tiles <= tau - 2, so the workers compute it
+//    while the chain is still on tile tau - 1.  The chain adds the previous
+//    tile's contribution itself (its own rows, 16 x 16 per row), right after
+//    finishing that tile.
+// Hand-off through global memory: base_ready[tau] counts the workers that
+// wrote their rows of Y for tile tau; chain_done[tau] is set once all chain
+// CTAs stored tile tau of W.  Release/acquire ordering, and every wait is
+// bounded by the global timer (ST_TIMEOUT on expiry).
+#include <algorithm>
+
+#include "devutil.cuh"
+#include "internal.cuh"
+
+namespace plnmf {
+namespace {
+
+constexpr int WT = kRowTile;        // tile width (16)
+constexpr int WNT = 512;            // threads per CTA
+constexpr int WNR = WNT - 32;       // row threads of a chain CTA
+constexpr int WMAXCL = 16;
+
+struct WParams {
+  float* X;            // N x Kp, old on entry, new on exit
+  const float* P;      // N x Kp
+  const float* Q;      // Kp x Kp
+  float* Y;            // N x Kp scratch: tile bases
+  int N, K, Kp;
+  float eps;
+  int* status;
+  int* sync;           // [0, nt): base_ready, [nt, 2 nt): chain_done
+  int cl;              // CTAs per cluster (chain cluster size)
+  int worker_rows;     // rows per worker pass (4 lanes per row)
+};
+
+__device__ __forceinline__ unsigned cluster_id_x() {
+  unsigned r;
+  asm volatile("mov.u32 %0, %%clusterid.x;" : "=r"(r));
+  return r;
+}
+
+// Bounded spin on a global counter; returns false on timeout.
+__device__ bool wait_counter(const int* p, int target, int* status) {
+  unsigned long long t0 = 0;
+  unsigned polls = 0;
+  while (ld_acquire_gpu(p) < target) {
+    if ((++polls & 15u) == 0) {
+      const unsigned long long now = global_ns();
+      if (t0 == 0) t0 = now;
+      else if (now - t0 > kWaitLimitNs) {
+        atomicOr(status, ST_TIMEOUT);
+        return false;
+      }
+    }
+  }
+  return true;
+}
+
+// --------------------------------------------------------------------------
+// Worker role: tile bases.
+// --------------------------------------------------------------------------
+__device__ void worker_role(const WParams& p, char* smem, int wid, int n_workers) {
+  const int nt = (p.K + WT - 1) / WT;
+  const int Kr = (p.Kp + WT - 1) / WT * WT;
+  const int ldx = p.Kp + 4;
+  float* Gc = reinterpret_cast<float*>(smem);                 // Kr x WT
+  float* Xs = Gc + Kr * WT;                                   // worker_rows x ldx
+  __shared__ __align__(8) unsigned long long bar;
+  __shared__ int go;
+  const int tid = threadIdx.x;
+  const int sub = tid & 3;
+  const int rl = tid >> 2;
+  const int RB = p.worker_rows;
+  const int nrb = (p.N + RB - 1) / RB;
+  if (tid == 0) {
+    mbar_init(smem_u32(&bar), 1);
+    fence_mbar_init();
+  }
+  __syncthreads();
+  unsigned phase = 0;
+  bool dead = false;
+  for (int tau = 0; tau < nt; ++tau) {
+    const int lo = tau * WT, hi = min(p.K, lo + WT);
+    const int new_end = tau >= 1 ? lo - WT : 0;
+    if (tid == 0) {
+      go = 1;
+      if (tau >= 2 && !dead) {
+        if (!wait_counter(p.sync + nt + tau - 2, 1, p.status)) dead = true;
+      }
+      fence_proxy_async_global();
+    }
+    __syncthreads();
+    // G block of this tile: Gc[j * WT + c] = Q[j][lo + c].
+    for (int base = tid; base < Kr * WT; base += 8 * WNT) {
+      float v[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int e = base + u * WNT;
+        const int j = e / WT, c = e % WT;
+        v[u] = (e < Kr * WT && j < p.K && lo + c < p.K) ? __ldg(p.Q + (int64_t)j * p.Kp + lo + c) : 0.f;
+      }
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int e = base + u * WNT;
+        if (e < Kr * WT) Gc[e] = v[u];
+      }
+    }
+    for (int rb = wid; rb < nrb; rb += n_workers) {
+      const int row0 = rb * RB;
+      const int nrows = min(RB, p.N - row0);
+      __syncthreads();                                        // Gc staged; Xs free
+      if (tid == 0) {
+        mbar_arrive_expect_tx(smem_u32(&bar), (unsigned)nrows * p.Kp * 4u);
+      }
+      __syncthreads();
+      if (tid < nrows) {
+        fence_proxy_async_global();
+        bulk_g2s(smem_u32(Xs + tid * ldx), p.X + (int64_t)(row0 + tid) * p.Kp, (unsigned)p.Kp * 4u,
+                 smem_u32(&bar));
+      }
+      {
+        unsigned long long t0 = 0;
+        unsigned polls = 0;
+        while (!dead && !mbar_try_wait_cta(smem_u32(&bar), phase)) {
+          if ((++polls & 63u) == 0) {
+            const unsigned long long now = global_ns();
+            if (t0 == 0) t0 = now;
+            else if (now - t0 > kWaitLimitNs) {
+              atomicOr(p.status, ST_TIMEOUT);
+              dead = true;
+            }
+          }
+        }
+        phase ^= 1u;
+      }
+      if (rl < nrows) {
+        const int row = row0 + rl;
+        const float* xr = Xs + rl * ldx;
+        float acc[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const int c = lo + 4 * sub + q;
+          acc[q] = c < hi ? __ldg(p.P + (int64_t)row * p.Kp + c) : 0.f;
+        }
+        auto outside = [&](int j0, int j1) {
+#pragma unroll 2
+          for (int j = j0; j < j1; j += 4) {
+            const float4 x4 = *reinterpret_cast<const float4*>(xr + j);
+            const float xs[4] = {x4.x, x4.y, x4.z, x4.w};
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+              const float4 g = *reinterpret_cast<const float4*>(Gc + (j + u) * WT + 4 * sub);
+              acc[0] = fmaf(-g.x, xs[u], acc[0]);
+              acc[1] = fmaf(-g.y, xs[u], acc[1]);
+              acc[2] = fmaf(-g.z, xs[u], acc[2]);
+              acc[3] = fmaf(-g.w, xs[u], acc[3]);
+            }
+          }
+        };
+        outside(0, new_end);
+        outside(lo + WT < p.Kp ? lo + WT : p.Kp, p.Kp);
+        float xo[WT];
+#pragma unroll
+        for (int q = 0; q < WT / 4; ++q) {
+          float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+          if (lo + 4 * q < p.Kp) v = *reinterpret_cast<const float4*>(xr + lo + 4 * q);
+          xo[4 * q] = v.x; xo[4 * q + 1] = v.y; xo[4 * q + 2] = v.z; xo[4 * q + 3] = v.w;
+        }
+#pragma unroll
+        for (int j = 1; j < WT; ++j) {
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            const int cl = 4 * sub + q;
+            if (j > cl) acc[q] = fmaf(-Gc[(lo + j) * WT + cl], xo[j], acc[q]);
+          }
+        }
+        float* yr = p.Y + (int64_t)row * p.Kp;
+        if (lo + 4 * sub + 3 < hi) {
+          *reinterpret_cast<float4*>(yr + lo + 4 * sub) = make_float4(acc[0], acc[1], acc[2], acc[3]);
+        } else {
+#pragma unroll
+          for (int q = 0; q < 4; ++q)
+            if (lo + 4 * sub + q < hi) yr[lo + 4 * sub + q] = acc[q];
+        }
+      }
+    }
+    __syncthreads();
+    if (tid == 0) {
+      __threadfence();
+      atomicAdd(p.sync + tau, 1);
+    }
+  }
+  if (__syncthreads_or(dead ? 1 : 0)) drain_grace();   // bulk copies still in flight
+  (void)go;
+}
+
+// --------------------------------------------------------------------------
+// Chain role: the column chain over all tiles.
+// --------------------------------------------------------------------------
+template <int RPT>
+__device__ void chain_role(const WParams& p, char* smem, int n_workers) {
+  constexpr int NW = WNT / 32;
+  constexpr int NS = WT + 1;
+  float* st = reinterpret_cast<float*>(smem);                 // RPT x WT x (WNR + 1)
+  __shared__ float Gs[WT][2 * WT];
+  __shared__ __align__(16) float Gn[WT][WT];                  // Q[tile][next tile]
+  __shared__ float wpart[NW];
+  __shared__ float cpart[2][WMAXCL];
+  __shared__ float col_inv;
+  __shared__ __align__(8) unsigned long long mbar[2];
+
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int tr = tid - 32;
+  const unsigned rank = cluster_ctarank();
+  const int CL = p.cl;
+  const int cta_base = (int)rank * WNR;
+  const int stride = CL * WNR;
+  const int nt = (p.K + WT - 1) / WT;
+  auto sidx = [](int i, int t, int r) { return (i * WT + t) * (WNR + 1) + r; };
+
+  if (tid == 0) {
+    mbar_init(smem_u32(&mbar[0]), 1);
+    mbar_init(smem_u32(&mbar[1]), 1);
+    mbar_arrive_expect_tx(smem_u32(&mbar[0]), CL * 4);
+    if (p.K > 1) mbar_arrive_expect_tx(smem_u32(&mbar[1]), CL * 4);
+    fence_mbar_init();
+  }
+  __syncthreads();
+  cluster_sync_all();
+
+  bool valid[RPT];
+#pragma unroll
+  for (int i = 0; i < RPT; ++i) valid[i] = warp > 0 && cta_base + i * stride + tr < p.N;
+  // y[i][1..16]: the tile's columns; between tiles y holds the previous
+  // tile's contribution to the next one (z), subtracted from the base.
+  float y[RPT][NS];
+#pragma unroll
+  for (int i = 0; i < RPT; ++i)
+#pragma unroll
+    for (int s = 0; s < NS; ++s) y[i][s] = 0.f;
+
+  bool dead = false;
+  int gcol = 0;                                                // global column index
+  for (int tau = 0; tau < nt; ++tau) {
+    const int lo = tau * WT, hi = min(p.K, lo + WT), Tw = hi - lo;
+    for (int e = tid; e < WT * 2 * WT; e += WNT) {
+      const int i = e / (2 * WT), j = e % (2 * WT);
+      Gs[i][j] = (i < Tw && j < Tw) ? p.Q[(int64_t)(lo + i) * p.Kp + lo + j] : 0.f;
+    }
+    if (tid == 0 && !dead) {
+      if (!wait_counter(p.sync + tau, n_workers, p.status)) dead = true;
+    }
+    __syncthreads();
+    // Base of the tile for this CTA's rows (4 lanes per row, 16 bytes each).
+    const int total = RPT * WNR * 4;
+    for (int base = tid; base < total; base += 4 * WNT) {
+      float v[4][4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int e = base + u * WNT;
+        const int i = e / (WNR * 4), rem = e % (WNR * 4);
+        const int r = rem >> 2, q = rem & 3;
+        const int row = cta_base + i * stride + r;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) v[u][j] = 0.f;
+        if (e < total && row < p.N) {
+          const float* src = p.Y + (int64_t)row * p.Kp + lo + 4 * q;
+          if (4 * q + 3 < Tw) {
+            const float4 f = *reinterpret_cast<const float4*>(src);
+            v[u][0] = f.x; v[u][1] = f.y; v[u][2] = f.z; v[u][3] = f.w;
+          } else {
+#pragma unroll
+            for (int j = 0; j < 4; ++j) v[u][j] = 4 * q + j < Tw ? src[j] : 0.f;
+          }
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int e = base + u * WNT;
+        if (e >= total) continue;
+        const int i = e / (WNR * 4), rem = e % (WNR * 4);
+        const int r = rem >> 2, q = rem & 3;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) st[sidx(i, 4 * q + j, r)] = v[u][j];
+      }
+    }
+    __syncthreads();
+    if (warp > 0) {
+#pragma unroll
+      for (int i = 0; i < RPT; ++i) {
+        y[i][0] = 0.f;
+#pragma unroll
+        for (int t = 0; t < WT; ++t) y[i][1 + t] = st[sidx(i, t, tr)] - y[i][1 + t];
+      }
+    }
+
+    float xp[RPT];
+#pragma unroll
+    for (int i = 0; i < RPT; ++i) xp[i] = 0.f;
+#pragma unroll 1
+    for (int t = 0; t < Tw; ++t, ++gcol) {
+      float x[RPT];
+      const int b = gcol & 1;
+      if (warp > 0) {
+        float ss = 0.f;
+#pragma unroll
+        for (int i = 0; i < RPT; ++i) {
+          x[i] = fmaxf(p.eps, y[i][1]);
+          if (valid[i]) ss = fmaf(x[i], x[i], ss);
+        }
+        ss = warp_sum(ss);
+        if (lane == 0) wpart[warp] = ss;
+      }
+      __syncthreads();
+      if (warp > 0) {
+        if (t > 0) {
+#pragma unroll
+          for (int s = 2; s < NS; ++s) {
+            const float g = Gs[t - 1][t + s - 1];             // slot s holds column t + s - 1
+#pragma unroll
+            for (int i = 0; i < RPT; ++i) y[i][s - 1] = fmaf(-xp[i], g, y[i][s]);
+          }
+        } else {
+#pragma unroll
+          for (int s = 2; s < NS; ++s)
+#pragma unroll
+            for (int i = 0; i < RPT; ++i) y[i][s - 1] = y[i][s];
+        }
+      } else {
+        float v = (lane >= 1 && lane < NW) ? wpart[lane] : 0.f;
+        v = warp_sum(v);
+        if (lane < CL && !dead) {
+          const unsigned raddr = mapa_u32(smem_u32(&cpart[b][rank]), lane);
+          const unsigned rbar = mapa_u32(smem_u32(&mbar[b]), lane);
+          st_async_f32(raddr, v, rbar);
+        }
+        if (!dead) {
+          const unsigned bar = smem_u32(&mbar[b]);
+          const unsigned parity = (gcol >> 1) & 1;
+          unsigned long long t0 = 0;
+          unsigned polls = 0;
+          while (!mbar_try_wait(bar, parity)) {
+            if ((++polls & 31u) == 0) {
+              const unsigned long long now = global_ns();
+              if (t0 == 0) {
+                t0 = now;
+              } else if (now - t0 > kWaitLimitNs) {
+                dead = true;
+                if (lane == 0) atomicOr(p.status, ST_TIMEOUT);
+                break;
+              }
+            }
+          }
+        }
+        dead = __any_sync(0xffffffffu, dead);
+        float tot = lane < CL ? cpart[b][lane] : 0.f;
+#pragma unroll
+        for (int o = 8; o > 0; o >>= 1) tot += __shfl_down_sync(0xffffffffu, tot, o);
+        if (lane == 0) {
+          const float nrm = sqrtf(tot);
+          col_inv = 1.0f / nrm;
+          if (gcol + 2 < p.K && !dead) mbar_arrive_expect_tx(smem_u32(&mbar[b]), CL * 4);
+          if (!(nrm > 0.f) || !(nrm < INFINITY)) {
+            if (rank == 0) atomicOr(p.status, ST_NUMERIC);
+          }
+        }
+      }
+      __syncthreads();
+      if (warp > 0) {
+        const float inv = col_inv;
+#pragma unroll
+        for (int i = 0; i < RPT; ++i) {
+          x[i] *= inv;
+          st[sidx(i, t, tr)] = x[i];
+        }
+        const float g1 = Gs[t][t + 1];
+#pragma unroll
+        for (int i = 0; i < RPT; ++i) {
+          y[i][1] = fmaf(-x[i], g1, y[i][1]);
+          xp[i] = x[i];
+        }
+      }
+    }
+    // Contribution of this tile to the next one, z = x_tile * Q[tile][next]
+    // for this CTA's rows (kept in y until the next base is loaded).
+    const int nlo = hi, nhi = min(p.K, nlo + WT), Tn = nhi - nlo;
+    for (int e = tid; e < WT * WT; e += WNT) {
+      const int i = e / WT, j = e % WT;
+      Gn[i][j] = (i < Tw && j < Tn) ? p.Q[(int64_t)(lo + i) * p.Kp + nlo + j] : 0.f;
+    }
+    __syncthreads();
+    if (warp > 0) {
+#pragma unroll
+      for (int i = 0; i < RPT; ++i)
+#pragma unroll
+        for (int s = 0; s < NS; ++s) y[i][s] = 0.f;
+      if (Tn > 0) {
+#pragma unroll 1
+        for (int j = 0; j < Tw; ++j) {
+          float xv[RPT];
+#pragma unroll
+          for (int i = 0; i < RPT; ++i) xv[i] = st[sidx(i, j, tr)];
+#pragma unroll
+          for (int cq = 0; cq < WT / 4; ++cq) {
+            const float4 g = *reinterpret_cast<const float4*>(&Gn[j][4 * cq]);
+#pragma unroll
+            for (int i = 0; i < RPT; ++i) {
+              y[i][1 + 4 * cq] = fmaf(g.x, xv[i], y[i][1 + 4 * cq]);
+              y[i][2 + 4 * cq] = fmaf(g.y, xv[i], y[i][2 + 4 * cq]);
+              y[i][3 + 4 * cq] = fmaf(g.z, xv[i], y[i][3 + 4 * cq]);
+              y[i][4 + 4 * cq] = fmaf(g.w, xv[i], y[i][4 + 4 * cq]);
+            }
+          }
+        }
+      }
+    }
+    // Store the finished tile (4 lanes per row), then publish it.
+    for (int e = tid; e < total; e += WNT) {
+      const int i = e / (WNR * 4), rem = e % (WNR * 4);
+      const int r = rem >> 2, q = rem & 3;
+      const int row = cta_base + i * stride + r;
+      if (row >= p.N) continue;
+      float v[4];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) v[j] = st[sidx(i, 4 * q + j, r)];
+      float* dst = p.X + (int64_t)row * p.Kp + lo + 4 * q;
+      if (4 * q + 3 < Tw) {
+        *reinterpret_cast<float4*>(dst) = make_float4(v[0], v[1], v[2], v[3]);
+      } else {
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+          if (4 * q + j < Tw) dst[j] = v[j];
+      }
+    }
+    __threadfence();
+    cluster_sync_all();
+    if (rank == 0 && tid == 0) st_release_gpu(p.sync + nt + tau, 1);
+  }
+  // A timed-out wait anywhere: let remote stores still in flight land before
+  // any CTA of the cluster leaves.
+  if (__syncthreads_or(dead ? 1 : 0)) drain_grace();
+  cluster_sync_all();
+}
+
+template <int RPT>
+__global__ void __launch_bounds__(WNT, 1) w_update_persistent_kernel(WParams p) {
+  extern __shared__ __align__(16) char smem[];
+  const unsigned cid = cluster_id_x();
+  const int n_workers = (int)gridDim.x - p.cl;
+  if (cid == 0) chain_role<RPT>(p, smem, n_workers);
+  else worker_role(p, smem, (int)blockIdx.x - p.cl, n_workers);
+}
+
+size_t persistent_smem(int rpt, int Kp, int worker_rows) {
+  const size_t chain = sizeof(float) * (size_t)rpt * WT * (WNR + 1);
+  const size_t worker = sizeof(float) * ((size_t)(Kp + WT - 1) / WT * WT * WT + (size_t)worker_rows * (Kp + 4));
+  return std::max(chain, worker);
+}
+
+template <int RPT>
+cudaError_t launch_persistent_t(const WParams& p, int n_clusters, size_t smem, cudaStream_t s) {
+  auto kern = w_update_persistent_kernel<RPT>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  if ((e = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1)) != cudaSuccess) return e;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(n_clusters * p.cl, 1, 1);
+  cfg.blockDim = dim3(WNT, 1, 1);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[2];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = p.cl;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  attr[1].id = cudaLaunchAttributeCooperative;
+  attr[1].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 2;
+  return cudaLaunchKernelEx(&cfg, kern, p);
+}
+
+template <int RPT>
+int max_clusters_t(int cl, size_t smem) {
+  auto kern = w_update_persistent_kernel<RPT>;
+  if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess ||
+      cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(cl, 1, 1);
+  cfg.blockDim = dim3(WNT, 1, 1);
+  cfg.dynamicSmemBytes = smem;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = cl;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  int n = 0;
+  if (cudaOccupancyMaxActiveClusters(&n, kern, &cfg) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  return n;
+}
+
+int max_clusters(int rpt, int cl, size_t smem) {
+  switch (rpt) {
+    case 1: return max_clusters_t<1>(cl, smem);
+    case 2: return max_clusters_t<2>(cl, smem);
+    case 3: return max_clusters_t<3>(cl, smem);
+    case 4: return max_clusters_t<4>(cl, smem);
+    default: return 0;
+  }
+}
+
+}  // namespace
+
+bool w_persistent_config(int N, int Kp, WPersistConfig* cfg) {
+  for (int cl : {16, 8}) {
+    const int rpt = (N + cl * WNR - 1) / (cl * WNR);
+    if (rpt > 4) continue;
+    int worker_rows = WNT / 4;
+    while (worker_rows > 16 && persistent_smem(rpt, Kp, worker_rows) > 200 * 1024) worker_rows /= 2;
+    const size_t smem = persistent_smem(rpt, Kp, worker_rows);
+    if (smem > 200 * 1024) continue;
+    const int nc = max_clusters(rpt, cl, smem);
+    if (nc < 2) continue;
+    cfg->cluster = cl;
+    cfg->rpt = rpt;
+    cfg->n_clusters = std::min(nc, 9);
+    cfg->worker_rows = worker_rows;
+    cfg->smem = smem;
+    return true;
+  }
+  return false;
+}
+
+cudaError_t w_persistent_run(float* X, const float* P, const float* Q, float* Y, int N, int K, int Kp, float eps,
+                             int* d_sync, int* d_status, const WPersistConfig& cfg, cudaStream_t s) {
+  const int nt = (K + WT - 1) / WT;
+  cudaError_t e = cudaMemsetAsync(d_sync, 0, sizeof(int) * 2 * nt, s);
+  if (e != cudaSuccess) return e;
+  WParams p{X, P, Q, Y, N, K, Kp, eps, d_status, d_sync, cfg.cluster, cfg.worker_rows};
+  switch (cfg.rpt) {
+    case 1: return launch_persistent_t<1>(p, cfg.n_clusters, cfg.smem, s);
+    case 2: return launch_persistent_t<2>(p, cfg.n_clusters, cfg.smem, s);
+    case 3: return launch_persistent_t<3>(p, cfg.n_clusters, cfg.smem, s);
+    case 4: return launch_persistent_t<4>(p, cfg.n_clusters, cfg.smem, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+}  // namespace plnmf

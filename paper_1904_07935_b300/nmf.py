@@ -39,8 +39,12 @@ class Problem(ctypes.Structure):
         ("nnz", ctypes.c_int64),
         ("W0", ctypes.c_void_p), ("H0", ctypes.c_void_p),
         ("seed", ctypes.c_uint64), ("eps", ctypes.c_float), ("tile_T", ctypes.c_int32),
-        ("prec", ctypes.c_int32), ("stream", ctypes.c_void_p),
+        ("prec", ctypes.c_int32), ("stream", ctypes.c_void_p), ("flags", ctypes.c_int32),
     ]
+
+
+FLAG_TC_GRAMS = 1
+FLAG_MULTI_LAUNCH_W = 2
 
 
 _vp, _i32, _i64, _dp = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.POINTER(ctypes.c_double)
@@ -57,6 +61,7 @@ _SIGS = {
     "nmf_query": ([_vp, ctypes.POINTER(_i32), ctypes.POINTER(_i32), ctypes.POINTER(_i32)], _i32),
     "nmf_profile": ([_vp, _i32, _vp], _i32),
     "nmf_destroy": ([_vp], None),
+    "nmf_gemm": ([_i32, _i32, _i32, _vp, _i64, _i32, _vp, _i64, _vp, _i64, _i32, _vp], _i32),
     "nmf_status_str": ([_i32], ctypes.c_char_p),
 }
 for _name, (_args, _res) in _SIGS.items():
@@ -103,7 +108,7 @@ class Nmf:
     """One factorisation context (nmf_ctx)."""
 
     def __init__(self, V, D, K, *, dense=None, ld=None, row_ptr=None, col_idx=None, val=None,
-                 W0=None, H0=None, seed=0, eps=0.0, tile_T=0, prec=PREC_FP32, stream=None):
+                 W0=None, H0=None, seed=0, eps=0.0, tile_T=0, prec=PREC_FP32, stream=None, flags=0):
         p = Problem()
         p.V, p.D, p.K = V, D, K
         self._keep = [dense, row_ptr, col_idx, val, W0, H0]
@@ -118,6 +123,7 @@ class Nmf:
         p.W0, p.H0 = ptr(W0), ptr(H0)
         p.seed, p.eps, p.tile_T, p.prec = seed, eps, tile_T, prec
         p.stream = _stream_ptr(stream)
+        p.flags = flags
         h = ctypes.c_void_p()
         check(lib.nmf_init(ctypes.byref(p), ctypes.byref(h)), "nmf_init")
         self.h = h
@@ -199,6 +205,14 @@ class Nmf:
         t, c, l = _i32(), _i32(), _i32()
         check(lib.nmf_query(self.h, ctypes.byref(t), ctypes.byref(c), ctypes.byref(l)), "nmf_query")
         return {"tile_T": t.value, "chain_ctas": c.value, "launches_per_iter": l.value}
+
+
+def gemm(A, B, C, *, transA=False, prec=PREC_FP32, stream=None):
+    """C = op(A) @ B on the tensor cores (device tensors, row-major)."""
+    M, N = C.shape
+    K = A.shape[0] if transA else A.shape[1]
+    check(lib.nmf_gemm(M, N, K, ptr(A), A.shape[1], 1 if transA else 0, ptr(B), B.shape[1], ptr(C), C.shape[1],
+                       prec, _stream_ptr(stream)), "nmf_gemm")
 
 
 def from_sparse(prob, K, device="cuda", **kw):

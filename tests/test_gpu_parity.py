@@ -289,3 +289,28 @@ def test_invalid_inputs_rejected(nmf):
     with pytest.raises(nmf.NmfError):
         nmf.Nmf(200, 100, 4, row_ptr=torch.from_numpy(rp).cuda(),
                 col_idx=torch.from_numpy(sp.A.col_idx).cuda(), val=torch.from_numpy(sp.A.val).cuda())
+
+
+@pytest.mark.parametrize("K", [16, 37, 160])
+def test_w_update_persistent_and_multi_launch_agree_with_alg1(nmf, K):
+    """The persistent (one cooperative launch) and the per-tile multi-launch W
+    updates both match Alg. 1 on a ragged K."""
+    V = 3000 if K < 100 else 9000
+    prob = synth.planted_dense(V, 400, 8, 101 + K)
+    W0, H0 = synth.init_factors(102 + K, V, 400, K)
+    W, H = _oracle_start(W0, H0)
+    A = prob.A.astype(np.float64)
+    P, Q = f32(A @ H.T), f32(H @ H.T)
+    Win = f32(W)
+    ref = fh.update_w(P.astype(np.float64), Q.astype(np.float64), Win, EPS)
+    outs = []
+    for flags in (0, nmf.FLAG_MULTI_LAUNCH_W):
+        ctx = _dense_ctx(nmf, prob.A, K, W0, H0, flags=flags)
+        ctx.set_buffer(nmf.BUF_P, P)
+        ctx.set_buffer(nmf.BUF_Q, Q)
+        ctx.set_buffer(nmf.BUF_W, Win)
+        ctx.run_step(nmf.STEP_UPDATE_W)
+        got = ctx.get_buffer(nmf.BUF_W)
+        assert rel_w(got, ref) < TOL_ITER, flags
+        outs.append(got)
+    assert rel_w(outs[0], outs[1]) < TOL_ITER
