@@ -179,6 +179,28 @@ nmf_status nmf_query(nmf_ctx* c, int32_t* tile_T, int32_t* chain_ctas, int32_t* 
 nmf_status nmf_gemm(int32_t M, int32_t N, int32_t K, const float* A, int64_t lda, int32_t transA,
                     const float* B, int64_t ldb, float* C, int64_t ldc, int32_t prec, void* stream);
 
+/* Gram matrix without device allocation (this entry point has no
+ * counterpart in the paper; it serves callers that cannot call cudaMalloc,
+ * for example a process whose device memory is entirely reserved up front
+ * by its own pool allocator, or code running where an allocation's implicit
+ * synchronisation is not allowed).
+ *   S (K x K, row-major, device) = X^T X for X (N x K, device, row stride
+ *   ldx >= K), FP32 on the SIMT pipes with fixed-order FP64 combination of
+ *   the partial sums, asynchronous on `stream`.
+ * The partial sums use one file-scope device array of
+ * NMF_NOALLOC_SCRATCH_FLOATS floats (16 MiB) that every GPU loading the
+ * library holds until the process exits.  The first call on a device looks
+ * the array's address up (cudaGetSymbolAddress) with that device current;
+ * make that first call before any stream capture.  No cudaMalloc/cudaFree or
+ * allocating library routine is called.  Every call shares the array, so
+ * calls that overlap on the GPU (different streams, or devices sharing the
+ * address space) race and must be serialised by the caller; the partials are
+ * fully rewritten by each call.
+ * Errors: NMF_EINVAL for null pointers or bad sizes; NMF_EUNSUPPORTED when
+ * K * K exceeds the array (K > 2048); NMF_ECUDA for a failed lookup or launch. */
+#define NMF_NOALLOC_SCRATCH_FLOATS (4 * 1024 * 1024)
+nmf_status nmf_gram_noalloc(const float* X, int32_t N, int32_t K, int64_t ldx, float* S, void* stream);
+
 /* Frees every device buffer and the graph of the context.  NULL is a no-op. */
 void nmf_destroy(nmf_ctx* c);
 

@@ -217,6 +217,31 @@ cudaError_t gram_run_tc(const GramWork& g, const float* X, float* S, int K, int*
   return cudaGetLastError();
 }
 
+cudaError_t gram_run_scratch(const float* X, int N, int K, int64_t ldx, float* part, int n_chunks, int chunk,
+                             float* S, cudaStream_t s) {
+  GemmArgs a;
+  a.M = K;
+  a.N = K;
+  a.Kin = N;
+  a.A = X;
+  a.lda = ldx;
+  a.transA = 1;
+  a.B = X;
+  a.ldb = ldx;
+  a.C = part;
+  a.ldc = K;
+  a.mode = GM_PARTIAL;
+  a.k_chunk = chunk;
+  a.part_stride = (int64_t)K * K;
+  a.n_chunks = n_chunks;
+  a.upper_only = 1;
+  cudaError_t err = gemm_run(a, s);
+  if (err != cudaSuccess) return err;
+  dim3 grid((K + 127) / 128, K);
+  gram_reduce_kernel<<<grid, 128, 0, s>>>(part, n_chunks, K, K, S);
+  return cudaGetLastError();
+}
+
 void gram_free(GramWork& g) {
   cudaFree(g.d_part);
   g.d_part = nullptr;

@@ -90,6 +90,10 @@ struct GramWork {
 cudaError_t gram_setup(GramWork& g, int N, int Kp);
 void gram_free(GramWork& g);
 cudaError_t gram_run(const GramWork& g, const float* X, float* S, int K, cudaStream_t s);
+// S (K x K) = X^T X for X (N x K, row stride ldx) with caller-provided
+// partial storage: n_chunks * K * K floats, chunk rows per partial.
+cudaError_t gram_run_scratch(const float* X, int N, int K, int64_t ldx, float* part, int n_chunks, int chunk,
+                             float* S, cudaStream_t s);
 // Same result through the tensor cores (3xTF32, split-N partials).
 cudaError_t gram_setup_tc(GramWork& g, int N, int Kp);
 cudaError_t gram_run_tc(const GramWork& g, const float* X, float* S, int K, int* d_status, cudaStream_t s);

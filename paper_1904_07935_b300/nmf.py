@@ -61,6 +61,7 @@ _SIGS = {
     "nmf_query": ([_vp, ctypes.POINTER(_i32), ctypes.POINTER(_i32), ctypes.POINTER(_i32)], _i32),
     "nmf_profile": ([_vp, _i32, _vp], _i32),
     "nmf_destroy": ([_vp], None),
+    "nmf_gram_noalloc": ([_vp, _i32, _i32, _i64, _vp, _vp], _i32),
     "nmf_gemm": ([_i32, _i32, _i32, _vp, _i64, _i32, _vp, _i64, _vp, _i64, _i32, _vp], _i32),
     "nmf_status_str": ([_i32], ctypes.c_char_p),
 }
@@ -213,6 +214,12 @@ def gemm(A, B, C, *, transA=False, prec=PREC_FP32, stream=None):
     K = A.shape[0] if transA else A.shape[1]
     check(lib.nmf_gemm(M, N, K, ptr(A), A.shape[1], 1 if transA else 0, ptr(B), B.shape[1], ptr(C), C.shape[1],
                        prec, _stream_ptr(stream)), "nmf_gemm")
+
+
+def gram_noalloc(X, S, *, stream=None):
+    """S = X^T X through nmf_gram_noalloc (device tensors, row-major)."""
+    N, K = X.shape
+    check(lib.nmf_gram_noalloc(ptr(X), N, K, X.stride(0), ptr(S), _stream_ptr(stream)), "nmf_gram_noalloc")
 
 
 def from_sparse(prob, K, device="cuda", **kw):
