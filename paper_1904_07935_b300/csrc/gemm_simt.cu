@@ -140,6 +140,122 @@ __global__ void __launch_bounds__(256) gemm_kernel(GemmArgs g) {
   }
 }
 
+// Split-N Gram for Kp <= 176: CTA z computes the whole Kp8 x Kp8 Gram of its
+// row chunk (Kp8 = Kp rounded up to 8), one 8 x 8 register micro-tile per
+// thread ((Kp8 / 8)^2 threads), rows of X staged GB at a time in shared
+// memory and read as 16-byte broadcasts (16 multiply-adds per load).
+constexpr int GB = 16;
+constexpr int kGramFullMaxKp = 176;               // (176 / 8)^2 = 484 threads
+constexpr int kGramFullMinKp = 64;                // >= 64 threads: <= 4 staged float4 each
+__global__ void __launch_bounds__(512) gram_full_kernel(const float* __restrict__ X, int N, int Kp, int Kp8,
+                                                        int chunk, float* __restrict__ part) {
+  extern __shared__ __align__(16) float xs[];      // 2 x GB x Kp8
+  const int nt = blockDim.x;
+  const int tpr = Kp8 / 8;                         // threads per output row of micro-tiles
+  const int tx = threadIdx.x % tpr, ty = threadIdx.x / tpr;
+  const int r0 = blockIdx.x * chunk, r1 = min(N, r0 + chunk);
+  float acc[8][8];
+#pragma unroll
+  for (int i = 0; i < 8; ++i)
+#pragma unroll
+    for (int j = 0; j < 8; ++j) acc[i][j] = 0.f;
+  const int kq = Kp8 / 4;                          // float4 per staged row
+  // Staging of a GB-row block: GB * Kp8 / 4 float4 over (Kp8 / 8)^2 threads,
+  // at most 256 / Kp8 <= 4 per thread for Kp8 >= 64; loaded into registers
+  // before the current block is multiplied, stored after it.
+  constexpr int MAXE = 4;
+  const int total = GB * kq;
+  auto load = [&](int rb, int e) {
+    float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (e < total) {
+      const int r = e / kq, q = e % kq;
+      const int row = rb + r;
+      if (row < r1 && 4 * q < Kp) v = __ldg(reinterpret_cast<const float4*>(X + (int64_t)row * Kp) + q);
+    }
+    return v;
+  };
+  auto store = [&](int buf, int e, float4 v) {
+    if (e < total) {
+      const int r = e / kq, q = e % kq;
+      *reinterpret_cast<float4*>(xs + buf * GB * Kp8 + r * Kp8 + 4 * q) = v;
+    }
+  };
+  int buf = 0;
+  {
+    float4 v[MAXE];
+#pragma unroll
+    for (int u = 0; u < MAXE; ++u) v[u] = load(r0, threadIdx.x + u * nt);
+#pragma unroll
+    for (int u = 0; u < MAXE; ++u) store(0, threadIdx.x + u * nt, v[u]);
+  }
+  __syncthreads();
+  for (int rb = r0; rb < r1; rb += GB) {
+    const bool more = rb + GB < r1;
+    float4 pre[MAXE];
+#pragma unroll
+    for (int u = 0; u < MAXE; ++u) pre[u] = more ? load(rb + GB, threadIdx.x + u * nt) : make_float4(0.f, 0.f, 0.f, 0.f);
+    const float* src = xs + buf * GB * Kp8;
+#pragma unroll 2
+    for (int r = 0; r < GB; ++r) {
+      const float4 a0 = *reinterpret_cast<const float4*>(src + r * Kp8 + 8 * ty);
+      const float4 a1 = *reinterpret_cast<const float4*>(src + r * Kp8 + 8 * ty + 4);
+      const float4 b0 = *reinterpret_cast<const float4*>(src + r * Kp8 + 8 * tx);
+      const float4 b1 = *reinterpret_cast<const float4*>(src + r * Kp8 + 8 * tx + 4);
+      const float av[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+      const float bv[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+#pragma unroll
+      for (int i = 0; i < 8; ++i)
+#pragma unroll
+        for (int j = 0; j < 8; ++j) acc[i][j] = fmaf(av[i], bv[j], acc[i][j]);
+    }
+    if (more) {
+#pragma unroll
+      for (int u = 0; u < MAXE; ++u) store(buf ^ 1, threadIdx.x + u * nt, pre[u]);
+    }
+    __syncthreads();
+    buf ^= 1;
+  }
+  float* out = part + (int64_t)blockIdx.x * Kp * Kp;
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    const int m = 8 * ty + i;
+    if (m >= Kp) continue;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      const int n = 8 * tx + j;
+      if (n < Kp) out[(int64_t)m * Kp + n] = acc[i][j];
+    }
+  }
+}
+
+// S = sum over chunks of the partial Grams, FP64, mirrored: 8 lanes per entry
+// (i <= j) each add every 8th chunk in order, then a fixed shuffle tree adds
+// the 8 sums, so the result does not depend on scheduling.
+__global__ void gram_reduce8_kernel(const float* __restrict__ part, int n_chunks, int Kp, int K,
+                                    float* __restrict__ S) {
+  const int lane = threadIdx.x & 7;
+  const int entry = (blockIdx.x * blockDim.x + threadIdx.x) >> 3;
+  const int i = entry / Kp, j = entry % Kp;
+  const bool in = entry < Kp * Kp;
+  double s = 0.0;
+  if (in && i < K && j < K && j >= i) {
+    const size_t stride = (size_t)Kp * Kp;
+    for (int z = lane; z < n_chunks; z += 8) s += (double)part[z * stride + (size_t)i * Kp + j];
+  }
+  s += __shfl_xor_sync(0xffffffffu, s, 4);
+  s += __shfl_xor_sync(0xffffffffu, s, 2);
+  s += __shfl_xor_sync(0xffffffffu, s, 1);
+  if (!in || lane != 0) return;
+  if (i >= K || j >= K) {
+    S[(int64_t)i * Kp + j] = 0.f;
+    return;
+  }
+  if (j < i) return;
+  const float f = (float)s;
+  S[(int64_t)i * Kp + j] = f;
+  S[(int64_t)j * Kp + i] = f;
+}
+
 // S[i][j] = sum_z part[z][i][j] (FP64, z ascending) for i <= j, mirrored.
 __global__ void gram_reduce_kernel(const float* __restrict__ part, int n_chunks, int Kp, int K,
                                    float* __restrict__ S) {
@@ -171,6 +287,14 @@ cudaError_t gemm_run(const GemmArgs& a, cudaStream_t s) {
 cudaError_t gram_setup(GramWork& g, int N, int Kp) {
   g.N = N;
   g.Kp = Kp;
+  if (Kp >= kGramFullMinKp && Kp <= kGramFullMaxKp) {
+    // gram_full_kernel: one CTA per SM.
+    int chunk = (N + 147) / 148;
+    chunk = std::max(GB, (chunk + GB - 1) / GB * GB);
+    g.chunk = chunk;
+    g.n_chunks = (N + chunk - 1) / chunk;
+    return cudaMalloc(&g.d_part, sizeof(float) * (size_t)g.n_chunks * Kp * Kp);
+  }
   // Enough chunks to cover about two waves of the 148 SMs.
   const int tiles = ((Kp + 63) / 64) * ((Kp + 63) / 64 + 1) / 2;
   int want = std::max(1, (296 + tiles - 1) / tiles);
@@ -248,6 +372,17 @@ void gram_free(GramWork& g) {
 }
 
 cudaError_t gram_run(const GramWork& g, const float* X, float* S, int K, cudaStream_t s) {
+  if (g.Kp >= kGramFullMinKp && g.Kp <= kGramFullMaxKp) {
+    const int Kp8 = (g.Kp + 7) / 8 * 8;
+    const int threads = (Kp8 / 8) * (Kp8 / 8);
+    const size_t smem = sizeof(float) * 2 * GB * Kp8;
+    gram_full_kernel<<<g.n_chunks, threads, smem, s>>>(X, g.N, g.Kp, Kp8, g.chunk, g.d_part);
+    cudaError_t err = cudaGetLastError();
+    if (err != cudaSuccess) return err;
+    const int entries = g.Kp * g.Kp;
+    gram_reduce8_kernel<<<(entries * 8 + 255) / 256, 256, 0, s>>>(g.d_part, g.n_chunks, g.Kp, K, S);
+    return cudaGetLastError();
+  }
   GemmArgs a;
   a.M = g.Kp;
   a.N = g.Kp;

@@ -97,13 +97,16 @@ constexpr int HL = 4;             // lanes per row
 constexpr int HROWS = 64;         // rows per CTA
 constexpr int HTHREADS = HROWS * HL;
 
-__global__ void __launch_bounds__(HTHREADS) h_update_kernel(float* __restrict__ X, const float* __restrict__ B,
-                                                            const float* __restrict__ G, int N, int K, int Kp,
-                                                            float eps, int* status) {
+// R rows per lane group: each group of 4 lanes owns R rows (4 tile columns per
+// lane), so a 16-byte load of S's column block serves R rows.
+template <int R>
+__global__ void __launch_bounds__(128) h_update_kernel(float* __restrict__ X, const float* __restrict__ B,
+                                                       const float* __restrict__ G, int N, int K, int Kp, float eps,
+                                                       int* status) {
   // Shared memory: Gc (Kr x HT) = G[j][lo + c] for the current tile, zero
-  // beyond K; Xs (HROWS x (Kp + 4)) = the CTA's rows of the factor, updated
-  // in place (row stride Kp + 4 keeps the 8 rows a warp touches on distinct
-  // banks).
+  // beyond K; Xs (32 R x (Kp + 4)) = the CTA's rows, updated in place (row
+  // stride Kp + 4 keeps the 8 rows a warp reads at once on distinct banks).
+  constexpr int NT = 128, ROWS = 32 * R;
   extern __shared__ __align__(16) float smem[];
   const int Kr = (Kp + HT - 1) / HT * HT;
   const int ldx = Kp + 4;
@@ -111,61 +114,63 @@ __global__ void __launch_bounds__(HTHREADS) h_update_kernel(float* __restrict__ 
   float* Xs = smem + Kr * HT;
   const int tid = threadIdx.x;
   const int sub = tid & (HL - 1);
-  const int rl = tid >> 2;
-  const int row0 = blockIdx.x * HROWS;
-  const int nrows = min(HROWS, N - row0);
-  const int row = row0 + rl;
-  const bool valid = rl < nrows;
+  const int grp = tid >> 2;                               // 0..31
+  const int row0 = blockIdx.x * ROWS;
+  const int nrows = min(ROWS, N - row0);
   const unsigned full = 0xffffffffu;
-  const float* br = B + (int64_t)(valid ? row : row0) * Kp;
-
   __shared__ __align__(8) unsigned long long bar;
   stage_rows_bulk(Xs, ldx, X, row0, nrows, Kp, &bar, status);
-  float* xr = Xs + rl * ldx;
+  // Row i of the group: local row grp + 32 i (so a warp's 8 groups touch 8
+  // consecutive rows for each i).
+  bool valid[R];
+  float* xr[R];
+  const float* br[R];
+#pragma unroll
+  for (int i = 0; i < R; ++i) {
+    const int rl = grp + 32 * i;
+    valid[i] = rl < nrows;
+    xr[i] = Xs + rl * ldx;
+    br[i] = B + (int64_t)(valid[i] ? row0 + rl : row0) * Kp;
+  }
 
   for (int lo = 0; lo < K; lo += HT) {
     const int hi = min(K, lo + HT);
     __syncthreads();
-    stage_gcols<HTHREADS>(Gc, G, Kp, K, lo, Kr);
+    stage_gcols<NT>(Gc, G, Kp, K, lo, Kr);
     __syncthreads();
-
-    // Old values of this row's tile (all 16, shared by the 4 lanes).
-    float xo[HT];
+    float acc[R][4];
 #pragma unroll
-    for (int q = 0; q < HT / 4; ++q) {
-      float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-      if (lo + 4 * q < Kp) v = *reinterpret_cast<const float4*>(xr + lo + 4 * q);
-      xo[4 * q] = v.x; xo[4 * q + 1] = v.y; xo[4 * q + 2] = v.z; xo[4 * q + 3] = v.w;
-    }
-    // Columns of this lane: lo + 4 * sub + q (its own old values read again
-    // so that no register array is indexed by the lane number).
-    float acc[4];
-    float4 own = make_float4(0.f, 0.f, 0.f, 0.f);
-    if (lo + 4 * sub < Kp) own = *reinterpret_cast<const float4*>(xr + lo + 4 * sub);
-    const float xown[4] = {own.x, own.y, own.z, own.w};
+    for (int i = 0; i < R; ++i) {
+      const float4 own = lo + 4 * sub < Kp ? *reinterpret_cast<const float4*>(xr[i] + lo + 4 * sub)
+                                           : make_float4(0.f, 0.f, 0.f, 0.f);
+      const float xown[4] = {own.x, own.y, own.z, own.w};
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const int cl = 4 * sub + q, c = lo + cl;
-      acc[q] = 0.f;
-      if (valid && c < hi) {
-        const float gcc = Gc[c * HT + cl];
-        acc[q] = fmaf(1.f - gcc, xown[q], br[c]);
+      for (int q = 0; q < 4; ++q) {
+        const int cl = 4 * sub + q, c = lo + cl;
+        acc[i][q] = 0.f;
+        if (valid[i] && c < hi) acc[i][q] = fmaf(1.f - Gc[c * HT + cl], xown[q], __ldg(br[i] + c));
       }
     }
-    // Columns outside the tile: j < lo (new) and j >= lo + HT (old); padding
-    // columns of X and rows of G are zero, so the loop runs to Kp.
+    // Columns outside the tile: j < lo (new) and j >= lo + HT (old).
     auto outside = [&](int j0, int j1) {
-#pragma unroll 2
+#pragma unroll 1
       for (int j = j0; j < j1; j += 4) {
-        const float4 x4 = *reinterpret_cast<const float4*>(xr + j);
-        const float xs[4] = {x4.x, x4.y, x4.z, x4.w};
+        float xs[R][4];
+#pragma unroll
+        for (int i = 0; i < R; ++i) {
+          const float4 x4 = *reinterpret_cast<const float4*>(xr[i] + j);
+          xs[i][0] = x4.x; xs[i][1] = x4.y; xs[i][2] = x4.z; xs[i][3] = x4.w;
+        }
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
           const float4 g = *reinterpret_cast<const float4*>(Gc + (j + u) * HT + 4 * sub);
-          acc[0] = fmaf(-g.x, xs[u], acc[0]);
-          acc[1] = fmaf(-g.y, xs[u], acc[1]);
-          acc[2] = fmaf(-g.z, xs[u], acc[2]);
-          acc[3] = fmaf(-g.w, xs[u], acc[3]);
+#pragma unroll
+          for (int i = 0; i < R; ++i) {
+            acc[i][0] = fmaf(-g.x, xs[i][u], acc[i][0]);
+            acc[i][1] = fmaf(-g.y, xs[i][u], acc[i][1]);
+            acc[i][2] = fmaf(-g.z, xs[i][u], acc[i][2]);
+            acc[i][3] = fmaf(-g.w, xs[i][u], acc[i][3]);
+          }
         }
       }
     };
@@ -173,39 +178,55 @@ __global__ void __launch_bounds__(HTHREADS) h_update_kernel(float* __restrict__ 
     outside(lo + HT < Kp ? lo + HT : Kp, Kp);
     // Old in-tile columns j > c.
 #pragma unroll
-    for (int j = 1; j < HT; ++j) {
+    for (int i = 0; i < R; ++i) {
+      float xo[HT];
 #pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        const int cl = 4 * sub + q;
-        if (j > cl) acc[q] = fmaf(-Gc[(lo + j) * HT + cl], xo[j], acc[q]);
+      for (int q = 0; q < HT / 4; ++q) {
+        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (lo + 4 * q < Kp) v = *reinterpret_cast<const float4*>(xr[i] + lo + 4 * q);
+        xo[4 * q] = v.x; xo[4 * q + 1] = v.y; xo[4 * q + 2] = v.z; xo[4 * q + 3] = v.w;
+      }
+#pragma unroll
+      for (int j = 1; j < HT; ++j) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const int cl = 4 * sub + q;
+          if (j > cl) acc[i][q] = fmaf(-Gc[(lo + j) * HT + cl], xo[j], acc[i][q]);
+        }
       }
     }
     // Finish the tile's columns in order; each new value is broadcast to the
-    // row's lanes and pushed into the later columns.
-    float xn[4];
+    // group's lanes and pushed into the later columns.
+    float xn[R][4];
 #pragma unroll
     for (int t = 0; t < HT; ++t) {
       const int owner = t >> 2, q = t & 3;
-      float v = 0.f;
-      if (sub == owner) {
-        v = fmaxf(eps, acc[q]);
-        xn[q] = v;
-      }
-      v = __shfl_sync(full, v, (threadIdx.x & 31 & ~(HL - 1)) + owner);
 #pragma unroll
-      for (int q2 = 0; q2 < 4; ++q2) {
-        const int c2 = 4 * sub + q2;
-        if (c2 > t) acc[q2] = fmaf(-Gc[(lo + t) * HT + c2], v, acc[q2]);
+      for (int i = 0; i < R; ++i) {
+        float v = 0.f;
+        if (sub == owner) {
+          v = fmaxf(eps, acc[i][q]);
+          xn[i][q] = v;
+        }
+        v = __shfl_sync(full, v, (threadIdx.x & 31 & ~(HL - 1)) + owner);
+#pragma unroll
+        for (int q2 = 0; q2 < 4; ++q2) {
+          const int c2 = 4 * sub + q2;
+          if (c2 > t) acc[i][q2] = fmaf(-Gc[(lo + t) * HT + c2], v, acc[i][q2]);
+        }
       }
     }
     __syncwarp();
-    if (lo + 4 * sub + 3 < hi) {
-      *reinterpret_cast<float4*>(xr + lo + 4 * sub) = make_float4(xn[0], xn[1], xn[2], xn[3]);
-    } else {
 #pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        const int c = lo + 4 * sub + q;
-        if (c < hi) xr[c] = xn[q];
+    for (int i = 0; i < R; ++i) {
+      if (lo + 4 * sub + 3 < hi) {
+        *reinterpret_cast<float4*>(xr[i] + lo + 4 * sub) = make_float4(xn[i][0], xn[i][1], xn[i][2], xn[i][3]);
+      } else {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const int c = lo + 4 * sub + q;
+          if (c < hi) xr[i][c] = xn[i][q];
+        }
       }
     }
   }
@@ -213,7 +234,7 @@ __global__ void __launch_bounds__(HTHREADS) h_update_kernel(float* __restrict__ 
   {
     const int kq = Kp / 4;
     float4* dst = reinterpret_cast<float4*>(X + (int64_t)row0 * Kp);
-    for (int e = tid; e < nrows * kq; e += HTHREADS) {
+    for (int e = tid; e < nrows * kq; e += NT) {
       const int r = e / kq, q = e % kq;
       dst[e] = *reinterpret_cast<const float4*>(Xs + r * ldx + 4 * q);
     }
@@ -311,14 +332,27 @@ cudaError_t w_prep_run(const float* X, const float* B, const float* G, float* Y,
   return cudaGetLastError();
 }
 
+template <int R>
+cudaError_t h_update_launch(float* X, const float* B, const float* G, int N, int K, int Kp, float eps, int* status,
+                            cudaStream_t s) {
+  const size_t smem = sizeof(float) * ((size_t)((Kp + HT - 1) / HT * HT) * HT + (size_t)32 * R * (Kp + 4));
+  auto kern = h_update_kernel<R>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  const int blocks = (N + 32 * R - 1) / (32 * R);
+  kern<<<blocks, 128, smem, s>>>(X, B, G, N, K, Kp, eps, status);
+  return cudaGetLastError();
+}
+
 cudaError_t h_update_run(float* X, const float* B, const float* G, int N, int K, int Kp, float eps,
                          int* status, cudaStream_t s) {
-  const size_t smem = sizeof(float) * ((size_t)((Kp + HT - 1) / HT * HT) * HT + (size_t)HROWS * (Kp + 4));
-  cudaError_t e = cudaFuncSetAttribute(h_update_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return e;
-  const int blocks = (N + HROWS - 1) / HROWS;
-  h_update_kernel<<<blocks, HTHREADS, smem, s>>>(X, B, G, N, K, Kp, eps, status);
-  return cudaGetLastError();
+  // Rows per lane group: as many as fit, while keeping at least ~one CTA per SM.
+  const size_t per_row = sizeof(float) * (size_t)(Kp + 4);
+  const size_t gc = sizeof(float) * (size_t)((Kp + HT - 1) / HT * HT) * HT;
+  auto fits = [&](int R) { return gc + per_row * 32 * R <= 200 * 1024; };
+  if (fits(4) && (N + 127) / 128 >= 64) return h_update_launch<4>(X, B, G, N, K, Kp, eps, status, s);
+  if (fits(2)) return h_update_launch<2>(X, B, G, N, K, Kp, eps, status, s);
+  return h_update_launch<1>(X, B, G, N, K, Kp, eps, status, s);
 }
 
 }  // namespace plnmf
