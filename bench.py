@@ -41,6 +41,19 @@ def _peaks():
         return 6400.0, "fallback"
 
 
+def _tensor_peak(bf16):
+    """BF16 dense burst peak (measured); the FP32 SIMT peak is 148 SMs x 128
+    lanes x 2 flop x the measured maximum SM clock."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        if bf16:
+            return float(p["bf16_tflops"]), "measured"
+        return 148 * 128 * 2 * float(p["sm_max_mhz"]) * 1e6 / 1e12, "derived (SM count x lanes x clock)"
+    except Exception:
+        return (1800.0, "fallback") if bf16 else (77.0, "fallback")
+
+
 def _dist_env():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -101,11 +114,38 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def make_workload(K: int):
+WORKLOADS = {
+    "text20ng": "text-20ng-like sparse NMF (26,214 x 11,314, ~1.13M nnz)",
+    "dense8192": "dense planted 8192 x 8192, rank 256",
+    "dense512": "dense planted 512 x 384, rank 16",
+}
+
+
+def make_workload(name: str, K: int):
     from paper_1904_07935_b300 import synth
-    prob = synth.text_20ng_like()
-    W0, H0 = synth.init_factors(0xC2, prob.A.n_rows, prob.A.n_cols, K)
+    if name == "text20ng":
+        prob = synth.text_20ng_like()
+        V, D = prob.A.n_rows, prob.A.n_cols
+        seed = 0xC2
+    elif name == "dense8192":
+        prob = synth.dense_large()
+        V, D = prob.A.shape
+        seed = 0xC3
+    else:
+        prob = synth.dense_small()
+        V, D = prob.A.shape
+        seed = 0xC1
+    W0, H0 = synth.init_factors(seed, V, D, K)
     return prob, W0, H0
+
+
+def dense_costs(V, D, K, bf16):
+    """Dense A: algorithmic bytes and flops per step (A read once per product)."""
+    a_bytes = V * D * (2 if bf16 else 4)
+    prod_flops = 2.0 * V * D * K
+    return {"R": a_bytes + 4 * V * K + 4 * D * K, "P": a_bytes + 4 * D * K + 4 * V * K,
+            "update_H": 12 * D * K, "update_W": 12 * V * K, "Q": 4 * D * K, "S": 4 * V * K,
+            "objective": 8 * V * K}, prod_flops
 
 
 def alg_bytes(V, D, nnz, K):
@@ -133,16 +173,26 @@ def run_gpu(args):
     dev = torch.device("cuda", local)
 
     K = args.k
-    prob, W0, H0 = make_workload(K)
-    V, D, nnz = prob.A.n_rows, prob.A.n_cols, prob.A.nnz
+    prob, W0, H0 = make_workload(args.workload, K)
+    dense = args.workload != "text20ng"
+    bf16 = args.prec == "bf16"
     stream = torch.cuda.Stream(device=dev)
-    rp = torch.from_numpy(prob.A.row_ptr).to(dev)
-    ci = torch.from_numpy(prob.A.col_idx).to(dev)
-    va = torch.from_numpy(prob.A.val).to(dev)
-    ctx = nmf.Nmf(V, D, K, row_ptr=rp, col_idx=ci, val=va,
-                  W0=torch.from_numpy(W0).to(dev), H0=torch.from_numpy(H0).to(dev),
-                  stream=stream, tile_T=args.tile,
-                  flags=nmf.FLAG_MULTI_LAUNCH_W if args.w_multi_launch else 0)
+    flags = nmf.FLAG_MULTI_LAUNCH_W if args.w_multi_launch else 0
+    prec = nmf.PREC_BF16 if bf16 else nmf.PREC_FP32
+    if dense:
+        V, D = prob.A.shape
+        nnz = V * D
+        Ad = torch.from_numpy(prob.A).to(dev)
+        ctx = nmf.Nmf(V, D, K, dense=Ad, W0=torch.from_numpy(W0).to(dev), H0=torch.from_numpy(H0).to(dev),
+                      stream=stream, tile_T=args.tile, flags=flags, prec=prec)
+    else:
+        V, D, nnz = prob.A.n_rows, prob.A.n_cols, prob.A.nnz
+        rp = torch.from_numpy(prob.A.row_ptr).to(dev)
+        ci = torch.from_numpy(prob.A.col_idx).to(dev)
+        va = torch.from_numpy(prob.A.val).to(dev)
+        ctx = nmf.Nmf(V, D, K, row_ptr=rp, col_idx=ci, val=va,
+                      W0=torch.from_numpy(W0).to(dev), H0=torch.from_numpy(H0).to(dev),
+                      stream=stream, tile_T=args.tile, flags=flags, prec=prec)
     flush = torch.empty(256 * 2 ** 20 // 4, dtype=torch.float32, device=dev)   # 256 MB > L2
 
     # warm-up (also captures the CUDA graph)
@@ -183,16 +233,26 @@ def run_gpu(args):
 
     # per-step breakdown with CUDA events (eager launches)
     prof = ctx.profile(max(3, min(10, args.steps)))
-    ab = alg_bytes(V, D, nnz, K)
-    dom = max(prof, key=prof.get)
     peak, peak_kind = _peaks()
-    achieved = ab[dom] / (prof[dom] * 1e-3) / 1e9
-    roofline = {"bound": "hbm", "achieved": round(achieved, 2), "peak": peak, "unit": "GB/s",
-                "frac": round(achieved / peak, 5), "traffic": None, "step": dom,
-                "peak_source": peak_kind,
-                "step_ms": {k: round(v, 5) for k, v in prof.items()},
-                "alg_bytes_per_iter": int(sum(ab.values())),
-                "iteration_frac_of_hbm": round(sum(ab.values()) / (ms * 1e-3) / 1e9 / peak, 5)}
+    if dense:
+        ab, prod_flops = dense_costs(V, D, K, bf16)
+        dom = max(prof, key=prof.get)
+        tflops = prod_flops / (prof["P"] * 1e-3) / 1e12
+        tpeak, tkind = _tensor_peak(bf16)
+        roofline = {"bound": "tensor" if bf16 else "fp32-simt", "achieved": round(tflops, 3), "peak": tpeak,
+                    "unit": "TFLOP/s", "frac": round(tflops / tpeak, 5), "traffic": None,
+                    "step": "P (A H^T)", "peak_source": tkind, "dominant_step": dom,
+                    "step_ms": {k: round(v, 5) for k, v in prof.items()}}
+    else:
+        ab = alg_bytes(V, D, nnz, K)
+        dom = max(prof, key=prof.get)
+        achieved = ab[dom] / (prof[dom] * 1e-3) / 1e9
+        roofline = {"bound": "hbm", "achieved": round(achieved, 2), "peak": peak, "unit": "GB/s",
+                    "frac": round(achieved / peak, 5), "traffic": None, "step": dom,
+                    "peak_source": peak_kind,
+                    "step_ms": {k: round(v, 5) for k, v in prof.items()},
+                    "alg_bytes_per_iter": int(sum(ab.values())),
+                    "iteration_frac_of_hbm": round(sum(ab.values()) / (ms * 1e-3) / 1e9 / peak, 5)}
 
     # end to end through the public API with host buffers: per step the
     # factors go host -> device, one iteration runs, and the factors and the
@@ -214,10 +274,10 @@ def run_gpu(args):
     out = {
         "metric": METRIC, "value": round(world * 1000.0 / ms, 3), "unit": "iter/s",
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 5),
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
-        "data": "synthetic (seeded Zipf/log-normal tf-idf CSR; no dataset)",
-        "config": {"workload": "text-20ng-like sparse NMF", "V": V, "D": D, "nnz": nnz, "K": K,
-                   "tile_T": q["tile_T"], "chain_ctas": q["chain_ctas"], "precision": "fp32",
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "bf16" if bf16 else "f32",
+        "data": "synthetic (seeded; no dataset)",
+        "config": {"workload": WORKLOADS[args.workload], "V": V, "D": D, "nnz": nnz, "K": K,
+                   "tile_T": q["tile_T"], "chain_ctas": q["chain_ctas"], "precision": args.prec,
                    "l2": "flushed between steps (256 MB write)", "parallelism": "replicas" if world > 1 else "single",
                    "ms_per_step_warm_l2": round(ms_warm, 5), "rel_err_final": rel},
         "e2e": {"value": round(1.0 / t_e2e, 3), "unit": "iter/s", "h2d_bytes_per_step": fac_bytes,
@@ -247,6 +307,7 @@ def _threads_used():
 def cpu_baseline(prob, W0, H0, K, iters):
     """The FP64 oracle (Alg. 1, un-reordered) timed on this host's cores on a
     bounded sample: `iters` full iterations of the same workload."""
+    V, D = W0.shape[0], H0.shape[1]
     from oracle import fast_hals as fh
     W = fh.normalize_init(W0)
     H = H0.astype(np.float64)
@@ -257,7 +318,7 @@ def cpu_baseline(prob, W0, H0, K, iters):
         W, H = fh.iteration(A, W, H)
     dt = (time.perf_counter() - t0) / iters
     return {"value": round(1.0 / dt, 5), "unit": "iter/s", "cores": _threads_used(), "kind": "oracle",
-            "sample": f"{iters} FP64 oracle iterations of the full {prob.A.n_rows}x{prob.A.n_cols} K={K} problem"}
+            "sample": f"{iters} FP64 oracle iterations of the full {V}x{D} K={K} problem"}
 
 
 def run_reference(args):
@@ -265,7 +326,7 @@ def run_reference(args):
     if rank != 0:
         return
     K = args.k
-    prob, W0, H0 = make_workload(K)
+    prob, W0, H0 = make_workload(args.workload, K)
     from oracle import fast_hals as fh
     A = fh._as_operator(prob.A)
     W = fh.normalize_init(W0)
@@ -283,8 +344,8 @@ def run_reference(args):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(dt * 1e3, 3),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic (seeded Zipf/log-normal tf-idf CSR; no dataset)",
-        "config": {"workload": "text-20ng-like sparse NMF", "V": prob.A.n_rows, "D": prob.A.n_cols,
-                   "nnz": prob.A.nnz, "K": K, "precision": "fp64 oracle"},
+        "config": {"workload": WORKLOADS[args.workload], "V": W0.shape[0], "D": H0.shape[1], "K": K,
+                   "precision": "fp64 oracle"},
         "cpu_baseline": {"value": v, "unit": "iter/s", "cores": cores, "kind": "oracle",
                          "sample": f"{args.steps} full iterations per timed region"},
         "e2e": {"value": v, "unit": "iter/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -298,7 +359,9 @@ def main():
     ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--k", type=int, default=160)
+    ap.add_argument("--k", type=int, default=0, help="rank (default: 160 text, 256 dense8192, 16 dense512)")
+    ap.add_argument("--workload", default="text20ng", choices=sorted(WORKLOADS))
+    ap.add_argument("--prec", default="fp32", choices=["fp32", "bf16"])
     ap.add_argument("--tile", type=int, default=0)
     ap.add_argument("--cpu-iters", type=int, default=5)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -308,6 +371,8 @@ def main():
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3
+    if args.k == 0:
+        args.k = {"text20ng": 160, "dense8192": 256, "dense512": 16}[args.workload]
     if args.impl == "reference":
         run_reference(args)
     else:

@@ -62,7 +62,9 @@ typedef enum { NMF_PREC_FP32 = 0, NMF_PREC_BF16 = 1 } nmf_precision;
  *   eps          clamp floor of Alg. 1 (paper leaves it unset; 0 -> 1e-16).
  *   tile_T       column-tile width T of Alg. 2; 0 -> library choice.
  *   prec         NMF_PREC_FP32 (all FP32) or NMF_PREC_BF16 (dense A only:
- *                products A H^T and A^T W with BF16 operands, FP32 accumulate).
+ *                products A H^T, A^T W and the Gram matrices on the tensor
+ *                cores with BF16 operands and FP32 accumulation; column
+ *                updates and norms FP32; A is copied to BF16 once).
  *   stream       cudaStream_t to run on (NULL -> the context creates one).
  */
 typedef struct {
@@ -95,6 +97,10 @@ typedef struct {
 /* Run the W update as separate launches per column tile instead of one
  * persistent cooperative launch (the default where the GPU supports it). */
 #define NMF_FLAG_MULTI_LAUNCH_W 2
+/* BF16 form (NMF_PREC_BF16): take the dense products A^T W and A H^T through
+ * the SIMT-staged tensor-core kernel instead of the TMA-fed one (the default
+ * where the driver exposes tensor-map encoding).  Same arithmetic. */
+#define NMF_FLAG_NO_TMA 4
 
 typedef struct nmf_ctx nmf_ctx;
 
@@ -112,6 +118,10 @@ nmf_status nmf_iterate(nmf_ctx* c, int32_t n_iters);
 
 /* Synchronises the stream and returns the latest objective
  * frob2 = ||A - WH||_F^2 and rel = sqrt(frob2 / ||A||_F^2) (Sec. 6.2.2).
+ * For dense A the value is Eq. 2 evaluated directly for the current factors,
+ * sum of (A - WH)^2 with FP32 products and FP64 accumulation (no cancellation;
+ * in the BF16 form it measures the fit to the FP32 A, not to its BF16 copy).
+ * For CSR A it is the latest per-iteration value (trace identity).
  * Before any iteration it evaluates the initial factors.  Also reports
  * device-side status (NMF_ETIMEOUT / NMF_ENUMERIC) raised since the last
  * call.  Either output pointer may be NULL. */
@@ -178,6 +188,17 @@ nmf_status nmf_query(nmf_ctx* c, int32_t* tile_T, int32_t* chain_ctas, int32_t* 
  * `stream`.  Returns NMF_EINVAL for non-positive sizes or null pointers. */
 nmf_status nmf_gemm(int32_t M, int32_t N, int32_t K, const float* A, int64_t lda, int32_t transA,
                     const float* B, int64_t ldb, float* C, int64_t ldc, int32_t prec, void* stream);
+
+/* BF16 product with TMA-fed tensor-core MMAs (the kernel of the BF16 form,
+ * Alg. 1 lines 4 and 10): C (M x N, FP32, row-major, ldc) = A B^T with
+ * A row-major M x K (lda) and B row-major N x K (ldb): both operands K-major
+ * bfloat16 (uint16 bit patterns), FP32 accumulation in tensor memory.  A and
+ * B must start on 16-byte boundaries and lda, ldb be multiples of 8;
+ * NMF_EINVAL otherwise and for non-positive sizes, short strides or null
+ * pointers; NMF_EUNSUPPORTED where the driver exposes no tensor-map encoding.
+ * All pointers device; asynchronous on `stream`. */
+nmf_status nmf_gemm_bf16(int32_t M, int32_t N, int32_t K, const uint16_t* A, int64_t lda, const uint16_t* B,
+                         int64_t ldb, float* C, int64_t ldc, void* stream);
 
 /* Gram matrix without device allocation (this entry point has no
  * counterpart in the paper; it serves callers that cannot call cudaMalloc,

@@ -15,6 +15,7 @@ objective   Eq. 2 directly and through the trace identity; the relative
 nnls        Fixed-W H subproblem (the H half of Alg. 1 repeated to
             convergence) and exact NNLS references for pins.
 mlp         FP64 forward / backward / Adam of the warm-start network.
+bf16        round-to-nearest-even to bfloat16 (operands of the BF16 form).
 tile_model  Data-movement model, Eq. 3 and Eqs. 7-11 (Sec. 5).
 
 Parity status: every function here is pinned by tests in

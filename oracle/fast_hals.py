@@ -70,21 +70,30 @@ def update_w(P: np.ndarray, Q: np.ndarray, W: np.ndarray, eps: float = DEFAULT_E
     return W
 
 
-def iteration(A, W: np.ndarray, H: np.ndarray, eps: float = DEFAULT_EPS, trace: dict | None = None):
+def iteration(A, W: np.ndarray, H: np.ndarray, eps: float = DEFAULT_EPS, trace: dict | None = None,
+              operand_round=None):
     """One REPEAT body of Alg. 1: update H, then W.  Returns (W, H).
 
     If ``trace`` is a dict it receives the intermediates R, S, H, P, Q, W.
+    ``operand_round`` (e.g. bf16.round_bf16) rounds the operands of the four
+    matrix products (lines 4, 5, 10, 11) before they are multiplied exactly
+    (FP64): the definition of a reduced-precision-product form of Alg. 1.
+    The k loops stay FP64.
     """
     Aop = _as_operator(A)
     W = np.asarray(W, dtype=np.float64)
     H = np.asarray(H, dtype=np.float64)
+    rnd = operand_round if operand_round is not None else (lambda x: x)
+    Ar = Aop if operand_round is None else rnd(Aop)
     # Updating H
-    R = np.asarray(Aop.T @ W)
-    S = W.T @ W
+    Wr = rnd(W)
+    R = np.asarray(Ar.T @ Wr)
+    S = Wr.T @ Wr
     H = update_h(R, S, H, eps)
     # Updating W
-    P = np.asarray(Aop @ H.T)
-    Q = H @ H.T
+    Hr = rnd(H)
+    P = np.asarray(Ar @ Hr.T)
+    Q = Hr @ Hr.T
     W = update_w(P, Q, W, eps)
     if trace is not None:
         trace.update(R=R, S=S, H=H, P=P, Q=Q, W=W)
@@ -92,7 +101,7 @@ def iteration(A, W: np.ndarray, H: np.ndarray, eps: float = DEFAULT_EPS, trace: 
 
 
 def run(A, W0: np.ndarray, H0: np.ndarray, n_iter: int, eps: float = DEFAULT_EPS,
-        normalize: bool = True, objective_every: int = 0):
+        normalize: bool = True, objective_every: int = 0, operand_round=None):
     """Alg. 1 for a fixed number of iterations from (W0, H0).
 
     Returns (W, H, history) where history lists the relative objective
@@ -104,7 +113,7 @@ def run(A, W0: np.ndarray, H0: np.ndarray, n_iter: int, eps: float = DEFAULT_EPS
     H = np.array(H0, dtype=np.float64)
     hist = []
     for it in range(n_iter):
-        W, H = iteration(A, W, H, eps)
+        W, H = iteration(A, W, H, eps, operand_round=operand_round)
         if objective_every and (it + 1) % objective_every == 0:
             hist.append(obj.relative_error(A, W, H))
     return W, H, hist

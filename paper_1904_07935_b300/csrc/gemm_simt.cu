@@ -7,6 +7,7 @@
 // thread, k staged through shared memory 16 at a time (double-buffered via
 // registers).  FP32 multiply-add with FP32 accumulation.
 #include <algorithm>
+#include <vector>
 
 #include "internal.cuh"
 
@@ -23,7 +24,7 @@ __device__ __forceinline__ float load_a(const GemmArgs& g, int m, int k) {
 __device__ __forceinline__ float load_b(const GemmArgs& g, int k, int n, int k_end) {
   if (k >= k_end || n >= g.N) return 0.f;
   if (g.mode == GM_PHASE1 && !(k > n)) return 0.f;   // strictly upper part only
-  return __ldg(g.B + (int64_t)k * g.ldb + n);
+  return g.transB ? __ldg(g.B + (int64_t)n * g.ldb + k) : __ldg(g.B + (int64_t)k * g.ldb + n);
 }
 
 __global__ void __launch_bounds__(256) gemm_kernel(GemmArgs g) {
@@ -106,6 +107,7 @@ __global__ void __launch_bounds__(256) gemm_kernel(GemmArgs g) {
   }
 
   // Epilogue.
+  double r2 = 0.0;
 #pragma unroll
   for (int i = 0; i < 4; ++i) {
     const int m = m0 + ty * 4 + i;
@@ -135,8 +137,23 @@ __global__ void __launch_bounds__(256) gemm_kernel(GemmArgs g) {
         case GM_PARTIAL:
           g.C[(int64_t)z * g.part_stride + (int64_t)m * g.ldc + n] = v;
           break;
+        case GM_RESID2: {
+          const double d = (double)g.E[(int64_t)m * g.lde + n] - (double)v;
+          r2 += d * d;
+          break;
+        }
       }
     }
+  }
+  if (g.mode == GM_RESID2) {
+    __shared__ double red[256];
+    red[threadIdx.x] = r2;
+    __syncthreads();
+    for (int off = 128; off > 0; off >>= 1) {
+      if ((int)threadIdx.x < off) red[threadIdx.x] += red[threadIdx.x + off];
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) g.dpart[blockIdx.y * gridDim.x + blockIdx.x] = red[0];
   }
 }
 
@@ -284,6 +301,29 @@ cudaError_t gemm_run(const GemmArgs& a, cudaStream_t s) {
   return cudaGetLastError();
 }
 
+int64_t resid2_partials(int V, int D) { return (int64_t)((D + BN - 1) / BN) * ((V + BM - 1) / BM); }
+
+cudaError_t resid2_dense(const float* A, int64_t lda, const float* W, const float* Ht, int V, int D, int K, int Kp,
+                         double* dpart, double* out, cudaStream_t s) {
+  GemmArgs a;
+  a.M = V; a.N = D; a.Kin = K;
+  a.A = W; a.lda = Kp; a.transA = 0;
+  a.B = Ht; a.ldb = Kp; a.transB = 1;
+  a.E = A; a.lde = lda;
+  a.mode = GM_RESID2;
+  a.dpart = dpart;
+  cudaError_t e = gemm_run(a, s);
+  if (e != cudaSuccess) return e;
+  const int64_t n = resid2_partials(V, D);
+  std::vector<double> h((size_t)n);
+  if ((e = cudaMemcpyAsync(h.data(), dpart, sizeof(double) * n, cudaMemcpyDeviceToHost, s)) != cudaSuccess) return e;
+  if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return e;
+  double t = 0.0;
+  for (double v : h) t += v;
+  *out = t;
+  return cudaSuccess;
+}
+
 cudaError_t gram_setup(GramWork& g, int N, int Kp) {
   g.N = N;
   g.Kp = Kp;
@@ -318,7 +358,8 @@ cudaError_t gram_setup_tc(GramWork& g, int N, int Kp) {
   return cudaMalloc(&g.d_part, sizeof(float) * (size_t)g.n_chunks * Kp * Kp);
 }
 
-cudaError_t gram_run_tc(const GramWork& g, const float* X, float* S, int K, int* d_status, cudaStream_t s) {
+cudaError_t gram_run_tc(const GramWork& g, const float* X, float* S, int K, int* d_status, cudaStream_t s,
+                        bool bf16) {
   GemmArgs a;
   a.M = g.Kp;
   a.N = g.Kp;
@@ -334,7 +375,7 @@ cudaError_t gram_run_tc(const GramWork& g, const float* X, float* S, int K, int*
   a.k_chunk = g.chunk;
   a.part_stride = (int64_t)g.Kp * g.Kp;
   a.n_chunks = g.n_chunks;
-  cudaError_t err = tc_gemm_run(a, TC_TF32X3, nullptr, 0, d_status, s);
+  cudaError_t err = tc_gemm_run(a, bf16 ? TC_BF16 : TC_TF32X3, nullptr, 0, d_status, s);
   if (err != cudaSuccess) return err;
   dim3 grid((g.Kp + 127) / 128, g.Kp);
   gram_reduce_kernel<<<grid, 128, 0, s>>>(g.d_part, g.n_chunks, g.Kp, K, S);

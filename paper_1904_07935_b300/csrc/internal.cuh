@@ -52,12 +52,13 @@ enum GemmMode : int {
   GM_PHASE1 = 1,    // C = E + c'_n * X[m][n] - acc  (strictly-upper masked B)
   GM_SUB = 2,       // C -= acc
   GM_PARTIAL = 3,   // C[z] = acc over k-chunk z (split-K partials)
+  GM_RESID2 = 4,    // dpart[block] = sum over the tile of (E - acc)^2 (FP64)
 };
 
 struct GemmArgs {
   int M = 0, N = 0, Kin = 0;
   const float* A = nullptr;  int64_t lda = 0;  int transA = 0;   // op(A)[m][k]
-  const float* B = nullptr;  int64_t ldb = 0;                    // B[k][n]
+  const float* B = nullptr;  int64_t ldb = 0;  int transB = 0;   // B[k][n] (or B[n][k] if transB)
   float* C = nullptr;        int64_t ldc = 0;
   int mode = GM_STORE;
   // GM_PHASE1 extras: E (M x N, lde), X (M x N, ldx) and the Gram G whose
@@ -71,6 +72,7 @@ struct GemmArgs {
   int k_chunk = 0;  int64_t part_stride = 0;  int n_chunks = 1;
   // Only tiles with (tile_n >= tile_m) are computed when upper_only (Grams).
   int upper_only = 0;
+  double* dpart = nullptr;   // GM_RESID2: one FP64 partial per CTA (grid.x * grid.y)
 };
 
 cudaError_t gemm_run(const GemmArgs& a, cudaStream_t s);
@@ -81,6 +83,22 @@ enum TcPrecision : int { TC_TF32X3 = 0, TC_BF16 = 1 };
 cudaError_t tc_gemm_run(const GemmArgs& g, TcPrecision prec, const void* a_bf16, int bn, int* d_status,
                         cudaStream_t s);
 int tc_pick_bn(int N);
+
+// BF16 products with TMA-fed tcgen05 MMAs: C (M x N, FP32) = A (M x Kd) B (N x Kd)^T,
+// A and B BF16, K-major, row strides lda / ldb multiples of 8 elements.
+bool tma_available();
+cudaError_t tc_bf16_tma_gemm(const void* A, int64_t lda, const void* B, int64_t ldb, float* C, int64_t ldc, int M,
+                             int N, int Kd, int* d_status, cudaStream_t s);
+// dst (cols x ldd, BF16) = transpose of src (rows x cols FP32, row stride lds); rows..ldd zero.
+cudaError_t transpose_to_bf16(const float* src, int rows, int cols, int64_t lds, void* dst, int64_t ldd,
+                              cudaStream_t s);
+
+// sum_{v,d} (A[v][d] - (W Ht^T)[v][d])^2: Eq. 2 evaluated directly for dense A
+// (FP32 products, FP64 sum of the squared residuals).  dpart: scratch of
+// resid2_partials(V, D) doubles; the result is written to *out (host).
+int64_t resid2_partials(int V, int D);
+cudaError_t resid2_dense(const float* A, int64_t lda, const float* W, const float* Ht, int V, int D, int K, int Kp,
+                         double* dpart, double* out, cudaStream_t s);
 
 // S (Kp x Kp) = X^T X for X (N x Kp): split-N partials, FP64 fixed-order sum.
 struct GramWork {
@@ -96,7 +114,8 @@ cudaError_t gram_run_scratch(const float* X, int N, int K, int64_t ldx, float* p
                              float* S, cudaStream_t s);
 // Same result through the tensor cores (3xTF32, split-N partials).
 cudaError_t gram_setup_tc(GramWork& g, int N, int Kp);
-cudaError_t gram_run_tc(const GramWork& g, const float* X, float* S, int K, int* d_status, cudaStream_t s);
+cudaError_t gram_run_tc(const GramWork& g, const float* X, float* S, int K, int* d_status, cudaStream_t s,
+                        bool bf16 = false);
 
 // ---------------------------------------------------------------------------
 // Tall-factor update (Alg. 2 regrouped): phase 1 GEMM, per-tile chain, phase 3.
@@ -152,6 +171,10 @@ cudaError_t fill_uniform_splitmix(float* dst, int rows, int cols, int ld, uint64
 cudaError_t fill_uniform_splitmix_t(float* dst, int rows, int cols, int ld, uint64_t seed,
                                     cudaStream_t s);
 cudaError_t normalize_columns(float* X, int N, int K, int ld, cudaStream_t s);
+// dst (rows x ld, BF16, round to nearest) = src (rows x cols, row stride ld), pads zero.
+// dst (rows x ldd, BF16 round-to-nearest-even) = src (rows x cols, row stride lds); columns cols..ldd zero.
+cudaError_t convert_bf16(const float* src, int64_t rows, int64_t cols, int64_t lds, void* dst, int64_t ldd,
+                         cudaStream_t s);
 // frob2 = normA2 - 2 <W, P> + <S, Q>, appended to the history ring.  The
 // dot products use compensated FP32 arithmetic (Dot2) per thread and FP64
 // across threads; `partial` holds 2 * n_partial doubles.

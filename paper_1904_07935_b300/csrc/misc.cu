@@ -1,4 +1,6 @@
 // Initialisation, column normalisation and FP64 reductions.
+#include <cuda_bf16.h>
+
 #include <algorithm>
 
 #include "internal.cuh"
@@ -167,7 +169,22 @@ __global__ void transpose_kernel(const float* __restrict__ src, int rows, int co
   }
 }
 
+__global__ void convert_bf16_kernel(const float* __restrict__ src, long long rows, long long cols, long long lds,
+                                    __nv_bfloat16* __restrict__ dst, long long ldd) {
+  const long long n = rows * ldd;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
+    const long long r = e / ldd, c = e - r * ldd;
+    dst[e] = __float2bfloat16_rn(c < cols ? src[r * lds + c] : 0.f);
+  }
+}
+
 }  // namespace
+
+cudaError_t convert_bf16(const float* src, int64_t rows, int64_t cols, int64_t lds, void* dst, int64_t ldd,
+                         cudaStream_t s) {
+  convert_bf16_kernel<<<1184, 256, 0, s>>>(src, rows, cols, lds, static_cast<__nv_bfloat16*>(dst), ldd);
+  return cudaGetLastError();
+}
 
 cudaError_t transpose_f32(const float* src, int rows, int cols, int lds, float* dst, int ldd, cudaStream_t s) {
   dim3 grid((cols + 31) / 32, (rows + 31) / 32);

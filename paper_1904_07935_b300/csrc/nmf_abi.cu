@@ -14,6 +14,14 @@ using namespace plnmf;
 struct nmf_ctx {
   int V = 0, D = 0, K = 0, Kp = 0, T = 16, fmt = 0, prec = 0;
   bool use_tc = false;      // FP32 Grams on the tensor cores (3xTF32)
+  bool bf16 = false;        // precision form: BF16 tensor-core products and Grams
+  void* A_bf16 = nullptr;   // BF16 copy of dense A (V x lda)
+  bool tma = false;         // BF16 products through the TMA-fed kernel
+  void* Ab8 = nullptr;      // BF16 A, V x ld8D (row stride a multiple of 8)
+  void* ATb8 = nullptr;     // BF16 A^T, D x ld8V
+  void* Fb8 = nullptr;      // BF16 transposed factor, Kp x max(ld8V, ld8D)
+  int64_t ld8V = 0, ld8D = 0;
+  double* resid_part = nullptr;     // dense A: partials of the direct objective
   float eps = 1e-16f;
   cudaStream_t stream = nullptr;
   bool own_stream = false;
@@ -96,6 +104,15 @@ cudaError_t enq_product_R(nmf_ctx* c) {   // R = A^T W  (D x Kp)
   a.B = c->W; a.ldb = c->Kp;
   a.C = c->R; a.ldc = c->Kp;
   c->launch_count += 1;
+  if (c->bf16 && c->tma) {
+    // R (D x Kp) = A^T (D x V) * (W^T)^T with W^T (Kp x V) in BF16.
+    cudaError_t e = transpose_to_bf16(c->W, c->V, c->Kp, c->Kp, c->Fb8, c->ld8V, c->stream);
+    if (e != cudaSuccess) return e;
+    c->launch_count += 1;
+    return tc_bf16_tma_gemm(c->ATb8, c->ld8V, c->Fb8, c->ld8V, c->R, c->Kp, c->D, c->Kp, c->V, c->d_status,
+                            c->stream);
+  }
+  if (c->bf16) return tc_gemm_run(a, TC_BF16, c->A_bf16, c->Kp > 128 ? 128 : 0, c->d_status, c->stream);
   return gemm_run(a, c->stream);
 }
 
@@ -110,12 +127,21 @@ cudaError_t enq_product_P(nmf_ctx* c) {   // P = A H^T  (V x Kp)
   a.B = c->Ht; a.ldb = c->Kp;
   a.C = c->P; a.ldc = c->Kp;
   c->launch_count += 1;
+  if (c->bf16 && c->tma) {
+    // P (V x Kp) = A (V x D) * (H)^T with H = (H^T)^T (Kp x D) in BF16.
+    cudaError_t e = transpose_to_bf16(c->Ht, c->D, c->Kp, c->Kp, c->Fb8, c->ld8D, c->stream);
+    if (e != cudaSuccess) return e;
+    c->launch_count += 1;
+    return tc_bf16_tma_gemm(c->Ab8, c->ld8D, c->Fb8, c->ld8D, c->P, c->Kp, c->V, c->Kp, c->D, c->d_status,
+                            c->stream);
+  }
+  if (c->bf16) return tc_gemm_run(a, TC_BF16, c->A_bf16, c->Kp > 128 ? 128 : 0, c->d_status, c->stream);
   return gemm_run(a, c->stream);
 }
 
 cudaError_t enq_gram(nmf_ctx* c, const GramWork& g, const float* X, float* out) {
   c->launch_count += 2;
-  if (c->use_tc) return gram_run_tc(g, X, out, c->K, c->d_status, c->stream);
+  if (c->use_tc || c->bf16) return gram_run_tc(g, X, out, c->K, c->d_status, c->stream, c->bf16);
   return gram_run(g, X, out, c->K, c->stream);
 }
 
@@ -344,7 +370,27 @@ nmf_status init_impl(const nmf_problem* p, nmf_ctx* c) {
   CK(cudaMemsetAsync(c->R, 0, sizeof(float) * nD, c->stream));
   CK(cudaMemsetAsync(c->Y, 0, sizeof(float) * nMax, c->stream));
   c->use_tc = (p->flags & NMF_FLAG_TC_GRAMS) != 0;
-  if (c->use_tc) {
+  c->bf16 = c->prec == NMF_PREC_BF16;
+  if (c->bf16) {
+    // BF16 copy of A for the tensor-core products; FP32 Grams and buffers for
+    // the objective against the FP32 A (nmf_error).
+    c->tma = tma_available() && !(p->flags & NMF_FLAG_NO_TMA);
+    if (!c->tma) {
+      CK(cudaMalloc(&c->A_bf16, sizeof(uint16_t) * (size_t)V * c->lda));
+      CK(convert_bf16(c->dense, V, D, c->lda, c->A_bf16, c->lda, c->stream));
+    } else {
+      c->ld8V = (V + 7) / 8 * 8;
+      c->ld8D = (D + 7) / 8 * 8;
+      CK(cudaMalloc(&c->Ab8, sizeof(uint16_t) * (size_t)V * c->ld8D));
+      CK(cudaMalloc(&c->ATb8, sizeof(uint16_t) * (size_t)D * c->ld8V));
+      CK(cudaMalloc(&c->Fb8, sizeof(uint16_t) * (size_t)Kp * std::max(c->ld8V, c->ld8D)));
+      // A (V x D) -> BF16 with row stride ld8D, and A^T (D x V) with ld8V.
+      CK(convert_bf16(c->dense, V, D, c->lda, c->Ab8, c->ld8D, c->stream));
+      CK(transpose_to_bf16(c->dense, V, D, c->lda, c->ATb8, c->ld8V, c->stream));
+    }
+  }
+  if (c->fmt == NMF_DENSE_F32) CK(dalloc(&c->resid_part, (size_t)resid2_partials(V, D)));
+  if (c->use_tc || c->bf16) {
     CK(gram_setup_tc(c->gramW, V, Kp));
     CK(gram_setup_tc(c->gramH, D, Kp));
   } else {
@@ -401,7 +447,9 @@ void free_ctx(nmf_ctx* c) {
   spmm_plan_free(c->planAt);
   gram_free(c->gramW);
   gram_free(c->gramH);
-  for (void* p : {(void*)c->d_sync, (void*)c->rpT, (void*)c->ciT, (void*)c->vaT, (void*)c->W, (void*)c->Ht, (void*)c->R,
+
+  for (void* p : {(void*)c->A_bf16, c->Ab8, c->ATb8, c->Fb8, (void*)c->resid_part,
+                  (void*)c->d_sync, (void*)c->rpT, (void*)c->ciT, (void*)c->vaT, (void*)c->W, (void*)c->Ht, (void*)c->R,
                   (void*)c->P, (void*)c->S, (void*)c->Q, (void*)c->Y, (void*)c->stage,
                   (void*)c->obj_partial, (void*)c->hist, (void*)c->d_counter, (void*)c->d_status})
     if (p) cudaFree(p);
@@ -440,7 +488,8 @@ nmf_status nmf_init(const nmf_problem* p, nmf_ctx** out) {
   if (p->K > kMaxK) return NMF_EUNSUPPORTED;
   if (!(p->eps >= 0.f) || !std::isfinite(p->eps)) return NMF_EINVAL;
   if (p->tile_T < 0) return NMF_EINVAL;
-  if (p->prec != NMF_PREC_FP32) return NMF_EUNSUPPORTED;
+  if (p->prec != NMF_PREC_FP32 && p->prec != NMF_PREC_BF16) return NMF_EINVAL;
+  if (p->prec == NMF_PREC_BF16 && p->fmt != NMF_DENSE_F32) return NMF_EUNSUPPORTED;
   nmf_ctx* c = new (std::nothrow) nmf_ctx();
   if (!c) return NMF_ENOMEM;
   nmf_status st = init_impl(p, c);
@@ -491,12 +540,19 @@ nmf_status nmf_error(nmf_ctx* c, double* frob2, double* rel) {
     CK(enq_objective(c));
     c->s_valid = true;
   }
+  double f = NAN;
+  if (c->fmt == NMF_DENSE_F32) {
+    // Dense A: Eq. 2 evaluated directly, sum of (A - WH)^2 accumulated in
+    // FP64 from the FP32 A (no cancellation; in the BF16 form this measures
+    // the fit to A itself rather than to its BF16 copy).
+    CK(resid2_dense(c->dense, c->lda, c->W, c->Ht, c->V, c->D, c->K, c->Kp, c->resid_part, &f, c->stream));
+  }
   CK(cudaStreamSynchronize(c->stream));
   nmf_status st = read_status(c);
   unsigned cnt = 0;
   CK(cudaMemcpy(&cnt, c->d_counter, sizeof(unsigned), cudaMemcpyDeviceToHost));
-  double f = NAN;
-  if (cnt > 0) CK(cudaMemcpy(&f, c->hist + (cnt - 1) % kHistCap, sizeof(double), cudaMemcpyDeviceToHost));
+  if (c->fmt != NMF_DENSE_F32 && cnt > 0)
+    CK(cudaMemcpy(&f, c->hist + (cnt - 1) % kHistCap, sizeof(double), cudaMemcpyDeviceToHost));
   if (frob2) *frob2 = f;
   if (rel) *rel = std::sqrt(std::max(f, 0.0) / c->normA2);
   return st;
@@ -681,6 +737,20 @@ nmf_status nmf_gemm(int32_t M, int32_t N, int32_t K, const float* A, int64_t lda
   g.mode = GM_STORE;
   return from_cuda(tc_gemm_run(g, prec == NMF_PREC_FP32 ? TC_TF32X3 : TC_BF16, nullptr, 0, d_status,
                                static_cast<cudaStream_t>(stream)));
+}
+
+nmf_status nmf_gemm_bf16(int32_t M, int32_t N, int32_t K, const uint16_t* A, int64_t lda, const uint16_t* B,
+                         int64_t ldb, float* C, int64_t ldc, void* stream) {
+  if (M <= 0 || N <= 0 || K <= 0 || !A || !B || !C || lda < K || ldb < K || ldc < N) return NMF_EINVAL;
+  if ((reinterpret_cast<uintptr_t>(A) & 15) || (reinterpret_cast<uintptr_t>(B) & 15) || (lda & 7) || (ldb & 7))
+    return NMF_EINVAL;
+  if (!tma_available()) return NMF_EUNSUPPORTED;
+  static int* d_status = nullptr;
+  if (!d_status) {
+    CK(cudaMalloc(&d_status, sizeof(int)));
+    CK(cudaMemset(d_status, 0, sizeof(int)));
+  }
+  return from_cuda(tc_bf16_tma_gemm(A, lda, B, ldb, C, ldc, M, N, K, d_status, static_cast<cudaStream_t>(stream)));
 }
 
 }  // extern "C"

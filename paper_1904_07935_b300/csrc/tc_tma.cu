@@ -1,0 +1,258 @@
+// BF16 products of the precision form on the tensor cores with TMA operand
+// loads: C (M x N, FP32, row-major) = A (M x Kd) * B (N x Kd)^T, both operands
+// K-major BF16 in global memory (A = the BF16 copy of A or of A^T, B = the
+// BF16 transposed factor, Alg. 1 lines 4 and 10).
+//
+// One CTA per 128 x 128 output tile.  Warp 0 (one lane) streams K slices of
+// 64 elements of A and B into a 4-stage ring of shared memory with
+// cp.async.bulk.tensor (128-byte swizzle, completion counted on the stage's
+// "full" mbarrier); warp 1 (one lane) waits for a full stage, issues four
+// tcgen05.mma (kind::f16, K = 16 each) into the FP32 accumulator in tensor
+// memory and commits to the stage's "empty" mbarrier; warps 2-5 wait for the
+// final commit and move the accumulator TMEM -> registers -> global memory.
+// Out-of-range rows / K are zero-filled by the TMA unit.  Every wait is
+// bounded (ST_TIMEOUT).
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cudaTypedefs.h>
+
+#include <mutex>
+
+#include "devutil.cuh"
+#include "internal.cuh"
+
+namespace plnmf {
+namespace {
+
+constexpr int TM = 128, TN = 128, TK = 64;        // tile; TK BF16 = 128 bytes
+constexpr int NSTAGE = 4;
+constexpr int A_STAGE = TM * 128, B_STAGE = TN * 128;
+constexpr int TMA_THREADS = 192;
+
+__device__ __forceinline__ unsigned long long desc_sw128(unsigned saddr) {
+  unsigned long long d = 0;
+  d |= (unsigned long long)((saddr & 0x3FFFFu) >> 4);
+  d |= (unsigned long long)(16u >> 4) << 16;
+  d |= (unsigned long long)(1024u >> 4) << 32;
+  d |= 1ull << 46;
+  d |= 2ull << 61;
+  return d;
+}
+
+__device__ __forceinline__ bool wait_bounded(unsigned bar, unsigned parity, int* status) {
+  unsigned long long t0 = 0;
+  unsigned polls = 0;
+  while (!mbar_try_wait_cta(bar, parity)) {
+    if ((++polls & 63u) == 0) {
+      const unsigned long long now = global_ns();
+      if (t0 == 0) t0 = now;
+      else if (now - t0 > kWaitLimitNs) {
+        atomicOr(status, ST_TIMEOUT);
+        return false;
+      }
+    }
+  }
+  return true;
+}
+
+__device__ __forceinline__ void tma_load_2d(unsigned dst, const CUtensorMap* map, int x, int y, unsigned bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+          dst),
+      "l"(map), "r"(x), "r"(y), "r"(bar)
+      : "memory");
+}
+
+__global__ void __launch_bounds__(TMA_THREADS, 1)
+    tc_tma_bf16_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB, float* C,
+                       int64_t ldc, int M, int N, int Kd, int* status) {
+  extern __shared__ __align__(1024) char smem_raw[];
+  __shared__ __align__(8) unsigned long long full[NSTAGE], empty[NSTAGE], done;
+  __shared__ unsigned tmem_base;
+  char* smem = reinterpret_cast<char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int m0 = blockIdx.y * TM, n0 = blockIdx.x * TN;
+  const int nk = (Kd + TK - 1) / TK;
+
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base)),
+                 "r"(TN)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  if (threadIdx.x == 32) {
+    for (int s = 0; s < NSTAGE; ++s) {
+      mbar_init(smem_u32(&full[s]), 1);
+      mbar_init(smem_u32(&empty[s]), 1);
+    }
+    mbar_init(smem_u32(&done), 1);
+    fence_mbar_init();
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const unsigned tmem = tmem_base;
+  bool ok = true;
+
+  if (warp == 0 && lane == 0) {
+    // Producer.
+    for (int kb = 0; kb < nk && ok; ++kb) {
+      const int s = kb % NSTAGE;
+      if (kb >= NSTAGE) ok = wait_bounded(smem_u32(&empty[s]), ((kb / NSTAGE) - 1) & 1, status);
+      if (!ok) break;
+      const unsigned a = smem_u32(smem + s * (A_STAGE + B_STAGE));
+      const unsigned b = a + A_STAGE;
+      mbar_arrive_expect_tx(smem_u32(&full[s]), A_STAGE + B_STAGE);
+      tma_load_2d(a, &mapA, kb * TK, m0, smem_u32(&full[s]));
+      tma_load_2d(b, &mapB, kb * TK, n0, smem_u32(&full[s]));
+    }
+  } else if (warp == 1 && lane == 0) {
+    // MMA issuer.
+    const unsigned idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((unsigned)(TN >> 3) << 17) | ((unsigned)(TM >> 4) << 24);
+    for (int kb = 0; kb < nk && ok; ++kb) {
+      const int s = kb % NSTAGE;
+      ok = wait_bounded(smem_u32(&full[s]), (kb / NSTAGE) & 1, status);
+      if (!ok) break;
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const unsigned a = smem_u32(smem + s * (A_STAGE + B_STAGE));
+      const unsigned b = a + A_STAGE;
+#pragma unroll
+      for (int kk = 0; kk < TK / 16; ++kk) {
+        const unsigned long long ad = desc_sw128(a + kk * 32), bd = desc_sw128(b + kk * 32);
+        const unsigned acc = (kb > 0 || kk > 0) ? 1u : 0u;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+            "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem),
+            "l"(ad), "l"(bd), "r"(idesc), "r"(acc)
+            : "memory");
+      }
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                       smem_u32(&empty[s]))
+                   : "memory");
+    }
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(&done))
+                 : "memory");
+  } else if (warp >= 2) {
+    // Epilogue: warp w reads TMEM lanes 32 (w % 4) .. + 31.
+    const int q = warp & 3;
+    const bool got = nk > 0 && wait_bounded(smem_u32(&done), 0, status);
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const int m = m0 + q * 32 + lane;
+#pragma unroll 1
+    for (int c0 = 0; c0 < TN; c0 += 16) {
+      unsigned r[16];
+      const unsigned taddr = tmem + ((unsigned)(q * 32) << 16) + (unsigned)c0;
+      asm volatile(
+          "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, "
+          "%13, %14, %15}, [%16];"
+          : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+            "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+          : "r"(taddr));
+      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+      if (m >= M) continue;
+      float* crow = C + (int64_t)m * ldc + n0 + c0;
+      if (n0 + c0 + 16 <= N && (ldc & 3) == 0) {
+#pragma unroll
+        for (int j = 0; j < 16; j += 4) {
+          const float4 v = make_float4(got ? __uint_as_float(r[j]) : 0.f, got ? __uint_as_float(r[j + 1]) : 0.f,
+                                       got ? __uint_as_float(r[j + 2]) : 0.f, got ? __uint_as_float(r[j + 3]) : 0.f);
+          *reinterpret_cast<float4*>(crow + j) = v;
+        }
+      } else {
+#pragma unroll
+        for (int j = 0; j < 16; ++j)
+          if (n0 + c0 + j < N) crow[j] = got ? __uint_as_float(r[j]) : 0.f;
+      }
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  if (__syncthreads_or(ok ? 0 : 1)) drain_grace();
+  if (warp == 0) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TN) : "memory");
+  }
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 get_encode() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    cudaDriverEntryPointQueryResult q;
+    void* p = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  });
+  return fn;
+}
+
+// 2-D BF16 tensor map: `rows` rows of `cols` elements (row stride ld
+// elements), box 64 x box_rows, 128-byte swizzle.
+bool make_map(CUtensorMap* map, const void* base, int64_t rows, int64_t cols, int64_t ld, int box_rows) {
+  auto enc = get_encode();
+  if (!enc) return false;
+  cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+  cuuint64_t strides[1] = {(cuuint64_t)(ld * 2)};
+  cuuint32_t box[2] = {(cuuint32_t)TK, (cuuint32_t)box_rows};
+  cuuint32_t es[2] = {1, 1};
+  return enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides, box, es,
+             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// dst (cols x ldd, BF16) = transpose of src (rows x cols, FP32, row stride lds).
+__global__ void transpose_bf16_kernel(const float* __restrict__ src, int rows, int cols, int64_t lds,
+                                      __nv_bfloat16* __restrict__ dst, int64_t ldd) {
+  __shared__ float tile[32][33];
+  const int r0 = blockIdx.y * 32, c0 = blockIdx.x * 32;
+  for (int i = threadIdx.y; i < 32; i += blockDim.y) {
+    const int r = r0 + i, c = c0 + threadIdx.x;
+    tile[i][threadIdx.x] = (r < rows && c < cols) ? src[(int64_t)r * lds + c] : 0.f;
+  }
+  __syncthreads();
+  for (int i = threadIdx.y; i < 32; i += blockDim.y) {
+    const int c = c0 + i, r = r0 + threadIdx.x;
+    if (c < cols && r < ldd) dst[(int64_t)c * ldd + r] = __float2bfloat16_rn(r < rows ? tile[threadIdx.x][i] : 0.f);
+  }
+}
+
+}  // namespace
+
+constexpr size_t kSmemBytes = (size_t)NSTAGE * (A_STAGE + B_STAGE) + 1024;
+
+// Tensor-map encoding reachable and the kernel's shared-memory opt-in done
+// (once per process, outside any stream capture).
+bool tma_available() {
+  static bool ok = false;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    ok = get_encode() != nullptr &&
+         cudaFuncSetAttribute(tc_tma_bf16_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBytes) ==
+             cudaSuccess;
+  });
+  return ok;
+}
+
+cudaError_t transpose_to_bf16(const float* src, int rows, int cols, int64_t lds, void* dst, int64_t ldd,
+                              cudaStream_t s) {
+  dim3 grid((cols + 31) / 32, (int)((ldd + 31) / 32));
+  if (grid.y > 65535 || ldd < rows) return cudaErrorInvalidValue;
+  transpose_bf16_kernel<<<grid, dim3(32, 8), 0, s>>>(src, rows, cols, lds, static_cast<__nv_bfloat16*>(dst), ldd);
+  return cudaGetLastError();
+}
+
+cudaError_t tc_bf16_tma_gemm(const void* A, int64_t lda, const void* B, int64_t ldb, float* C, int64_t ldc, int M,
+                             int N, int Kd, int* d_status, cudaStream_t s) {
+  if (M <= 0 || N <= 0 || Kd <= 0) return cudaSuccess;
+  // TMA rules: 16-byte aligned bases and row strides (multiples of 8 BF16).
+  if ((reinterpret_cast<uintptr_t>(A) & 15) || (reinterpret_cast<uintptr_t>(B) & 15) || (lda & 7) || (ldb & 7))
+    return cudaErrorInvalidValue;
+  if (!tma_available()) return cudaErrorNotSupported;
+  CUtensorMap ma, mb;
+  if (!make_map(&ma, A, M, Kd, lda, TM) || !make_map(&mb, B, N, Kd, ldb, TN)) return cudaErrorInvalidValue;
+  dim3 grid((N + TN - 1) / TN, (M + TM - 1) / TM);
+  if (grid.y > 65535) return cudaErrorInvalidValue;
+  tc_tma_bf16_kernel<<<grid, TMA_THREADS, kSmemBytes, s>>>(ma, mb, C, ldc, M, N, Kd, d_status);
+  return cudaGetLastError();
+}
+
+}  // namespace plnmf

@@ -45,6 +45,7 @@ class Problem(ctypes.Structure):
 
 FLAG_TC_GRAMS = 1
 FLAG_MULTI_LAUNCH_W = 2
+FLAG_NO_TMA = 4
 
 
 _vp, _i32, _i64, _dp = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.POINTER(ctypes.c_double)
@@ -63,6 +64,7 @@ _SIGS = {
     "nmf_destroy": ([_vp], None),
     "nmf_gram_noalloc": ([_vp, _i32, _i32, _i64, _vp, _vp], _i32),
     "nmf_gemm": ([_i32, _i32, _i32, _vp, _i64, _i32, _vp, _i64, _vp, _i64, _i32, _vp], _i32),
+    "nmf_gemm_bf16": ([_i32, _i32, _i32, _vp, _i64, _vp, _i64, _vp, _i64, _vp], _i32),
     "nmf_status_str": ([_i32], ctypes.c_char_p),
 }
 for _name, (_args, _res) in _SIGS.items():
@@ -214,6 +216,18 @@ def gemm(A, B, C, *, transA=False, prec=PREC_FP32, stream=None):
     K = A.shape[0] if transA else A.shape[1]
     check(lib.nmf_gemm(M, N, K, ptr(A), A.shape[1], 1 if transA else 0, ptr(B), B.shape[1], ptr(C), C.shape[1],
                        prec, _stream_ptr(stream)), "nmf_gemm")
+
+
+def gemm_bf16(A, B, C, *, stream=None):
+    """C = A @ B^T with A (M x K) and B (N x K) torch.bfloat16 device tensors
+    (row strides multiples of 8), C float32 (M x N)."""
+    M, N = C.shape
+    K = A.shape[1]
+    for x in (A, B, C):
+        if x.stride(1) != 1:
+            raise ValueError("rows must be contiguous")
+    check(lib.nmf_gemm_bf16(M, N, K, A.data_ptr(), A.stride(0), B.data_ptr(), B.stride(0), C.data_ptr(),
+                            C.stride(0), _stream_ptr(stream)), "nmf_gemm_bf16")
 
 
 def gram_noalloc(X, S, *, stream=None):

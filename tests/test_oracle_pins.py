@@ -303,3 +303,27 @@ def test_pins_catch_planted_mistakes(monkeypatch):
     Wb, _ = fh.iteration(A, w, H0[:1].astype(np.float64), EPS)
     monkeypatch.undo()
     assert abs(np.linalg.norm(Wb[:, 0]) - 1.0) > 1e-3
+
+
+# --- BF16 rounding (operands of the BF16 form) ---------------------------------
+
+def test_round_bf16_definition_and_library_agree():
+    import torch
+    from oracle.bf16 import round_bf16
+    rng = np.random.default_rng(3)
+    x = np.concatenate([rng.normal(size=20000) * 10.0 ** rng.integers(-6, 6, size=20000),
+                        np.array([0.0, 1.0, 1.0 + 2 ** -8, 1.0 + 3 * 2 ** -8, 1.0 + 2 ** -7, 65504.0])])
+    ref = torch.from_numpy(x.astype(np.float32)).to(torch.bfloat16).to(torch.float64).numpy()
+    assert np.array_equal(round_bf16(x), ref)
+    # ties to even: 1 + 2^-8 is halfway between 1 and 1 + 2^-7 -> 1
+    assert round_bf16(np.array([1.0 + 2 ** -8]))[0] == 1.0
+    assert round_bf16(np.array([1.0 + 3 * 2 ** -8]))[0] == 1.0 + 2 ** -6
+
+
+def test_operand_rounding_hook_is_identity_when_unset():
+    A = _dense(30, 20, 3, 4)
+    W0, H0 = synth.init_factors(5, 30, 20, 4)
+    W, H = fh.normalize_init(W0), H0.astype(np.float64)
+    a = fh.iteration(A, W, H, EPS)
+    b = fh.iteration(A, W, H, EPS, operand_round=lambda x: x)
+    assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
