@@ -95,7 +95,9 @@ typedef struct {
  * the tensor cores. */
 #define NMF_FLAG_TC_GRAMS 1
 /* Run the W update as separate launches per column tile instead of one
- * persistent cooperative launch (the default where the GPU supports it). */
+ * persistent cooperative launch (the default where the GPU supports it and
+ * no CUDA tool such as a kernel profiler is injected into the process:
+ * with CUDA_INJECTION64_PATH set the per-tile launches are always used). */
 #define NMF_FLAG_MULTI_LAUNCH_W 2
 /* BF16 form (NMF_PREC_BF16): take the dense products A^T W and A H^T through
  * the SIMT-staged tensor-core kernel instead of the TMA-fed one (the default

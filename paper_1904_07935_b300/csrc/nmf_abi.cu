@@ -7,6 +7,8 @@
 #include <new>
 #include <vector>
 
+#include <cstdlib>
+
 #include "internal.cuh"
 
 using namespace plnmf;
@@ -416,8 +418,12 @@ nmf_status init_impl(const nmf_problem* p, nmf_ctx* c) {
   }
   CK(normalize_columns(c->W, V, p->K, Kp, c->stream));
   // Persistent W update: probe the cooperative cluster launch once with no
-  // rows (nothing is read or written but the hand-off flags).
-  if (!(p->flags & NMF_FLAG_MULTI_LAUNCH_W) && w_persistent_config(V, Kp, &c->wp)) {
+  // rows (nothing is read or written but the hand-off flags).  Not with a
+  // CUDA tool injected into the process (a kernel profiler): the cooperative
+  // cluster launch has failed under one, taking the context with it, so the
+  // per-tile launches run instead.
+  const bool tool_attached = std::getenv("CUDA_INJECTION64_PATH") != nullptr;
+  if (!(p->flags & NMF_FLAG_MULTI_LAUNCH_W) && !tool_attached && w_persistent_config(V, Kp, &c->wp)) {
     CK(cudaStreamSynchronize(c->stream));
     cudaError_t e = w_persistent_run(c->W, c->P, c->Q, c->Y, 0, c->K, Kp, c->eps, c->d_sync, c->d_status, c->wp,
                                      c->stream);
