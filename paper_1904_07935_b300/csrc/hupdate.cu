@@ -93,6 +93,32 @@ __device__ __forceinline__ void stage_gcols(float* Gc, const float* __restrict__
     }
   }
 }
+// Asynchronous form of stage_gcols for the H update: 16-byte cp.async copies
+// (L2 only) into Gc, committed as one group, so the next tile's block of G
+// loads while the current tile computes.  A chunk of 4 columns entirely in
+// range is copied; one entirely out of range is zero-filled by the copy
+// (source size 0); a chunk straddling K (K not a multiple of 4) is written
+// with plain stores, masked.
+template <int NT>
+__device__ __forceinline__ void prefetch_gcols(float* Gc, const float* __restrict__ G, int Kp, int K, int lo, int Kr) {
+  const int total = Kr * (HT / 4);
+  for (int e = threadIdx.x; e < total; e += NT) {
+    const int j = e >> 2, q = e & 3;
+    const int c = lo + 4 * q;
+    float* d = Gc + j * HT + 4 * q;
+    if (j < K && c < K && c + 3 >= K) {
+#pragma unroll
+      for (int u = 0; u < 4; ++u) d[u] = c + u < K ? G[(int64_t)j * Kp + c + u] : 0.f;
+      continue;
+    }
+    const bool ok = j < K && c + 3 < K;
+    const float* src = ok ? G + (int64_t)j * Kp + c : G;
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(smem_u32(d)), "l"(src), "r"(ok ? 16 : 0)
+                 : "memory");
+  }
+  asm volatile("cp.async.commit_group;" ::: "memory");
+}
+
 constexpr int HL = 4;             // lanes per row
 constexpr int HROWS = 64;         // rows per CTA
 constexpr int HTHREADS = HROWS * HL;
@@ -103,15 +129,15 @@ template <int R>
 __global__ void __launch_bounds__(128) h_update_kernel(float* __restrict__ X, const float* __restrict__ B,
                                                        const float* __restrict__ G, int N, int K, int Kp, float eps,
                                                        int* status) {
-  // Shared memory: Gc (Kr x HT) = G[j][lo + c] for the current tile, zero
-  // beyond K; Xs (32 R x (Kp + 4)) = the CTA's rows, updated in place (row
-  // stride Kp + 4 keeps the 8 rows a warp reads at once on distinct banks).
+  // Shared memory: two Gc buffers (Kr x HT each) = G[j][lo + c] for the
+  // current and the next tile, zero beyond K; Xs (32 R x (Kp + 4)) = the CTA's
+  // rows, updated in place (row stride Kp + 4 keeps the 8 rows a warp reads at
+  // once on distinct banks).
   constexpr int NT = 128, ROWS = 32 * R;
   extern __shared__ __align__(16) float smem[];
   const int Kr = (Kp + HT - 1) / HT * HT;
   const int ldx = Kp + 4;
-  float* Gc = smem;
-  float* Xs = smem + Kr * HT;
+  float* Xs = smem + 2 * Kr * HT;
   const int tid = threadIdx.x;
   const int sub = tid & (HL - 1);
   const int grp = tid >> 2;                               // 0..31
@@ -119,6 +145,7 @@ __global__ void __launch_bounds__(128) h_update_kernel(float* __restrict__ X, co
   const int nrows = min(ROWS, N - row0);
   const unsigned full = 0xffffffffu;
   __shared__ __align__(8) unsigned long long bar;
+  prefetch_gcols<NT>(smem, G, Kp, K, 0, Kr);
   stage_rows_bulk(Xs, ldx, X, row0, nrows, Kp, &bar, status);
   // Row i of the group: local row grp + 32 i (so a warp's 8 groups touch 8
   // consecutive rows for each i).
@@ -132,12 +159,22 @@ __global__ void __launch_bounds__(128) h_update_kernel(float* __restrict__ X, co
     xr[i] = Xs + rl * ldx;
     br[i] = B + (int64_t)(valid[i] ? row0 + rl : row0) * Kp;
   }
+  // R values of the current tile, loaded one tile ahead.
+  float rb[R][4];
+#pragma unroll
+  for (int i = 0; i < R; ++i)
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int c = 4 * sub + q;
+      rb[i][q] = (valid[i] && c < K) ? __ldg(br[i] + c) : 0.f;
+    }
 
-  for (int lo = 0; lo < K; lo += HT) {
+  for (int lo = 0, tb = 0; lo < K; lo += HT, tb ^= 1) {
     const int hi = min(K, lo + HT);
-    __syncthreads();
-    stage_gcols<NT>(Gc, G, Kp, K, lo, Kr);
-    __syncthreads();
+    const float* Gc = smem + tb * Kr * HT;
+    asm volatile("cp.async.wait_group 0;" ::: "memory");
+    __syncthreads();                                      // Gc of this tile landed; the other buffer is free
+    if (lo + HT < K) prefetch_gcols<NT>(smem + (tb ^ 1) * Kr * HT, G, Kp, K, lo + HT, Kr);
     float acc[R][4];
 #pragma unroll
     for (int i = 0; i < R; ++i) {
@@ -148,9 +185,16 @@ __global__ void __launch_bounds__(128) h_update_kernel(float* __restrict__ X, co
       for (int q = 0; q < 4; ++q) {
         const int cl = 4 * sub + q, c = lo + cl;
         acc[i][q] = 0.f;
-        if (valid[i] && c < hi) acc[i][q] = fmaf(1.f - Gc[c * HT + cl], xown[q], __ldg(br[i] + c));
+        if (valid[i] && c < hi) acc[i][q] = fmaf(1.f - Gc[c * HT + cl], xown[q], rb[i][q]);
       }
     }
+#pragma unroll
+    for (int i = 0; i < R; ++i)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int c = lo + HT + 4 * sub + q;
+        rb[i][q] = (valid[i] && c < K) ? __ldg(br[i] + c) : 0.f;
+      }
     // Columns outside the tile: j < lo (new) and j >= lo + HT (old).
     auto outside = [&](int j0, int j1) {
 #pragma unroll 1
@@ -335,7 +379,7 @@ cudaError_t w_prep_run(const float* X, const float* B, const float* G, float* Y,
 template <int R>
 cudaError_t h_update_launch(float* X, const float* B, const float* G, int N, int K, int Kp, float eps, int* status,
                             cudaStream_t s) {
-  const size_t smem = sizeof(float) * ((size_t)((Kp + HT - 1) / HT * HT) * HT + (size_t)32 * R * (Kp + 4));
+  const size_t smem = sizeof(float) * (2 * (size_t)((Kp + HT - 1) / HT * HT) * HT + (size_t)32 * R * (Kp + 4));
   auto kern = h_update_kernel<R>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
@@ -346,12 +390,22 @@ cudaError_t h_update_launch(float* X, const float* B, const float* G, int N, int
 
 cudaError_t h_update_run(float* X, const float* B, const float* G, int N, int K, int Kp, float eps,
                          int* status, cudaStream_t s) {
-  // Rows per lane group: as many as fit, while keeping at least ~one CTA per SM.
+  // Rows per lane group R: register blocking (one 16-byte load of S serves R
+  // rows) only while the grid still gives every SM about three CTAs of four
+  // warps; the in-tile column chain is a dependent shuffle sequence whose
+  // latency needs several resident warps to hide.
+  static int sms = 0;
+  if (sms == 0) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+      sms = 148;
+  }
   const size_t per_row = sizeof(float) * (size_t)(Kp + 4);
   const size_t gc = sizeof(float) * (size_t)((Kp + HT - 1) / HT * HT) * HT;
-  auto fits = [&](int R) { return gc + per_row * 32 * R <= 200 * 1024; };
-  if (fits(4) && (N + 127) / 128 >= 64) return h_update_launch<4>(X, B, G, N, K, Kp, eps, status, s);
-  if (fits(2)) return h_update_launch<2>(X, B, G, N, K, Kp, eps, status, s);
+  auto fits = [&](int R) { return 2 * gc + per_row * 32 * R <= 200 * 1024; };
+  auto enough = [&](int R) { return (long long)(N + 32 * R - 1) / (32 * R) >= 3LL * sms; };
+  if (fits(4) && enough(4)) return h_update_launch<4>(X, B, G, N, K, Kp, eps, status, s);
+  if (fits(2) && enough(2)) return h_update_launch<2>(X, B, G, N, K, Kp, eps, status, s);
   return h_update_launch<1>(X, B, G, N, K, Kp, eps, status, s);
 }
 
