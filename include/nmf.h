@@ -191,6 +191,40 @@ nmf_status nmf_query(nmf_ctx* c, int32_t* tile_T, int32_t* chain_ctas, int32_t* 
 nmf_status nmf_gemm(int32_t M, int32_t N, int32_t K, const float* A, int64_t lda, int32_t transA,
                     const float* B, int64_t ldb, float* C, int64_t ldc, int32_t prec, void* stream);
 
+/* Batched form: many independent problems advanced together (repeated NMF
+ * of many small matrices; the paper motivates repeated factorisation in
+ * Sec. 1).  A batch holds existing contexts ("members"); one CUDA graph
+ * holds one iteration of every member, each member's launches on its own
+ * stream as parallel branches, so the GPU runs the members side by side.
+ *
+ * nmf_batch_create: members must be distinct contexts on distinct streams,
+ *   and `stream` (the batch's launch stream; NULL = a new one owned by the
+ *   batch) must differ from all of them (NMF_EINVAL otherwise, and for
+ *   n < 1).  Members switch to the per-tile W launches (the persistent W
+ *   launch occupies every SM); a member's own single-problem graph is
+ *   re-captured on its next nmf_iterate.  autotune != 0: for each member
+ *   the W column chain's cluster size (4, 8 or 16 CTAs, where the rows fit)
+ *   is chosen by timing three W updates per size and keeping the least
+ *   SM-time (CTAs x time); W is restored, so tuning does not advance the
+ *   factorisation.  Synchronous.  The batch does not own the members:
+ *   destroy the batch before them.
+ * nmf_batch_iterate: n_iters iterations of every member, asynchronous on the
+ *   batch stream; ordered after all work already queued on the members'
+ *   streams, and each member's stream is made to wait for the batch, so
+ *   nmf_error / nmf_get_factors on a member see the result.
+ * nmf_batch_query: member i's chain cluster size and, if autotuned, the
+ *   measured W-update time (microseconds) of the chosen size.
+ * nmf_batch_submit: nmf_init of ps[0..n) (each ps[i].stream NULL or
+ *   distinct), an autotuned batch, n_iters iterations; the contexts are
+ *   returned in outs (caller destroys them); on failure none is returned.
+ *   Returns once the iterations are queued. */
+typedef struct nmf_batch nmf_batch;
+nmf_status nmf_batch_create(nmf_ctx* const* ctxs, int32_t n, int32_t autotune, void* stream, nmf_batch** out);
+nmf_status nmf_batch_iterate(nmf_batch* b, int32_t n_iters);
+nmf_status nmf_batch_query(nmf_batch* b, int32_t i, int32_t* chain_ctas, float* w_update_us);
+void nmf_batch_destroy(nmf_batch* b);
+nmf_status nmf_batch_submit(const nmf_problem* ps, int32_t n, int32_t n_iters, nmf_ctx** outs);
+
 /* BF16 product with TMA-fed tensor-core MMAs (the kernel of the BF16 form,
  * Alg. 1 lines 4 and 10): C (M x N, FP32, row-major, ldc) = A B^T with
  * A row-major M x K (lda) and B row-major N x K (ldb): both operands K-major

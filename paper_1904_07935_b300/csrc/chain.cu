@@ -439,6 +439,25 @@ bool chain_config_for(int N, bool normalize, int T, ChainConfig* cfg) {
   return false;
 }
 
+// Same, for a given cluster size (1..16 CTAs): false when the rows do not fit
+// 4 per thread or the cluster cannot be resident.
+bool chain_config_cluster(int N, int T, int cl, ChainConfig* cfg) {
+  if (T < 1 || T > kMaxChainTile || cl < 1 || cl > kMaxCluster) return false;
+  for (int nt : {256, 512}) {
+    const int nr = nt - 32;
+    const int rpt = (N + cl * nr - 1) / (cl * nr);
+    if (rpt > 4) continue;
+    const int got = nt == 256 ? max_cluster_for<256>(rpt) : max_cluster_for<512>(rpt);
+    if (got < cl) continue;
+    cfg->cluster = cl;
+    cfg->threads = nt;
+    cfg->rpt = rpt;
+    cfg->tt = T;
+    return true;
+  }
+  return false;
+}
+
 cudaError_t chain_run(float* Y, float* X, const float* G, int N, int Kp, int lo, int hi, int prev_lo, float eps,
                       bool normalize, const ChainConfig& cfg, int* d_status, cudaStream_t s) {
   ChainParams p{Y, X, G, N, Kp, lo, hi, prev_lo, eps, d_status, cfg.cluster};

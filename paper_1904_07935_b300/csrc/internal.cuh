@@ -136,6 +136,7 @@ cudaError_t chain_run(float* Y, float* X, const float* G, int N, int Kp, int lo,
                       float eps, bool normalize, const ChainConfig& cfg, int* d_status,
                       cudaStream_t s);
 bool chain_config_for(int N, bool normalize, int T, ChainConfig* cfg);
+bool chain_config_cluster(int N, int T, int cl, ChainConfig* cfg);
 
 // Whole H update in one launch (rows independent): X (N x Kp) old -> new in
 // place, B = R, G = S.

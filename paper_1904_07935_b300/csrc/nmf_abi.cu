@@ -471,6 +471,231 @@ void free_ctx(nmf_ctx* c) {
 
 }  // namespace
 
+// ---------------------------------------------------------------------------
+// Batched form: independent problems advanced together.  One CUDA graph holds
+// one iteration of every member, each member's launches on its own stream
+// (graph branches joined at the end), so the hardware runs the members'
+// kernels side by side on the SMs one small problem leaves idle.  Members
+// use the per-tile W launches: the persistent W kernel occupies every SM.
+// ---------------------------------------------------------------------------
+struct nmf_batch {
+  std::vector<nmf_ctx*> m;
+  cudaStream_t root = nullptr;
+  bool own_root = false;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  cudaEvent_t fork = nullptr, done = nullptr;
+  std::vector<cudaEvent_t> join, ready;
+  std::vector<float> w_us;        // autotuner: W update time of the chosen configuration
+};
+
+namespace {
+
+void free_batch(nmf_batch* b) {
+  if (!b) return;
+  if (b->root) cudaStreamSynchronize(b->root);
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  if (b->graph) cudaGraphDestroy(b->graph);
+  for (auto e : b->join) if (e) cudaEventDestroy(e);
+  for (auto e : b->ready) if (e) cudaEventDestroy(e);
+  if (b->fork) cudaEventDestroy(b->fork);
+  if (b->done) cudaEventDestroy(b->done);
+  if (b->own_root && b->root) cudaStreamDestroy(b->root);
+  delete b;
+}
+
+// Drop a member's cached single-problem graph (it is re-captured on the next
+// nmf_iterate with the member's current W configuration).
+void drop_graph(nmf_ctx* c) {
+  if (c->graph_exec) cudaGraphExecDestroy(c->graph_exec);
+  if (c->graph) cudaGraphDestroy(c->graph);
+  c->graph_exec = nullptr;
+  c->graph = nullptr;
+}
+
+// Autotuner for a batch member: the W update's column chain runs on one
+// cluster of 4, 8 or 16 CTAs; a wider cluster finishes the chain sooner but
+// holds more SMs, which the other members could use.  Each fitting size is
+// timed (three W updates from the same start, CUDA events) and the one with
+// the least SM-time (CTAs x microseconds) is kept.  W is restored afterwards,
+// so tuning does not advance the factorisation.
+cudaError_t autotune_member(nmf_ctx* c, float* w_us_out) {
+  const size_t bytes = sizeof(float) * (size_t)c->V * c->Kp;
+  float* saved = nullptr;
+  cudaError_t e = cudaMalloc(&saved, bytes);
+  if (e != cudaSuccess) return e;
+  cudaEvent_t t0 = nullptr, t1 = nullptr;
+  auto fail = [&](cudaError_t err) {
+    if (t0) cudaEventDestroy(t0);
+    if (t1) cudaEventDestroy(t1);
+    cudaFree(saved);
+    return err;
+  };
+  if ((e = cudaEventCreate(&t0)) != cudaSuccess || (e = cudaEventCreate(&t1)) != cudaSuccess) return fail(e);
+  if ((e = cudaMemcpyAsync(saved, c->W, bytes, cudaMemcpyDeviceToDevice, c->stream)) != cudaSuccess) return fail(e);
+  // P and Q of the current H: the W update's inputs.
+  if ((e = enq_product_P(c)) != cudaSuccess) return fail(e);
+  if ((e = enq_gram(c, c->gramH, c->Ht, c->Q)) != cudaSuccess) return fail(e);
+  ChainConfig best = c->chainW;
+  float best_cost = INFINITY, best_us = 0.f;
+  for (int cl : {16, 8, 4}) {
+    ChainConfig cfg;
+    if (!chain_config_cluster(c->V, kRowTile, cl, &cfg)) continue;
+    c->chainW = cfg;
+    // warm-up, then three timed updates
+    for (int rep = 0; rep < 4; ++rep) {
+      if ((e = cudaMemcpyAsync(c->W, saved, bytes, cudaMemcpyDeviceToDevice, c->stream)) != cudaSuccess) return fail(e);
+      if (rep == 1 && (e = cudaEventRecord(t0, c->stream)) != cudaSuccess) return fail(e);
+      if ((e = enq_update(c, c->W, c->Q, c->P, c->V, true)) != cudaSuccess) return fail(e);
+    }
+    if ((e = cudaEventRecord(t1, c->stream)) != cudaSuccess) return fail(e);
+    if ((e = cudaEventSynchronize(t1)) != cudaSuccess) return fail(e);
+    float ms = 0.f;
+    if ((e = cudaEventElapsedTime(&ms, t0, t1)) != cudaSuccess) return fail(e);
+    const float us = ms * 1000.f / 3.f;       // includes the three restoring copies (same for every size)
+    const float cost = us * (float)cl;
+    if (cost < best_cost) {
+      best_cost = cost;
+      best = cfg;
+      best_us = us;
+    }
+  }
+  c->chainW = best;
+  *w_us_out = best_us;
+  if ((e = cudaMemcpyAsync(c->W, saved, bytes, cudaMemcpyDeviceToDevice, c->stream)) != cudaSuccess) return fail(e);
+  if ((e = cudaStreamSynchronize(c->stream)) != cudaSuccess) return fail(e);
+  return fail(cudaSuccess);
+}
+
+}  // namespace
+
+extern "C" {
+
+nmf_status nmf_batch_create(nmf_ctx* const* ctxs, int32_t n, int32_t autotune, void* stream, nmf_batch** out) {
+  if (!ctxs || n < 1 || !out) return NMF_EINVAL;
+  *out = nullptr;
+  for (int i = 0; i < n; ++i) {
+    if (!ctxs[i]) return NMF_EINVAL;
+    for (int j = 0; j < i; ++j)
+      if (ctxs[j] == ctxs[i] || ctxs[j]->stream == ctxs[i]->stream) return NMF_EINVAL;
+  }
+  nmf_batch* b = new (std::nothrow) nmf_batch;
+  if (!b) return NMF_ENOMEM;
+  b->m.assign(ctxs, ctxs + n);
+  b->w_us.assign(n, 0.f);
+  cudaError_t e = cudaSuccess;
+  auto bail = [&](cudaError_t err) {
+    cudaGetLastError();
+    free_batch(b);
+    return from_cuda(err);
+  };
+  if (stream) {
+    b->root = static_cast<cudaStream_t>(stream);
+    for (auto* c : b->m)
+      if (c->stream == b->root) {
+        free_batch(b);
+        return NMF_EINVAL;
+      }
+  } else {
+    if ((e = cudaStreamCreateWithFlags(&b->root, cudaStreamNonBlocking)) != cudaSuccess) return bail(e);
+    b->own_root = true;
+  }
+  if ((e = cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming)) != cudaSuccess) return bail(e);
+  if ((e = cudaEventCreateWithFlags(&b->done, cudaEventDisableTiming)) != cudaSuccess) return bail(e);
+  b->join.assign(n, nullptr);
+  b->ready.assign(n, nullptr);
+  for (int i = 0; i < n; ++i) {
+    if ((e = cudaEventCreateWithFlags(&b->join[i], cudaEventDisableTiming)) != cudaSuccess) return bail(e);
+    if ((e = cudaEventCreateWithFlags(&b->ready[i], cudaEventDisableTiming)) != cudaSuccess) return bail(e);
+  }
+  for (int i = 0; i < n; ++i) {
+    nmf_ctx* c = b->m[i];
+    c->w_persistent = false;
+    drop_graph(c);
+    if (!c->s_valid) {
+      if ((e = enq_gram(c, c->gramW, c->W, c->S)) != cudaSuccess) return bail(e);
+      c->s_valid = true;
+    }
+    if (autotune) {
+      if ((e = autotune_member(c, &b->w_us[i])) != cudaSuccess) return bail(e);
+    }
+    if ((e = cudaStreamSynchronize(c->stream)) != cudaSuccess) return bail(e);
+  }
+  // Capture one iteration of every member as branches of one graph.
+  if ((e = cudaStreamBeginCapture(b->root, cudaStreamCaptureModeThreadLocal)) != cudaSuccess) return bail(e);
+  cudaError_t ce = cudaEventRecord(b->fork, b->root);
+  for (int i = 0; i < n && ce == cudaSuccess; ++i) {
+    nmf_ctx* c = b->m[i];
+    if ((ce = cudaStreamWaitEvent(c->stream, b->fork, 0)) != cudaSuccess) break;
+    c->launch_count = 0;
+    if ((ce = enq_iteration(c)) != cudaSuccess) break;
+    c->launches_per_iter = c->launch_count;
+    if ((ce = cudaEventRecord(b->join[i], c->stream)) != cudaSuccess) break;
+    ce = cudaStreamWaitEvent(b->root, b->join[i], 0);
+  }
+  cudaGraph_t g = nullptr;
+  e = cudaStreamEndCapture(b->root, &g);
+  if (ce != cudaSuccess || e != cudaSuccess) {
+    if (g) cudaGraphDestroy(g);
+    return bail(ce != cudaSuccess ? ce : e);
+  }
+  b->graph = g;
+  if ((e = cudaGraphInstantiate(&b->exec, g, 0)) != cudaSuccess) return bail(e);
+  *out = b;
+  return NMF_OK;
+}
+
+nmf_status nmf_batch_iterate(nmf_batch* b, int32_t n_iters) {
+  if (!b || n_iters < 0) return NMF_EINVAL;
+  if (n_iters == 0) return NMF_OK;
+  const int n = (int)b->m.size();
+  // Order after whatever the members' own streams hold (factor uploads, ...).
+  for (int i = 0; i < n; ++i) {
+    CK(cudaEventRecord(b->ready[i], b->m[i]->stream));
+    CK(cudaStreamWaitEvent(b->root, b->ready[i], 0));
+  }
+  for (int it = 0; it < n_iters; ++it) CK(cudaGraphLaunch(b->exec, b->root));
+  CK(cudaEventRecord(b->done, b->root));
+  for (auto* c : b->m) {
+    CK(cudaStreamWaitEvent(c->stream, b->done, 0));
+    c->iters_run += n_iters;
+  }
+  return NMF_OK;
+}
+
+nmf_status nmf_batch_query(nmf_batch* b, int32_t i, int32_t* chain_ctas, float* w_update_us) {
+  if (!b || i < 0 || i >= (int)b->m.size()) return NMF_EINVAL;
+  if (chain_ctas) *chain_ctas = b->m[i]->chainW.cluster;
+  if (w_update_us) *w_update_us = b->w_us[i];
+  return NMF_OK;
+}
+
+void nmf_batch_destroy(nmf_batch* b) { free_batch(b); }
+
+nmf_status nmf_batch_submit(const nmf_problem* ps, int32_t n, int32_t n_iters, nmf_ctx** outs) {
+  if (!ps || n < 1 || n_iters < 0 || !outs) return NMF_EINVAL;
+  for (int i = 0; i < n; ++i) outs[i] = nullptr;
+  auto undo = [&](nmf_status st) {
+    for (int i = 0; i < n; ++i) {
+      nmf_destroy(outs[i]);
+      outs[i] = nullptr;
+    }
+    return st;
+  };
+  for (int i = 0; i < n; ++i) {
+    const nmf_status st = nmf_init(&ps[i], &outs[i]);
+    if (st != NMF_OK) return undo(st);
+  }
+  nmf_batch* b = nullptr;
+  nmf_status st = nmf_batch_create(outs, n, 1, nullptr, &b);
+  if (st != NMF_OK) return undo(st);
+  st = nmf_batch_iterate(b, n_iters);
+  nmf_batch_destroy(b);       // waits for the batch's launches
+  return st == NMF_OK ? NMF_OK : undo(st);
+}
+
+}  // extern "C"
+
 extern "C" {
 
 const char* nmf_status_str(int32_t s) {

@@ -65,6 +65,11 @@ _SIGS = {
     "nmf_gram_noalloc": ([_vp, _i32, _i32, _i64, _vp, _vp], _i32),
     "nmf_gemm": ([_i32, _i32, _i32, _vp, _i64, _i32, _vp, _i64, _vp, _i64, _i32, _vp], _i32),
     "nmf_gemm_bf16": ([_i32, _i32, _i32, _vp, _i64, _vp, _i64, _vp, _i64, _vp], _i32),
+    "nmf_batch_create": ([_vp, _i32, _i32, _vp, _vp], _i32),
+    "nmf_batch_iterate": ([_vp, _i32], _i32),
+    "nmf_batch_query": ([_vp, _i32, _vp, _vp], _i32),
+    "nmf_batch_destroy": ([_vp], None),
+    "nmf_batch_submit": ([_vp, _i32, _i32, _vp], _i32),
     "nmf_status_str": ([_i32], ctypes.c_char_p),
 }
 for _name, (_args, _res) in _SIGS.items():
@@ -107,26 +112,39 @@ def _stream_ptr(stream) -> int | None:
     return int(stream)
 
 
+def problem_struct(V, D, K, *, dense=None, ld=None, row_ptr=None, col_idx=None, val=None, W0=None, H0=None,
+                   seed=0, eps=0.0, tile_T=0, prec=PREC_FP32, stream=None, flags=0):
+    """nmf_problem for device tensors; returns (struct, objects to keep alive)."""
+    p = Problem()
+    p.V, p.D, p.K = V, D, K
+    keep = [dense, row_ptr, col_idx, val, W0, H0]
+    if dense is not None:
+        p.fmt = DENSE_F32
+        p.dense = ptr(dense)
+        p.ld = D if ld is None else ld
+    else:
+        p.fmt = CSR_F32_I32
+        p.row_ptr, p.col_idx, p.val = ptr(row_ptr), ptr(col_idx), ptr(val)
+        p.nnz = int(val.shape[0]) if val is not None else 0
+    p.W0, p.H0 = ptr(W0), ptr(H0)
+    p.seed, p.eps, p.tile_T, p.prec = seed, eps, tile_T, prec
+    p.stream = _stream_ptr(stream)
+    p.flags = flags
+    return p, keep
+
+
 class Nmf:
     """One factorisation context (nmf_ctx)."""
 
     def __init__(self, V, D, K, *, dense=None, ld=None, row_ptr=None, col_idx=None, val=None,
-                 W0=None, H0=None, seed=0, eps=0.0, tile_T=0, prec=PREC_FP32, stream=None, flags=0):
-        p = Problem()
-        p.V, p.D, p.K = V, D, K
-        self._keep = [dense, row_ptr, col_idx, val, W0, H0]
-        if dense is not None:
-            p.fmt = DENSE_F32
-            p.dense = ptr(dense)
-            p.ld = D if ld is None else ld
-        else:
-            p.fmt = CSR_F32_I32
-            p.row_ptr, p.col_idx, p.val = ptr(row_ptr), ptr(col_idx), ptr(val)
-            p.nnz = int(val.shape[0]) if val is not None else 0
-        p.W0, p.H0 = ptr(W0), ptr(H0)
-        p.seed, p.eps, p.tile_T, p.prec = seed, eps, tile_T, prec
-        p.stream = _stream_ptr(stream)
-        p.flags = flags
+                 W0=None, H0=None, seed=0, eps=0.0, tile_T=0, prec=PREC_FP32, stream=None, flags=0, _handle=None):
+        if _handle is not None:                      # adopt a context made by nmf_batch_submit
+            self.h, self._keep = _handle, []
+            self.V, self.D, self.K = V, D, K
+            return
+        p, self._keep = problem_struct(V, D, K, dense=dense, ld=ld, row_ptr=row_ptr, col_idx=col_idx, val=val,
+                                       W0=W0, H0=H0, seed=seed, eps=eps, tile_T=tile_T, prec=prec,
+                                       stream=stream, flags=flags)
         h = ctypes.c_void_p()
         check(lib.nmf_init(ctypes.byref(p), ctypes.byref(h)), "nmf_init")
         self.h = h
@@ -216,6 +234,63 @@ def gemm(A, B, C, *, transA=False, prec=PREC_FP32, stream=None):
     K = A.shape[0] if transA else A.shape[1]
     check(lib.nmf_gemm(M, N, K, ptr(A), A.shape[1], 1 if transA else 0, ptr(B), B.shape[1], ptr(C), C.shape[1],
                        prec, _stream_ptr(stream)), "nmf_gemm")
+
+
+class Batch:
+    """Contexts advanced together by one CUDA graph (nmf_batch)."""
+
+    def __init__(self, members, *, autotune=True, stream=None):
+        arr = (ctypes.c_void_p * len(members))(*[m.h.value for m in members])
+        h = ctypes.c_void_p()
+        check(lib.nmf_batch_create(arr, len(members), 1 if autotune else 0, _stream_ptr(stream), ctypes.byref(h)),
+              "nmf_batch_create")
+        self.h = h
+        self.members = list(members)
+
+    def iterate(self, n=1):
+        check(lib.nmf_batch_iterate(self.h, n), "nmf_batch_iterate")
+
+    def query(self, i):
+        """(chain cluster size, autotuned W-update microseconds) of member i."""
+        cl, us = ctypes.c_int32(), ctypes.c_float()
+        check(lib.nmf_batch_query(self.h, i, ctypes.byref(cl), ctypes.byref(us)), "nmf_batch_query")
+        return cl.value, us.value
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib.nmf_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        self.close()
+
+
+def sparse_device(prob, device="cuda"):
+    """CSR arrays of a synth.SparseProblem on the device (torch tensors)."""
+    import torch
+    A = prob.A
+    return (torch.from_numpy(A.row_ptr).to(device), torch.from_numpy(A.col_idx).to(device),
+            torch.from_numpy(A.val).to(device))
+
+
+def batch_submit(specs, n_iters):
+    """nmf_batch_submit.  specs: list of dicts of problem_struct keyword
+    arguments (V, D, K and the device arrays).  Returns Nmf objects owning the
+    contexts."""
+    structs, keep = [], []
+    for s in specs:
+        p, k = problem_struct(**s)
+        structs.append(p)
+        keep.append(k)
+    arr = (Problem * len(structs))(*structs)
+    outs = (ctypes.c_void_p * len(structs))()
+    check(lib.nmf_batch_submit(arr, len(structs), n_iters, outs), "nmf_batch_submit")
+    res = []
+    for s, k, h in zip(specs, keep, outs):
+        m = Nmf(s["V"], s["D"], s["K"], _handle=ctypes.c_void_p(h))
+        m._keep = k
+        res.append(m)
+    return res
 
 
 def gemm_bf16(A, B, C, *, stream=None):
