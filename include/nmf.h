@@ -225,6 +225,59 @@ nmf_status nmf_batch_query(nmf_batch* b, int32_t i, int32_t* chain_ctas, float* 
 void nmf_batch_destroy(nmf_batch* b);
 nmf_status nmf_batch_submit(const nmf_problem* ps, int32_t n, int32_t n_iters, nmf_ctx** outs);
 
+/* Learned warm start for new documents with W fixed (fixed-W H subproblem).
+ * With W fixed, repeating the H loop of Alg. 1 (lines 4-8; S = W^T W) is
+ * exact coordinate descent on min_{h >= eps} ||a - W h||^2 per document and
+ * converges to the unique optimum h*.  A small network predicts a starting
+ * h from r = W^T a so that fewer sweeps are needed.  The network (not in the
+ * paper): K -> hidden -> hidden -> K,
+ *   z1 = x W1 + b1, a1 = GELU(z1), z2 = a1 W2 + b2, a2 = GELU(z2),
+ *   z3 = a2 W3 + b3, y = softplus(z3)
+ * with GELU(x) = x Phi(x) (erf form), softplus(x) = log(1 + e^x), = x above
+ * 20; parameters [W1, b1, W2, b2, W3, b3], Wl row-major n_in x n_out, FP32.
+ * Products on the tensor cores with BF16 operands and FP32 accumulation;
+ * master weights, Adam state and elementwise work FP32.
+ *
+ * nmf_mlp_create: K and hidden positive multiples of 8 (row strides of the
+ *   BF16 operands), NMF_EINVAL otherwise; He-uniform weights
+ *   U(-sqrt(6/n_in), sqrt(6/n_in)) from SplitMix64 draws of seed + layer,
+ *   zero biases.  NMF_EUNSUPPORTED without tensor-map support.
+ * nmf_mlp_set_params / nmf_mlp_get_params: six arrays (host or device),
+ *   sizes K*hidden, hidden, hidden*hidden, hidden, hidden*K, K.  Synchronous.
+ * nmf_mlp_forward: Y (rows x K) = network(X (rows x K)); X device, Y host or
+ *   device; asynchronous on `stream`.
+ * nmf_mlp_grads: gradients of the mean squared error mean((y - T)^2) over
+ *   rows x K at the current parameters into grads[0..5] (host or device;
+ *   NULL entries skipped) and the loss into *loss.  X host or device, T
+ *   device.  Synchronous.
+ * nmf_mlp_train_step: one Adam step (beta1 0.9, beta2 0.999, eps 1e-8, bias
+ *   corrected) on that loss; X host or device, T device; asynchronous on
+ *   `stream` unless loss is non-NULL (then it synchronises to return it).
+ *
+ * nmf_warm_h: new documents `new_docs` (CSR, V = fixedW's V word rows,
+ *   D = N documents, K = fixedW's K) against the current W of `fixedW`:
+ *   R = A_new^T W (SpMM), h0 = network(R) (mlp != NULL) or, cold, SplitMix
+ *   U[0,1) draws as nmf_init draws H (seed = new_docs->seed); then sweeps of
+ *   the H loop with S = W^T W fixed until the stopping value is <= tol or
+ *   max_sweeps sweeps ran.  Stopping value: with H_ref (K x N row-major,
+ *   host or device) ||H - H_ref||_F / ||H_ref||_F, else the relative change
+ *   ||H_s - H_{s-1}||_F / ||H_{s-1}||_F.  Outputs: H_out (K x N row-major,
+ *   host or device), R_out (N x K row-major, optional), *sweeps_out, and
+ *   trace[s] = the stopping value after sweep s + 1 (optional, max_sweeps
+ *   doubles).  W and the context's own H are not changed.  Synchronous. */
+typedef struct nmf_mlp nmf_mlp;
+nmf_status nmf_mlp_create(int32_t K, int32_t hidden, uint64_t seed, nmf_mlp** out);
+nmf_status nmf_mlp_set_params(nmf_mlp* n, const float* const* params);
+nmf_status nmf_mlp_get_params(nmf_mlp* n, float* const* params);
+nmf_status nmf_mlp_forward(nmf_mlp* n, const float* X, int32_t rows, float* Y, void* stream);
+nmf_status nmf_mlp_grads(nmf_mlp* n, const float* X, const float* T, int32_t rows, float* const* grads,
+                         double* loss);
+nmf_status nmf_mlp_train_step(nmf_mlp* n, const float* X, const float* T, int32_t rows, float lr, double* loss,
+                              void* stream);
+void nmf_mlp_destroy(nmf_mlp* n);
+nmf_status nmf_warm_h(nmf_ctx* fixedW, nmf_mlp* mlp, const nmf_problem* new_docs, float tol, int32_t max_sweeps,
+                      const float* H_ref, float* H_out, float* R_out, int32_t* sweeps_out, double* trace);
+
 /* BF16 product with TMA-fed tensor-core MMAs (the kernel of the BF16 form,
  * Alg. 1 lines 4 and 10): C (M x N, FP32, row-major, ldc) = A B^T with
  * A row-major M x K (lda) and B row-major N x K (ldb): both operands K-major

@@ -12,6 +12,12 @@ whose definition is fixed here so that the GPU kernels can be checked:
   theta <- theta - lr * (m / (1 - b1^t)) / (sqrt(v / (1 - b2^t)) + eps).
 
 Layer l maps x (B x n_in) to x @ Wl + bl with Wl stored n_in x n_out.
+
+``operand_round`` (e.g. bf16.round_bf16) rounds the two operands of every
+matrix product (three in the forward pass, six in the backward pass) before
+they are multiplied exactly in FP64; biases, activations, their derivatives
+and the bias gradients stay unrounded.  This defines the reduced-precision-
+product form of the network that the tensor-core kernels compute.
 """
 
 from __future__ import annotations
@@ -41,15 +47,20 @@ def softplus_grad(x):
     return np.where(x > SOFTPLUS_THRESHOLD, 1.0, 1.0 / (1.0 + np.exp(-x)))
 
 
-def forward(params, x):
+def _ident(a):
+    return a
+
+
+def forward(params, x, operand_round=None):
     """params = [W1, b1, W2, b2, W3, b3]; returns (y, cache)."""
+    r = operand_round or _ident
     W1, b1, W2, b2, W3, b3 = [np.asarray(p, dtype=np.float64) for p in params]
     x = np.asarray(x, dtype=np.float64)
-    z1 = x @ W1 + b1
+    z1 = r(x) @ r(W1) + b1
     a1 = gelu(z1)
-    z2 = a1 @ W2 + b2
+    z2 = r(a1) @ r(W2) + b2
     a2 = gelu(z2)
-    z3 = a2 @ W3 + b3
+    z3 = r(a2) @ r(W3) + b3
     y = softplus(z3)
     return y, (x, z1, a1, z2, a2, z3)
 
@@ -59,22 +70,23 @@ def loss(params, x, target):
     return float(np.mean((y - np.asarray(target, dtype=np.float64)) ** 2))
 
 
-def backward(params, cache, y, target):
+def backward(params, cache, y, target, operand_round=None):
     """Gradients of the mean-squared loss w.r.t. [W1, b1, W2, b2, W3, b3]."""
+    r = operand_round or _ident
     W1, b1, W2, b2, W3, b3 = [np.asarray(p, dtype=np.float64) for p in params]
     x, z1, a1, z2, a2, z3 = cache
     n = y.size
     dy = 2.0 * (y - np.asarray(target, dtype=np.float64)) / n
     dz3 = dy * softplus_grad(z3)
-    gW3 = a2.T @ dz3
+    gW3 = r(a2).T @ r(dz3)
     gb3 = dz3.sum(axis=0)
-    da2 = dz3 @ W3.T
+    da2 = r(dz3) @ r(W3).T
     dz2 = da2 * gelu_grad(z2)
-    gW2 = a1.T @ dz2
+    gW2 = r(a1).T @ r(dz2)
     gb2 = dz2.sum(axis=0)
-    da1 = dz2 @ W2.T
+    da1 = r(dz2) @ r(W2).T
     dz1 = da1 * gelu_grad(z1)
-    gW1 = x.T @ dz1
+    gW1 = r(x).T @ r(dz1)
     gb1 = dz1.sum(axis=0)
     return [gW1, gb1, gW2, gb2, gW3, gb3]
 

@@ -188,4 +188,19 @@ cudaError_t sumsq_dense_f64(const float* A, int64_t rows, int64_t cols, int64_t 
 cudaError_t transpose_f32(const float* src, int rows, int cols, int lds, float* dst, int ldd,
                           cudaStream_t s);
 
+// ---------------------------------------------------------------------------
+// Warm start (warmstart.cu).
+// ---------------------------------------------------------------------------
+cudaError_t scale_shift(float* x, int64_t n, float a, float b, cudaStream_t s);
+// h_out[0] = sum (H - Href)^2, h_out[1] = sum Href^2 (sum H^2 without Href),
+// over rows x K of row-stride-ld buffers; FP64; synchronises the stream.
+// d_part holds diff_norm_partials() doubles.
+cudaError_t diff_norm(const float* H, const float* Href, int rows, int K, int ld, double* d_part, double* h_out,
+                      cudaStream_t s);
+size_t diff_norm_partials();
+// Network forward of `rows` inputs x (row stride ldx) into y (row stride ldy).
+cudaError_t mlp_forward_dev(nmf_mlp* n, const float* x, int64_t ldx, int rows, float* y, int64_t ldy,
+                            cudaStream_t s);
+int mlp_K(const nmf_mlp* n);
+
 }  // namespace plnmf

@@ -760,6 +760,107 @@ nmf_status nmf_iterate(nmf_ctx* c, int32_t n_iters) {
   return NMF_OK;
 }
 
+nmf_status nmf_warm_h(nmf_ctx* c, nmf_mlp* mlp, const nmf_problem* nd, float tol, int32_t max_sweeps,
+                      const float* H_ref, float* H_out, float* R_out, int32_t* sweeps_out, double* trace) {
+  if (!c || !nd || !H_out || max_sweeps < 0 || !(tol >= 0.f)) return NMF_EINVAL;
+  if (nd->fmt != NMF_CSR_F32_I32 || nd->V != c->V || nd->K != c->K || nd->D < 1) return NMF_EINVAL;
+  if (mlp && mlp_K(mlp) != c->K) return NMF_EINVAL;
+  const int V = c->V, N = nd->D, K = c->K, Kp = c->Kp;
+  cudaStream_t s = c->stream;
+  std::vector<int> rp, ci;
+  std::vector<float> va;
+  double normA2 = 0.0;
+  nmf_status st = validate_and_copy_csr(nd, rp, ci, va, &normA2);
+  if (st != NMF_OK) return st;
+  // CSR of A_new^T (documents as rows), stable counting sort.
+  const int64_t nnz = nd->nnz;
+  std::vector<int> rpT((size_t)N + 1, 0), ciT((size_t)nnz);
+  std::vector<float> vaT((size_t)nnz);
+  for (int64_t e = 0; e < nnz; ++e) rpT[(size_t)ci[e] + 1]++;
+  for (int d = 0; d < N; ++d) rpT[d + 1] += rpT[d];
+  {
+    std::vector<int> fill(rpT.begin(), rpT.end() - 1);
+    for (int r = 0; r < V; ++r)
+      for (int e = rp[r]; e < rp[r + 1]; ++e) {
+        const int pos = fill[ci[e]]++;
+        ciT[pos] = r;
+        vaT[pos] = va[e];
+      }
+  }
+  int* d_ciT = nullptr;
+  float* d_vaT = nullptr;
+  float *Rn = nullptr, *Hn = nullptr, *Hp = nullptr, *Hr = nullptr, *tmp = nullptr;
+  double* part = nullptr;
+  SpmmPlan plan;
+  auto cleanup = [&](nmf_status r) {
+    cudaStreamSynchronize(s);
+    spmm_plan_free(plan);
+    for (void* q : {(void*)d_ciT, (void*)d_vaT, (void*)Rn, (void*)Hn, (void*)Hp, (void*)Hr, (void*)tmp, (void*)part})
+      if (q) cudaFree(q);
+    return r;
+  };
+#define WK(x)                                     \
+  do {                                            \
+    const cudaError_t e_ = (x);                   \
+    if (e_ != cudaSuccess) {                      \
+      cudaGetLastError();                         \
+      return cleanup(from_cuda(e_));              \
+    }                                             \
+  } while (0)
+  const size_t nk = (size_t)N * Kp;
+  WK(cudaMalloc(&d_ciT, sizeof(int) * std::max<size_t>(1, ciT.size())));
+  WK(cudaMalloc(&d_vaT, sizeof(float) * std::max<size_t>(1, vaT.size())));
+  if (nnz > 0) {
+    WK(cudaMemcpy(d_ciT, ciT.data(), sizeof(int) * ciT.size(), cudaMemcpyHostToDevice));
+    WK(cudaMemcpy(d_vaT, vaT.data(), sizeof(float) * vaT.size(), cudaMemcpyHostToDevice));
+  }
+  WK(spmm_plan_build(plan, rpT, N, V, Kp, 512));
+  WK(cudaMalloc(&Rn, sizeof(float) * nk));
+  WK(cudaMalloc(&Hn, sizeof(float) * nk));
+  WK(cudaMalloc(&tmp, sizeof(float) * std::max(nk, (size_t)K * N)));
+  WK(cudaMalloc(&part, sizeof(double) * diff_norm_partials()));
+  WK(cudaMemsetAsync(Hn, 0, sizeof(float) * nk, s));
+  if (H_ref) {
+    WK(cudaMalloc(&Hr, sizeof(float) * nk));
+    WK(cudaMemcpyAsync(tmp, H_ref, sizeof(float) * (size_t)K * N, cudaMemcpyDefault, s));
+    WK(cudaMemsetAsync(Hr, 0, sizeof(float) * nk, s));
+    WK(transpose_f32(tmp, K, N, N, Hr, Kp, s));
+  } else {
+    WK(cudaMalloc(&Hp, sizeof(float) * nk));
+  }
+  // S = W^T W of the fixed W; R = A_new^T W.
+  if (!c->s_valid) {
+    WK(enq_gram(c, c->gramW, c->W, c->S));
+    c->s_valid = true;
+  }
+  WK(spmm_run(plan, d_ciT, d_vaT, c->W, Rn, Kp, s));
+  if (R_out) WK(cudaMemcpy2DAsync(R_out, sizeof(float) * K, Rn, sizeof(float) * Kp, sizeof(float) * K, N,
+                                  cudaMemcpyDefault, s));
+  if (mlp) {
+    WK(mlp_forward_dev(mlp, Rn, Kp, N, Hn, Kp, s));
+  } else {
+    WK(fill_uniform_splitmix_t(Hn, N, K, Kp, nd->seed ^ 0x4848484848484848ull, s));
+  }
+  int done = 0;
+  for (int sw = 1; sw <= max_sweeps; ++sw) {
+    if (!H_ref) WK(cudaMemcpyAsync(Hp, Hn, sizeof(float) * nk, cudaMemcpyDeviceToDevice, s));
+    WK(h_update_run(Hn, Rn, c->S, N, K, Kp, c->eps, c->d_status, s));
+    double o[2] = {0.0, 0.0};
+    WK(diff_norm(Hn, H_ref ? Hr : Hp, N, K, Kp, part, o, s));
+    const double val = o[1] > 0.0 ? std::sqrt(o[0] / o[1]) : std::sqrt(o[0]);
+    if (trace) trace[sw - 1] = val;
+    done = sw;
+    if (val <= (double)tol) break;
+  }
+  WK(transpose_f32(Hn, N, K, Kp, tmp, N, s));
+  WK(cudaMemcpyAsync(H_out, tmp, sizeof(float) * (size_t)K * N, cudaMemcpyDefault, s));
+  WK(cudaStreamSynchronize(s));
+#undef WK
+  if (sweeps_out) *sweeps_out = done;
+  const nmf_status rs = read_status(c);
+  return cleanup(rs);
+}
+
 nmf_status nmf_error(nmf_ctx* c, double* frob2, double* rel) {
   if (!c) return NMF_EINVAL;
   if (c->iters_run == 0) {

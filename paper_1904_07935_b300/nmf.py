@@ -70,6 +70,14 @@ _SIGS = {
     "nmf_batch_query": ([_vp, _i32, _vp, _vp], _i32),
     "nmf_batch_destroy": ([_vp], None),
     "nmf_batch_submit": ([_vp, _i32, _i32, _vp], _i32),
+    "nmf_mlp_create": ([_i32, _i32, ctypes.c_uint64, _vp], _i32),
+    "nmf_mlp_set_params": ([_vp, _vp], _i32),
+    "nmf_mlp_get_params": ([_vp, _vp], _i32),
+    "nmf_mlp_forward": ([_vp, _vp, _i32, _vp, _vp], _i32),
+    "nmf_mlp_grads": ([_vp, _vp, _vp, _i32, _vp, _vp], _i32),
+    "nmf_mlp_train_step": ([_vp, _vp, _vp, _i32, ctypes.c_float, _vp, _vp], _i32),
+    "nmf_mlp_destroy": ([_vp], None),
+    "nmf_warm_h": ([_vp, _vp, _vp, ctypes.c_float, _i32, _vp, _vp, _vp, _vp, _vp], _i32),
     "nmf_status_str": ([_i32], ctypes.c_char_p),
 }
 for _name, (_args, _res) in _SIGS.items():
@@ -291,6 +299,84 @@ def batch_submit(specs, n_iters):
         m._keep = k
         res.append(m)
     return res
+
+
+class Mlp:
+    """Warm-start network K -> hidden -> hidden -> K (nmf_mlp)."""
+
+    def __init__(self, K, hidden=256, seed=0):
+        h = ctypes.c_void_p()
+        check(lib.nmf_mlp_create(K, hidden, seed, ctypes.byref(h)), "nmf_mlp_create")
+        self.h, self.K, self.hidden = h, K, hidden
+
+    def shapes(self):
+        K, H = self.K, self.hidden
+        return [(K, H), (H,), (H, H), (H,), (H, K), (K,)]
+
+    def set_params(self, params):
+        arrs = [np.ascontiguousarray(p, dtype=np.float32) for p in params]
+        for a, s in zip(arrs, self.shapes()):
+            if a.shape != s:
+                raise ValueError(f"parameter shape {a.shape} != {s}")
+        ptrs = (ctypes.c_void_p * 6)(*[a.ctypes.data for a in arrs])
+        check(lib.nmf_mlp_set_params(self.h, ptrs), "nmf_mlp_set_params")
+
+    def get_params(self):
+        arrs = [np.empty(s, dtype=np.float32) for s in self.shapes()]
+        ptrs = (ctypes.c_void_p * 6)(*[a.ctypes.data for a in arrs])
+        check(lib.nmf_mlp_get_params(self.h, ptrs), "nmf_mlp_get_params")
+        return arrs
+
+    def forward(self, X, Y=None, stream=None):
+        """X: rows x K float32 CUDA tensor; returns Y (CUDA tensor)."""
+        import torch
+        if Y is None:
+            Y = torch.empty_like(X)
+        check(lib.nmf_mlp_forward(self.h, ptr(X), X.shape[0], ptr(Y), _stream_ptr(stream)), "nmf_mlp_forward")
+        return Y
+
+    def grads(self, X, T):
+        arrs = [np.empty(s, dtype=np.float32) for s in self.shapes()]
+        ptrs = (ctypes.c_void_p * 6)(*[a.ctypes.data for a in arrs])
+        loss = ctypes.c_double()
+        check(lib.nmf_mlp_grads(self.h, ptr(X), ptr(T), X.shape[0], ptrs, ctypes.byref(loss)), "nmf_mlp_grads")
+        return arrs, loss.value
+
+    def train_step(self, X, T, lr=1e-3, want_loss=False, stream=None):
+        loss = ctypes.c_double()
+        check(lib.nmf_mlp_train_step(self.h, ptr(X), ptr(T), X.shape[0], lr,
+                                     ctypes.byref(loss) if want_loss else None, _stream_ptr(stream)),
+              "nmf_mlp_train_step")
+        return loss.value if want_loss else None
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib.nmf_mlp_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        self.close()
+
+
+def warm_h(ctx, prob, *, mlp=None, tol=1e-3, max_sweeps=100, H_ref=None, want_R=False, seed=0):
+    """nmf_warm_h for the new documents of a synth.SparseProblem (V x N CSR).
+    Returns dict(H (K x N), R (N x K) or None, sweeps, trace)."""
+    import torch
+    A = prob.A
+    rp, ci, va = sparse_device(prob)
+    p, keep = problem_struct(A.n_rows, A.n_cols, ctx.K, row_ptr=rp, col_idx=ci, val=va, seed=seed)
+    N, K = A.n_cols, ctx.K
+    H = np.empty((K, N), dtype=np.float32)
+    R = np.empty((N, K), dtype=np.float32) if want_R else None
+    href = None
+    if H_ref is not None:
+        href = H_ref if hasattr(H_ref, "data_ptr") else np.ascontiguousarray(H_ref, dtype=np.float32)
+    sweeps = ctypes.c_int32()
+    trace = np.zeros(max(1, max_sweeps), dtype=np.float64)
+    check(lib.nmf_warm_h(ctx.h, mlp.h if mlp is not None else None, ctypes.byref(p), tol, max_sweeps, ptr(href),
+                         H.ctypes.data, ptr(R), ctypes.byref(sweeps), trace.ctypes.data), "nmf_warm_h")
+    del keep
+    return {"H": H, "R": R, "sweeps": sweeps.value, "trace": trace[:sweeps.value]}
 
 
 def gemm_bf16(A, B, C, *, stream=None):

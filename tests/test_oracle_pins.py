@@ -225,6 +225,38 @@ def test_mlp_gradients_finite_difference():
             assert abs(num - ana) <= 1e-7 * max(1.0, abs(ana)) + 1e-9
 
 
+def test_mlp_operand_rounding_is_exact_on_representable_operands():
+    """The reduced-precision-product form rounds only product operands: a
+    network whose input, weights and hidden activations are all exactly
+    representable in BF16 gives the same output with and without rounding
+    (x and weights are small dyadic numbers; zero first-layer weights make
+    a1 = GELU(b1) with b1 = 0 -> a1 = 0, and W2 = 0 makes a2 = GELU(0) = 0),
+    while generic operands move the output by about the BF16 unit roundoff
+    (2^-8 relative per operand; bounded over three layers)."""
+    from oracle.bf16 import round_bf16
+    rng = np.random.default_rng(3)
+    x = rng.integers(-4, 5, size=(6, 5)) / 4.0
+    params = [np.zeros((5, 8)), np.zeros(8), np.zeros((8, 8)), np.zeros(8),
+              rng.integers(-3, 4, size=(8, 5)) / 8.0, rng.integers(-3, 4, size=5) / 8.0]
+    y0, _ = mlp.forward(params, x)
+    y1, _ = mlp.forward(params, x, operand_round=round_bf16)
+    assert np.array_equal(y0, y1)
+    # generic operands: a change that is present but BF16-sized
+    params = []
+    for (i, o) in [(5, 8), (8, 8), (8, 5)]:
+        params += [rng.normal(scale=0.5, size=(i, o)), rng.normal(scale=0.1, size=o)]
+    x = rng.normal(size=(6, 5))
+    t = np.abs(rng.normal(size=(6, 5)))
+    y0, c0 = mlp.forward(params, x)
+    y1, c1 = mlp.forward(params, x, operand_round=round_bf16)
+    d = np.linalg.norm(y1 - y0) / np.linalg.norm(y0)
+    assert 1e-5 < d < 6 * 2.0 ** -8
+    g0 = mlp.backward(params, c0, y0, t)
+    g1 = mlp.backward(params, c1, y1, t, operand_round=round_bf16)
+    for a, b in zip(g0, g1):
+        assert np.linalg.norm(a - b) <= 12 * 2.0 ** -8 * np.linalg.norm(a)
+
+
 def test_mlp_activation_closed_forms():
     # GELU(0) = 0, GELU(x) -> x for large x, softplus(0) = ln 2, threshold branch.
     assert mlp.gelu(np.array(0.0)) == 0.0
