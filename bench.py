@@ -71,10 +71,6 @@ class ClockSampler:
     begin() and end() count.  Falls back to nvidia-smi (-lms 100) without
     NVML."""
 
-    REASONS = (("hw_slowdown", "HwSlowdown"), ("hw_thermal_slowdown", "HwThermalSlowdown"),
-               ("sw_thermal_slowdown", "SwThermalSlowdown"), ("hw_power_brake", "HwPowerBrakeSlowdown"),
-               ("sw_power_cap", "SwPowerCap"))
-
     def __init__(self, cuda_index: int):
         self.cuda_index = cuda_index
         self.samples = []           # (perf_counter, sm_mhz, max_mhz, reason names)
@@ -93,20 +89,59 @@ class ClockSampler:
         except Exception:
             return nv.nvmlDeviceGetHandleByIndex(self.cuda_index)
 
-    def start(self):
+    def _nvml(self):
+        """(sm_clock(), max_sm_clock, reasons()) through pynvml, else through a
+        ctypes binding of the driver's libnvidia-ml (read-only queries)."""
+        import ctypes
         try:
             import pynvml as nv
             nv.nvmlInit()
             h = self._handle(nv)
-            get_reasons = getattr(nv, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+            get = getattr(nv, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
                 nv.nvmlDeviceGetCurrentClocksThrottleReasons
-            masks = []
-            for name, suffix in self.REASONS:
-                m = getattr(nv, "nvmlClocksEventReason" + suffix, None)
-                if m is None:
-                    m = getattr(nv, "nvmlClocksThrottleReason" + suffix, 0)
-                masks.append((name, m))
-            smax = float(nv.nvmlDeviceGetMaxClockInfo(h, nv.NVML_CLOCK_SM))
+            return (lambda: float(nv.nvmlDeviceGetClockInfo(h, nv.NVML_CLOCK_SM)),
+                    float(nv.nvmlDeviceGetMaxClockInfo(h, nv.NVML_CLOCK_SM)), lambda: int(get(h)))
+        except ImportError:
+            pass
+        lib = ctypes.CDLL("libnvidia-ml.so.1")
+        if lib.nvmlInit_v2() != 0:
+            raise RuntimeError("nvmlInit_v2 failed")
+        h = ctypes.c_void_p()
+        ok = False
+        try:
+            import torch
+            p = torch.cuda.get_device_properties(self.cuda_index)
+            bus = f"{p.pci_domain_id:08x}:{p.pci_bus_id:02x}:{p.pci_device_id:02x}.0".encode()
+            ok = lib.nvmlDeviceGetHandleByPciBusId_v2(ctypes.c_char_p(bus), ctypes.byref(h)) == 0
+        except Exception:
+            ok = False
+        if not ok and lib.nvmlDeviceGetHandleByIndex_v2(ctypes.c_uint(self.cuda_index), ctypes.byref(h)) != 0:
+            raise RuntimeError("no NVML handle")
+        SM = ctypes.c_int(1)                                   # NVML_CLOCK_SM
+        mx = ctypes.c_uint()
+        if lib.nvmlDeviceGetMaxClockInfo(h, SM, ctypes.byref(mx)) != 0:
+            raise RuntimeError("nvmlDeviceGetMaxClockInfo failed")
+        rfn = getattr(lib, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+            lib.nvmlDeviceGetCurrentClocksThrottleReasons
+
+        def clock():
+            c = ctypes.c_uint()
+            lib.nvmlDeviceGetClockInfo(h, SM, ctypes.byref(c))
+            return float(c.value)
+
+        def reasons():
+            r = ctypes.c_ulonglong()
+            rfn(h, ctypes.byref(r))
+            return int(r.value)
+        return clock, float(mx.value), reasons
+
+    # clock-event reason bits of the NVML API
+    BITS = {"sw_power_cap": 0x4, "hw_slowdown": 0x8, "sw_thermal_slowdown": 0x20, "hw_thermal_slowdown": 0x40,
+            "hw_power_brake": 0x80}
+
+    def start(self):
+        try:
+            clock, smax, reasons = self._nvml()
         except Exception as e:                      # no NVML: nvidia-smi samples instead
             self.nvml_error = f"{type(e).__name__}: {e}"[:160]
             self._start_smi()
@@ -115,10 +150,10 @@ class ClockSampler:
         def poll():
             while not self._stop.is_set():
                 try:
-                    sm = float(nv.nvmlDeviceGetClockInfo(h, nv.NVML_CLOCK_SM))
-                    r = get_reasons(h)
+                    sm = clock()
+                    r = reasons()
                     self.samples.append((time.perf_counter(), sm, smax,
-                                         tuple(n for n, m in masks if m and (r & m))))
+                                         tuple(n for n, m in self.BITS.items() if r & m)))
                 except Exception:
                     pass
                 time.sleep(0.002)

@@ -56,6 +56,8 @@ struct nmf_ctx {
   int* d_status = nullptr;
   double normA2 = 0.0;
   bool s_valid = false;       // S == W^T W for the current W
+  bool r_valid = false;       // R == A^T W for the current W
+  cudaEvent_t evx[4] = {};    // fork / join events of the overlapped step pairs
   long long iters_run = 0;
   int launches_per_iter = 0;
   int launch_count = 0;       // kernels issued by the last enqueue sequence
@@ -95,10 +97,11 @@ bool is_device_ptr(const void* p) {
 
 // ---- launch sequence --------------------------------------------------------
 
-cudaError_t enq_product_R(nmf_ctx* c) {   // R = A^T W  (D x Kp)
+cudaError_t enq_product_R(nmf_ctx* c, cudaStream_t s = nullptr) {   // R = A^T W  (D x Kp)
+  if (!s) s = c->stream;
   if (c->fmt == NMF_CSR_F32_I32) {
     c->launch_count += 1 + (c->planAt.n_long > 0);
-    return spmm_run(c->planAt, c->ciT, c->vaT, c->W, c->R, c->Kp, c->stream);
+    return spmm_run(c->planAt, c->ciT, c->vaT, c->W, c->R, c->Kp, s);
   }
   GemmArgs a;
   a.M = c->D; a.N = c->Kp; a.Kin = c->V;
@@ -108,14 +111,13 @@ cudaError_t enq_product_R(nmf_ctx* c) {   // R = A^T W  (D x Kp)
   c->launch_count += 1;
   if (c->bf16 && c->tma) {
     // R (D x Kp) = A^T (D x V) * (W^T)^T with W^T (Kp x V) in BF16.
-    cudaError_t e = transpose_to_bf16(c->W, c->V, c->Kp, c->Kp, c->Fb8, c->ld8V, c->stream);
+    cudaError_t e = transpose_to_bf16(c->W, c->V, c->Kp, c->Kp, c->Fb8, c->ld8V, s);
     if (e != cudaSuccess) return e;
     c->launch_count += 1;
-    return tc_bf16_tma_gemm(c->ATb8, c->ld8V, c->Fb8, c->ld8V, c->R, c->Kp, c->D, c->Kp, c->V, c->d_status,
-                            c->stream);
+    return tc_bf16_tma_gemm(c->ATb8, c->ld8V, c->Fb8, c->ld8V, c->R, c->Kp, c->D, c->Kp, c->V, c->d_status, s);
   }
-  if (c->bf16) return tc_gemm_run(a, TC_BF16, c->A_bf16, c->Kp > 128 ? 128 : 0, c->d_status, c->stream);
-  return gemm_run(a, c->stream);
+  if (c->bf16) return tc_gemm_run(a, TC_BF16, c->A_bf16, c->Kp > 128 ? 128 : 0, c->d_status, s);
+  return gemm_run(a, s);
 }
 
 cudaError_t enq_product_P(nmf_ctx* c) {   // P = A H^T  (V x Kp)
@@ -141,10 +143,11 @@ cudaError_t enq_product_P(nmf_ctx* c) {   // P = A H^T  (V x Kp)
   return gemm_run(a, c->stream);
 }
 
-cudaError_t enq_gram(nmf_ctx* c, const GramWork& g, const float* X, float* out) {
+cudaError_t enq_gram(nmf_ctx* c, const GramWork& g, const float* X, float* out, cudaStream_t s = nullptr) {
+  if (!s) s = c->stream;
   c->launch_count += 2;
-  if (c->use_tc || c->bf16) return gram_run_tc(g, X, out, c->K, c->d_status, c->stream, c->bf16);
-  return gram_run(g, X, out, c->K, c->stream);
+  if (c->use_tc || c->bf16) return gram_run_tc(g, X, out, c->K, c->d_status, s, c->bf16);
+  return gram_run(g, X, out, c->K, s);
 }
 
 // Regrouped update of one tall factor X (N x Kp) with Gram G and data term B.
@@ -206,16 +209,44 @@ cudaError_t enq_objective(nmf_ctx* c) {
                        c->n_obj_partial, c->hist, c->d_counter, kHistCap, c->stream);
 }
 
-// One iteration; S must equal W^T W on entry and does again on exit.
+// One iteration.  On entry S = W^T W and R = A^T W for the current W (Alg. 1
+// lines 4-5); on exit the same holds for the new W.  R is therefore formed at
+// the end of the previous iteration, right after the W update, where it runs
+// beside S; likewise Q beside P.  Each pair is independent (same inputs,
+// disjoint outputs and work buffers), so the graph has two branches there:
+//   H update -> { P | Q } -> W update -> { S -> objective | R }.
 cudaError_t enq_iteration(nmf_ctx* c) {
   cudaError_t e;
-  if ((e = enq_product_R(c)) != cudaSuccess) return e;
+  cudaStream_t m = c->stream, b = c->side;
   if ((e = enq_update(c, c->Ht, c->S, c->R, c->D, false)) != cudaSuccess) return e;
+  if ((e = cudaEventRecord(c->evx[0], m)) != cudaSuccess) return e;
+  if ((e = cudaStreamWaitEvent(b, c->evx[0], 0)) != cudaSuccess) return e;
+  if ((e = enq_gram(c, c->gramH, c->Ht, c->Q, b)) != cudaSuccess) return e;
+  if ((e = cudaEventRecord(c->evx[1], b)) != cudaSuccess) return e;
   if ((e = enq_product_P(c)) != cudaSuccess) return e;
-  if ((e = enq_gram(c, c->gramH, c->Ht, c->Q)) != cudaSuccess) return e;
+  if ((e = cudaStreamWaitEvent(m, c->evx[1], 0)) != cudaSuccess) return e;
   if ((e = enq_update(c, c->W, c->Q, c->P, c->V, true)) != cudaSuccess) return e;
+  if ((e = cudaEventRecord(c->evx[2], m)) != cudaSuccess) return e;
+  if ((e = cudaStreamWaitEvent(b, c->evx[2], 0)) != cudaSuccess) return e;
+  if ((e = enq_product_R(c, b)) != cudaSuccess) return e;
+  if ((e = cudaEventRecord(c->evx[3], b)) != cudaSuccess) return e;
   if ((e = enq_gram(c, c->gramW, c->W, c->S)) != cudaSuccess) return e;
-  return enq_objective(c);
+  if ((e = enq_objective(c)) != cudaSuccess) return e;
+  return cudaStreamWaitEvent(m, c->evx[3], 0);
+}
+
+// Establish the iteration's entry state (S and R of the current W).
+cudaError_t ensure_entry(nmf_ctx* c) {
+  cudaError_t e;
+  if (!c->s_valid) {
+    if ((e = enq_gram(c, c->gramW, c->W, c->S)) != cudaSuccess) return e;
+    c->s_valid = true;
+  }
+  if (!c->r_valid) {
+    if ((e = enq_product_R(c)) != cudaSuccess) return e;
+    c->r_valid = true;
+  }
+  return cudaSuccess;
 }
 
 nmf_status read_status(nmf_ctx* c) {
@@ -290,6 +321,7 @@ nmf_status init_impl(const nmf_problem* p, nmf_ctx* c) {
     const int nt = (c->K + kRowTile - 1) / kRowTile;
     c->ev.assign(1 + 2 * nt, nullptr);
     for (auto& e : c->ev) CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    for (auto& e : c->evx) CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
   }
   CK(dalloc(&c->d_status, 1));
   CK(cudaMemset(c->d_status, 0, sizeof(int)));
@@ -465,6 +497,8 @@ void free_ctx(nmf_ctx* c) {
   }
   for (auto e : c->ev)
     if (e) cudaEventDestroy(e);
+  for (auto e : c->evx)
+    if (e) cudaEventDestroy(e);
   if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
   delete c;
 }
@@ -612,10 +646,7 @@ nmf_status nmf_batch_create(nmf_ctx* const* ctxs, int32_t n, int32_t autotune, v
     nmf_ctx* c = b->m[i];
     c->w_persistent = false;
     drop_graph(c);
-    if (!c->s_valid) {
-      if ((e = enq_gram(c, c->gramW, c->W, c->S)) != cudaSuccess) return bail(e);
-      c->s_valid = true;
-    }
+    if ((e = ensure_entry(c)) != cudaSuccess) return bail(e);
     if (autotune) {
       if ((e = autotune_member(c, &b->w_us[i])) != cudaSuccess) return bail(e);
     }
@@ -649,7 +680,9 @@ nmf_status nmf_batch_iterate(nmf_batch* b, int32_t n_iters) {
   if (!b || n_iters < 0) return NMF_EINVAL;
   if (n_iters == 0) return NMF_OK;
   const int n = (int)b->m.size();
-  // Order after whatever the members' own streams hold (factor uploads, ...).
+  // Entry state of every member (S, R of its current W), then order after
+  // whatever the members' own streams hold (factor uploads, ...).
+  for (int i = 0; i < n; ++i) CK(ensure_entry(b->m[i]));
   for (int i = 0; i < n; ++i) {
     CK(cudaEventRecord(b->ready[i], b->m[i]->stream));
     CK(cudaStreamWaitEvent(b->root, b->ready[i], 0));
@@ -736,11 +769,8 @@ nmf_status nmf_init(const nmf_problem* p, nmf_ctx** out) {
 nmf_status nmf_iterate(nmf_ctx* c, int32_t n_iters) {
   if (!c || n_iters < 0) return NMF_EINVAL;
   if (n_iters == 0) return NMF_OK;
-  if (!c->s_valid) {
-    c->launch_count = 0;
-    CK(enq_gram(c, c->gramW, c->W, c->S));
-    c->s_valid = true;
-  }
+  c->launch_count = 0;
+  CK(ensure_entry(c));
   if (!c->graph_exec) {
     c->launch_count = 0;
     CK(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
@@ -923,6 +953,7 @@ nmf_status nmf_set_factors(nmf_ctx* c, const float* W, const float* H) {
     CK(cudaMemcpy2DAsync(c->W, sizeof(float) * Kp, W, sizeof(float) * K, sizeof(float) * K, c->V,
                          cudaMemcpyDefault, c->stream));
     c->s_valid = false;
+    c->r_valid = false;
   }
   if (H) {
     CK(cudaMemcpyAsync(c->stage, H, sizeof(float) * (size_t)K * c->D, cudaMemcpyDefault, c->stream));
@@ -936,12 +967,16 @@ nmf_status nmf_run_step(nmf_ctx* c, int32_t step) {
   if (!c) return NMF_EINVAL;
   c->launch_count = 0;
   switch (step) {
-    case NMF_STEP_R: CK(enq_product_R(c)); break;
+    case NMF_STEP_R: CK(enq_product_R(c)); c->r_valid = true; break;
     case NMF_STEP_S: CK(enq_gram(c, c->gramW, c->W, c->S)); c->s_valid = true; break;
     case NMF_STEP_UPDATE_H: CK(enq_update(c, c->Ht, c->S, c->R, c->D, false)); break;
     case NMF_STEP_P: CK(enq_product_P(c)); break;
     case NMF_STEP_Q: CK(enq_gram(c, c->gramH, c->Ht, c->Q)); break;
-    case NMF_STEP_UPDATE_W: CK(enq_update(c, c->W, c->Q, c->P, c->V, true)); c->s_valid = false; break;
+    case NMF_STEP_UPDATE_W:
+      CK(enq_update(c, c->W, c->Q, c->P, c->V, true));
+      c->s_valid = false;
+      c->r_valid = false;
+      break;
     case NMF_STEP_OBJECTIVE:
       CK(enq_gram(c, c->gramW, c->W, c->S));
       c->s_valid = true;
@@ -979,9 +1014,9 @@ nmf_status nmf_set_buffer(nmf_ctx* c, int32_t which, const float* src, int64_t c
   float* dst = nullptr;
   int rows = 0;
   switch (which) {
-    case NMF_BUF_W: dst = c->W; rows = c->V; c->s_valid = false; break;
+    case NMF_BUF_W: dst = c->W; rows = c->V; c->s_valid = false; c->r_valid = false; break;
     case NMF_BUF_HT: dst = c->Ht; rows = c->D; break;
-    case NMF_BUF_R: dst = c->R; rows = c->D; break;
+    case NMF_BUF_R: dst = c->R; rows = c->D; c->r_valid = false; break;
     case NMF_BUF_P: dst = c->P; rows = c->V; break;
     case NMF_BUF_S: dst = c->S; rows = K; c->s_valid = false; break;
     case NMF_BUF_Q: dst = c->Q; rows = K; break;
@@ -1030,6 +1065,8 @@ nmf_status nmf_profile(nmf_ctx* c, int32_t n_iters, float* step_ms) {
     st = from_cuda(e);
   }
   for (auto& e : ev) cudaEventDestroy(e);
+  c->s_valid = true;          // S of the new W was the last product formed
+  c->r_valid = false;         // R was formed from the W before the update
   if (st != NMF_OK) return st;
   c->iters_run += n_iters;
   for (int k = 0; k < NMF_PROFILE_STEPS; ++k) step_ms[k] = (float)(acc[k] / n_iters);
