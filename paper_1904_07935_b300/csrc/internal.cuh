@@ -158,7 +158,8 @@ struct WPersistConfig {
   size_t smem = 0;
 };
 bool w_persistent_config(int N, int Kp, WPersistConfig* cfg);
-// d_sync: 2 * ceil(K / 16) ints (zeroed by the call, on the stream).
+// d_sync: w_sync_ints(K) ints (zeroed by the call, on the stream).
+size_t w_sync_ints(int K);
 cudaError_t w_persistent_run(float* X, const float* P, const float* Q, float* Y, int N, int K, int Kp, float eps,
                              int* d_sync, int* d_status, const WPersistConfig& cfg, cudaStream_t s);
 

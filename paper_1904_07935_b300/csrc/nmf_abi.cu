@@ -325,7 +325,7 @@ nmf_status init_impl(const nmf_problem* p, nmf_ctx* c) {
   }
   CK(dalloc(&c->d_status, 1));
   CK(cudaMemset(c->d_status, 0, sizeof(int)));
-  CK(dalloc(&c->d_sync, 2 * ((c->K + kRowTile - 1) / kRowTile)));
+  CK(dalloc(&c->d_sync, w_sync_ints(c->K)));
   CK(dalloc(&c->d_counter, 1));
   CK(cudaMemset(c->d_counter, 0, sizeof(unsigned)));
   CK(dalloc(&c->hist, kHistCap));

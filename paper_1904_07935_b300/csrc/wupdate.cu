@@ -60,11 +60,20 @@ __device__ __forceinline__ unsigned cluster_id_x() {
   return r;
 }
 
-// Bounded spin on a global counter; returns false on timeout.
+// Hand-off flags live one per 128-byte line (kSyncStride ints apart), so the
+// workers' polling and the chain's release do not share a line.
+constexpr int kSyncStride = 32;
+
+// Bounded spin on a global counter with exponential backoff (32 ns .. 512 ns
+// between polls, so that many waiting CTAs do not keep the line's L2 slice
+// busy); returns false on timeout.
 __device__ bool wait_counter(const int* p, int target, int* status) {
   unsigned long long t0 = 0;
   unsigned polls = 0;
+  unsigned sleep_ns = 32;
   while (ld_acquire_gpu(p) < target) {
+    __nanosleep(sleep_ns);
+    if (sleep_ns < 512) sleep_ns <<= 1;
     if ((++polls & 15u) == 0) {
       const unsigned long long now = global_ns();
       if (t0 == 0) t0 = now;
@@ -106,7 +115,7 @@ __device__ void worker_role(const WParams& p, char* smem, int wid, int n_workers
     if (tid == 0) {
       go = 1;
       if (tau >= 2 && !dead) {
-        if (!wait_counter(p.sync + nt + tau - 2, 1, p.status)) dead = true;
+        if (!wait_counter(p.sync + (nt + tau - 2) * kSyncStride, 1, p.status)) dead = true;
       }
       fence_proxy_async_global();
     }
@@ -208,7 +217,7 @@ __device__ void worker_role(const WParams& p, char* smem, int wid, int n_workers
     __syncthreads();
     if (tid == 0) {
       __threadfence();
-      atomicAdd(p.sync + tau, 1);
+      atomicAdd(p.sync + tau * kSyncStride, 1);
     }
   }
   if (__syncthreads_or(dead ? 1 : 0)) drain_grace();   // bulk copies still in flight
@@ -269,7 +278,7 @@ __device__ void chain_role(const WParams& p, char* smem, int n_workers) {
       Gs[i][j] = (i < Tw && j < Tw) ? p.Q[(int64_t)(lo + i) * p.Kp + lo + j] : 0.f;
     }
     if (tid == 0 && !dead) {
-      if (!wait_counter(p.sync + tau, n_workers, p.status)) dead = true;
+      if (!wait_counter(p.sync + tau * kSyncStride, n_workers, p.status)) dead = true;
     }
     __syncthreads();
     // Base of the tile for this CTA's rows (4 lanes per row, 16 bytes each).
@@ -455,7 +464,7 @@ __device__ void chain_role(const WParams& p, char* smem, int n_workers) {
     }
     __threadfence();
     cluster_sync_all();
-    if (rank == 0 && tid == 0) st_release_gpu(p.sync + nt + tau, 1);
+    if (rank == 0 && tid == 0) st_release_gpu(p.sync + (nt + tau) * kSyncStride, 1);
   }
   // A timed-out wait anywhere: let remote stores still in flight land before
   // any CTA of the cluster leaves.
@@ -540,6 +549,8 @@ int max_clusters(int rpt, int cl, size_t smem) {
 
 }  // namespace
 
+size_t w_sync_ints(int K) { return (size_t)2 * ((K + WT - 1) / WT) * kSyncStride; }
+
 bool w_persistent_config(int N, int Kp, WPersistConfig* cfg) {
   for (int cl : {16, 8}) {
     const int rpt = (N + cl * WNR - 1) / (cl * WNR);
@@ -563,7 +574,7 @@ bool w_persistent_config(int N, int Kp, WPersistConfig* cfg) {
 cudaError_t w_persistent_run(float* X, const float* P, const float* Q, float* Y, int N, int K, int Kp, float eps,
                              int* d_sync, int* d_status, const WPersistConfig& cfg, cudaStream_t s) {
   const int nt = (K + WT - 1) / WT;
-  cudaError_t e = cudaMemsetAsync(d_sync, 0, sizeof(int) * 2 * nt, s);
+  cudaError_t e = cudaMemsetAsync(d_sync, 0, sizeof(int) * w_sync_ints(K), s);
   if (e != cudaSuccess) return e;
   WParams p{X, P, Q, Y, N, K, Kp, eps, d_status, d_sync, cfg.cluster, cfg.worker_rows};
   switch (cfg.rpt) {
