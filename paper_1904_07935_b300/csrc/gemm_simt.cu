@@ -245,30 +245,67 @@ __global__ void __launch_bounds__(512) gram_full_kernel(const float* __restrict_
   }
 }
 
-// S = sum over chunks of the partial Grams, FP64, mirrored: 8 lanes per entry
-// (i <= j) each add every 8th chunk in order, then a fixed shuffle tree adds
-// the 8 sums, so the result does not depend on scheduling.
-__global__ void gram_reduce8_kernel(const float* __restrict__ part, int n_chunks, int Kp, int K,
-                                    float* __restrict__ S) {
-  const int lane = threadIdx.x & 7;
-  const int entry = (blockIdx.x * blockDim.x + threadIdx.x) >> 3;
+// Error-free addition (Knuth's TwoSum): s + e == a + b exactly, s = fl(a + b).
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = a + b;
+  const float bp = s - a;
+  e = (a - (s - bp)) + (b - bp);
+}
+
+// S[i][j] = sum_z part[z][i][j] for i <= j, mirrored.  Compensated FP32
+// summation (a TwoSum cascade: the running sum plus the sum of its exact
+// rounding errors), which is as accurate as summing in twice the working
+// precision and rounding once, on the FP32 pipes (B300's FP64 rate is a
+// small fraction of its FP32 rate).  Coalesced loads and one memory latency:
+// a block covers 32 consecutive entries x 8 chunk lanes (a warp = 32 entries
+// of one chunk lane); chunk lane c adds chunks c, c + 8, ... (all its loads
+// issued before the first add), then the lanes' (sum, error) pairs are added
+// for c = 0..7 through shared memory.  Fixed order, so the result does not
+// depend on scheduling.
+constexpr int kReduceLanes = 8, kReducePer = 32;     // n_chunks <= 256
+__global__ void __launch_bounds__(256) gram_reduce32_kernel(const float* __restrict__ part, int n_chunks, int Kp,
+                                                            int K, float* __restrict__ S) {
+  __shared__ float sh_s[kReduceLanes][33], sh_e[kReduceLanes][33];
+  const int ej = threadIdx.x & 31, cl = threadIdx.x >> 5;
+  const int entry = blockIdx.x * 32 + ej;
   const int i = entry / Kp, j = entry % Kp;
-  const bool in = entry < Kp * Kp;
-  double s = 0.0;
-  if (in && i < K && j < K && j >= i) {
+  const bool inside = entry < Kp * Kp;
+  const bool need = inside && i < K && j < K && j >= i;
+  float s = 0.f, c = 0.f;
+  if (need) {
     const size_t stride = (size_t)Kp * Kp;
-    for (int z = lane; z < n_chunks; z += 8) s += (double)part[z * stride + (size_t)i * Kp + j];
+    const float* src = part + (size_t)i * Kp + j;
+    float v[kReducePer];
+#pragma unroll
+    for (int k = 0; k < kReducePer; ++k) {
+      const int z = cl + kReduceLanes * k;
+      v[k] = z < n_chunks ? src[z * stride] : 0.f;
+    }
+#pragma unroll
+    for (int k = 0; k < kReducePer; ++k) {
+      if (cl + kReduceLanes * k >= n_chunks) break;
+      float e;
+      two_sum(s, v[k], s, e);
+      c += e;
+    }
   }
-  s += __shfl_xor_sync(0xffffffffu, s, 4);
-  s += __shfl_xor_sync(0xffffffffu, s, 2);
-  s += __shfl_xor_sync(0xffffffffu, s, 1);
-  if (!in || lane != 0) return;
+  sh_s[cl][ej] = s;
+  sh_e[cl][ej] = c;
+  __syncthreads();
+  if (cl != 0 || !inside) return;
   if (i >= K || j >= K) {
     S[(int64_t)i * Kp + j] = 0.f;
     return;
   }
   if (j < i) return;
-  const float f = (float)s;
+  float t = 0.f, ct = 0.f;
+#pragma unroll
+  for (int q = 0; q < kReduceLanes; ++q) {
+    float e;
+    two_sum(t, sh_s[q][ej], t, e);
+    ct += e + sh_e[q][ej];
+  }
+  const float f = t + ct;
   S[(int64_t)i * Kp + j] = f;
   S[(int64_t)j * Kp + i] = f;
 }
@@ -358,6 +395,17 @@ cudaError_t gram_setup_tc(GramWork& g, int N, int Kp) {
   return cudaMalloc(&g.d_part, sizeof(float) * (size_t)g.n_chunks * Kp * Kp);
 }
 
+// Sum of n_chunks partial Grams (Kp x Kp each) into S, FP64, fixed order.
+cudaError_t gram_reduce(const float* part, int n_chunks, int Kp, int K, float* S, cudaStream_t s) {
+  if (n_chunks <= kReduceLanes * kReducePer) {
+    gram_reduce32_kernel<<<(Kp * Kp + 31) / 32, 256, 0, s>>>(part, n_chunks, Kp, K, S);
+  } else {
+    dim3 grid((Kp + 127) / 128, Kp);
+    gram_reduce_kernel<<<grid, 128, 0, s>>>(part, n_chunks, Kp, K, S);
+  }
+  return cudaGetLastError();
+}
+
 cudaError_t gram_run_tc(const GramWork& g, const float* X, float* S, int K, int* d_status, cudaStream_t s,
                         bool bf16) {
   GemmArgs a;
@@ -377,9 +425,7 @@ cudaError_t gram_run_tc(const GramWork& g, const float* X, float* S, int K, int*
   a.n_chunks = g.n_chunks;
   cudaError_t err = tc_gemm_run(a, bf16 ? TC_BF16 : TC_TF32X3, nullptr, 0, d_status, s);
   if (err != cudaSuccess) return err;
-  dim3 grid((g.Kp + 127) / 128, g.Kp);
-  gram_reduce_kernel<<<grid, 128, 0, s>>>(g.d_part, g.n_chunks, g.Kp, K, S);
-  return cudaGetLastError();
+  return gram_reduce(g.d_part, g.n_chunks, g.Kp, K, S, s);
 }
 
 cudaError_t gram_run_scratch(const float* X, int N, int K, int64_t ldx, float* part, int n_chunks, int chunk,
@@ -402,9 +448,7 @@ cudaError_t gram_run_scratch(const float* X, int N, int K, int64_t ldx, float* p
   a.upper_only = 1;
   cudaError_t err = gemm_run(a, s);
   if (err != cudaSuccess) return err;
-  dim3 grid((K + 127) / 128, K);
-  gram_reduce_kernel<<<grid, 128, 0, s>>>(part, n_chunks, K, K, S);
-  return cudaGetLastError();
+  return gram_reduce(part, n_chunks, K, K, S, s);
 }
 
 void gram_free(GramWork& g) {
@@ -420,9 +464,7 @@ cudaError_t gram_run(const GramWork& g, const float* X, float* S, int K, cudaStr
     gram_full_kernel<<<g.n_chunks, threads, smem, s>>>(X, g.N, g.Kp, Kp8, g.chunk, g.d_part);
     cudaError_t err = cudaGetLastError();
     if (err != cudaSuccess) return err;
-    const int entries = g.Kp * g.Kp;
-    gram_reduce8_kernel<<<(entries * 8 + 255) / 256, 256, 0, s>>>(g.d_part, g.n_chunks, g.Kp, K, S);
-    return cudaGetLastError();
+    return gram_reduce(g.d_part, g.n_chunks, g.Kp, K, S, s);
   }
   GemmArgs a;
   a.M = g.Kp;
@@ -442,9 +484,7 @@ cudaError_t gram_run(const GramWork& g, const float* X, float* S, int K, cudaStr
   a.upper_only = 1;
   cudaError_t err = gemm_run(a, s);
   if (err != cudaSuccess) return err;
-  dim3 grid((g.Kp + 127) / 128, g.Kp);
-  gram_reduce_kernel<<<grid, 128, 0, s>>>(g.d_part, g.n_chunks, g.Kp, K, S);
-  return cudaGetLastError();
+  return gram_reduce(g.d_part, g.n_chunks, g.Kp, K, S, s);
 }
 
 }  // namespace plnmf

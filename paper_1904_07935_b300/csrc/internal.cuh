@@ -89,6 +89,15 @@ int tc_pick_bn(int N);
 bool tma_available();
 cudaError_t tc_bf16_tma_gemm(const void* A, int64_t lda, const void* B, int64_t ldb, float* C, int64_t ldc, int M,
                              int N, int Kd, int* d_status, cudaStream_t s);
+// Split-K partial Grams of X (N x Kp) given X^T in BF16 (Kp x ldx, ldx a
+// multiple of 8): part[z] (Kp x Kp) = X^T X over the z-th K slice,
+// z < splits (tma_gram_splits gives a full-GPU count); sum with gram_reduce.
+cudaError_t tc_bf16_tma_gram_partials(const void* Xt, int64_t ldx, int Kp, int N, float* part, int splits,
+                                      int* d_status, cudaStream_t s);
+int tma_gram_splits(int Kp, int N);
+// S (Kp x Kp, pads zero) = sum of n_chunks partial Grams, FP64 in a fixed
+// order, upper triangle mirrored.
+cudaError_t gram_reduce(const float* part, int n_chunks, int Kp, int K, float* S, cudaStream_t s);
 // dst (cols x ldd, BF16) = transpose of src (rows x cols FP32, row stride lds); rows..ldd zero.
 cudaError_t transpose_to_bf16(const float* src, int rows, int cols, int64_t lds, void* dst, int64_t ldd,
                               cudaStream_t s);

@@ -23,6 +23,8 @@ struct nmf_ctx {
   void* ATb8 = nullptr;     // BF16 A^T, D x ld8V
   void* Fb8 = nullptr;      // BF16 transposed factor, Kp x max(ld8V, ld8D)
   int64_t ld8V = 0, ld8D = 0;
+  float* gpart = nullptr;   // BF16 form: split-K partial Grams, gsplits x Kp x Kp
+  int gsplits = 0;
   double* resid_part = nullptr;     // dense A: partials of the direct objective
   float eps = 1e-16f;
   cudaStream_t stream = nullptr;
@@ -97,7 +99,16 @@ bool is_device_ptr(const void* p) {
 
 // ---- launch sequence --------------------------------------------------------
 
-cudaError_t enq_product_R(nmf_ctx* c, cudaStream_t s = nullptr) {   // R = A^T W  (D x Kp)
+// BF16 form with TMA: the factor operand of a product or Gram is the factor
+// transposed to BF16 in Fb8 (W^T for R and S, H for P and Q); operand_ready
+// means the iteration already made it for both branches.
+cudaError_t bf16_operand(nmf_ctx* c, bool w, cudaStream_t s) {
+  c->launch_count += 1;
+  return w ? transpose_to_bf16(c->W, c->V, c->Kp, c->Kp, c->Fb8, c->ld8V, s)
+           : transpose_to_bf16(c->Ht, c->D, c->Kp, c->Kp, c->Fb8, c->ld8D, s);
+}
+
+cudaError_t enq_product_R(nmf_ctx* c, cudaStream_t s = nullptr, bool operand_ready = false) {   // R = A^T W
   if (!s) s = c->stream;
   if (c->fmt == NMF_CSR_F32_I32) {
     c->launch_count += 1 + (c->planAt.n_long > 0);
@@ -111,16 +122,17 @@ cudaError_t enq_product_R(nmf_ctx* c, cudaStream_t s = nullptr) {   // R = A^T W
   c->launch_count += 1;
   if (c->bf16 && c->tma) {
     // R (D x Kp) = A^T (D x V) * (W^T)^T with W^T (Kp x V) in BF16.
-    cudaError_t e = transpose_to_bf16(c->W, c->V, c->Kp, c->Kp, c->Fb8, c->ld8V, s);
-    if (e != cudaSuccess) return e;
-    c->launch_count += 1;
+    if (!operand_ready) {
+      cudaError_t e = bf16_operand(c, true, s);
+      if (e != cudaSuccess) return e;
+    }
     return tc_bf16_tma_gemm(c->ATb8, c->ld8V, c->Fb8, c->ld8V, c->R, c->Kp, c->D, c->Kp, c->V, c->d_status, s);
   }
   if (c->bf16) return tc_gemm_run(a, TC_BF16, c->A_bf16, c->Kp > 128 ? 128 : 0, c->d_status, s);
   return gemm_run(a, s);
 }
 
-cudaError_t enq_product_P(nmf_ctx* c) {   // P = A H^T  (V x Kp)
+cudaError_t enq_product_P(nmf_ctx* c, bool operand_ready = false) {   // P = A H^T  (V x Kp)
   if (c->fmt == NMF_CSR_F32_I32) {
     c->launch_count += 1 + (c->planA.n_long > 0);
     return spmm_run(c->planA, c->ci, c->va, c->Ht, c->P, c->Kp, c->stream);
@@ -133,9 +145,10 @@ cudaError_t enq_product_P(nmf_ctx* c) {   // P = A H^T  (V x Kp)
   c->launch_count += 1;
   if (c->bf16 && c->tma) {
     // P (V x Kp) = A (V x D) * (H)^T with H = (H^T)^T (Kp x D) in BF16.
-    cudaError_t e = transpose_to_bf16(c->Ht, c->D, c->Kp, c->Kp, c->Fb8, c->ld8D, c->stream);
-    if (e != cudaSuccess) return e;
-    c->launch_count += 1;
+    if (!operand_ready) {
+      cudaError_t e = bf16_operand(c, false, c->stream);
+      if (e != cudaSuccess) return e;
+    }
     return tc_bf16_tma_gemm(c->Ab8, c->ld8D, c->Fb8, c->ld8D, c->P, c->Kp, c->V, c->Kp, c->D, c->d_status,
                             c->stream);
   }
@@ -143,8 +156,23 @@ cudaError_t enq_product_P(nmf_ctx* c) {   // P = A H^T  (V x Kp)
   return gemm_run(a, c->stream);
 }
 
-cudaError_t enq_gram(nmf_ctx* c, const GramWork& g, const float* X, float* out, cudaStream_t s = nullptr) {
+cudaError_t enq_gram(nmf_ctx* c, const GramWork& g, const float* X, float* out, cudaStream_t s = nullptr,
+                     bool operand_ready = false) {
   if (!s) s = c->stream;
+  if (c->bf16 && c->tma && c->gpart) {
+    // Split-K partial Grams on the tensor cores from the BF16 transposed
+    // factor, then a fixed-order FP64 sum.
+    const bool w = X == c->W;
+    cudaError_t e;
+    if (!operand_ready && (e = bf16_operand(c, w, s)) != cudaSuccess) return e;
+    const int N = w ? c->V : c->D;
+    const int splits = tma_gram_splits(c->Kp, N);
+    c->launch_count += 2;
+    if ((e = tc_bf16_tma_gram_partials(c->Fb8, w ? c->ld8V : c->ld8D, c->Kp, N, c->gpart, splits, c->d_status, s)) !=
+        cudaSuccess)
+      return e;
+    return gram_reduce(c->gpart, splits, c->Kp, c->K, out, s);
+  }
   c->launch_count += 2;
   if (c->use_tc || c->bf16) return gram_run_tc(g, X, out, c->K, c->d_status, s, c->bf16);
   return gram_run(g, X, out, c->K, s);
@@ -218,19 +246,22 @@ cudaError_t enq_objective(nmf_ctx* c) {
 cudaError_t enq_iteration(nmf_ctx* c) {
   cudaError_t e;
   cudaStream_t m = c->stream, b = c->side;
+  const bool shared_op = c->bf16 && c->tma;      // one BF16 factor operand for both branches
   if ((e = enq_update(c, c->Ht, c->S, c->R, c->D, false)) != cudaSuccess) return e;
+  if (shared_op && (e = bf16_operand(c, false, m)) != cudaSuccess) return e;
   if ((e = cudaEventRecord(c->evx[0], m)) != cudaSuccess) return e;
   if ((e = cudaStreamWaitEvent(b, c->evx[0], 0)) != cudaSuccess) return e;
-  if ((e = enq_gram(c, c->gramH, c->Ht, c->Q, b)) != cudaSuccess) return e;
+  if ((e = enq_gram(c, c->gramH, c->Ht, c->Q, b, shared_op)) != cudaSuccess) return e;
   if ((e = cudaEventRecord(c->evx[1], b)) != cudaSuccess) return e;
-  if ((e = enq_product_P(c)) != cudaSuccess) return e;
+  if ((e = enq_product_P(c, shared_op)) != cudaSuccess) return e;
   if ((e = cudaStreamWaitEvent(m, c->evx[1], 0)) != cudaSuccess) return e;
   if ((e = enq_update(c, c->W, c->Q, c->P, c->V, true)) != cudaSuccess) return e;
+  if (shared_op && (e = bf16_operand(c, true, m)) != cudaSuccess) return e;
   if ((e = cudaEventRecord(c->evx[2], m)) != cudaSuccess) return e;
   if ((e = cudaStreamWaitEvent(b, c->evx[2], 0)) != cudaSuccess) return e;
-  if ((e = enq_product_R(c, b)) != cudaSuccess) return e;
+  if ((e = enq_product_R(c, b, shared_op)) != cudaSuccess) return e;
   if ((e = cudaEventRecord(c->evx[3], b)) != cudaSuccess) return e;
-  if ((e = enq_gram(c, c->gramW, c->W, c->S)) != cudaSuccess) return e;
+  if ((e = enq_gram(c, c->gramW, c->W, c->S, nullptr, shared_op)) != cudaSuccess) return e;
   if ((e = enq_objective(c)) != cudaSuccess) return e;
   return cudaStreamWaitEvent(m, c->evx[3], 0);
 }
@@ -418,6 +449,8 @@ nmf_status init_impl(const nmf_problem* p, nmf_ctx* c) {
       CK(cudaMalloc(&c->Ab8, sizeof(uint16_t) * (size_t)V * c->ld8D));
       CK(cudaMalloc(&c->ATb8, sizeof(uint16_t) * (size_t)D * c->ld8V));
       CK(cudaMalloc(&c->Fb8, sizeof(uint16_t) * (size_t)Kp * std::max(c->ld8V, c->ld8D)));
+      c->gsplits = std::max(tma_gram_splits(Kp, V), tma_gram_splits(Kp, D));
+      CK(cudaMalloc(&c->gpart, sizeof(float) * (size_t)c->gsplits * Kp * Kp));
       // A (V x D) -> BF16 with row stride ld8D, and A^T (D x V) with ld8V.
       CK(convert_bf16(c->dense, V, D, c->lda, c->Ab8, c->ld8D, c->stream));
       CK(transpose_to_bf16(c->dense, V, D, c->lda, c->ATb8, c->ld8V, c->stream));
@@ -486,7 +519,7 @@ void free_ctx(nmf_ctx* c) {
   gram_free(c->gramW);
   gram_free(c->gramH);
 
-  for (void* p : {(void*)c->A_bf16, c->Ab8, c->ATb8, c->Fb8, (void*)c->resid_part,
+  for (void* p : {(void*)c->A_bf16, c->Ab8, c->ATb8, c->Fb8, (void*)c->gpart, (void*)c->resid_part,
                   (void*)c->d_sync, (void*)c->rpT, (void*)c->ciT, (void*)c->vaT, (void*)c->W, (void*)c->Ht, (void*)c->R,
                   (void*)c->P, (void*)c->S, (void*)c->Q, (void*)c->Y, (void*)c->stage,
                   (void*)c->obj_partial, (void*)c->hist, (void*)c->d_counter, (void*)c->d_status})

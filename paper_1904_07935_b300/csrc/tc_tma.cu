@@ -16,6 +16,7 @@
 #include <cuda_bf16.h>
 #include <cudaTypedefs.h>
 
+#include <algorithm>
 #include <mutex>
 
 #include "devutil.cuh"
@@ -65,14 +66,18 @@ __device__ __forceinline__ void tma_load_2d(unsigned dst, const CUtensorMap* map
 
 __global__ void __launch_bounds__(TMA_THREADS, 1)
     tc_tma_bf16_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB, float* C,
-                       int64_t ldc, int M, int N, int Kd, int* status) {
+                       int64_t ldc, int M, int N, int Kd, int kps, int64_t split_stride, int* status) {
   extern __shared__ __align__(1024) char smem_raw[];
   __shared__ __align__(8) unsigned long long full[NSTAGE], empty[NSTAGE], done;
   __shared__ unsigned tmem_base;
   char* smem = reinterpret_cast<char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int m0 = blockIdx.y * TM, n0 = blockIdx.x * TN;
-  const int nk = (Kd + TK - 1) / TK;
+  // Split K: this CTA adds K slice [k0, k1) (kps a multiple of TK) into its
+  // own partial output C + z * split_stride.
+  const int k0 = blockIdx.z * kps, k1 = min(Kd, k0 + kps);
+  const int nk = k1 > k0 ? (k1 - k0 + TK - 1) / TK : 0;
+  C += (int64_t)blockIdx.z * split_stride;
 
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base)),
@@ -103,8 +108,8 @@ __global__ void __launch_bounds__(TMA_THREADS, 1)
       const unsigned a = smem_u32(smem + s * (A_STAGE + B_STAGE));
       const unsigned b = a + A_STAGE;
       mbar_arrive_expect_tx(smem_u32(&full[s]), A_STAGE + B_STAGE);
-      tma_load_2d(a, &mapA, kb * TK, m0, smem_u32(&full[s]));
-      tma_load_2d(b, &mapB, kb * TK, n0, smem_u32(&full[s]));
+      tma_load_2d(a, &mapA, k0 + kb * TK, m0, smem_u32(&full[s]));
+      tma_load_2d(b, &mapB, k0 + kb * TK, n0, smem_u32(&full[s]));
     }
   } else if (warp == 1 && lane == 0) {
     // MMA issuer.
@@ -251,8 +256,29 @@ cudaError_t tc_bf16_tma_gemm(const void* A, int64_t lda, const void* B, int64_t 
   if (!make_map(&ma, A, M, Kd, lda, TM) || !make_map(&mb, B, N, Kd, ldb, TN)) return cudaErrorInvalidValue;
   dim3 grid((N + TN - 1) / TN, (M + TM - 1) / TM);
   if (grid.y > 65535) return cudaErrorInvalidValue;
-  tc_tma_bf16_kernel<<<grid, TMA_THREADS, kSmemBytes, s>>>(ma, mb, C, ldc, M, N, Kd, d_status);
+  tc_tma_bf16_kernel<<<grid, TMA_THREADS, kSmemBytes, s>>>(ma, mb, C, ldc, M, N, Kd, Kd, 0, d_status);
   return cudaGetLastError();
+}
+
+cudaError_t tc_bf16_tma_gram_partials(const void* Xt, int64_t ldx, int Kp, int N, float* part, int splits,
+                                      int* d_status, cudaStream_t s) {
+  if (Kp <= 0 || N <= 0 || splits < 1) return cudaErrorInvalidValue;
+  if ((reinterpret_cast<uintptr_t>(Xt) & 15) || (ldx & 7)) return cudaErrorInvalidValue;
+  if (!tma_available()) return cudaErrorNotSupported;
+  CUtensorMap m;
+  if (!make_map(&m, Xt, Kp, N, ldx, TM)) return cudaErrorInvalidValue;
+  const int kps = ((N + splits - 1) / splits + TK - 1) / TK * TK;
+  dim3 grid((Kp + TN - 1) / TN, (Kp + TM - 1) / TM, splits);
+  tc_tma_bf16_kernel<<<grid, TMA_THREADS, kSmemBytes, s>>>(m, m, part, Kp, Kp, Kp, N, kps, (int64_t)Kp * Kp,
+                                                            d_status);
+  return cudaGetLastError();
+}
+
+int tma_gram_splits(int Kp, int N) {
+  const int tiles = ((Kp + TN - 1) / TN) * ((Kp + TM - 1) / TM);
+  int splits = std::max(1, 148 / tiles);
+  splits = std::min(splits, std::max(1, (N + TK - 1) / TK));     // at least one K slice each
+  return std::min(splits, 256);
 }
 
 }  // namespace plnmf
