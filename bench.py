@@ -57,6 +57,17 @@ def _tensor_peak(bf16):
         return (1800.0, "fallback") if bf16 else (77.0, "fallback")
 
 
+def max_over_ranks(x: float, dist: bool, device) -> float:
+    """The largest value of x over all ranks (x itself on one process)."""
+    if not dist:
+        return x
+    import torch
+    import torch.distributed as tdist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def _dist_env():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -340,10 +351,7 @@ def run_gpu(args):
         if clocks is not None:
             clocks["remeasured_after"] = first
     f2, rel = ctx.error()
-    if dist:
-        t = torch.tensor([ms], device=dev)
-        tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ms, dist, dev)
 
     # warm-L2 steady state (iterations back to back, no flush), for context
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
