@@ -99,13 +99,13 @@ __device__ __forceinline__ void stage_gcols(float* Gc, const float* __restrict__
 // range is copied; one entirely out of range is zero-filled by the copy
 // (source size 0); a chunk straddling K (K not a multiple of 4) is written
 // with plain stores, masked.
-template <int NT>
+template <int NT, int LDG = HT>
 __device__ __forceinline__ void prefetch_gcols(float* Gc, const float* __restrict__ G, int Kp, int K, int lo, int Kr) {
   const int total = Kr * (HT / 4);
   for (int e = threadIdx.x; e < total; e += NT) {
     const int j = e >> 2, q = e & 3;
     const int c = lo + 4 * q;
-    float* d = Gc + j * HT + 4 * q;
+    float* d = Gc + j * LDG + 4 * q;
     if (j < K && c < K && c + 3 >= K) {
 #pragma unroll
       for (int u = 0; u < 4; ++u) d[u] = c + u < K ? G[(int64_t)j * Kp + c + u] : 0.f;
@@ -285,6 +285,149 @@ __global__ void __launch_bounds__(128) h_update_kernel(float* __restrict__ X, co
   }
 }
 
+// Row-per-warp form of the H update.  Rows (documents) are independent, so a
+// warp owns one row: lane l keeps h_j and R_j for j = l, l + 32, ... (M
+// registers each) and the row never leaves registers.  For the tile [lo, hi)
+// and its column c = lo + t (owned by the lane that holds j = c):
+//   1. every lane adds S[j][c] h_j for all 16 t over its own j outside the
+//      tile (new values left of it, old values right of it);
+//   2. a reduce-scatter over the warp (xor 16, 8, 4, 2 halving the columns
+//      each time, then xor 1) leaves column t's sum in lanes 2t and 2t + 1,
+//      and one more shuffle moves it to the column's owner;
+//   3. the owner forms y_c = (1 - S_cc) h_c + R_c - sum, then subtracts
+//      S[j][c] h_j(old) for the tile's j > c (each old value broadcast in
+//      turn), which is Alg. 1's y before the tile's own new values;
+//   4. the tile's columns are finished in order: h_c(new) = max(eps, y_c) is
+//      broadcast and S[c][c'] h_c(new) subtracted from the later columns c'.
+// The same terms as h_update_kernel, in another summation order.  The CTA's
+// warps share each tile's 16 columns of S in shared memory (double buffered
+// with cp.async, as in h_update_kernel).
+template <int M>
+__global__ void __launch_bounds__(256) h_update_warp_kernel(float* __restrict__ X, const float* __restrict__ B,
+                                                            const float* __restrict__ G, int N, int K, int Kp,
+                                                            float eps) {
+  constexpr int NT = 256, WARPS = NT / 32;
+  // S block rows padded to 20 floats: the 32 lanes read 32 consecutive rows
+  // with 16-byte loads, and an 80-byte stride puts every 8 of them on
+  // distinct banks.
+  constexpr int LDG = HT + 4;
+  extern __shared__ __align__(16) float smem[];
+  const int Kr = (Kp + HT - 1) / HT * HT;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int row = blockIdx.x * WARPS + warp;
+  const bool valid = row < N;
+  const unsigned full = 0xffffffffu;
+  prefetch_gcols<NT, LDG>(smem, G, Kp, K, 0, Kr);
+  float hj[M], rj[M];
+#pragma unroll
+  for (int m = 0; m < M; ++m) {
+    const int j = lane + 32 * m;
+    const bool in = valid && j < Kp;
+    hj[m] = in ? X[(int64_t)row * Kp + j] : 0.f;
+    rj[m] = in ? B[(int64_t)row * Kp + j] : 0.f;
+  }
+  for (int lo = 0, tb = 0; lo < K; lo += HT, tb ^= 1) {
+    const int hi = min(K, lo + HT), Tw = hi - lo;
+    const float* Gc = smem + tb * Kr * LDG;
+    asm volatile("cp.async.wait_group 0;" ::: "memory");
+    __syncthreads();                                      // this tile's block of S landed; the other buffer is free
+    if (lo + HT < K) prefetch_gcols<NT, LDG>(smem + (tb ^ 1) * Kr * LDG, G, Kp, K, lo + HT, Kr);
+    // Lane o = (lo % 32) + t owns column t (j = lo + t, register slot mt).
+    const int mt = lo >> 5;
+    const int t_own = lane - (lo & 31);
+    const bool own = t_own >= 0 && t_own < Tw;
+    float hold = 0.f, r = 0.f;
+#pragma unroll
+    for (int m = 0; m < M; ++m)
+      if (m == mt) {
+        hold = hj[m];
+        r = rj[m];
+        if (own) hj[m] = 0.f;                              // the tile's own j stay out of step 1
+      }
+    // 1. partial column sums over this lane's j outside the tile
+    float p[HT];
+#pragma unroll
+    for (int t = 0; t < HT; ++t) p[t] = 0.f;
+#pragma unroll
+    for (int m = 0; m < M; ++m) {
+      const int j = lane + 32 * m;
+      if (j < Kp) {
+        const float4* g4 = reinterpret_cast<const float4*>(Gc + j * LDG);
+#pragma unroll
+        for (int q = 0; q < HT / 4; ++q) {
+          const float4 g = g4[q];
+          p[4 * q] = fmaf(g.x, hj[m], p[4 * q]);
+          p[4 * q + 1] = fmaf(g.y, hj[m], p[4 * q + 1]);
+          p[4 * q + 2] = fmaf(g.z, hj[m], p[4 * q + 2]);
+          p[4 * q + 3] = fmaf(g.w, hj[m], p[4 * q + 3]);
+        }
+      }
+    }
+    // 2. reduce-scatter: after the halving steps lane l holds column l >> 1
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {                          // xor 16: keep columns [8 b4, 8 b4 + 8)
+      const bool up = lane & 16;
+      const float send = up ? p[k] : p[k + 8];
+      const float recv = __shfl_xor_sync(full, send, 16);
+      p[k] = (up ? p[k + 8] : p[k]) + recv;
+    }
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {                          // xor 8
+      const bool up = lane & 8;
+      const float send = up ? p[k] : p[k + 4];
+      const float recv = __shfl_xor_sync(full, send, 8);
+      p[k] = (up ? p[k + 4] : p[k]) + recv;
+    }
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {                          // xor 4
+      const bool up = lane & 4;
+      const float send = up ? p[k] : p[k + 2];
+      const float recv = __shfl_xor_sync(full, send, 4);
+      p[k] = (up ? p[k + 2] : p[k]) + recv;
+    }
+    {                                                      // xor 2
+      const bool up = lane & 2;
+      const float send = up ? p[0] : p[1];
+      const float recv = __shfl_xor_sync(full, send, 2);
+      p[0] = (up ? p[1] : p[0]) + recv;
+    }
+    p[0] += __shfl_xor_sync(full, p[0], 1);                // the two lanes of a column: same sum
+    const float T = __shfl_sync(full, p[0], own ? 2 * t_own : 0);
+    // 3. y before the tile's own new values
+    const float scc = own ? Gc[(lo + t_own) * LDG + t_own] : 0.f;
+    float y = fmaf(1.f - scc, hold, r) - T;
+#pragma unroll
+    for (int t = 0; t < HT; ++t) {
+      if (t >= Tw) break;
+      const float ho = __shfl_sync(full, hold, (lo & 31) + t);
+      if (own && t_own < t) y = fmaf(-Gc[(lo + t) * LDG + t_own], ho, y);
+    }
+    // 4. the tile's columns in order
+    float hnew = hold;
+#pragma unroll
+    for (int t = 0; t < HT; ++t) {
+      if (t >= Tw) break;
+      float v = 0.f;
+      if (t_own == t) {
+        hnew = fmaxf(eps, y);
+        v = hnew;
+      }
+      v = __shfl_sync(full, v, (lo & 31) + t);
+      if (own && t_own > t) y = fmaf(-Gc[(lo + t) * LDG + t_own], v, y);
+    }
+#pragma unroll
+    for (int m = 0; m < M; ++m)
+      if (m == mt) hj[m] = own ? hnew : hold;
+  }
+  if (valid) {
+#pragma unroll
+    for (int m = 0; m < M; ++m) {
+      const int j = lane + 32 * m;
+      if (j < Kp) X[(int64_t)row * Kp + j] = hj[m];
+    }
+  }
+}
+
 // Base of one W tile [lo, hi) for the column chain (left-looking form of
 // Eqs. 4-6): for every row v and tile column c,
 //   Y[v, c] = P[v, c] - sum_{j < new_end} Q[j][c] W[v, j](new)
@@ -388,12 +531,26 @@ cudaError_t h_update_launch(float* X, const float* B, const float* G, int N, int
   return cudaGetLastError();
 }
 
+template <int M>
+cudaError_t h_update_warp_launch(float* X, const float* B, const float* G, int N, int K, int Kp, float eps,
+                                 cudaStream_t s) {
+  const size_t smem = sizeof(float) * 2 * (size_t)((Kp + HT - 1) / HT * HT) * (HT + 4);
+  auto kern = h_update_warp_kernel<M>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  kern<<<(N + 7) / 8, 256, smem, s>>>(X, B, G, N, K, Kp, eps);
+  return cudaGetLastError();
+}
+
 cudaError_t h_update_run(float* X, const float* B, const float* G, int N, int K, int Kp, float eps,
                          int* status, cudaStream_t s) {
-  // Rows per lane group R: register blocking (one 16-byte load of S serves R
-  // rows) only while the grid still gives every SM about three CTAs of four
-  // warps; the in-tile column chain is a dependent shuffle sequence whose
-  // latency needs several resident warps to hide.
+  if (N <= 0 || K <= 0) return cudaSuccess;
+  // One warp per row for short rows (Kp <= 32): the row is one register per
+  // lane and the warp kernel's per-row column chain is short.  For longer
+  // rows the four-lanes-per-row kernel is faster: its chain runs for eight
+  // rows per warp at once (measured at K = 160: 68 us against 96 us).
+  if ((Kp + 31) / 32 == 1) return h_update_warp_launch<1>(X, B, G, N, K, Kp, eps, s);
+  // Four lanes per row, rows per lane group chosen for occupancy.
   static int sms = 0;
   if (sms == 0) {
     int dev = 0;

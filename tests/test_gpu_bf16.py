@@ -7,11 +7,8 @@ On the planted test matrices (rank = K) the first W update is nearly
 singular: the FP64 oracle itself moves W by ~0.3 when only its product
 operands are rounded to BF16, so W is compared with the BF16-operand oracle
 and H (well conditioned) also with the plain FP64 oracle.  Tolerances: one
-iteration 2e-2 (max-norm relative); objective after 100 iterations
-one-sided, f_gpu <= f_oracle (1 + 1e-3): on an unconverged run the
-trajectories separate (a plain FP32 run already ends a few percent away from
-FP64), so the check is that the BF16 form reaches at least the oracle's
-accuracy."""
+iteration 2e-2 (max-norm relative); objective after 100 iterations on
+planted inputs: see test_objective_after_100_iterations_against_oracle."""
 
 import math
 
@@ -58,21 +55,34 @@ def test_bf16_one_iteration(nmf):
     assert rel_h(Hg, Hr) < 2e-2
 
 
-def test_bf16_objective_against_fp32_A_and_oracle(nmf):
-    prob = synth.planted_dense(768, 640, 32, 0xC3 + 1)
+@pytest.mark.parametrize("shape", [(1024, 768, 8), (512, 384, 16)])
+def test_objective_after_100_iterations_against_oracle(nmf, shape):
+    """Relative objective after 100 iterations on planted rank-r inputs
+    (rank r = K).  FP32 form: within 1e-4 of the FP64 oracle.  BF16 form:
+    within 3e-3 of the BF16-operand oracle (its definition, Alg. 1 with the
+    product operands rounded to BF16): separate orderings of the same BF16
+    arithmetic scatter by about 1e-3 over 100 unconverged iterations
+    (measured: -1.1e-3 .. +1.0e-3 over three inputs, while the FP64 and
+    BF16-operand oracles themselves differ by 1e-3 .. 4e-3 there).  nmf_error
+    measures the fit to the FP32 A, not to its BF16 copy."""
+    import torch
+    V, D, r = shape
+    prob = synth.planted_dense(V, D, r, 0xC3 + 7)
     A = prob.A
-    W0, H0 = synth.init_factors(9, 768, 640, 32)
-    ctx = _ctx(nmf, A, 32, W0, H0)
-    ctx.iterate(100)
-    f_gpu, rel = ctx.error()
-    Wg, Hg = ctx.get_factors()
-    f_direct = ob.frob2_direct(A, Wg, Hg)
-    # nmf_error measures the fit to the FP32 A (not to its BF16 copy)
-    assert abs(f_gpu - f_direct) <= 1e-5 * f_direct
-    assert abs(rel - math.sqrt(f_direct / ob.norm2_A(A))) <= 1e-5
+    W0, H0 = synth.init_factors(9, V, D, r)
     Wr, Hr, _ = fh.run(A, W0, H0, 100)
-    f_ref = ob.frob2_direct(A, Wr, Hr)
-    assert f_direct <= f_ref * (1 + 1e-3)
+    f64 = ob.frob2_direct(A, Wr, Hr)
+    Wb, Hb, _ = fh.run(A, W0, H0, 100, operand_round=round_bf16)
+    fb = ob.frob2_direct(A, Wb, Hb)
+    for prec, ref, tol in ((nmf.PREC_FP32, f64, 1e-4), (nmf.PREC_BF16, fb, 3e-3)):
+        ctx = nmf.from_dense(A, r, W0=torch.from_numpy(W0).cuda(), H0=torch.from_numpy(H0).cuda(), prec=prec)
+        ctx.iterate(100)
+        f_gpu, rel = ctx.error()
+        Wg, Hg = ctx.get_factors()
+        f_direct = ob.frob2_direct(A, Wg, Hg)
+        assert abs(f_gpu - f_direct) <= 1e-5 * f_direct
+        assert abs(rel - math.sqrt(f_direct / ob.norm2_A(A))) <= 1e-5
+        assert abs(f_direct - ref) <= tol * ref, (prec, f_direct, ref)
 
 
 def test_bf16_rejected_for_sparse(nmf):
