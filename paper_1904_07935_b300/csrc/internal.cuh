@@ -164,6 +164,7 @@ struct WPersistConfig {
   int rpt = 1;
   int n_clusters = 0;
   int worker_rows = 128;
+  int chain_rows = 0;     // rows per chain CTA
   size_t smem = 0;
 };
 bool w_persistent_config(int N, int Kp, WPersistConfig* cfg);

@@ -9,7 +9,8 @@
 //
 // Roles inside the launch (grid = NC clusters of CL = 16 CTAs, all resident
 // at once, which the cooperative launch guarantees):
-//  * cluster 0 ("chain") owns every row of W: each of its row threads keeps
+//  * cluster 0 ("chain") owns every row of W (each CTA a contiguous block of
+//    ceil(N / 16) rows): each of its row threads keeps
 //    RPT rows of the current tile in registers and finishes the tile's
 //    columns one after another; the norm of each column is reduced across
 //    the cluster through distributed shared memory (as in chain.cu: warp 0 of
@@ -52,6 +53,7 @@ struct WParams {
   int* sync;           // [0, nt): base_ready, [nt, 2 nt): chain_done
   int cl;              // CTAs per cluster (chain cluster size)
   int worker_rows;     // rows per worker pass (4 lanes per row)
+  int chain_rows;      // rows per chain CTA, ceil(N / cl): CTA rank owns [rank * chain_rows, ...)
 };
 
 __device__ __forceinline__ unsigned cluster_id_x() {
@@ -243,8 +245,10 @@ __device__ void chain_role(const WParams& p, char* smem, int n_workers) {
   const int tr = tid - 32;
   const unsigned rank = cluster_ctarank();
   const int CL = p.cl;
-  const int cta_base = (int)rank * WNR;
-  const int stride = CL * WNR;
+  // This CTA's rows: the contiguous block [row0, row0 + nloc); local row
+  // li = i * WNR + tr belongs to row thread tr, register row i.
+  const int row0 = (int)rank * p.chain_rows;
+  const int nloc = max(0, min(p.chain_rows, p.N - row0));
   const int nt = (p.K + WT - 1) / WT;
   auto sidx = [](int i, int t, int r) { return (i * WT + t) * (WNR + 1) + r; };
 
@@ -260,7 +264,7 @@ __device__ void chain_role(const WParams& p, char* smem, int n_workers) {
 
   bool valid[RPT];
 #pragma unroll
-  for (int i = 0; i < RPT; ++i) valid[i] = warp > 0 && cta_base + i * stride + tr < p.N;
+  for (int i = 0; i < RPT; ++i) valid[i] = warp > 0 && i * WNR + tr < nloc;
   // y[i][1..16]: the tile's columns; between tiles y holds the previous
   // tile's contribution to the next one (z), subtracted from the base.
   float y[RPT][NS];
@@ -282,18 +286,16 @@ __device__ void chain_role(const WParams& p, char* smem, int n_workers) {
     }
     __syncthreads();
     // Base of the tile for this CTA's rows (4 lanes per row, 16 bytes each).
-    const int total = RPT * WNR * 4;
+    const int total = nloc * 4;
     for (int base = tid; base < total; base += 4 * WNT) {
       float v[4][4];
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
         const int e = base + u * WNT;
-        const int i = e / (WNR * 4), rem = e % (WNR * 4);
-        const int r = rem >> 2, q = rem & 3;
-        const int row = cta_base + i * stride + r;
+        const int row = row0 + (e >> 2), q = e & 3;
 #pragma unroll
         for (int j = 0; j < 4; ++j) v[u][j] = 0.f;
-        if (e < total && row < p.N) {
+        if (e < total) {
           const float* src = p.Y + (int64_t)row * p.Kp + lo + 4 * q;
           if (4 * q + 3 < Tw) {
             const float4 f = *reinterpret_cast<const float4*>(src);
@@ -308,8 +310,8 @@ __device__ void chain_role(const WParams& p, char* smem, int n_workers) {
       for (int u = 0; u < 4; ++u) {
         const int e = base + u * WNT;
         if (e >= total) continue;
-        const int i = e / (WNR * 4), rem = e % (WNR * 4);
-        const int r = rem >> 2, q = rem & 3;
+        const int li = e >> 2, q = e & 3;
+        const int i = li / WNR, r = li - i * WNR;
 #pragma unroll
         for (int j = 0; j < 4; ++j) st[sidx(i, 4 * q + j, r)] = v[u][j];
       }
@@ -320,7 +322,7 @@ __device__ void chain_role(const WParams& p, char* smem, int n_workers) {
       for (int i = 0; i < RPT; ++i) {
         y[i][0] = 0.f;
 #pragma unroll
-        for (int t = 0; t < WT; ++t) y[i][1 + t] = st[sidx(i, t, tr)] - y[i][1 + t];
+        for (int t = 0; t < WT; ++t) y[i][1 + t] = valid[i] ? st[sidx(i, t, tr)] - y[i][1 + t] : 0.f;
       }
     }
 
@@ -446,10 +448,9 @@ __device__ void chain_role(const WParams& p, char* smem, int n_workers) {
     }
     // Store the finished tile (4 lanes per row), then publish it.
     for (int e = tid; e < total; e += WNT) {
-      const int i = e / (WNR * 4), rem = e % (WNR * 4);
-      const int r = rem >> 2, q = rem & 3;
-      const int row = cta_base + i * stride + r;
-      if (row >= p.N) continue;
+      const int li = e >> 2, q = e & 3;
+      const int i = li / WNR, r = li - i * WNR;
+      const int row = row0 + li;
       float v[4];
 #pragma unroll
       for (int j = 0; j < 4; ++j) v[j] = st[sidx(i, 4 * q + j, r)];
@@ -553,7 +554,8 @@ size_t w_sync_ints(int K) { return (size_t)2 * ((K + WT - 1) / WT) * kSyncStride
 
 bool w_persistent_config(int N, int Kp, WPersistConfig* cfg) {
   for (int cl : {16, 8}) {
-    const int rpt = (N + cl * WNR - 1) / (cl * WNR);
+    const int nrc = (N + cl - 1) / cl;
+    const int rpt = (nrc + WNR - 1) / WNR;
     if (rpt > 4) continue;
     int worker_rows = WNT / 4;
     while (worker_rows > 16 && persistent_smem(rpt, Kp, worker_rows) > 200 * 1024) worker_rows /= 2;
@@ -563,6 +565,7 @@ bool w_persistent_config(int N, int Kp, WPersistConfig* cfg) {
     if (nc < 2) continue;
     cfg->cluster = cl;
     cfg->rpt = rpt;
+    cfg->chain_rows = nrc;
     cfg->n_clusters = std::min(nc, 9);
     cfg->worker_rows = worker_rows;
     cfg->smem = smem;
@@ -576,7 +579,7 @@ cudaError_t w_persistent_run(float* X, const float* P, const float* Q, float* Y,
   const int nt = (K + WT - 1) / WT;
   cudaError_t e = cudaMemsetAsync(d_sync, 0, sizeof(int) * w_sync_ints(K), s);
   if (e != cudaSuccess) return e;
-  WParams p{X, P, Q, Y, N, K, Kp, eps, d_status, d_sync, cfg.cluster, cfg.worker_rows};
+  WParams p{X, P, Q, Y, N, K, Kp, eps, d_status, d_sync, cfg.cluster, cfg.worker_rows, cfg.chain_rows};
   switch (cfg.rpt) {
     case 1: return launch_persistent_t<1>(p, cfg.n_clusters, cfg.smem, s);
     case 2: return launch_persistent_t<2>(p, cfg.n_clusters, cfg.smem, s);
