@@ -438,7 +438,8 @@ __global__ void __launch_bounds__(256) h_update_warp_kernel(float* __restrict__ 
 // new_end = lo - 16 the previous tile is left out, so the kernel can run
 // while the chain is still finishing that tile (columns in [new_end, lo) are
 // neither read for the result nor written here), and the chain adds the
-// previous tile's contribution itself.
+// previous tile's contribution itself.  B == nullptr leaves the data term out
+// (Y = -sums; the caller adds P later).
 __global__ void __launch_bounds__(HTHREADS) w_prep_kernel(const float* __restrict__ X, const float* __restrict__ B,
                                                           const float* __restrict__ G, float* __restrict__ Y,
                                                           int N, int K, int Kp, int lo, int new_end, int* status) {
@@ -465,7 +466,7 @@ __global__ void __launch_bounds__(HTHREADS) w_prep_kernel(const float* __restric
 #pragma unroll
   for (int q = 0; q < 4; ++q) {
     const int c = lo + 4 * sub + q;
-    acc[q] = c < hi ? __ldg(B + (int64_t)row * Kp + c) : 0.f;
+    acc[q] = (c < hi && B) ? __ldg(B + (int64_t)row * Kp + c) : 0.f;
   }
   auto outside = [&](int j0, int j1) {
 #pragma unroll 2

@@ -170,8 +170,11 @@ struct WPersistConfig {
 bool w_persistent_config(int N, int Kp, WPersistConfig* cfg);
 // d_sync: w_sync_ints(K) ints (zeroed by the call, on the stream).
 size_t w_sync_ints(int K);
+// pre0: Y's columns [0, 16) already hold tile 0's base less P (w_prep_run
+// with B = nullptr, lo = new_end = 0); the launch then only adds P there.
 cudaError_t w_persistent_run(float* X, const float* P, const float* Q, float* Y, int N, int K, int Kp, float eps,
-                             int* d_sync, int* d_status, const WPersistConfig& cfg, cudaStream_t s);
+                             int* d_sync, int* d_status, const WPersistConfig& cfg, cudaStream_t s,
+                             bool pre0 = false);
 
 // ---------------------------------------------------------------------------
 // Misc kernels.

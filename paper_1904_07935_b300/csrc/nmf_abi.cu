@@ -183,7 +183,7 @@ cudaError_t enq_gram(nmf_ctx* c, const GramWork& g, const float* X, float* out, 
 //  W: per tile of 16 columns, a full-grid kernel forms the tile's base from the
 //     current rows (new columns left of the tile, old ones right of it), then
 //     the cluster kernel finishes the tile's columns with their norms.
-cudaError_t enq_update(nmf_ctx* c, float* X, const float* G, const float* B, int N, bool is_w) {
+cudaError_t enq_update(nmf_ctx* c, float* X, const float* G, const float* B, int N, bool is_w, bool pre0 = false) {
   const int K = c->K, Kp = c->Kp;
   if (!is_w) {
     c->launch_count += 1;
@@ -191,7 +191,7 @@ cudaError_t enq_update(nmf_ctx* c, float* X, const float* G, const float* B, int
   }
   if (c->w_persistent) {
     c->launch_count += 1;
-    return w_persistent_run(X, B, G, c->Y, N, K, Kp, c->eps, c->d_sync, c->d_status, c->wp, c->stream);
+    return w_persistent_run(X, B, G, c->Y, N, K, Kp, c->eps, c->d_sync, c->d_status, c->wp, c->stream, pre0);
   }
   // W: tile tau's base without tile tau-1 ("main") runs on the side stream
   // while the chain of tile tau-1 runs; the chain of tile tau adds tile
@@ -252,10 +252,17 @@ cudaError_t enq_iteration(nmf_ctx* c) {
   if ((e = cudaEventRecord(c->evx[0], m)) != cudaSuccess) return e;
   if ((e = cudaStreamWaitEvent(b, c->evx[0], 0)) != cudaSuccess) return e;
   if ((e = enq_gram(c, c->gramH, c->Ht, c->Q, b, shared_op)) != cudaSuccess) return e;
+  // Persistent W update: tile 0's base less P (it needs Q and the old W
+  // only) on this branch, while P is still running.
+  const bool pre0 = c->w_persistent;
+  if (pre0) {
+    c->launch_count += 1;
+    if ((e = w_prep_run(c->W, nullptr, c->Q, c->Y, c->V, c->K, c->Kp, 0, 0, c->d_status, b)) != cudaSuccess) return e;
+  }
   if ((e = cudaEventRecord(c->evx[1], b)) != cudaSuccess) return e;
   if ((e = enq_product_P(c, shared_op)) != cudaSuccess) return e;
   if ((e = cudaStreamWaitEvent(m, c->evx[1], 0)) != cudaSuccess) return e;
-  if ((e = enq_update(c, c->W, c->Q, c->P, c->V, true)) != cudaSuccess) return e;
+  if ((e = enq_update(c, c->W, c->Q, c->P, c->V, true, pre0)) != cudaSuccess) return e;
   if (shared_op && (e = bf16_operand(c, true, m)) != cudaSuccess) return e;
   if ((e = cudaEventRecord(c->evx[2], m)) != cudaSuccess) return e;
   if ((e = cudaStreamWaitEvent(b, c->evx[2], 0)) != cudaSuccess) return e;

@@ -54,6 +54,7 @@ struct WParams {
   int cl;              // CTAs per cluster (chain cluster size)
   int worker_rows;     // rows per worker pass (4 lanes per row)
   int chain_rows;      // rows per chain CTA, ceil(N / cl): CTA rank owns [rank * chain_rows, ...)
+  int pre0;            // Y's first tile already holds tile 0's base less P (computed before the launch)
 };
 
 __device__ __forceinline__ unsigned cluster_id_x() {
@@ -137,7 +138,7 @@ __device__ void worker_role(const WParams& p, char* smem, int wid, int n_workers
         if (e < Kr * WT) Gc[e] = v[u];
       }
     }
-    for (int rb = wid; rb < nrb; rb += n_workers) {
+    for (int rb = (tau == 0 && p.pre0) ? nrb : wid; rb < nrb; rb += n_workers) {
       const int row0 = rb * RB;
       const int nrows = min(RB, p.N - row0);
       __syncthreads();                                        // Gc staged; Xs free
@@ -303,6 +304,11 @@ __device__ void chain_role(const WParams& p, char* smem, int n_workers) {
           } else {
 #pragma unroll
             for (int j = 0; j < 4; ++j) v[u][j] = 4 * q + j < Tw ? src[j] : 0.f;
+          }
+          if (tau == 0 && p.pre0) {                           // tile 0's base less P: add P here
+            const float* ps = p.P + (int64_t)row * p.Kp + lo + 4 * q;
+#pragma unroll
+            for (int j = 0; j < 4; ++j) v[u][j] += 4 * q + j < Tw ? ps[j] : 0.f;
           }
         }
       }
@@ -575,11 +581,11 @@ bool w_persistent_config(int N, int Kp, WPersistConfig* cfg) {
 }
 
 cudaError_t w_persistent_run(float* X, const float* P, const float* Q, float* Y, int N, int K, int Kp, float eps,
-                             int* d_sync, int* d_status, const WPersistConfig& cfg, cudaStream_t s) {
+                             int* d_sync, int* d_status, const WPersistConfig& cfg, cudaStream_t s, bool pre0) {
   const int nt = (K + WT - 1) / WT;
   cudaError_t e = cudaMemsetAsync(d_sync, 0, sizeof(int) * w_sync_ints(K), s);
   if (e != cudaSuccess) return e;
-  WParams p{X, P, Q, Y, N, K, Kp, eps, d_status, d_sync, cfg.cluster, cfg.worker_rows, cfg.chain_rows};
+  WParams p{X, P, Q, Y, N, K, Kp, eps, d_status, d_sync, cfg.cluster, cfg.worker_rows, cfg.chain_rows, pre0 ? 1 : 0};
   switch (cfg.rpt) {
     case 1: return launch_persistent_t<1>(p, cfg.n_clusters, cfg.smem, s);
     case 2: return launch_persistent_t<2>(p, cfg.n_clusters, cfg.smem, s);
