@@ -338,6 +338,48 @@ cudaError_t gemm_run(const GemmArgs& a, cudaStream_t s) {
   return cudaGetLastError();
 }
 
+// C (M x N, row stride ldc) = sum over z of part[z] (M x N contiguous),
+// compensated FP32 (TwoSum cascade) in z order.
+__global__ void partial_sum_kernel(const float* __restrict__ part, int n_chunks, int M, int N,
+                                   float* __restrict__ C, int64_t ldc) {
+  const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (e >= (int64_t)M * N) return;
+  const int64_t stride = (int64_t)M * N;
+  float s = 0.f, c = 0.f;
+  for (int z = 0; z < n_chunks; ++z) {
+    float err;
+    two_sum(s, part[z * stride + e], s, err);
+    c += err;
+  }
+  const int64_t m = e / N, n = e - m * N;
+  C[m * ldc + n] = s + c;
+}
+
+int splitk_chunks(int M, int N, int Kin) {
+  const int tiles = ((N + BN - 1) / BN) * ((M + BM - 1) / BM);
+  if (tiles >= 148) return 1;
+  const int want = (296 + tiles - 1) / tiles;                 // about two waves of the SMs
+  const int most = std::max(1, Kin / (4 * BK));              // at least four K steps each
+  return std::max(1, std::min(std::min(want, most), 64));
+}
+
+cudaError_t gemm_run_split(GemmArgs a, float* part, int n_chunks, cudaStream_t s) {
+  if (n_chunks <= 1 || !part || a.mode != GM_STORE) return gemm_run(a, s);
+  float* C = a.C;
+  const int64_t ldc = a.ldc;
+  a.mode = GM_PARTIAL;
+  a.k_chunk = ((a.Kin + n_chunks - 1) / n_chunks + BK - 1) / BK * BK;
+  a.n_chunks = (a.Kin + a.k_chunk - 1) / a.k_chunk;
+  a.C = part;
+  a.ldc = a.N;
+  a.part_stride = (int64_t)a.M * a.N;
+  cudaError_t e = gemm_run(a, s);
+  if (e != cudaSuccess) return e;
+  const int64_t total = (int64_t)a.M * a.N;
+  partial_sum_kernel<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(part, a.n_chunks, a.M, a.N, C, ldc);
+  return cudaGetLastError();
+}
+
 int64_t resid2_partials(int V, int D) { return (int64_t)((D + BN - 1) / BN) * ((V + BM - 1) / BM); }
 
 cudaError_t resid2_dense(const float* A, int64_t lda, const float* W, const float* Ht, int V, int D, int K, int Kp,
@@ -372,11 +414,13 @@ cudaError_t gram_setup(GramWork& g, int N, int Kp) {
     g.n_chunks = (N + chunk - 1) / chunk;
     return cudaMalloc(&g.d_part, sizeof(float) * (size_t)g.n_chunks * Kp * Kp);
   }
-  // Enough chunks to cover about two waves of the 148 SMs.
+  // Enough chunks to cover about two waves of the 148 SMs (chunks of at
+  // least 2 BK rows; at most 256 chunks, the compensated reduction's limit).
   const int tiles = ((Kp + 63) / 64) * ((Kp + 63) / 64 + 1) / 2;
   int want = std::max(1, (296 + tiles - 1) / tiles);
   int chunk = (N + want - 1) / want;
-  chunk = std::max(256, ((chunk + BK - 1) / BK) * BK);
+  chunk = std::max(2 * BK, ((chunk + BK - 1) / BK) * BK);
+  chunk = std::max(chunk, ((N + 255) / 256 + BK - 1) / BK * BK);
   g.chunk = chunk;
   g.n_chunks = (N + chunk - 1) / chunk;
   return cudaMalloc(&g.d_part, sizeof(float) * (size_t)g.n_chunks * Kp * Kp);

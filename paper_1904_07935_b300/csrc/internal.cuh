@@ -98,6 +98,11 @@ int tma_gram_splits(int Kp, int N);
 // S (Kp x Kp, pads zero) = sum of n_chunks partial Grams, FP64 in a fixed
 // order, upper triangle mirrored.
 cudaError_t gram_reduce(const float* part, int n_chunks, int Kp, int K, float* S, cudaStream_t s);
+// Split-K for products whose tile grid leaves SMs idle: K slices per
+// product (1 = no split) and the split run, partials in part
+// (n_chunks x M x N floats) summed into a.C in a fixed order.
+int splitk_chunks(int M, int N, int Kin);
+cudaError_t gemm_run_split(GemmArgs a, float* part, int n_chunks, cudaStream_t s);
 // dst (cols x ldd, BF16) = transpose of src (rows x cols FP32, row stride lds); rows..ldd zero.
 cudaError_t transpose_to_bf16(const float* src, int rows, int cols, int64_t lds, void* dst, int64_t ldd,
                               cudaStream_t s);

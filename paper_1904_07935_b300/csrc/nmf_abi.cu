@@ -24,6 +24,8 @@ struct nmf_ctx {
   void* Fb8 = nullptr;      // BF16 transposed factor, Kp x max(ld8V, ld8D)
   int64_t ld8V = 0, ld8D = 0;
   float* gpart = nullptr;   // BF16 form: split-K partial Grams, gsplits x Kp x Kp
+  float* ppart = nullptr;   // dense FP32 products: split-K partials
+  int splitR = 1, splitP = 1;
   int gsplits = 0;
   double* resid_part = nullptr;     // dense A: partials of the direct objective
   float eps = 1e-16f;
@@ -129,7 +131,8 @@ cudaError_t enq_product_R(nmf_ctx* c, cudaStream_t s = nullptr, bool operand_rea
     return tc_bf16_tma_gemm(c->ATb8, c->ld8V, c->Fb8, c->ld8V, c->R, c->Kp, c->D, c->Kp, c->V, c->d_status, s);
   }
   if (c->bf16) return tc_gemm_run(a, TC_BF16, c->A_bf16, c->Kp > 128 ? 128 : 0, c->d_status, s);
-  return gemm_run(a, s);
+  c->launch_count += c->splitR > 1;
+  return gemm_run_split(a, c->ppart, c->splitR, s);
 }
 
 cudaError_t enq_product_P(nmf_ctx* c, bool operand_ready = false) {   // P = A H^T  (V x Kp)
@@ -153,7 +156,8 @@ cudaError_t enq_product_P(nmf_ctx* c, bool operand_ready = false) {   // P = A H
                             c->stream);
   }
   if (c->bf16) return tc_gemm_run(a, TC_BF16, c->A_bf16, c->Kp > 128 ? 128 : 0, c->d_status, c->stream);
-  return gemm_run(a, c->stream);
+  c->launch_count += c->splitP > 1;
+  return gemm_run_split(a, c->ppart, c->splitP, c->stream);
 }
 
 cudaError_t enq_gram(nmf_ctx* c, const GramWork& g, const float* X, float* out, cudaStream_t s = nullptr,
@@ -406,6 +410,12 @@ nmf_status init_impl(const nmf_problem* p, nmf_ctx* c) {
     if (!is_device_ptr(p->dense)) return NMF_EINVAL;
     c->dense = p->dense;
     c->lda = p->ld;
+    // Small products: split K so that every SM has work (R is D x Kp over V,
+    // P is V x Kp over D); the two never run at the same time.
+    c->splitR = splitk_chunks(D, Kp, V);
+    c->splitP = splitk_chunks(V, Kp, D);
+    if (c->splitR > 1 || c->splitP > 1)
+      CK(dalloc(&c->ppart, std::max((size_t)c->splitR * D, (size_t)c->splitP * V) * Kp));
     double* d_part = nullptr;
     int* d_bad = nullptr;
     CK(dalloc(&d_part, kSumsqBlocks));
@@ -526,7 +536,7 @@ void free_ctx(nmf_ctx* c) {
   gram_free(c->gramW);
   gram_free(c->gramH);
 
-  for (void* p : {(void*)c->A_bf16, c->Ab8, c->ATb8, c->Fb8, (void*)c->gpart, (void*)c->resid_part,
+  for (void* p : {(void*)c->A_bf16, c->Ab8, c->ATb8, c->Fb8, (void*)c->gpart, (void*)c->ppart, (void*)c->resid_part,
                   (void*)c->d_sync, (void*)c->rpT, (void*)c->ciT, (void*)c->vaT, (void*)c->W, (void*)c->Ht, (void*)c->R,
                   (void*)c->P, (void*)c->S, (void*)c->Q, (void*)c->Y, (void*)c->stage,
                   (void*)c->obj_partial, (void*)c->hist, (void*)c->d_counter, (void*)c->d_status})
