@@ -239,7 +239,6 @@ __device__ void chain_role(const WParams& p, char* smem, int n_workers) {
   __shared__ __align__(16) float Gn[WT][WT];                  // Q[tile][next tile]
   __shared__ float wpart[NW];
   __shared__ float cpart[2][WMAXCL];
-  __shared__ float col_inv;
   __shared__ __align__(8) unsigned long long mbar[2];
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -337,14 +336,16 @@ __device__ void chain_role(const WParams& p, char* smem, int n_workers) {
     for (int i = 0; i < RPT; ++i) xp[i] = 0.f;
 #pragma unroll 1
     for (int t = 0; t < Tw; ++t, ++gcol) {
-      float x[RPT];
       const int b = gcol & 1;
       if (warp > 0) {
+        // The clamped column goes to this thread's slots of st (normalised
+        // there after the exchange), keeping registers free across the wait.
         float ss = 0.f;
 #pragma unroll
         for (int i = 0; i < RPT; ++i) {
-          x[i] = fmaxf(p.eps, y[i][1]);
-          if (valid[i]) ss = fmaf(x[i], x[i], ss);
+          const float x = fmaxf(p.eps, y[i][1]);
+          st[sidx(i, t, tr)] = x;
+          if (valid[i]) ss = fmaf(x, x, ss);
         }
         ss = warp_sum(ss);
         if (lane == 0) wpart[warp] = ss;
@@ -372,50 +373,49 @@ __device__ void chain_role(const WParams& p, char* smem, int n_workers) {
           const unsigned rbar = mapa_u32(smem_u32(&mbar[b]), lane);
           st_async_f32(raddr, v, rbar);
         }
-        if (!dead) {
-          const unsigned bar = smem_u32(&mbar[b]);
-          const unsigned parity = (gcol >> 1) & 1;
-          unsigned long long t0 = 0;
-          unsigned polls = 0;
-          while (!mbar_try_wait(bar, parity)) {
-            if ((++polls & 31u) == 0) {
-              const unsigned long long now = global_ns();
-              if (t0 == 0) {
-                t0 = now;
-              } else if (now - t0 > kWaitLimitNs) {
-                dead = true;
-                if (lane == 0) atomicOr(p.status, ST_TIMEOUT);
-                break;
-              }
+      }
+      // Every warp waits for the column's CL partials itself and adds them in
+      // the same fixed order (no second block barrier): the partials of
+      // column gcol + 2 cannot arrive before every warp here has sent
+      // column gcol + 1, which it does only after reading these.
+      if (!dead) {
+        const unsigned bar = smem_u32(&mbar[b]);
+        const unsigned parity = (gcol >> 1) & 1;
+        unsigned long long t0 = 0;
+        unsigned polls = 0;
+        while (!mbar_try_wait(bar, parity)) {
+          if ((++polls & 31u) == 0) {
+            const unsigned long long now = global_ns();
+            if (t0 == 0) {
+              t0 = now;
+            } else if (now - t0 > kWaitLimitNs) {
+              dead = true;
+              if (lane == 0) atomicOr(p.status, ST_TIMEOUT);
+              break;
             }
           }
         }
-        dead = __any_sync(0xffffffffu, dead);
-        float tot = lane < CL ? cpart[b][lane] : 0.f;
-#pragma unroll
-        for (int o = 8; o > 0; o >>= 1) tot += __shfl_down_sync(0xffffffffu, tot, o);
-        if (lane == 0) {
-          const float nrm = sqrtf(tot);
-          col_inv = 1.0f / nrm;
-          if (gcol + 2 < p.K && !dead) mbar_arrive_expect_tx(smem_u32(&mbar[b]), CL * 4);
-          if (!(nrm > 0.f) || !(nrm < INFINITY)) {
-            if (rank == 0) atomicOr(p.status, ST_NUMERIC);
-          }
-        }
       }
-      __syncthreads();
-      if (warp > 0) {
-        const float inv = col_inv;
+      dead = __any_sync(0xffffffffu, dead);
+      float tot = lane < CL ? cpart[b][lane] : 0.f;
 #pragma unroll
-        for (int i = 0; i < RPT; ++i) {
-          x[i] *= inv;
-          st[sidx(i, t, tr)] = x[i];
-        }
+      for (int o = 8; o > 0; o >>= 1) tot += __shfl_down_sync(0xffffffffu, tot, o);
+      tot = __shfl_sync(0xffffffffu, tot, 0);
+      const float nrm = sqrtf(tot);
+      const float inv = 1.0f / nrm;
+      if (tid == 0) {
+        // Re-arm this parity for column gcol + 2 (before this warp's next send).
+        if (gcol + 2 < p.K && !dead) mbar_arrive_expect_tx(smem_u32(&mbar[b]), CL * 4);
+        if (rank == 0 && (!(nrm > 0.f) || !(nrm < INFINITY))) atomicOr(p.status, ST_NUMERIC);
+      }
+      if (warp > 0) {
         const float g1 = Gs[t][t + 1];
 #pragma unroll
         for (int i = 0; i < RPT; ++i) {
-          y[i][1] = fmaf(-x[i], g1, y[i][1]);
-          xp[i] = x[i];
+          const float x = st[sidx(i, t, tr)] * inv;
+          st[sidx(i, t, tr)] = x;
+          y[i][1] = fmaf(-x, g1, y[i][1]);
+          xp[i] = x;
         }
       }
     }
