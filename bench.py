@@ -696,6 +696,79 @@ def run_warmstart(args):
         print(json.dumps(out), flush=True)
 
 
+def run_time_to_error(args):
+    """Time to relative error (accuracy 1e-3): e_ref = the FP64 oracle's
+    relative error sqrt(f / ||A||^2) after N iterations from the same start
+    (N = 50 for the 512 x 384 case, 100 otherwise); the GPU form iterates
+    from that start, checking its relative error every CHECK iterations,
+    until e <= e_ref (1 + 1e-3) or 20 N iterations.  Reports the iterations
+    taken and the time (device time of the iterations, CUDA events; the
+    checks' host round trips are reported separately)."""
+    import torch
+    from paper_1904_07935_b300 import nmf
+    from oracle import fast_hals as fh
+    from oracle import objective as ob
+
+    world, rank, local = _dist_env()
+    torch.cuda.set_device(local)
+    K = args.k
+    prob, W0, H0 = make_workload(args.workload, K)
+    n_ref = 50 if args.workload == "dense512" else 100
+    t0 = time.perf_counter()
+    Wr, Hr, _ = fh.run(prob.A, W0, H0, n_ref)
+    e_ref = ob.relative_error(prob.A, Wr, Hr)
+    t_oracle = time.perf_counter() - t0
+    target = e_ref * (1 + 1e-3)
+    CHECK = 5
+    results = {}
+    forms = ["fp32", "bf16"] if args.workload.startswith("dense8192") or args.workload == "dense512" else ["fp32"]
+    for form in forms:
+        prec = nmf.PREC_BF16 if form == "bf16" else nmf.PREC_FP32
+        stream = torch.cuda.Stream()
+        if hasattr(prob.A, "to_scipy"):
+            rp, ci, va = nmf.sparse_device(prob)
+            ctx = nmf.Nmf(prob.A.n_rows, prob.A.n_cols, K, row_ptr=rp, col_idx=ci, val=va,
+                          W0=torch.from_numpy(W0).cuda(), H0=torch.from_numpy(H0).cuda(), stream=stream)
+            ctx._keep += [rp, ci, va]
+        else:
+            ctx = nmf.from_dense(prob.A, K, W0=torch.from_numpy(W0).cuda(), H0=torch.from_numpy(H0).cuda(),
+                                 prec=prec, stream=stream)
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        dev_ms, its, e, reached = 0.0, 0, None, False
+        th0 = time.perf_counter()
+        while its < 20 * n_ref:
+            ev0.record(stream)
+            ctx.iterate(CHECK)
+            ev1.record(stream)
+            _, e = ctx.error()                                  # synchronises the stream
+            dev_ms += ev0.elapsed_time(ev1)
+            its += CHECK
+            if e <= target:
+                reached = True
+                break
+        wall = time.perf_counter() - th0
+        results[form] = {"reached": reached, "iterations": its, "seconds_device": round(dev_ms / 1e3, 6),
+                         "seconds_wall_with_checks": round(wall, 6), "rel_err": e}
+        del ctx
+    fp = results["fp32"]
+    out = {
+        "metric": "time to relative error (target e_ref (1 + 1e-3))", "value": fp["seconds_device"], "unit": "s",
+        "n_gpus": world, "steps": fp["iterations"], "warmup": 0,
+        "ms_per_step": round(1e3 * fp["seconds_device"] / max(1, fp["iterations"]), 5),
+        "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic (seeded; no dataset)",
+        "config": {"workload": WORKLOADS[args.workload], "K": K, "e_ref": e_ref, "target": target,
+                   "oracle_iterations": n_ref, "oracle_seconds": round(t_oracle, 3), "check_every": CHECK,
+                   "forms": results},
+    }
+    if "bf16" in results:
+        bf = results["bf16"]
+        out["config"]["bf16_vs_fp32_time"] = (round(fp["seconds_device"] / bf["seconds_device"], 3)
+                                              if bf["reached"] and fp["reached"] else None)
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -708,6 +781,8 @@ def main():
     ap.add_argument("--tile", type=int, default=0)
     ap.add_argument("--cpu-iters", type=int, default=5)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--time-to-error", action="store_true",
+                    help="time for the FP32 (and BF16) forms to reach the FP64 oracle's relative error (1e-3)")
     ap.add_argument("--ws-train", type=int, default=200000, help="warmstart: training documents")
     ap.add_argument("--ws-eval", type=int, default=100000, help="warmstart: evaluation documents")
     ap.add_argument("--ws-epochs", type=int, default=20, help="warmstart: training epochs")
@@ -721,6 +796,9 @@ def main():
         args.k = {"text20ng": 160, "dense8192": 256, "dense512": 16, "batch64": 0, "warmstart": 160}[args.workload]
     if args.workload == "batch64" and args.impl != "reference":
         run_batch(args)
+        return
+    if args.time_to_error and args.impl != "reference":
+        run_time_to_error(args)
         return
     if args.workload == "warmstart":
         if args.impl == "reference":
