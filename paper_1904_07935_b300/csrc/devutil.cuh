@@ -1,6 +1,7 @@
 // Device helpers shared by the kernels of libplnmf: shared-memory addresses,
 // thread-block-cluster barriers and distributed shared memory, mbarriers,
-// bulk (TMA) copies, the global timer used to bound every wait, and warp sums.
+// bulk (TMA) copies, the global timer used to bound every wait, warp sums, and
+// compensated accumulation.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -104,6 +105,27 @@ __device__ __forceinline__ float warp_sum(float v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   return v;
+}
+
+// Error-free addition (Knuth's TwoSum): s + e == a + b exactly, s = fl(a + b).
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = a + b;
+  const float bp = s - a;
+  e = (a - (s - bp)) + (b - bp);
+}
+
+// Blocked compensated subtraction for the factor updates, whose results
+// cancel most of their data term (y = b - sum of many non-negative terms):
+// terms are gathered in a short block partial t with plain multiply-adds;
+// comp_fold subtracts the block from the running value v with TwoSum and
+// keeps the exact rounding error in c, so that v + c carries the running
+// value to about one rounding of the block partials, not of every term.
+__device__ __forceinline__ void comp_fold(float& v, float& c, float& t) {
+  float s, e;
+  two_sum(v, -t, s, e);
+  v = s;
+  c += e;
+  t = 0.f;
 }
 
 }  // namespace plnmf

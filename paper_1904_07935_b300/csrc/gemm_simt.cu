@@ -5,10 +5,13 @@
 //
 // 64 x 64 output tile per 256-thread CTA, 4 x 4 register micro-tile per
 // thread, k staged through shared memory 16 at a time (double-buffered via
-// registers).  FP32 multiply-add with FP32 accumulation.
+// registers).  FP32 multiply-add; FP32 accumulation, blocked and compensated
+// (blocks of 64 terms added to running sums with TwoSum, as in the 128 x 128
+// kernel below, the running sums here in registers).
 #include <algorithm>
 #include <vector>
 
+#include "devutil.cuh"
 #include "internal.cuh"
 
 namespace plnmf {
@@ -73,17 +76,18 @@ __global__ void __launch_bounds__(256) gemm_kernel(GemmArgs g) {
     }
   };
 
-  float acc[4][4];
+  float acc[4][4], run[4][4];
 #pragma unroll
   for (int i = 0; i < 4; ++i)
 #pragma unroll
-    for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
+    for (int j = 0; j < 4; ++j) acc[i][j] = run[i][j] = 0.f;
 
   int buf = 0;
   if (k_begin < k_end) {
     fetch(k_begin);
     stash(0);
     __syncthreads();
+    int steps = 0;
     for (int kk = k_begin; kk < k_end; kk += BK) {
       const bool more = kk + BK < k_end;
       if (more) fetch(kk + BK);
@@ -98,6 +102,13 @@ __global__ void __launch_bounds__(256) gemm_kernel(GemmArgs g) {
 #pragma unroll
           for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(av[i], bv[j], acc[i][j]);
       }
+      if (++steps == 64 / BK) {                 // running sum += block; the error restarts the block
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+          for (int j = 0; j < 4; ++j) two_sum(run[i][j], acc[i][j], run[i][j], acc[i][j]);
+        steps = 0;
+      }
       if (more) {
         stash(buf ^ 1);
         __syncthreads();
@@ -105,6 +116,10 @@ __global__ void __launch_bounds__(256) gemm_kernel(GemmArgs g) {
       }
     }
   }
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = run[i][j] + acc[i][j];
 
   // Epilogue.
   double r2 = 0.0;
@@ -245,11 +260,165 @@ __global__ void __launch_bounds__(512) gram_full_kernel(const float* __restrict_
   }
 }
 
-// Error-free addition (Knuth's TwoSum): s + e == a + b exactly, s = fl(a + b).
-__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
-  s = a + b;
-  const float bp = s - a;
-  e = (a - (s - bp)) + (b - bp);
+// Large products (dense A H^T and A^T W): 128 x 128 output tile per
+// 256-thread CTA, 8 x 8 register tile per thread (rows ty*4 + {0..3} and
+// 64 + ty*4 + {0..3}, columns likewise with tx), k staged 8 at a time through
+// shared memory (double-buffered via registers, one 16-byte global load per
+// operand per thread and step).  Operands need 16-byte aligned bases and row
+// strides that are multiples of 4 floats (checked by the caller).  Modes
+// GM_STORE and GM_PARTIAL.
+//
+// Accumulation is blocked and compensated: the registers gather 64 terms
+// (kFoldTiles k-steps of SBK), then each is added to its running sum with
+// TwoSum; the running sums live in dynamic shared memory (64 floats per
+// thread, laid out so that a warp's 16-byte accesses are conflict-free) and
+// the exact rounding error of each addition stays in the register as the
+// start of the next block.  Over a sum of L terms the error is then about
+// one rounding of the result plus sqrt(64) roundings of a 64-term block,
+// instead of about sqrt(L) roundings of the result (the dense factor updates
+// cancel most of P and R, which magnifies the products' error).
+constexpr int SB = 128, SBK = 8, SLD = SB + 4;
+constexpr int kFoldTiles = 8;
+constexpr int kSgemmThreads = 256;
+constexpr size_t kSgemmDynSmem = sizeof(float4) * 16 * kSgemmThreads;   // 64 KB of running sums
+
+// Elements (r, c .. c + 3) of a row-major matrix, zero outside rows < rmax,
+// columns < cmax.
+__device__ __forceinline__ float4 ldg4_guard(const float* __restrict__ base, int64_t ld, int r, int c, int rmax,
+                                             int cmax) {
+  float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+  if (r >= rmax) return v;
+  const float* p = base + (int64_t)r * ld + c;
+  if (c + 3 < cmax) return __ldg(reinterpret_cast<const float4*>(p));
+  if (c < cmax) v.x = __ldg(p);
+  if (c + 1 < cmax) v.y = __ldg(p + 1);
+  if (c + 2 < cmax) v.z = __ldg(p + 2);
+  return v;
+}
+
+__global__ void __launch_bounds__(kSgemmThreads, 2) sgemm128_kernel(GemmArgs g) {
+  __shared__ __align__(16) float As[2][SBK][SLD];
+  __shared__ __align__(16) float Bs[2][SBK][SLD];
+  extern __shared__ float4 run_sum[];                         // [16][256]: this thread's at [q * 256 + tid]
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  const int m0 = blockIdx.y * SB, n0 = blockIdx.x * SB;
+  int k_begin = 0, k_end = g.Kin;
+  if (g.mode == GM_PARTIAL) {
+    k_begin = blockIdx.z * g.k_chunk;
+    k_end = min(g.Kin, k_begin + g.k_chunk);
+  }
+  float4 ra, rb;
+  auto fetch = [&](int kk) {
+    if (!g.transA) ra = ldg4_guard(g.A, g.lda, m0 + (tid >> 1), kk + (tid & 1) * 4, g.M, k_end);
+    else ra = ldg4_guard(g.A, g.lda, kk + (tid >> 5), m0 + (tid & 31) * 4, k_end, g.M);
+    if (!g.transB) rb = ldg4_guard(g.B, g.ldb, kk + (tid >> 5), n0 + (tid & 31) * 4, k_end, g.N);
+    else rb = ldg4_guard(g.B, g.ldb, n0 + (tid >> 1), kk + (tid & 1) * 4, g.N, k_end);
+  };
+  auto stash = [&](int buf) {
+    if (!g.transA) {
+      const int m = tid >> 1, kq = (tid & 1) * 4;
+      As[buf][kq][m] = ra.x;
+      As[buf][kq + 1][m] = ra.y;
+      As[buf][kq + 2][m] = ra.z;
+      As[buf][kq + 3][m] = ra.w;
+    } else {
+      *reinterpret_cast<float4*>(&As[buf][tid >> 5][(tid & 31) * 4]) = ra;
+    }
+    if (!g.transB) {
+      *reinterpret_cast<float4*>(&Bs[buf][tid >> 5][(tid & 31) * 4]) = rb;
+    } else {
+      const int n = tid >> 1, kq = (tid & 1) * 4;
+      Bs[buf][kq][n] = rb.x;
+      Bs[buf][kq + 1][n] = rb.y;
+      Bs[buf][kq + 2][n] = rb.z;
+      Bs[buf][kq + 3][n] = rb.w;
+    }
+  };
+  float acc[8][8];
+#pragma unroll
+  for (int i = 0; i < 8; ++i)
+#pragma unroll
+    for (int j = 0; j < 8; ++j) acc[i][j] = 0.f;
+#pragma unroll
+  for (int q = 0; q < 16; ++q) run_sum[q * kSgemmThreads + tid] = make_float4(0.f, 0.f, 0.f, 0.f);
+  // Running sum += block (TwoSum); the rounding error restarts the block.
+  auto fold = [&]() {
+#pragma unroll
+    for (int q = 0; q < 16; ++q) {
+      float4 r = run_sum[q * kSgemmThreads + tid];
+      float* a = &acc[q >> 1][4 * (q & 1)];
+      two_sum(r.x, a[0], r.x, a[0]);
+      two_sum(r.y, a[1], r.y, a[1]);
+      two_sum(r.z, a[2], r.z, a[2]);
+      two_sum(r.w, a[3], r.w, a[3]);
+      run_sum[q * kSgemmThreads + tid] = r;
+    }
+  };
+  int buf = 0;
+  if (k_begin < k_end) {
+    fetch(k_begin);
+    stash(0);
+    __syncthreads();
+    int steps = 0;
+    for (int kk = k_begin; kk < k_end; kk += SBK) {
+      const bool more = kk + SBK < k_end;
+      if (more) fetch(kk + SBK);
+#pragma unroll
+      for (int q = 0; q < SBK; ++q) {
+        const float4 a0 = *reinterpret_cast<const float4*>(&As[buf][q][ty * 4]);
+        const float4 a1 = *reinterpret_cast<const float4*>(&As[buf][q][64 + ty * 4]);
+        const float4 b0 = *reinterpret_cast<const float4*>(&Bs[buf][q][tx * 4]);
+        const float4 b1 = *reinterpret_cast<const float4*>(&Bs[buf][q][64 + tx * 4]);
+        const float av[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+        const float bv[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+#pragma unroll
+        for (int i = 0; i < 8; ++i)
+#pragma unroll
+          for (int j = 0; j < 8; ++j) acc[i][j] = fmaf(av[i], bv[j], acc[i][j]);
+      }
+      if (++steps == kFoldTiles) {
+        fold();
+        steps = 0;
+      }
+      if (more) {
+        stash(buf ^ 1);
+        __syncthreads();
+        buf ^= 1;
+      }
+    }
+  }
+  float* C = g.C + (g.mode == GM_PARTIAL ? (int64_t)blockIdx.z * g.part_stride : 0);
+  const bool vec = (g.ldc & 3) == 0;
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    const int m = m0 + (i < 4 ? ty * 4 + i : 64 + ty * 4 + i - 4);
+    if (m >= g.M) continue;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int n = n0 + h * 64 + tx * 4;
+      const float4 r = run_sum[(2 * i + h) * kSgemmThreads + tid];
+      const float v[4] = {r.x + acc[i][4 * h], r.y + acc[i][4 * h + 1], r.z + acc[i][4 * h + 2],
+                          r.w + acc[i][4 * h + 3]};
+      float* dst = C + (int64_t)m * g.ldc + n;
+      if (vec && n + 3 < g.N) {
+        *reinterpret_cast<float4*>(dst) = make_float4(v[0], v[1], v[2], v[3]);
+      } else {
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+          if (n + j < g.N) dst[j] = v[j];
+      }
+    }
+  }
+}
+
+// The 128 x 128 kernel applies: plain or partial products, operands 16-byte
+// aligned with row strides that are multiples of 4 floats, wide enough.
+bool use_sgemm128(const GemmArgs& a) {
+  if (a.mode != GM_STORE && a.mode != GM_PARTIAL) return false;
+  if (a.upper_only || a.M < 64 || a.N < 96 || a.Kin < 64) return false;
+  if ((a.lda & 3) || (a.ldb & 3)) return false;
+  if ((reinterpret_cast<uintptr_t>(a.A) & 15) || (reinterpret_cast<uintptr_t>(a.B) & 15)) return false;
+  return true;
 }
 
 // S[i][j] = sum_z part[z][i][j] for i <= j, mirrored.  Compensated FP32
@@ -333,6 +502,14 @@ __global__ void gram_reduce_kernel(const float* __restrict__ part, int n_chunks,
 
 cudaError_t gemm_run(const GemmArgs& a, cudaStream_t s) {
   if (a.M <= 0 || a.N <= 0) return cudaSuccess;
+  if (use_sgemm128(a)) {
+    static const cudaError_t attr = cudaFuncSetAttribute(sgemm128_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                         (int)kSgemmDynSmem);
+    if (attr != cudaSuccess) return attr;
+    dim3 grid((a.N + SB - 1) / SB, (a.M + SB - 1) / SB, a.mode == GM_PARTIAL ? a.n_chunks : 1);
+    sgemm128_kernel<<<grid, kSgemmThreads, kSgemmDynSmem, s>>>(a);
+    return cudaGetLastError();
+  }
   dim3 grid((a.N + BN - 1) / BN, (a.M + BM - 1) / BM, a.mode == GM_PARTIAL ? a.n_chunks : 1);
   gemm_kernel<<<grid, 256, 0, s>>>(a);
   return cudaGetLastError();
@@ -356,9 +533,11 @@ __global__ void partial_sum_kernel(const float* __restrict__ part, int n_chunks,
 }
 
 int splitk_chunks(int M, int N, int Kin) {
-  const int tiles = ((N + BN - 1) / BN) * ((M + BM - 1) / BM);
-  if (tiles >= 148) return 1;
-  const int want = (296 + tiles - 1) / tiles;                 // about two waves of the SMs
+  // Tile grid of the kernel gemm_run will pick for a plain product.
+  const int tb = (M >= 64 && N >= 96 && Kin >= 64) ? SB : BM;
+  const int tiles = ((N + tb - 1) / tb) * ((M + tb - 1) / tb);
+  if (tiles >= 296) return 1;
+  const int want = (296 + tiles - 1) / tiles;                 // about two CTAs per SM
   const int most = std::max(1, Kin / (4 * BK));              // at least four K steps each
   return std::max(1, std::min(std::min(want, most), 64));
 }
@@ -368,7 +547,7 @@ cudaError_t gemm_run_split(GemmArgs a, float* part, int n_chunks, cudaStream_t s
   float* C = a.C;
   const int64_t ldc = a.ldc;
   a.mode = GM_PARTIAL;
-  a.k_chunk = ((a.Kin + n_chunks - 1) / n_chunks + BK - 1) / BK * BK;
+  a.k_chunk = ((a.Kin + n_chunks - 1) / n_chunks + BK - 1) / BK * BK;        // a multiple of SBK too
   a.n_chunks = (a.Kin + a.k_chunk - 1) / a.k_chunk;
   a.C = part;
   a.ldc = a.N;

@@ -12,19 +12,11 @@
 // their later columns (Eq. 5).  Earlier tiles are already written back, so
 // row j < lo of the factor holds new values and j >= lo old ones: the
 // contributions of Eqs. 4 and 6 are one pass over the row.
+#include "devutil.cuh"
 #include "internal.cuh"
 
 namespace plnmf {
 namespace {
-
-__device__ __forceinline__ unsigned smem_u32(const void* p) {
-  return static_cast<unsigned>(__cvta_generic_to_shared(p));
-}
-__device__ __forceinline__ unsigned long long global_ns() {
-  unsigned long long t;
-  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-  return t;
-}
 
 // Rows [row0, row0 + nrows) of X (row stride Kp) into shared memory with row
 // stride ldx, one bulk copy (TMA, cp.async.bulk) per row, completed on `bar`.
@@ -195,31 +187,49 @@ __global__ void __launch_bounds__(128) h_update_kernel(float* __restrict__ X, co
         const int c = lo + HT + 4 * sub + q;
         rb[i][q] = (valid[i] && c < K) ? __ldg(br[i] + c) : 0.f;
       }
-    // Columns outside the tile: j < lo (new) and j >= lo + HT (old).
+    // Columns outside the tile: j < lo (new) and j >= lo + HT (old), in
+    // blocks of HT terms folded into acc with compensation (comp_fold).
+    float cmp[R][4], blk[R][4];
+#pragma unroll
+    for (int i = 0; i < R; ++i)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) cmp[i][q] = blk[i][q] = 0.f;
     auto outside = [&](int j0, int j1) {
 #pragma unroll 1
-      for (int j = j0; j < j1; j += 4) {
-        float xs[R][4];
-#pragma unroll
-        for (int i = 0; i < R; ++i) {
-          const float4 x4 = *reinterpret_cast<const float4*>(xr[i] + j);
-          xs[i][0] = x4.x; xs[i][1] = x4.y; xs[i][2] = x4.z; xs[i][3] = x4.w;
-        }
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-          const float4 g = *reinterpret_cast<const float4*>(Gc + (j + u) * HT + 4 * sub);
+      for (int jb = j0; jb < j1; jb += HT) {
+        const int je = min(j1, jb + HT);
+#pragma unroll 1
+        for (int j = jb; j < je; j += 4) {
+          float xs[R][4];
 #pragma unroll
           for (int i = 0; i < R; ++i) {
-            acc[i][0] = fmaf(-g.x, xs[i][u], acc[i][0]);
-            acc[i][1] = fmaf(-g.y, xs[i][u], acc[i][1]);
-            acc[i][2] = fmaf(-g.z, xs[i][u], acc[i][2]);
-            acc[i][3] = fmaf(-g.w, xs[i][u], acc[i][3]);
+            const float4 x4 = *reinterpret_cast<const float4*>(xr[i] + j);
+            xs[i][0] = x4.x; xs[i][1] = x4.y; xs[i][2] = x4.z; xs[i][3] = x4.w;
+          }
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            const float4 g = *reinterpret_cast<const float4*>(Gc + (j + u) * HT + 4 * sub);
+#pragma unroll
+            for (int i = 0; i < R; ++i) {
+              blk[i][0] = fmaf(g.x, xs[i][u], blk[i][0]);
+              blk[i][1] = fmaf(g.y, xs[i][u], blk[i][1]);
+              blk[i][2] = fmaf(g.z, xs[i][u], blk[i][2]);
+              blk[i][3] = fmaf(g.w, xs[i][u], blk[i][3]);
+            }
           }
         }
+#pragma unroll
+        for (int i = 0; i < R; ++i)
+#pragma unroll
+          for (int q = 0; q < 4; ++q) comp_fold(acc[i][q], cmp[i][q], blk[i][q]);
       }
     };
     outside(0, lo);
     outside(lo + HT < Kp ? lo + HT : Kp, Kp);
+#pragma unroll
+    for (int i = 0; i < R; ++i)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) acc[i][q] += cmp[i][q];
     // Old in-tile columns j > c.
 #pragma unroll
     for (int i = 0; i < R; ++i) {
@@ -468,23 +478,33 @@ __global__ void __launch_bounds__(HTHREADS) w_prep_kernel(const float* __restric
     const int c = lo + 4 * sub + q;
     acc[q] = (c < hi && B) ? __ldg(B + (int64_t)row * Kp + c) : 0.f;
   }
+  // Blocks of HT terms folded into acc with compensation (comp_fold).
+  float cmp[4] = {0.f, 0.f, 0.f, 0.f}, blk[4] = {0.f, 0.f, 0.f, 0.f};
   auto outside = [&](int j0, int j1) {
+#pragma unroll 1
+    for (int jb = j0; jb < j1; jb += HT) {
+      const int je = min(j1, jb + HT);
 #pragma unroll 2
-    for (int j = j0; j < j1; j += 4) {
-      const float4 x4 = *reinterpret_cast<const float4*>(xr + j);
-      const float xs[4] = {x4.x, x4.y, x4.z, x4.w};
+      for (int j = jb; j < je; j += 4) {
+        const float4 x4 = *reinterpret_cast<const float4*>(xr + j);
+        const float xs[4] = {x4.x, x4.y, x4.z, x4.w};
 #pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        const float4 g = *reinterpret_cast<const float4*>(Gc + (j + u) * HT + 4 * sub);
-        acc[0] = fmaf(-g.x, xs[u], acc[0]);
-        acc[1] = fmaf(-g.y, xs[u], acc[1]);
-        acc[2] = fmaf(-g.z, xs[u], acc[2]);
-        acc[3] = fmaf(-g.w, xs[u], acc[3]);
+        for (int u = 0; u < 4; ++u) {
+          const float4 g = *reinterpret_cast<const float4*>(Gc + (j + u) * HT + 4 * sub);
+          blk[0] = fmaf(g.x, xs[u], blk[0]);
+          blk[1] = fmaf(g.y, xs[u], blk[1]);
+          blk[2] = fmaf(g.z, xs[u], blk[2]);
+          blk[3] = fmaf(g.w, xs[u], blk[3]);
+        }
       }
+#pragma unroll
+      for (int q = 0; q < 4; ++q) comp_fold(acc[q], cmp[q], blk[q]);
     }
   };
   outside(0, new_end);
   outside(lo + HT < Kp ? lo + HT : Kp, Kp);
+#pragma unroll
+  for (int q = 0; q < 4; ++q) acc[q] += cmp[q];
   float xo[HT];
 #pragma unroll
   for (int q = 0; q < HT / 4; ++q) {

@@ -175,23 +175,33 @@ __device__ void worker_role(const WParams& p, char* smem, int wid, int n_workers
           const int c = lo + 4 * sub + q;
           acc[q] = c < hi ? __ldg(p.P + (int64_t)row * p.Kp + c) : 0.f;
         }
+        // Blocks of WT terms folded into acc with compensation (comp_fold).
+        float cmp[4] = {0.f, 0.f, 0.f, 0.f}, blk[4] = {0.f, 0.f, 0.f, 0.f};
         auto outside = [&](int j0, int j1) {
+#pragma unroll 1
+          for (int jb = j0; jb < j1; jb += WT) {
+            const int je = min(j1, jb + WT);
 #pragma unroll 2
-          for (int j = j0; j < j1; j += 4) {
-            const float4 x4 = *reinterpret_cast<const float4*>(xr + j);
-            const float xs[4] = {x4.x, x4.y, x4.z, x4.w};
+            for (int j = jb; j < je; j += 4) {
+              const float4 x4 = *reinterpret_cast<const float4*>(xr + j);
+              const float xs[4] = {x4.x, x4.y, x4.z, x4.w};
 #pragma unroll
-            for (int u = 0; u < 4; ++u) {
-              const float4 g = *reinterpret_cast<const float4*>(Gc + (j + u) * WT + 4 * sub);
-              acc[0] = fmaf(-g.x, xs[u], acc[0]);
-              acc[1] = fmaf(-g.y, xs[u], acc[1]);
-              acc[2] = fmaf(-g.z, xs[u], acc[2]);
-              acc[3] = fmaf(-g.w, xs[u], acc[3]);
+              for (int u = 0; u < 4; ++u) {
+                const float4 g = *reinterpret_cast<const float4*>(Gc + (j + u) * WT + 4 * sub);
+                blk[0] = fmaf(g.x, xs[u], blk[0]);
+                blk[1] = fmaf(g.y, xs[u], blk[1]);
+                blk[2] = fmaf(g.z, xs[u], blk[2]);
+                blk[3] = fmaf(g.w, xs[u], blk[3]);
+              }
             }
+#pragma unroll
+            for (int q = 0; q < 4; ++q) comp_fold(acc[q], cmp[q], blk[q]);
           }
         };
         outside(0, new_end);
         outside(lo + WT < p.Kp ? lo + WT : p.Kp, p.Kp);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) acc[q] += cmp[q];
         float xo[WT];
 #pragma unroll
         for (int q = 0; q < WT / 4; ++q) {

@@ -179,6 +179,30 @@ def test_one_iteration_dense_512x384_k16_from_iterate_10(nmf):
     assert rel_w(Wg, Wr) < TOL_ITER
 
 
+def test_one_iteration_dense_wide_rank_from_iterate_30(nmf):
+    """Dense products with K >= 96 take the 128 x 128 SIMT kernel (both
+    A^T W and A H^T, with split K): 1000 x 900 is ragged against its tiles,
+    K = 100.  One iteration from the oracle's 30th iterate (rounded to FP32
+    and given to both sides), strict 1e-5.  At the 10th iterate this planted
+    rank-100 input is still ill-conditioned (rounding P, Q and W to FP32 once
+    moves W by ~5e-5); by the 30th that floor is ~2e-6, which the test checks
+    so that the strict bound stays meaningful."""
+    prob = synth.planted_dense(1000, 900, 100, 0xC6)
+    W0, H0 = synth.init_factors(0xC6, 1000, 900, 100)
+    W30, H30, _ = fh.run(prob.A, W0, H0, 30)
+    W30, H30 = f32(W30), f32(H30)
+    W, H = W30.astype(np.float64), H30.astype(np.float64)
+    dW, dH = fp32_storage_sensitivity(prob.A, W, H)
+    assert dW < 0.3 * TOL_ITER and dH < 0.3 * TOL_ITER
+    ctx = _dense_ctx(nmf, prob.A, 100, W0, H0)
+    ctx.set_factors(W30, H30)
+    ctx.iterate(1)
+    Wg, Hg = ctx.get_factors()
+    Wr, Hr = fh.iteration(prob.A, W, H, EPS)
+    assert rel_h(Hg, Hr) < TOL_ITER
+    assert rel_w(Wg, Wr) < TOL_ITER
+
+
 def test_one_iteration_sparse_small_ragged(nmf):
     sp = synth.sparse_termdoc(2500, 1300, 51, mean_terms=30)
     W0, H0 = synth.init_factors(52, 2500, 1300, 21)
