@@ -74,6 +74,14 @@ __device__ __forceinline__ void bulk_g2s(unsigned dst, const void* src, unsigned
                "l"(src), "r"(bytes), "r"(bar)
                : "memory");
 }
+// 4-byte asynchronous copy global -> shared (cp.async); in == false writes
+// zero (source size 0) and reads nothing.
+__device__ __forceinline__ void cp_async4(void* dst, const float* src, bool in) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(smem_u32(dst)), "l"(src), "r"(in ? 4 : 0)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 // Orders earlier generic-proxy global accesses (made visible by an acquire)
 // before later async-proxy (bulk copy) accesses of this thread.
 __device__ __forceinline__ void fence_proxy_async_global() {

@@ -449,10 +449,13 @@ __global__ void __launch_bounds__(256) h_update_warp_kernel(float* __restrict__ 
 // while the chain is still finishing that tile (columns in [new_end, lo) are
 // neither read for the result nor written here), and the chain adds the
 // previous tile's contribution itself.  B == nullptr leaves the data term out
-// (Y = -sums; the caller adds P later).
+// (Y = -sums; the caller adds P later); with Ylo given, the compensation of
+// the sum goes to Ylo (N x HT) instead of being rounded into Y, since P and
+// the sum cancel when the caller adds them.
 __global__ void __launch_bounds__(HTHREADS) w_prep_kernel(const float* __restrict__ X, const float* __restrict__ B,
                                                           const float* __restrict__ G, float* __restrict__ Y,
-                                                          int N, int K, int Kp, int lo, int new_end, int* status) {
+                                                          float* __restrict__ Ylo, int N, int K, int Kp, int lo,
+                                                          int new_end, int* status) {
   // Shared memory: Gc (Kr x HT) = G[j][lo + c], zero beyond K; Xs = the CTA's
   // rows of X (row stride Kp + 4, see h_update_kernel).
   extern __shared__ __align__(16) float smem[];
@@ -503,8 +506,7 @@ __global__ void __launch_bounds__(HTHREADS) w_prep_kernel(const float* __restric
   };
   outside(0, new_end);
   outside(lo + HT < Kp ? lo + HT : Kp, Kp);
-#pragma unroll
-  for (int q = 0; q < 4; ++q) acc[q] += cmp[q];
+  // Old in-tile columns j > c: one more block.
   float xo[HT];
 #pragma unroll
   for (int q = 0; q < HT / 4; ++q) {
@@ -517,26 +519,34 @@ __global__ void __launch_bounds__(HTHREADS) w_prep_kernel(const float* __restric
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
       const int cl = 4 * sub + q;
-      if (j > cl) acc[q] = fmaf(-Gc[(lo + j) * HT + cl], xo[j], acc[q]);
+      if (j > cl) blk[q] = fmaf(Gc[(lo + j) * HT + cl], xo[j], blk[q]);
     }
   }
+#pragma unroll
+  for (int q = 0; q < 4; ++q) comp_fold(acc[q], cmp[q], blk[q]);
   float* yr = Y + (int64_t)row * Kp;
 #pragma unroll
   for (int q = 0; q < 4; ++q) {
     const int c = lo + 4 * sub + q;
-    if (c < hi) yr[c] = acc[q];
+    if (c >= hi) continue;
+    if (Ylo) {
+      yr[c] = acc[q];
+      Ylo[(int64_t)row * HT + c - lo] = cmp[q];
+    } else {
+      yr[c] = acc[q] + cmp[q];
+    }
   }
 }
 
 }  // namespace
 
 cudaError_t w_prep_run(const float* X, const float* B, const float* G, float* Y, int N, int K, int Kp, int lo,
-                       int new_end, int* status, cudaStream_t s) {
+                       int new_end, int* status, cudaStream_t s, float* Ylo) {
   const size_t smem = sizeof(float) * ((size_t)((Kp + HT - 1) / HT * HT) * HT + (size_t)HROWS * (Kp + 4));
   cudaError_t e = cudaFuncSetAttribute(w_prep_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   const int blocks = (N + HROWS - 1) / HROWS;
-  w_prep_kernel<<<blocks, HTHREADS, smem, s>>>(X, B, G, Y, N, K, Kp, lo, new_end, status);
+  w_prep_kernel<<<blocks, HTHREADS, smem, s>>>(X, B, G, Y, B ? nullptr : Ylo, N, K, Kp, lo, new_end, status);
   return cudaGetLastError();
 }
 

@@ -158,8 +158,11 @@ cudaError_t h_update_run(float* X, const float* B, const float* G, int N, int K,
                          int* status, cudaStream_t s);
 // Base of W tile [lo, lo + 16) for the chain: Y[:, tile] from B = P, G = Q and
 // the current (partly updated) factor X, with the new columns [0, new_end).
+// B == nullptr leaves the data term out; then, with Ylo (N x 16) given, the
+// compensated sum is returned unrounded as Y[:, tile] + Ylo (the caller adds
+// P to Y first: the two cancel, so the early rounding would be magnified).
 cudaError_t w_prep_run(const float* X, const float* B, const float* G, float* Y, int N, int K, int Kp, int lo,
-                       int new_end, int* status, cudaStream_t s);
+                       int new_end, int* status, cudaStream_t s, float* Ylo = nullptr);
 constexpr int kRowTile = 16;   // tile width of the row-parallel update kernels
 
 // Persistent, cooperative W update (one launch per update): cluster 0 runs the
@@ -175,11 +178,12 @@ struct WPersistConfig {
 bool w_persistent_config(int N, int Kp, WPersistConfig* cfg);
 // d_sync: w_sync_ints(K) ints (zeroed by the call, on the stream).
 size_t w_sync_ints(int K);
-// pre0: Y's columns [0, 16) already hold tile 0's base less P (w_prep_run
-// with B = nullptr, lo = new_end = 0); the launch then only adds P there.
+// pre0 != nullptr: Y's columns [0, 16) plus pre0 (N x 16) already hold tile
+// 0's base less P (w_prep_run with B = nullptr, lo = new_end = 0, Ylo =
+// pre0); the launch then adds P there.
 cudaError_t w_persistent_run(float* X, const float* P, const float* Q, float* Y, int N, int K, int Kp, float eps,
                              int* d_sync, int* d_status, const WPersistConfig& cfg, cudaStream_t s,
-                             bool pre0 = false);
+                             const float* pre0 = nullptr);
 
 // ---------------------------------------------------------------------------
 // Misc kernels.

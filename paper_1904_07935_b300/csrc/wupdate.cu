@@ -26,8 +26,8 @@
 //    tile's contribution itself (its own rows, 16 x 16 per row), right after
 //    finishing that tile.
 // Hand-off through global memory: base_ready[tau] counts the workers that
-// wrote their rows of Y for tile tau; chain_done[tau] is set once all chain
-// CTAs stored tile tau of W.  Release/acquire ordering, and every wait is
+// wrote their rows of Y for tile tau; chain_done[tau] counts the chain CTAs
+// that stored their rows of tile tau of W.  Release/acquire ordering, and every wait is
 // bounded by the global timer (ST_TIMEOUT on expiry).
 #include <algorithm>
 
@@ -54,7 +54,7 @@ struct WParams {
   int cl;              // CTAs per cluster (chain cluster size)
   int worker_rows;     // rows per worker pass (4 lanes per row)
   int chain_rows;      // rows per chain CTA, ceil(N / cl): CTA rank owns [rank * chain_rows, ...)
-  int pre0;            // Y's first tile already holds tile 0's base less P (computed before the launch)
+  const float* pre0;   // non-null: Y's first tile + pre0 (N x 16) hold tile 0's base less P (formed before the launch)
 };
 
 __device__ __forceinline__ unsigned cluster_id_x() {
@@ -118,7 +118,7 @@ __device__ void worker_role(const WParams& p, char* smem, int wid, int n_workers
     if (tid == 0) {
       go = 1;
       if (tau >= 2 && !dead) {
-        if (!wait_counter(p.sync + (nt + tau - 2) * kSyncStride, 1, p.status)) dead = true;
+        if (!wait_counter(p.sync + (nt + tau - 2) * kSyncStride, p.cl, p.status)) dead = true;
       }
       fence_proxy_async_global();
     }
@@ -245,7 +245,7 @@ __device__ void chain_role(const WParams& p, char* smem, int n_workers) {
   constexpr int NW = WNT / 32;
   constexpr int NS = WT + 1;
   float* st = reinterpret_cast<float*>(smem);                 // RPT x WT x (WNR + 1)
-  __shared__ float Gs[WT][2 * WT];
+  __shared__ float Gs[2][WT][2 * WT];                         // Q[tile][tile], zero beyond the tile
   __shared__ __align__(16) float Gn[WT][WT];                  // Q[tile][next tile]
   __shared__ float wpart[NW];
   __shared__ float cpart[2][WMAXCL];
@@ -283,18 +283,44 @@ __device__ void chain_role(const WParams& p, char* smem, int n_workers) {
 #pragma unroll
     for (int s = 0; s < NS; ++s) y[i][s] = 0.f;
 
+  // The Q blocks a tile needs are copied asynchronously (cp.async, zero-
+  // filled outside the blocks) one tile ahead, off the tile transitions:
+  // Gs of tile tq into Gs[tq & 1]; Gn of tile tq.
+  auto fetch_gs = [&](int tq) {
+    const int qlo = tq * WT, qw = min(p.K, qlo + WT) - qlo;
+    for (int e = tid; e < WT * 2 * WT; e += WNT) {
+      const int i = e / (2 * WT), j = e % (2 * WT);
+      const bool in = i < qw && j < qw;
+      cp_async4(&Gs[tq & 1][i][j], p.Q + (in ? (int64_t)(qlo + i) * p.Kp + qlo + j : 0), in);
+    }
+  };
+  auto fetch_gn = [&](int tq) {
+    const int qlo = tq * WT, qw = min(p.K, qlo + WT) - qlo;
+    const int nlo = qlo + qw, nw = min(p.K, nlo + WT) - nlo;
+    for (int e = tid; e < WT * WT; e += WNT) {
+      const int i = e / WT, j = e % WT;
+      const bool in = i < qw && j < nw;
+      cp_async4(&Gn[i][j], p.Q + (in ? (int64_t)(qlo + i) * p.Kp + nlo + j : 0), in);
+    }
+  };
+  fetch_gs(0);
+  cp_async_commit();
+
   bool dead = false;
   int gcol = 0;                                                // global column index
   for (int tau = 0; tau < nt; ++tau) {
     const int lo = tau * WT, hi = min(p.K, lo + WT), Tw = hi - lo;
-    for (int e = tid; e < WT * 2 * WT; e += WNT) {
-      const int i = e / (2 * WT), j = e % (2 * WT);
-      Gs[i][j] = (i < Tw && j < Tw) ? p.Q[(int64_t)(lo + i) * p.Kp + lo + j] : 0.f;
-    }
+    cp_async_wait_all();                                       // Gs of this tile (issued a tile ahead)
     if (tid == 0 && !dead) {
       if (!wait_counter(p.sync + tau * kSyncStride, n_workers, p.status)) dead = true;
     }
     __syncthreads();
+    // Gn of this tile and Gs of the next: the buffers are free (tile tau - 1
+    // finished reading them before the barrier above).
+    fetch_gn(tau);
+    if (tau + 1 < nt) fetch_gs(tau + 1);
+    cp_async_commit();
+    const float(*G)[2 * WT] = Gs[tau & 1];
     // Base of the tile for this CTA's rows (4 lanes per row, 16 bytes each).
     const int total = nloc * 4;
     for (int base = tid; base < total; base += 4 * WNT) {
@@ -315,9 +341,12 @@ __device__ void chain_role(const WParams& p, char* smem, int n_workers) {
             for (int j = 0; j < 4; ++j) v[u][j] = 4 * q + j < Tw ? src[j] : 0.f;
           }
           if (tau == 0 && p.pre0) {                           // tile 0's base less P: add P here
+            // P and the early base cancel: P + hi first (nearly exact), then
+            // the early base's compensation.
             const float* ps = p.P + (int64_t)row * p.Kp + lo + 4 * q;
+            const float* cs = p.pre0 + (int64_t)row * WT + 4 * q;
 #pragma unroll
-            for (int j = 0; j < 4; ++j) v[u][j] += 4 * q + j < Tw ? ps[j] : 0.f;
+            for (int j = 0; j < 4; ++j) v[u][j] = 4 * q + j < Tw ? (ps[j] + v[u][j]) + cs[j] : 0.f;
           }
         }
       }
@@ -365,7 +394,7 @@ __device__ void chain_role(const WParams& p, char* smem, int n_workers) {
         if (t > 0) {
 #pragma unroll
           for (int s = 2; s < NS; ++s) {
-            const float g = Gs[t - 1][t + s - 1];             // slot s holds column t + s - 1
+            const float g = G[t - 1][t + s - 1];              // slot s holds column t + s - 1
 #pragma unroll
             for (int i = 0; i < RPT; ++i) y[i][s - 1] = fmaf(-xp[i], g, y[i][s]);
           }
@@ -419,7 +448,7 @@ __device__ void chain_role(const WParams& p, char* smem, int n_workers) {
         if (rank == 0 && (!(nrm > 0.f) || !(nrm < INFINITY))) atomicOr(p.status, ST_NUMERIC);
       }
       if (warp > 0) {
-        const float g1 = Gs[t][t + 1];
+        const float g1 = G[t][t + 1];
 #pragma unroll
         for (int i = 0; i < RPT; ++i) {
           const float x = st[sidx(i, t, tr)] * inv;
@@ -432,10 +461,7 @@ __device__ void chain_role(const WParams& p, char* smem, int n_workers) {
     // Contribution of this tile to the next one, z = x_tile * Q[tile][next]
     // for this CTA's rows (kept in y until the next base is loaded).
     const int nlo = hi, nhi = min(p.K, nlo + WT), Tn = nhi - nlo;
-    for (int e = tid; e < WT * WT; e += WNT) {
-      const int i = e / WT, j = e % WT;
-      Gn[i][j] = (i < Tw && j < Tn) ? p.Q[(int64_t)(lo + i) * p.Kp + nlo + j] : 0.f;
-    }
+    cp_async_wait_all();                                       // Gn of this tile, Gs of the next
     __syncthreads();
     if (warp > 0) {
 #pragma unroll
@@ -479,9 +505,14 @@ __device__ void chain_role(const WParams& p, char* smem, int n_workers) {
           if (4 * q + j < Tw) dst[j] = v[j];
       }
     }
-    __threadfence();
-    cluster_sync_all();
-    if (rank == 0 && tid == 0) st_release_gpu(p.sync + (nt + tau) * kSyncStride, 1);
+    // Every CTA publishes its own rows (the workers wait for all CL): a
+    // block barrier, then one thread's fence and count (cumulative release),
+    // with no cluster barrier, so no CTA waits for the slowest one here.
+    __syncthreads();
+    if (tid == 0) {
+      __threadfence();
+      atomicAdd(p.sync + (nt + tau) * kSyncStride, 1);
+    }
   }
   // A timed-out wait anywhere: let remote stores still in flight land before
   // any CTA of the cluster leaves.
@@ -591,11 +622,12 @@ bool w_persistent_config(int N, int Kp, WPersistConfig* cfg) {
 }
 
 cudaError_t w_persistent_run(float* X, const float* P, const float* Q, float* Y, int N, int K, int Kp, float eps,
-                             int* d_sync, int* d_status, const WPersistConfig& cfg, cudaStream_t s, bool pre0) {
+                             int* d_sync, int* d_status, const WPersistConfig& cfg, cudaStream_t s,
+                             const float* pre0) {
   const int nt = (K + WT - 1) / WT;
   cudaError_t e = cudaMemsetAsync(d_sync, 0, sizeof(int) * w_sync_ints(K), s);
   if (e != cudaSuccess) return e;
-  WParams p{X, P, Q, Y, N, K, Kp, eps, d_status, d_sync, cfg.cluster, cfg.worker_rows, cfg.chain_rows, pre0 ? 1 : 0};
+  WParams p{X, P, Q, Y, N, K, Kp, eps, d_status, d_sync, cfg.cluster, cfg.worker_rows, cfg.chain_rows, pre0};
   switch (cfg.rpt) {
     case 1: return launch_persistent_t<1>(p, cfg.n_clusters, cfg.smem, s);
     case 2: return launch_persistent_t<2>(p, cfg.n_clusters, cfg.smem, s);
