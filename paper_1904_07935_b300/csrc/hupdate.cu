@@ -194,34 +194,46 @@ __global__ void __launch_bounds__(128) h_update_kernel(float* __restrict__ X, co
     for (int i = 0; i < R; ++i)
 #pragma unroll
       for (int q = 0; q < 4; ++q) cmp[i][q] = blk[i][q] = 0.f;
-    auto outside = [&](int j0, int j1) {
-#pragma unroll 1
-      for (int jb = j0; jb < j1; jb += HT) {
-        const int je = min(j1, jb + HT);
-#pragma unroll 1
-        for (int j = jb; j < je; j += 4) {
-          float xs[R][4];
+    // Four columns j .. j+3 into the block partials.
+    auto step = [&](int j) {
+      float xs[R][4];
 #pragma unroll
-          for (int i = 0; i < R; ++i) {
-            const float4 x4 = *reinterpret_cast<const float4*>(xr[i] + j);
-            xs[i][0] = x4.x; xs[i][1] = x4.y; xs[i][2] = x4.z; xs[i][3] = x4.w;
-          }
+      for (int i = 0; i < R; ++i) {
+        const float4 x4 = *reinterpret_cast<const float4*>(xr[i] + j);
+        xs[i][0] = x4.x; xs[i][1] = x4.y; xs[i][2] = x4.z; xs[i][3] = x4.w;
+      }
 #pragma unroll
-          for (int u = 0; u < 4; ++u) {
-            const float4 g = *reinterpret_cast<const float4*>(Gc + (j + u) * HT + 4 * sub);
+      for (int u = 0; u < 4; ++u) {
+        const float4 g = *reinterpret_cast<const float4*>(Gc + (j + u) * HT + 4 * sub);
 #pragma unroll
-            for (int i = 0; i < R; ++i) {
-              blk[i][0] = fmaf(g.x, xs[i][u], blk[i][0]);
-              blk[i][1] = fmaf(g.y, xs[i][u], blk[i][1]);
-              blk[i][2] = fmaf(g.z, xs[i][u], blk[i][2]);
-              blk[i][3] = fmaf(g.w, xs[i][u], blk[i][3]);
-            }
-          }
+        for (int i = 0; i < R; ++i) {
+          blk[i][0] = fmaf(g.x, xs[i][u], blk[i][0]);
+          blk[i][1] = fmaf(g.y, xs[i][u], blk[i][1]);
+          blk[i][2] = fmaf(g.z, xs[i][u], blk[i][2]);
+          blk[i][3] = fmaf(g.w, xs[i][u], blk[i][3]);
         }
+      }
+    };
+    auto fold = [&]() {
 #pragma unroll
-        for (int i = 0; i < R; ++i)
+      for (int i = 0; i < R; ++i)
 #pragma unroll
-          for (int q = 0; q < 4; ++q) comp_fold(acc[i][q], cmp[i][q], blk[i][q]);
+        for (int q = 0; q < 4; ++q) comp_fold(acc[i][q], cmp[i][q], blk[i][q]);
+    };
+    // Full blocks of HT columns unrolled (constant offsets, loads scheduled
+    // ahead); a ragged last block (Kp not a multiple of HT) step by step.
+    auto outside = [&](int j0, int j1) {
+      int jb = j0;
+#pragma unroll 1
+      for (; jb + HT <= j1; jb += HT) {
+#pragma unroll
+        for (int jj = 0; jj < HT; jj += 4) step(jb + jj);
+        fold();
+      }
+      if (jb < j1) {
+#pragma unroll 1
+        for (int j = jb; j < j1; j += 4) step(j);
+        fold();
       }
     };
     outside(0, lo);
@@ -483,23 +495,31 @@ __global__ void __launch_bounds__(HTHREADS) w_prep_kernel(const float* __restric
   }
   // Blocks of HT terms folded into acc with compensation (comp_fold).
   float cmp[4] = {0.f, 0.f, 0.f, 0.f}, blk[4] = {0.f, 0.f, 0.f, 0.f};
-  auto outside = [&](int j0, int j1) {
-#pragma unroll 1
-    for (int jb = j0; jb < j1; jb += HT) {
-      const int je = min(j1, jb + HT);
-#pragma unroll 2
-      for (int j = jb; j < je; j += 4) {
-        const float4 x4 = *reinterpret_cast<const float4*>(xr + j);
-        const float xs[4] = {x4.x, x4.y, x4.z, x4.w};
+  auto step = [&](int j) {
+    const float4 x4 = *reinterpret_cast<const float4*>(xr + j);
+    const float xs[4] = {x4.x, x4.y, x4.z, x4.w};
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
-          const float4 g = *reinterpret_cast<const float4*>(Gc + (j + u) * HT + 4 * sub);
-          blk[0] = fmaf(g.x, xs[u], blk[0]);
-          blk[1] = fmaf(g.y, xs[u], blk[1]);
-          blk[2] = fmaf(g.z, xs[u], blk[2]);
-          blk[3] = fmaf(g.w, xs[u], blk[3]);
-        }
-      }
+    for (int u = 0; u < 4; ++u) {
+      const float4 g = *reinterpret_cast<const float4*>(Gc + (j + u) * HT + 4 * sub);
+      blk[0] = fmaf(g.x, xs[u], blk[0]);
+      blk[1] = fmaf(g.y, xs[u], blk[1]);
+      blk[2] = fmaf(g.z, xs[u], blk[2]);
+      blk[3] = fmaf(g.w, xs[u], blk[3]);
+    }
+  };
+  // Full blocks unrolled; a ragged last block step by step.
+  auto outside = [&](int j0, int j1) {
+    int jb = j0;
+#pragma unroll 1
+    for (; jb + HT <= j1; jb += HT) {
+#pragma unroll
+      for (int jj = 0; jj < HT; jj += 4) step(jb + jj);
+#pragma unroll
+      for (int q = 0; q < 4; ++q) comp_fold(acc[q], cmp[q], blk[q]);
+    }
+    if (jb < j1) {
+#pragma unroll 1
+      for (int j = jb; j < j1; j += 4) step(j);
 #pragma unroll
       for (int q = 0; q < 4; ++q) comp_fold(acc[q], cmp[q], blk[q]);
     }

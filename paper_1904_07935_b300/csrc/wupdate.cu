@@ -177,23 +177,31 @@ __device__ void worker_role(const WParams& p, char* smem, int wid, int n_workers
         }
         // Blocks of WT terms folded into acc with compensation (comp_fold).
         float cmp[4] = {0.f, 0.f, 0.f, 0.f}, blk[4] = {0.f, 0.f, 0.f, 0.f};
-        auto outside = [&](int j0, int j1) {
-#pragma unroll 1
-          for (int jb = j0; jb < j1; jb += WT) {
-            const int je = min(j1, jb + WT);
-#pragma unroll 2
-            for (int j = jb; j < je; j += 4) {
-              const float4 x4 = *reinterpret_cast<const float4*>(xr + j);
-              const float xs[4] = {x4.x, x4.y, x4.z, x4.w};
+        auto step = [&](int j) {
+          const float4 x4 = *reinterpret_cast<const float4*>(xr + j);
+          const float xs[4] = {x4.x, x4.y, x4.z, x4.w};
 #pragma unroll
-              for (int u = 0; u < 4; ++u) {
-                const float4 g = *reinterpret_cast<const float4*>(Gc + (j + u) * WT + 4 * sub);
-                blk[0] = fmaf(g.x, xs[u], blk[0]);
-                blk[1] = fmaf(g.y, xs[u], blk[1]);
-                blk[2] = fmaf(g.z, xs[u], blk[2]);
-                blk[3] = fmaf(g.w, xs[u], blk[3]);
-              }
-            }
+          for (int u = 0; u < 4; ++u) {
+            const float4 g = *reinterpret_cast<const float4*>(Gc + (j + u) * WT + 4 * sub);
+            blk[0] = fmaf(g.x, xs[u], blk[0]);
+            blk[1] = fmaf(g.y, xs[u], blk[1]);
+            blk[2] = fmaf(g.z, xs[u], blk[2]);
+            blk[3] = fmaf(g.w, xs[u], blk[3]);
+          }
+        };
+        // Full blocks unrolled; a ragged last block step by step.
+        auto outside = [&](int j0, int j1) {
+          int jb = j0;
+#pragma unroll 1
+          for (; jb + WT <= j1; jb += WT) {
+#pragma unroll
+            for (int jj = 0; jj < WT; jj += 4) step(jb + jj);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) comp_fold(acc[q], cmp[q], blk[q]);
+          }
+          if (jb < j1) {
+#pragma unroll 1
+            for (int j = jb; j < j1; j += 4) step(j);
 #pragma unroll
             for (int q = 0; q < 4; ++q) comp_fold(acc[q], cmp[q], blk[q]);
           }
@@ -243,9 +251,8 @@ __device__ void worker_role(const WParams& p, char* smem, int wid, int n_workers
 template <int RPT>
 __device__ void chain_role(const WParams& p, char* smem, int n_workers) {
   constexpr int NW = WNT / 32;
-  constexpr int NS = WT + 1;
   float* st = reinterpret_cast<float*>(smem);                 // RPT x WT x (WNR + 1)
-  __shared__ float Gs[2][WT][2 * WT];                         // Q[tile][tile], zero beyond the tile
+  __shared__ float Gs[2][WT][WT];                             // Q[tile][tile], zero beyond the tile
   __shared__ __align__(16) float Gn[WT][WT];                  // Q[tile][next tile]
   __shared__ float wpart[NW];
   __shared__ float cpart[2][WMAXCL];
@@ -275,21 +282,24 @@ __device__ void chain_role(const WParams& p, char* smem, int n_workers) {
   bool valid[RPT];
 #pragma unroll
   for (int i = 0; i < RPT; ++i) valid[i] = warp > 0 && i * WNR + tr < nloc;
-  // y[i][1..16]: the tile's columns; between tiles y holds the previous
+  // y[i][0..15]: the tile's columns; between tiles y holds the previous
   // tile's contribution to the next one (z), subtracted from the base.
-  float y[RPT][NS];
+  float y[RPT][WT];
 #pragma unroll
   for (int i = 0; i < RPT; ++i)
 #pragma unroll
-    for (int s = 0; s < NS; ++s) y[i][s] = 0.f;
+    for (int s = 0; s < WT; ++s) y[i][s] = 0.f;
 
-  // The Q blocks a tile needs are copied asynchronously (cp.async, zero-
-  // filled outside the blocks) one tile ahead, off the tile transitions:
-  // Gs of tile tq into Gs[tq & 1]; Gn of tile tq.
+  // Barrier of the row warps only (warps 1 .. NW-1): warp 0 may meanwhile be
+  // publishing the previous tile.
+  auto row_bar = []() { asm volatile("bar.sync 1, %0;" ::"n"(WNR) : "memory"); };
+  // The Q blocks a tile needs are copied asynchronously by the row threads
+  // (cp.async, zero-filled outside the blocks) one tile ahead, off the tile
+  // transitions: Gs of tile tq into Gs[tq & 1]; Gn of tile tq.
   auto fetch_gs = [&](int tq) {
     const int qlo = tq * WT, qw = min(p.K, qlo + WT) - qlo;
-    for (int e = tid; e < WT * 2 * WT; e += WNT) {
-      const int i = e / (2 * WT), j = e % (2 * WT);
+    for (int e = tr; e < WT * WT; e += WNR) {
+      const int i = e / WT, j = e % WT;
       const bool in = i < qw && j < qw;
       cp_async4(&Gs[tq & 1][i][j], p.Q + (in ? (int64_t)(qlo + i) * p.Kp + qlo + j : 0), in);
     }
@@ -297,84 +307,101 @@ __device__ void chain_role(const WParams& p, char* smem, int n_workers) {
   auto fetch_gn = [&](int tq) {
     const int qlo = tq * WT, qw = min(p.K, qlo + WT) - qlo;
     const int nlo = qlo + qw, nw = min(p.K, nlo + WT) - nlo;
-    for (int e = tid; e < WT * WT; e += WNT) {
+    for (int e = tr; e < WT * WT; e += WNR) {
       const int i = e / WT, j = e % WT;
       const bool in = i < qw && j < nw;
       cp_async4(&Gn[i][j], p.Q + (in ? (int64_t)(qlo + i) * p.Kp + nlo + j : 0), in);
     }
   };
-  fetch_gs(0);
-  cp_async_commit();
+  if (warp > 0) {
+    fetch_gs(0);
+    cp_async_commit();
+  }
 
   bool dead = false;
   int gcol = 0;                                                // global column index
   for (int tau = 0; tau < nt; ++tau) {
     const int lo = tau * WT, hi = min(p.K, lo + WT), Tw = hi - lo;
-    cp_async_wait_all();                                       // Gs of this tile (issued a tile ahead)
-    if (tid == 0 && !dead) {
-      if (!wait_counter(p.sync + tau * kSyncStride, n_workers, p.status)) dead = true;
-    }
-    __syncthreads();
-    // Gn of this tile and Gs of the next: the buffers are free (tile tau - 1
-    // finished reading them before the barrier above).
-    fetch_gn(tau);
-    if (tau + 1 < nt) fetch_gs(tau + 1);
-    cp_async_commit();
-    const float(*G)[2 * WT] = Gs[tau & 1];
-    // Base of the tile for this CTA's rows (4 lanes per row, 16 bytes each).
-    const int total = nloc * 4;
-    for (int base = tid; base < total; base += 4 * WNT) {
-      float v[4][4];
+    const float(*G)[WT] = Gs[tau & 1];
+    // The row warps start the tile on their own; warp 0 joins at the first
+    // column's barrier.
+    if (warp > 0) {
+      cp_async_wait_all();                                       // Gs of this tile (issued a tile ahead)
+      if (tid == 32 && !dead) {
+        if (!wait_counter(p.sync + tau * kSyncStride, n_workers, p.status)) dead = true;
+      }
+      row_bar();
+      // Gn of this tile and Gs of the next: the buffers are free (tile tau - 1
+      // finished reading them before the barrier ending it).
+      fetch_gn(tau);
+      if (tau + 1 < nt) fetch_gs(tau + 1);
+      cp_async_commit();
+      // Base of the tile for this CTA's rows (4 lanes per row, 16 bytes each),
+      // staged through st; each row thread then takes its own rows.
+      const int total = nloc * 4;
+      for (int base = tr; base < total; base += 4 * WNR) {
+        float4 v[4];
 #pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        const int e = base + u * WNT;
-        const int row = row0 + (e >> 2), q = e & 3;
-#pragma unroll
-        for (int j = 0; j < 4; ++j) v[u][j] = 0.f;
-        if (e < total) {
-          const float* src = p.Y + (int64_t)row * p.Kp + lo + 4 * q;
+        for (int u = 0; u < 4; ++u) {
+          const int e = base + u * WNR;
+          const int row = row0 + (e >> 2), q = e & 3;
+          v[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+          if (e >= total) continue;
+          const int64_t off = (int64_t)row * p.Kp + lo + 4 * q;
+          const bool pre = tau == 0 && p.pre0 != nullptr;
           if (4 * q + 3 < Tw) {
-            const float4 f = *reinterpret_cast<const float4*>(src);
-            v[u][0] = f.x; v[u][1] = f.y; v[u][2] = f.z; v[u][3] = f.w;
+            v[u] = *reinterpret_cast<const float4*>(p.Y + off);
+            if (pre) {                                          // tile 0's base less P: add P here
+              // P and the early base cancel: P + hi first (nearly exact),
+              // then the early base's compensation.
+              const float4 pp = *reinterpret_cast<const float4*>(p.P + off);
+              const float4 cc = *reinterpret_cast<const float4*>(p.pre0 + (int64_t)row * WT + 4 * q);
+              v[u] = make_float4((pp.x + v[u].x) + cc.x, (pp.y + v[u].y) + cc.y, (pp.z + v[u].z) + cc.z,
+                                 (pp.w + v[u].w) + cc.w);
+            }
           } else {
+            float w[4];
 #pragma unroll
-            for (int j = 0; j < 4; ++j) v[u][j] = 4 * q + j < Tw ? src[j] : 0.f;
-          }
-          if (tau == 0 && p.pre0) {                           // tile 0's base less P: add P here
-            // P and the early base cancel: P + hi first (nearly exact), then
-            // the early base's compensation.
-            const float* ps = p.P + (int64_t)row * p.Kp + lo + 4 * q;
-            const float* cs = p.pre0 + (int64_t)row * WT + 4 * q;
-#pragma unroll
-            for (int j = 0; j < 4; ++j) v[u][j] = 4 * q + j < Tw ? (ps[j] + v[u][j]) + cs[j] : 0.f;
+            for (int j = 0; j < 4; ++j) {
+              w[j] = 0.f;
+              if (4 * q + j < Tw) {
+                w[j] = p.Y[off + j];
+                if (pre) w[j] = (p.P[off + j] + w[j]) + p.pre0[(int64_t)row * WT + 4 * q + j];
+              }
+            }
+            v[u] = make_float4(w[0], w[1], w[2], w[3]);
           }
         }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int e = base + u * WNR;
+          if (e >= total) continue;
+          const int li = e >> 2, q = e & 3;
+          const int i = li / WNR, r = li - i * WNR;
+          st[sidx(i, 4 * q, r)] = v[u].x;
+          st[sidx(i, 4 * q + 1, r)] = v[u].y;
+          st[sidx(i, 4 * q + 2, r)] = v[u].z;
+          st[sidx(i, 4 * q + 3, r)] = v[u].w;
+        }
       }
+      row_bar();
 #pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        const int e = base + u * WNT;
-        if (e >= total) continue;
-        const int li = e >> 2, q = e & 3;
-        const int i = li / WNR, r = li - i * WNR;
+      for (int i = 0; i < RPT; ++i)
 #pragma unroll
-        for (int j = 0; j < 4; ++j) st[sidx(i, 4 * q + j, r)] = v[u][j];
-      }
-    }
-    __syncthreads();
-    if (warp > 0) {
-#pragma unroll
-      for (int i = 0; i < RPT; ++i) {
-        y[i][0] = 0.f;
-#pragma unroll
-        for (int t = 0; t < WT; ++t) y[i][1 + t] = valid[i] ? st[sidx(i, t, tr)] - y[i][1 + t] : 0.f;
-      }
+        for (int t = 0; t < WT; ++t) y[i][t] = valid[i] ? st[sidx(i, t, tr)] - y[i][t] : 0.f;
     }
 
+    // Columns t = 0 .. Tw-1 of the tile, unrolled so that every register slot
+    // is static: column t is finished, the previous column's contribution is
+    // pushed into columns t+1.. (column t already has it), and every fourth
+    // column the last four finished ones go to global memory, off the
+    // critical path.
     float xp[RPT];
 #pragma unroll
     for (int i = 0; i < RPT; ++i) xp[i] = 0.f;
-#pragma unroll 1
-    for (int t = 0; t < Tw; ++t, ++gcol) {
+#pragma unroll
+    for (int t = 0; t < WT; ++t) {
+      if (t >= Tw) break;
       const int b = gcol & 1;
       if (warp > 0) {
         // The clamped column goes to this thread's slots of st (normalised
@@ -382,7 +409,7 @@ __device__ void chain_role(const WParams& p, char* smem, int n_workers) {
         float ss = 0.f;
 #pragma unroll
         for (int i = 0; i < RPT; ++i) {
-          const float x = fmaxf(p.eps, y[i][1]);
+          const float x = fmaxf(p.eps, y[i][t]);
           st[sidx(i, t, tr)] = x;
           if (valid[i]) ss = fmaf(x, x, ss);
         }
@@ -393,16 +420,20 @@ __device__ void chain_role(const WParams& p, char* smem, int n_workers) {
       if (warp > 0) {
         if (t > 0) {
 #pragma unroll
-          for (int s = 2; s < NS; ++s) {
-            const float g = G[t - 1][t + s - 1];              // slot s holds column t + s - 1
+          for (int s2 = t + 1; s2 < WT; ++s2) {
+            const float g = G[t - 1][s2];
 #pragma unroll
-            for (int i = 0; i < RPT; ++i) y[i][s - 1] = fmaf(-xp[i], g, y[i][s]);
+            for (int i = 0; i < RPT; ++i) y[i][s2] = fmaf(-xp[i], g, y[i][s2]);
           }
-        } else {
+        }
+        if (t >= 4 && (t & 3) == 0) {
 #pragma unroll
-          for (int s = 2; s < NS; ++s)
-#pragma unroll
-            for (int i = 0; i < RPT; ++i) y[i][s - 1] = y[i][s];
+          for (int i = 0; i < RPT; ++i) {
+            if (!valid[i]) continue;
+            const float4 v = make_float4(st[sidx(i, t - 4, tr)], st[sidx(i, t - 3, tr)], st[sidx(i, t - 2, tr)],
+                                         st[sidx(i, t - 1, tr)]);
+            *reinterpret_cast<float4*>(p.X + (int64_t)(row0 + i * WNR + tr) * p.Kp + lo + t - 4) = v;
+          }
         }
       } else {
         float v = (lane >= 1 && lane < NW) ? wpart[lane] : 0.f;
@@ -448,26 +479,40 @@ __device__ void chain_role(const WParams& p, char* smem, int n_workers) {
         if (rank == 0 && (!(nrm > 0.f) || !(nrm < INFINITY))) atomicOr(p.status, ST_NUMERIC);
       }
       if (warp > 0) {
-        const float g1 = G[t][t + 1];
+        const float g1 = t + 1 < WT ? G[t][t + 1] : 0.f;
 #pragma unroll
         for (int i = 0; i < RPT; ++i) {
           const float x = st[sidx(i, t, tr)] * inv;
           st[sidx(i, t, tr)] = x;
-          y[i][1] = fmaf(-x, g1, y[i][1]);
+          if (t + 1 < WT) y[i][t + 1] = fmaf(-x, g1, y[i][t + 1]);
           xp[i] = x;
         }
       }
+      ++gcol;
     }
     // Contribution of this tile to the next one, z = x_tile * Q[tile][next]
-    // for this CTA's rows (kept in y until the next base is loaded).
+    // for this CTA's rows (kept in y until the next base is loaded), and the
+    // columns not yet stored.
     const int nlo = hi, nhi = min(p.K, nlo + WT), Tn = nhi - nlo;
-    cp_async_wait_all();                                       // Gn of this tile, Gs of the next
-    __syncthreads();
     if (warp > 0) {
+      cp_async_wait_all();                                     // Gn of this tile, Gs of the next
+      row_bar();
+      const int sdone = 4 * ((Tw - 1) / 4);                    // columns [0, sdone) already stored
+#pragma unroll
+      for (int i = 0; i < RPT; ++i) {
+        if (!valid[i]) continue;
+        float* dst = p.X + (int64_t)(row0 + i * WNR + tr) * p.Kp + lo;
+        if (Tw - sdone == 4) {
+          *reinterpret_cast<float4*>(dst + sdone) = make_float4(st[sidx(i, sdone, tr)], st[sidx(i, sdone + 1, tr)],
+                                                                st[sidx(i, sdone + 2, tr)], st[sidx(i, sdone + 3, tr)]);
+        } else {
+          for (int c = sdone; c < Tw; ++c) dst[c] = st[sidx(i, c, tr)];
+        }
+      }
 #pragma unroll
       for (int i = 0; i < RPT; ++i)
 #pragma unroll
-        for (int s = 0; s < NS; ++s) y[i][s] = 0.f;
+        for (int s2 = 0; s2 < WT; ++s2) y[i][s2] = 0.f;
       if (Tn > 0) {
 #pragma unroll 1
         for (int j = 0; j < Tw; ++j) {
@@ -479,37 +524,22 @@ __device__ void chain_role(const WParams& p, char* smem, int n_workers) {
             const float4 g = *reinterpret_cast<const float4*>(&Gn[j][4 * cq]);
 #pragma unroll
             for (int i = 0; i < RPT; ++i) {
-              y[i][1 + 4 * cq] = fmaf(g.x, xv[i], y[i][1 + 4 * cq]);
-              y[i][2 + 4 * cq] = fmaf(g.y, xv[i], y[i][2 + 4 * cq]);
-              y[i][3 + 4 * cq] = fmaf(g.z, xv[i], y[i][3 + 4 * cq]);
-              y[i][4 + 4 * cq] = fmaf(g.w, xv[i], y[i][4 + 4 * cq]);
+              y[i][4 * cq] = fmaf(g.x, xv[i], y[i][4 * cq]);
+              y[i][4 * cq + 1] = fmaf(g.y, xv[i], y[i][4 * cq + 1]);
+              y[i][4 * cq + 2] = fmaf(g.z, xv[i], y[i][4 * cq + 2]);
+              y[i][4 * cq + 3] = fmaf(g.w, xv[i], y[i][4 * cq + 3]);
             }
           }
         }
       }
     }
-    // Store the finished tile (4 lanes per row), then publish it.
-    for (int e = tid; e < total; e += WNT) {
-      const int li = e >> 2, q = e & 3;
-      const int i = li / WNR, r = li - i * WNR;
-      const int row = row0 + li;
-      float v[4];
-#pragma unroll
-      for (int j = 0; j < 4; ++j) v[j] = st[sidx(i, 4 * q + j, r)];
-      float* dst = p.X + (int64_t)row * p.Kp + lo + 4 * q;
-      if (4 * q + 3 < Tw) {
-        *reinterpret_cast<float4*>(dst) = make_float4(v[0], v[1], v[2], v[3]);
-      } else {
-#pragma unroll
-        for (int j = 0; j < 4; ++j)
-          if (4 * q + j < Tw) dst[j] = v[j];
-      }
-    }
     // Every CTA publishes its own rows (the workers wait for all CL): a
     // block barrier, then one thread's fence and count (cumulative release),
     // with no cluster barrier, so no CTA waits for the slowest one here.
+    // Warp 0 publishes while the row warps already start the next tile.  The
+    // workers read tile tau only for the bases of tiles >= tau + 2.
     __syncthreads();
-    if (tid == 0) {
+    if (tid == 0 && tau + 2 < nt) {
       __threadfence();
       atomicAdd(p.sync + (nt + tau) * kSyncStride, 1);
     }
