@@ -236,10 +236,7 @@ __device__ void worker_role(const WParams& p, char* smem, int wid, int n_workers
       }
     }
     __syncthreads();
-    if (tid == 0) {
-      __threadfence();
-      atomicAdd(p.sync + tau * kSyncStride, 1);
-    }
+    if (tid == 0) red_release_add_gpu(p.sync + tau * kSyncStride, 1);
   }
   if (__syncthreads_or(dead ? 1 : 0)) drain_grace();   // bulk copies still in flight
   (void)go;
@@ -291,8 +288,15 @@ __device__ void chain_role(const WParams& p, char* smem, int n_workers) {
     for (int s = 0; s < WT; ++s) y[i][s] = 0.f;
 
   // Barrier of the row warps only (warps 1 .. NW-1): warp 0 may meanwhile be
-  // publishing the previous tile.
-  auto row_bar = []() { asm volatile("bar.sync 1, %0;" ::"n"(WNR) : "memory"); };
+  // publishing the previous tile.  The compiler's named-barrier intrinsic
+  // (not inline asm), after an explicit warp reconvergence: a hardware
+  // barrier counts a whole warp as arrived when any of its lanes executes
+  // it, so a warp split by a divergent wait (thread 32 polls the base
+  // flag) would otherwise complete a barrier without its waiting lane.
+  auto row_bar = []() {
+    __syncwarp();
+    __barrier_sync_count(1, WNR);
+  };
   // The Q blocks a tile needs are copied asynchronously by the row threads
   // (cp.async, zero-filled outside the blocks) one tile ahead, off the tile
   // transitions: Gs of tile tq into Gs[tq & 1]; Gn of tile tq.
@@ -467,16 +471,17 @@ __device__ void chain_role(const WParams& p, char* smem, int n_workers) {
         }
       }
       dead = __any_sync(0xffffffffu, dead);
-      float tot = lane < CL ? cpart[b][lane] : 0.f;
+      // The CL partials summed by an xor butterfly over lanes 0..15 (lanes
+      // 16..31 mirror them): each step adds the same two operands in every
+      // lane it pairs, so every lane of every CTA gets the same squared norm.
+      float tot = (lane & 15) < CL ? cpart[b][lane & 15] : 0.f;
 #pragma unroll
-      for (int o = 8; o > 0; o >>= 1) tot += __shfl_down_sync(0xffffffffu, tot, o);
-      tot = __shfl_sync(0xffffffffu, tot, 0);
-      const float nrm = sqrtf(tot);
-      const float inv = 1.0f / nrm;
+      for (int o = 8; o > 0; o >>= 1) tot += __shfl_xor_sync(0xffffffffu, tot, o);
+      const float inv = rsqrtf(tot);                           // 1 / ||column||
       if (tid == 0) {
         // Re-arm this parity for column gcol + 2 (before this warp's next send).
         if (gcol + 2 < p.K && !dead) mbar_arrive_expect_tx(smem_u32(&mbar[b]), CL * 4);
-        if (rank == 0 && (!(nrm > 0.f) || !(nrm < INFINITY))) atomicOr(p.status, ST_NUMERIC);
+        if (rank == 0 && (!(tot > 0.f) || !(tot < INFINITY))) atomicOr(p.status, ST_NUMERIC);
       }
       if (warp > 0) {
         const float g1 = t + 1 < WT ? G[t][t + 1] : 0.f;
@@ -490,13 +495,11 @@ __device__ void chain_role(const WParams& p, char* smem, int n_workers) {
       }
       ++gcol;
     }
-    // Contribution of this tile to the next one, z = x_tile * Q[tile][next]
-    // for this CTA's rows (kept in y until the next base is loaded), and the
-    // columns not yet stored.
+    // The columns not yet stored, then the tile is published (below), then
+    // the contribution of this tile to the next one, z = x_tile * Q[tile][next]
+    // for this CTA's rows (kept in y until the next base is loaded).
     const int nlo = hi, nhi = min(p.K, nlo + WT), Tn = nhi - nlo;
     if (warp > 0) {
-      cp_async_wait_all();                                     // Gn of this tile, Gs of the next
-      row_bar();
       const int sdone = 4 * ((Tw - 1) / 4);                    // columns [0, sdone) already stored
 #pragma unroll
       for (int i = 0; i < RPT; ++i) {
@@ -509,13 +512,24 @@ __device__ void chain_role(const WParams& p, char* smem, int n_workers) {
           for (int c = sdone; c < Tw; ++c) dst[c] = st[sidx(i, c, tr)];
         }
       }
+    }
+    // Every CTA publishes its own rows (the workers wait for all CL): a
+    // block barrier, then one thread's release count (cumulative), with no
+    // cluster barrier, so no CTA waits for the slowest one here.  Warp 0
+    // publishes while the row warps compute z and start the next tile.  The
+    // workers read tile tau only for the bases of tiles >= tau + 2.
+    __syncthreads();
+    if (tid == 0 && tau + 2 < nt) red_release_add_gpu(p.sync + (nt + tau) * kSyncStride, 1);
+    if (warp > 0) {
+      cp_async_wait_all();                                     // Gn of this tile, Gs of the next
+      row_bar();
 #pragma unroll
       for (int i = 0; i < RPT; ++i)
 #pragma unroll
         for (int s2 = 0; s2 < WT; ++s2) y[i][s2] = 0.f;
-      if (Tn > 0) {
-#pragma unroll 1
-        for (int j = 0; j < Tw; ++j) {
+      if (Tn > 0) {                                            // then Tw == WT (only the last tile is partial)
+#pragma unroll 4
+        for (int j = 0; j < WT; ++j) {
           float xv[RPT];
 #pragma unroll
           for (int i = 0; i < RPT; ++i) xv[i] = st[sidx(i, j, tr)];
@@ -532,16 +546,6 @@ __device__ void chain_role(const WParams& p, char* smem, int n_workers) {
           }
         }
       }
-    }
-    // Every CTA publishes its own rows (the workers wait for all CL): a
-    // block barrier, then one thread's fence and count (cumulative release),
-    // with no cluster barrier, so no CTA waits for the slowest one here.
-    // Warp 0 publishes while the row warps already start the next tile.  The
-    // workers read tile tau only for the bases of tiles >= tau + 2.
-    __syncthreads();
-    if (tid == 0 && tau + 2 < nt) {
-      __threadfence();
-      atomicAdd(p.sync + (nt + tau) * kSyncStride, 1);
     }
   }
   // A timed-out wait anywhere: let remote stores still in flight land before
