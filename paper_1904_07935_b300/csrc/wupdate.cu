@@ -99,7 +99,6 @@ __device__ void worker_role(const WParams& p, char* smem, int wid, int n_workers
   float* Gc = reinterpret_cast<float*>(smem);                 // Kr x WT
   float* Xs = Gc + Kr * WT;                                   // worker_rows x ldx
   __shared__ __align__(8) unsigned long long bar;
-  __shared__ int go;
   const int tid = threadIdx.x;
   const int sub = tid & 3;
   const int rl = tid >> 2;
@@ -116,7 +115,6 @@ __device__ void worker_role(const WParams& p, char* smem, int wid, int n_workers
     const int lo = tau * WT, hi = min(p.K, lo + WT);
     const int new_end = tau >= 1 ? lo - WT : 0;
     if (tid == 0) {
-      go = 1;
       if (tau >= 2 && !dead) {
         if (!wait_counter(p.sync + (nt + tau - 2) * kSyncStride, p.cl, p.status)) dead = true;
       }
@@ -239,7 +237,6 @@ __device__ void worker_role(const WParams& p, char* smem, int wid, int n_workers
     if (tid == 0) red_release_add_gpu(p.sync + tau * kSyncStride, 1);
   }
   if (__syncthreads_or(dead ? 1 : 0)) drain_grace();   // bulk copies still in flight
-  (void)go;
 }
 
 // --------------------------------------------------------------------------
@@ -658,7 +655,6 @@ bool w_persistent_config(int N, int Kp, WPersistConfig* cfg) {
 cudaError_t w_persistent_run(float* X, const float* P, const float* Q, float* Y, int N, int K, int Kp, float eps,
                              int* d_sync, int* d_status, const WPersistConfig& cfg, cudaStream_t s,
                              const float* pre0) {
-  const int nt = (K + WT - 1) / WT;
   cudaError_t e = cudaMemsetAsync(d_sync, 0, sizeof(int) * w_sync_ints(K), s);
   if (e != cudaSuccess) return e;
   WParams p{X, P, Q, Y, N, K, Kp, eps, d_status, d_sync, cfg.cluster, cfg.worker_rows, cfg.chain_rows, pre0};
