@@ -338,12 +338,14 @@ __device__ void chain_role(const WParams& p, char* smem, int n_workers) {
       if (tau + 1 < nt) fetch_gs(tau + 1);
       cp_async_commit();
       // Base of the tile for this CTA's rows (4 lanes per row, 16 bytes each),
-      // staged through st; each row thread then takes its own rows.
+      // staged through st (8 loads in flight per thread); each row thread
+      // then takes its own rows.
+      constexpr int SU = 8;
       const int total = nloc * 4;
-      for (int base = tr; base < total; base += 4 * WNR) {
-        float4 v[4];
+      for (int base = tr; base < total; base += SU * WNR) {
+        float4 v[SU];
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
+        for (int u = 0; u < SU; ++u) {
           const int e = base + u * WNR;
           const int row = row0 + (e >> 2), q = e & 3;
           v[u] = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -374,7 +376,7 @@ __device__ void chain_role(const WParams& p, char* smem, int n_workers) {
           }
         }
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
+        for (int u = 0; u < SU; ++u) {
           const int e = base + u * WNR;
           if (e >= total) continue;
           const int li = e >> 2, q = e & 3;
