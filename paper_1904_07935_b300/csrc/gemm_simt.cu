@@ -266,7 +266,7 @@ __global__ void __launch_bounds__(512) gram_full_kernel(const float* __restrict_
 // shared memory (double-buffered via registers, one 16-byte global load per
 // operand per thread and step).  Operands need 16-byte aligned bases and row
 // strides that are multiples of 4 floats (checked by the caller).  Modes
-// GM_STORE and GM_PARTIAL.
+// GM_STORE and GM_PARTIAL (upper_only: tiles below the diagonal skipped).
 //
 // Accumulation is blocked and compensated: the registers gather 64 terms
 // (kFoldTiles k-steps of SBK), then each is added to its running sum with
@@ -301,6 +301,7 @@ __global__ void __launch_bounds__(kSgemmThreads, 2) sgemm128_kernel(GemmArgs g) 
   __shared__ __align__(16) float Bs[2][SBK][SLD];
   extern __shared__ float4 run_sum[];                         // [16][256]: this thread's at [q * 256 + tid]
   const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  if (g.upper_only && blockIdx.x < blockIdx.y) return;        // Gram: tiles below the diagonal are not needed
   const int m0 = blockIdx.y * SB, n0 = blockIdx.x * SB;
   int k_begin = 0, k_end = g.Kin;
   if (g.mode == GM_PARTIAL) {
@@ -415,7 +416,7 @@ __global__ void __launch_bounds__(kSgemmThreads, 2) sgemm128_kernel(GemmArgs g) 
 // aligned with row strides that are multiples of 4 floats, wide enough.
 bool use_sgemm128(const GemmArgs& a) {
   if (a.mode != GM_STORE && a.mode != GM_PARTIAL) return false;
-  if (a.upper_only || a.M < 64 || a.N < 96 || a.Kin < 64) return false;
+  if (a.M < 64 || a.N < 96 || a.Kin < 64) return false;
   if ((a.lda & 3) || (a.ldb & 3)) return false;
   if ((reinterpret_cast<uintptr_t>(a.A) & 15) || (reinterpret_cast<uintptr_t>(a.B) & 15)) return false;
   return true;
@@ -595,7 +596,9 @@ cudaError_t gram_setup(GramWork& g, int N, int Kp) {
   }
   // Enough chunks to cover about two waves of the 148 SMs (chunks of at
   // least 2 BK rows; at most 256 chunks, the compensated reduction's limit).
-  const int tiles = ((Kp + 63) / 64) * ((Kp + 63) / 64 + 1) / 2;
+  // Upper-triangle tiles: 128 x 128 for Kp >= 96 (sgemm128_kernel), else 64 x 64.
+  const int tw = Kp >= 96 ? 128 : 64;
+  const int tiles = ((Kp + tw - 1) / tw) * ((Kp + tw - 1) / tw + 1) / 2;
   int want = std::max(1, (296 + tiles - 1) / tiles);
   int chunk = (N + want - 1) / want;
   chunk = std::max(2 * BK, ((chunk + BK - 1) / BK) * BK);

@@ -212,6 +212,19 @@ def test_one_iteration_sparse_small_ragged(nmf):
     assert rel_w(Wg, Wr) < TOL_ITER
 
 
+@pytest.mark.parametrize("K", [80, 240, 400])
+def test_one_iteration_sparse_k_sweep(nmf, K):
+    """The ranks of the text-like K sweep other than 160 (different SpMM lane
+    layouts, tile counts and update variants), on an 8000 x 4000 matrix of the
+    same generator, one iteration against the FP64 oracle."""
+    sp = synth.sparse_termdoc(8000, 4000, 0xC2 + K, mean_terms=100)
+    W0, H0 = synth.init_factors(0xC2 + K + 1, 8000, 4000, K)
+    ctx = _sparse_ctx(nmf, sp, K, W0, H0)
+    Wg, Hg, Wr, Hr = _one_iteration(nmf, sp.A, ctx, W0, H0)
+    assert rel_h(Hg, Hr) < TOL_ITER
+    assert rel_w(Wg, Wr) < TOL_ITER
+
+
 @pytest.fixture(scope="module")
 def text_full():
     return synth.text_20ng_like()
