@@ -384,6 +384,24 @@ def run_gpu(args):
                     "alg_bytes_per_iter": int(sum(ab.values())),
                     "iteration_frac_of_hbm": round(sum(ab.values()) / (ms * 1e-3) / 1e9 / peak, 5)}
 
+    # Latency floor of the W update (K sequential cluster-wide column norms):
+    # the same update on a 512 x 512 problem at the same K, where the rows'
+    # work is negligible, timed the same way.
+    if args.workload != "dense512":
+        nf = 512
+        Af = torch.rand(nf, nf, generator=torch.Generator().manual_seed(5), dtype=torch.float32).to(dev)
+        Wf = torch.rand(nf, K, generator=torch.Generator().manual_seed(6), dtype=torch.float32).to(dev)
+        Hf = torch.rand(K, nf, generator=torch.Generator().manual_seed(7), dtype=torch.float32).to(dev)
+        cf = nmf.Nmf(nf, nf, K, dense=Af, W0=Wf, H0=Hf, stream=stream, flags=flags, prec=nmf.PREC_FP32)
+        cf.iterate(2)
+        pf = cf.profile(10)
+        del cf
+        wf = pf["update_W"]
+        roofline["latency_floor"] = {
+            "what": "W update at the same K on a 512 x 512 problem (row work negligible): the column chain's "
+                    "synchronisation cost", "us": round(1e3 * wf, 2), "per_column_us": round(1e3 * wf / K, 4),
+            "frac_of_w_update": round(wf / prof["update_W"], 4)}
+
     # end to end through the public API with host buffers: per step the
     # factors go host -> device, one iteration runs, and the factors and the
     # relative error come back.
