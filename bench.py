@@ -238,6 +238,8 @@ WORKLOADS = {
     "text20ng": "text-20ng-like sparse NMF (26,214 x 11,314, ~1.13M nnz)",
     "dense8192": "dense planted 8192 x 8192, rank 256",
     "dense512": "dense planted 512 x 384, rank 16",
+    "att": "dense face-image-shaped 400 x 10,304 (AT&T shape, synthetic)",
+    "pie": "dense face-image-shaped 11,554 x 4,096 (PIE shape, synthetic)",
     "warmstart": "learned warm start for new text-like documents, W fixed (K=160), to rel-err 1e-3",
     "batch64": "64 independent sparse instances (V 1k-20k, D 0.5k-8k, density 0.1-1%, K in {16,32,64,128})",
 }
@@ -253,6 +255,10 @@ def make_workload(name: str, K: int):
         prob = synth.dense_large()
         V, D = prob.A.shape
         seed = 0xC3
+    elif name in ("att", "pie"):
+        prob = synth.faces_like(name)
+        V, D = prob.A.shape
+        seed = 0xF4
     else:
         prob = synth.dense_small()
         V, D = prob.A.shape
@@ -739,7 +745,7 @@ def run_time_to_error(args):
     target = e_ref * (1 + 1e-3)
     CHECK = 5
     results = {}
-    forms = ["fp32", "bf16"] if args.workload.startswith("dense8192") or args.workload == "dense512" else ["fp32"]
+    forms = ["fp32", "bf16"] if args.workload in ("dense8192", "dense512", "att", "pie") else ["fp32"]
     for form in forms:
         prec = nmf.PREC_BF16 if form == "bf16" else nmf.PREC_FP32
         stream = torch.cuda.Stream()
@@ -793,7 +799,7 @@ def main():
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--k", type=int, default=0, help="rank (default: 160 text, 256 dense8192, 16 dense512)")
+    ap.add_argument("--k", type=int, default=0, help="rank (default: 160 text, att, pie; 256 dense8192; 16 dense512)")
     ap.add_argument("--workload", default="text20ng", choices=sorted(WORKLOADS))
     ap.add_argument("--prec", default="fp32", choices=["fp32", "bf16"])
     ap.add_argument("--tile", type=int, default=0)
@@ -811,7 +817,8 @@ def main():
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3
     if args.k == 0:
-        args.k = {"text20ng": 160, "dense8192": 256, "dense512": 16, "batch64": 0, "warmstart": 160}[args.workload]
+        args.k = {"text20ng": 160, "dense8192": 256, "dense512": 16, "att": 160, "pie": 160, "batch64": 0,
+                  "warmstart": 160}[args.workload]
     if args.workload == "batch64" and args.impl != "reference":
         run_batch(args)
         return

@@ -236,6 +236,42 @@ def dense_large() -> DenseProblem:
     return planted_dense(8192, 8192, 256, SEED_DENSE_LARGE)
 
 
+SEED_FACES = 0xF4
+
+
+def faces_like(kind: str, seed: int = SEED_FACES) -> DenseProblem:
+    """Face-image-shaped dense matrices with the shapes of the paper's AT&T
+    (400 x 10,304: 400 images of 112 x 92 pixels) and PIE (11,554 x 4,096:
+    64 x 64 pixels) datasets; synthetic contents only.  Each of r basis
+    images (200 / 256: poses, lighting and expressions as well as subjects)
+    is non-negative and smooth (three Gaussian blobs of
+    random position and width over a gentle gradient); a row of A mixes the r
+    bases with U[0,1) weights; |N(0, 0.01^2)| noise; A scaled to max 1 like
+    pixel intensities.  W0 (images x r) and H0 (r x pixels) are the planted
+    factors (scaled with A)."""
+    if kind == "att":
+        n_img, h, w, r = 400, 112, 92, 200
+    elif kind == "pie":
+        n_img, h, w, r = 11554, 64, 64, 256
+    else:
+        raise ValueError(kind)
+    rng = np.random.Generator(np.random.Philox(seed + (0 if kind == "att" else 1)))
+    yy, xx = np.meshgrid(np.arange(h) / h, np.arange(w) / w, indexing="ij")
+    H0 = np.empty((r, h * w))
+    for k in range(r):
+        img = 0.2 * (1.0 + rng.uniform(-1, 1) * (yy - 0.5) + rng.uniform(-1, 1) * (xx - 0.5))
+        for _ in range(3):
+            cy, cx = rng.uniform(0.15, 0.85, size=2)
+            sy, sx = rng.uniform(0.05, 0.25, size=2)
+            img += rng.uniform(0.5, 1.0) * np.exp(-0.5 * (((yy - cy) / sy) ** 2 + ((xx - cx) / sx) ** 2))
+        H0[k] = img.ravel()
+    W0 = rng.random((n_img, r))
+    A = W0 @ H0
+    A += np.abs(rng.normal(0.0, 0.01, size=A.shape))
+    scale = 1.0 / A.max()
+    return DenseProblem(A=(A * scale).astype(np.float32), W0=W0 * scale, H0=H0)
+
+
 def text_20ng_like(seed: int = SEED_TEXT) -> SparseProblem:
     """26,214 words x 11,314 documents, about 1.1M non-zeros (20NG-shaped)."""
     return sparse_termdoc(26214, 11314, seed)
