@@ -323,8 +323,11 @@ def run_gpu(args):
                       stream=stream, tile_T=args.tile, flags=flags, prec=prec)
     flush = torch.empty(256 * 2 ** 20 // 4, dtype=torch.float32, device=dev)   # 256 MB > L2
 
+    alg1 = args.algo == "alg1"
+    step = (lambda n: ctx.iterate_alg1(n)) if alg1 else (lambda n: ctx.iterate(n))
+
     # warm-up (also captures the CUDA graph)
-    ctx.iterate(max(1, args.warmup))
+    step(max(1, args.warmup))
     ctx.error()
     q = ctx.query()
 
@@ -341,7 +344,7 @@ def run_gpu(args):
             for i in range(args.steps):
                 flush.fill_(float(i))                       # evict A, W, H from L2 between steps
                 starts[i].record(stream)
-                ctx.iterate(1)
+                step(1)
                 ends[i].record(stream)
         torch.cuda.synchronize()
         sampler.end()
@@ -362,13 +365,14 @@ def run_gpu(args):
     # warm-L2 steady state (iterations back to back, no flush), for context
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     ev0.record(stream)
-    ctx.iterate(args.steps)
+    step(args.steps)
     ev1.record(stream)
     torch.cuda.synchronize()
     ms_warm = ev0.elapsed_time(ev1) / args.steps
 
     # per-step breakdown with CUDA events (eager launches)
-    prof = ctx.profile(max(3, min(10, args.steps)))
+    prof = ctx.iterate_alg1(max(3, min(10, args.steps)), profile=True) if alg1 else \
+        ctx.profile(max(3, min(10, args.steps)))
     peak, peak_kind = _peaks()
     if dense:
         ab, prod_flops = dense_costs(V, D, K, bf16)
@@ -393,7 +397,7 @@ def run_gpu(args):
     # Latency floor of the W update (K sequential cluster-wide column norms):
     # the same update on a 512 x 512 problem at the same K, where the rows'
     # work is negligible, timed the same way.
-    if args.workload != "dense512":
+    if args.workload != "dense512" and not alg1:
         nf = 512
         Af = torch.rand(nf, nf, generator=torch.Generator().manual_seed(5), dtype=torch.float32).to(dev)
         Wf = torch.rand(nf, K, generator=torch.Generator().manual_seed(6), dtype=torch.float32).to(dev)
@@ -419,7 +423,7 @@ def run_gpu(args):
     t0 = time.perf_counter()
     for _ in range(e2e_steps):
         ctx.set_factors(Wh, Hh)
-        ctx.iterate(1)
+        step(1)
         ctx.error()
         ctx.get_factors(Wh, Hh)
     t_e2e = (time.perf_counter() - t0) / e2e_steps
@@ -433,7 +437,8 @@ def run_gpu(args):
         "config": {"workload": WORKLOADS[args.workload], "V": V, "D": D, "nnz": nnz, "K": K,
                    "tile_T": q["tile_T"], "chain_ctas": q["chain_ctas"], "precision": args.prec,
                    "l2": "flushed between steps (256 MB write)", "parallelism": "replicas" if world > 1 else "single",
-                   "ms_per_step_warm_l2": round(ms_warm, 5), "rel_err_final": rel},
+                   "ms_per_step_warm_l2": round(ms_warm, 5), "rel_err_final": rel,
+                   "algorithm": "Alg. 1 column by column (no tiling)" if alg1 else "Alg. 2 tiled order (PL-NMF)"},
         "e2e": {"value": round(1.0 / t_e2e, 3), "unit": "iter/s", "h2d_bytes_per_step": fac_bytes,
                 "d2h_bytes_per_step": fac_bytes + 16},
         "gpu_launches": int(q["launches_per_iter"]) * args.steps,
@@ -803,6 +808,8 @@ def main():
     ap.add_argument("--workload", default="text20ng", choices=sorted(WORKLOADS))
     ap.add_argument("--prec", default="fp32", choices=["fp32", "bf16"])
     ap.add_argument("--tile", type=int, default=0)
+    ap.add_argument("--algo", default="tiled", choices=["tiled", "alg1"],
+                    help="alg1: the updates column by column as Alg. 1 is written (comparator of the tiled form)")
     ap.add_argument("--cpu-iters", type=int, default=5)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--time-to-error", action="store_true",

@@ -168,6 +168,22 @@ typedef enum {
 nmf_status nmf_get_buffer(nmf_ctx* c, int32_t which, float* dst, int64_t count);
 nmf_status nmf_set_buffer(nmf_ctx* c, int32_t which, const float* src, int64_t count);
 
+/* Alg. 1 as written, without the column tiling (the form the paper's
+ * regrouping, Alg. 2, is measured against; Sec. 5, Table 5): the same
+ * products (R = A^T W, P = A H^T, Q = H H^T, S = W^T W) and objective, but
+ * the H and W updates run column by column, each column one grid-wide step
+ * (W: two, the second normalising the column before the next one reads it),
+ * so an iteration is 3K + O(1) dependent launches.  H^T S_k and W Q_k use
+ * the current factor and include the j = k term (Alg. 1 lines 6-8, 12-16);
+ * FP32 with FP32 dot products (no compensation).  n_iters iterations of
+ * the context's factors (same entry/exit state as nmf_iterate, so the two
+ * can be mixed).  step_ms: NULL -> the iterations run as a CUDA graph
+ * (captured on the first call), asynchronous on the context stream; else
+ * NMF_PROFILE_STEPS floats receive the mean milliseconds of each step as
+ * in nmf_profile (eager launches, CUDA events), synchronous.  Returns
+ * NMF_EINVAL for n_iters < 0 or a NULL context. */
+nmf_status nmf_iterate_alg1(nmf_ctx* c, int32_t n_iters, float* step_ms);
+
 /* Step timing (tracing): runs n_iters iterations eagerly (no graph) with a
  * CUDA event between consecutive steps on the context stream and writes the
  * mean milliseconds per iteration of each step to step_ms[0..6]:

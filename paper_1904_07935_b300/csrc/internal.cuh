@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <algorithm>
 #include <vector>
 
 #include "../../include/nmf.h"
@@ -164,6 +165,16 @@ cudaError_t h_update_run(float* X, const float* B, const float* G, int N, int K,
 cudaError_t w_prep_run(const float* X, const float* B, const float* G, float* Y, int N, int K, int Kp, int lo,
                        int new_end, int* status, cudaStream_t s, float* Ylo = nullptr);
 constexpr int kRowTile = 16;   // tile width of the row-parallel update kernels
+
+// Alg. 1 as written (no column tiling): the H and W updates column by
+// column, K (H) or 2K (W) dependent grid-wide launches; `part` holds
+// alg1_parts(V) floats (per-CTA sums of squares); `launches` (optional) is
+// incremented by the number of kernels enqueued.
+int alg1_parts(int V);
+cudaError_t alg1_update_h(float* Ht, const float* R, const float* S, int D, int K, int Kp, float eps,
+                          cudaStream_t s, int* launches);
+cudaError_t alg1_update_w(float* W, const float* P, const float* Q, int V, int K, int Kp, float eps, float* part,
+                          int* status, cudaStream_t s, int* launches);
 
 // Persistent, cooperative W update (one launch per update): cluster 0 runs the
 // column chain over all tiles, the other clusters compute the tile bases.

@@ -68,6 +68,10 @@ struct nmf_ctx {
   int launch_count = 0;       // kernels issued by the last enqueue sequence
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t graph_exec = nullptr;
+  // Alg. 1 as written (nmf_iterate_alg1): per-CTA sums of squares, graph.
+  float* alg1_part = nullptr;
+  cudaGraph_t graph_alg1 = nullptr;
+  cudaGraphExec_t graph_alg1_exec = nullptr;
 };
 
 namespace {
@@ -310,6 +314,10 @@ void destroy_graph(nmf_ctx* c) {
   if (c->graph) cudaGraphDestroy(c->graph);
   c->graph_exec = nullptr;
   c->graph = nullptr;
+  if (c->graph_alg1_exec) cudaGraphExecDestroy(c->graph_alg1_exec);
+  if (c->graph_alg1) cudaGraphDestroy(c->graph_alg1);
+  c->graph_alg1_exec = nullptr;
+  c->graph_alg1 = nullptr;
 }
 
 nmf_status validate_and_copy_csr(const nmf_problem* p, std::vector<int>& rp, std::vector<int>& ci,
@@ -452,6 +460,7 @@ nmf_status init_impl(const nmf_problem* p, nmf_ctx* c) {
   CK(dalloc(&c->Y, nMax));
   CK(dalloc(&c->stage, nMax));
   CK(dalloc(&c->Y0lo, (size_t)V * kRowTile));
+  CK(dalloc(&c->alg1_part, (size_t)alg1_parts(V)));
   CK(cudaMemsetAsync(c->P, 0, sizeof(float) * nV, c->stream));
   CK(cudaMemsetAsync(c->R, 0, sizeof(float) * nD, c->stream));
   CK(cudaMemsetAsync(c->Y, 0, sizeof(float) * nMax, c->stream));
@@ -542,7 +551,7 @@ void free_ctx(nmf_ctx* c) {
 
   for (void* p : {(void*)c->A_bf16, c->Ab8, c->ATb8, c->Fb8, (void*)c->gpart, (void*)c->ppart, (void*)c->resid_part,
                   (void*)c->d_sync, (void*)c->rpT, (void*)c->ciT, (void*)c->vaT, (void*)c->W, (void*)c->Ht, (void*)c->R,
-                  (void*)c->P, (void*)c->S, (void*)c->Q, (void*)c->Y, (void*)c->stage, (void*)c->Y0lo,
+                  (void*)c->P, (void*)c->S, (void*)c->Q, (void*)c->Y, (void*)c->stage, (void*)c->Y0lo, (void*)c->alg1_part,
                   (void*)c->obj_partial, (void*)c->hist, (void*)c->d_counter, (void*)c->d_status})
     if (p) cudaFree(p);
   if (c->side) {
@@ -840,6 +849,83 @@ nmf_status nmf_iterate(nmf_ctx* c, int32_t n_iters) {
     CK(cudaGraphInstantiate(&c->graph_exec, g, 0));
   }
   for (int i = 0; i < n_iters; ++i) CK(cudaGraphLaunch(c->graph_exec, c->stream));
+  c->iters_run += n_iters;
+  return NMF_OK;
+}
+
+// One iteration of Alg. 1 as written: the same products as enq_iteration,
+// the two updates column by column (alg1.cu), steps in sequence.  Entry and
+// exit invariant as enq_iteration: S = W^T W and R = A^T W for the current W.
+cudaError_t enq_alg1_iteration(nmf_ctx* c) {
+  cudaError_t e;
+  if ((e = alg1_update_h(c->Ht, c->R, c->S, c->D, c->K, c->Kp, c->eps, c->stream, &c->launch_count)) != cudaSuccess)
+    return e;
+  if ((e = enq_product_P(c)) != cudaSuccess) return e;
+  if ((e = enq_gram(c, c->gramH, c->Ht, c->Q)) != cudaSuccess) return e;
+  if ((e = alg1_update_w(c->W, c->P, c->Q, c->V, c->K, c->Kp, c->eps, c->alg1_part, c->d_status, c->stream,
+                         &c->launch_count)) != cudaSuccess)
+    return e;
+  if ((e = enq_product_R(c)) != cudaSuccess) return e;
+  if ((e = enq_gram(c, c->gramW, c->W, c->S)) != cudaSuccess) return e;
+  return enq_objective(c);
+}
+
+nmf_status nmf_iterate_alg1(nmf_ctx* c, int32_t n_iters, float* step_ms) {
+  if (!c || n_iters < 0) return NMF_EINVAL;
+  if (n_iters == 0) return NMF_OK;
+  CK(ensure_entry(c));
+  if (step_ms) {
+    // Steps in NMF_PROFILE_STEPS order: 0 R, 1 H, 2 P, 3 Q, 4 W, 5 S, 6 objective.
+    cudaEvent_t ev[8];
+    for (auto& e : ev) CK(cudaEventCreate(&e));
+    double acc[NMF_PROFILE_STEPS] = {0};
+    cudaError_t e = cudaSuccess;
+    for (int it = 0; it < n_iters && e == cudaSuccess; ++it) {
+      cudaStream_t s = c->stream;
+      e = cudaEventRecord(ev[0], s);                                           // H
+      if (e == cudaSuccess) e = alg1_update_h(c->Ht, c->R, c->S, c->D, c->K, c->Kp, c->eps, s, nullptr);
+      if (e == cudaSuccess) e = cudaEventRecord(ev[1], s);                     // P
+      if (e == cudaSuccess) e = enq_product_P(c);
+      if (e == cudaSuccess) e = cudaEventRecord(ev[2], s);                     // Q
+      if (e == cudaSuccess) e = enq_gram(c, c->gramH, c->Ht, c->Q);
+      if (e == cudaSuccess) e = cudaEventRecord(ev[3], s);                     // W
+      if (e == cudaSuccess)
+        e = alg1_update_w(c->W, c->P, c->Q, c->V, c->K, c->Kp, c->eps, c->alg1_part, c->d_status, s, nullptr);
+      if (e == cudaSuccess) e = cudaEventRecord(ev[4], s);                     // R
+      if (e == cudaSuccess) e = enq_product_R(c);
+      if (e == cudaSuccess) e = cudaEventRecord(ev[5], s);                     // S
+      if (e == cudaSuccess) e = enq_gram(c, c->gramW, c->W, c->S);
+      if (e == cudaSuccess) e = cudaEventRecord(ev[6], s);                     // objective
+      if (e == cudaSuccess) e = enq_objective(c);
+      if (e == cudaSuccess) e = cudaEventRecord(ev[7], s);
+      if (e == cudaSuccess) e = cudaEventSynchronize(ev[7]);
+      const int slot[7] = {1, 2, 3, 4, 0, 5, 6};
+      for (int k = 0; k < 7 && e == cudaSuccess; ++k) {
+        float ms = 0.f;
+        e = cudaEventElapsedTime(&ms, ev[k], ev[k + 1]);
+        acc[slot[k]] += ms;
+      }
+    }
+    for (auto& x : ev) cudaEventDestroy(x);
+    CK(e);
+    for (int k = 0; k < NMF_PROFILE_STEPS; ++k) step_ms[k] = (float)(acc[k] / n_iters);
+    c->iters_run += n_iters;
+    return read_status(c);
+  }
+  if (!c->graph_alg1_exec) {
+    c->launch_count = 0;
+    CK(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
+    cudaError_t e = enq_alg1_iteration(c);
+    cudaGraph_t g = nullptr;
+    cudaError_t e2 = cudaStreamEndCapture(c->stream, &g);
+    if (e != cudaSuccess || e2 != cudaSuccess) {
+      if (g) cudaGraphDestroy(g);
+      return from_cuda(e != cudaSuccess ? e : e2);
+    }
+    c->graph_alg1 = g;
+    CK(cudaGraphInstantiate(&c->graph_alg1_exec, g, 0));
+  }
+  for (int i = 0; i < n_iters; ++i) CK(cudaGraphLaunch(c->graph_alg1_exec, c->stream));
   c->iters_run += n_iters;
   return NMF_OK;
 }
