@@ -245,6 +245,13 @@ WORKLOADS = {
 }
 
 
+ALGOS = {
+    "tiled": "FAST-HALS in the tiled order of Alg. 2 (PL-NMF)",
+    "alg1": "FAST-HALS as Alg. 1 is written, column by column (comparator)",
+    "mu": "multiplicative updates, Lee & Seung (comparator)",
+}
+
+
 def make_workload(name: str, K: int):
     from paper_1904_07935_b300 import synth
     if name == "text20ng":
@@ -323,8 +330,8 @@ def run_gpu(args):
                       stream=stream, tile_T=args.tile, flags=flags, prec=prec)
     flush = torch.empty(256 * 2 ** 20 // 4, dtype=torch.float32, device=dev)   # 256 MB > L2
 
-    alg1 = args.algo == "alg1"
-    step = (lambda n: ctx.iterate_alg1(n)) if alg1 else (lambda n: ctx.iterate(n))
+    alg1 = args.algo != "tiled"
+    step = {"tiled": ctx.iterate, "alg1": ctx.iterate_alg1, "mu": ctx.iterate_mu}[args.algo]
 
     # warm-up (also captures the CUDA graph)
     step(max(1, args.warmup))
@@ -371,8 +378,9 @@ def run_gpu(args):
     ms_warm = ev0.elapsed_time(ev1) / args.steps
 
     # per-step breakdown with CUDA events (eager launches)
-    prof = ctx.iterate_alg1(max(3, min(10, args.steps)), profile=True) if alg1 else \
-        ctx.profile(max(3, min(10, args.steps)))
+    n_prof = max(3, min(10, args.steps))
+    prof = {"tiled": lambda: ctx.profile(n_prof), "alg1": lambda: ctx.iterate_alg1(n_prof, profile=True),
+            "mu": lambda: ctx.iterate_mu(n_prof, profile=True)}[args.algo]()
     peak, peak_kind = _peaks()
     if dense:
         ab, prod_flops = dense_costs(V, D, K, bf16)
@@ -438,7 +446,7 @@ def run_gpu(args):
                    "tile_T": q["tile_T"], "chain_ctas": q["chain_ctas"], "precision": args.prec,
                    "l2": "flushed between steps (256 MB write)", "parallelism": "replicas" if world > 1 else "single",
                    "ms_per_step_warm_l2": round(ms_warm, 5), "rel_err_final": rel,
-                   "algorithm": "Alg. 1 column by column (no tiling)" if alg1 else "Alg. 2 tiled order (PL-NMF)"},
+                   "algorithm": ALGOS[args.algo]},
         "e2e": {"value": round(1.0 / t_e2e, 3), "unit": "iter/s", "h2d_bytes_per_step": fac_bytes,
                 "d2h_bytes_per_step": fac_bytes + 16},
         "gpu_launches": int(q["launches_per_iter"]) * args.steps,
@@ -765,9 +773,10 @@ def run_time_to_error(args):
         ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         dev_ms, its, e, reached = 0.0, 0, None, False
         th0 = time.perf_counter()
+        advance = {"tiled": ctx.iterate, "alg1": ctx.iterate_alg1, "mu": ctx.iterate_mu}[args.algo]
         while its < 20 * n_ref:
             ev0.record(stream)
-            ctx.iterate(CHECK)
+            advance(CHECK)
             ev1.record(stream)
             _, e = ctx.error()                                  # synchronises the stream
             dev_ms += ev0.elapsed_time(ev1)
@@ -786,7 +795,8 @@ def run_time_to_error(args):
         "ms_per_step": round(1e3 * fp["seconds_device"] / max(1, fp["iterations"]), 5),
         "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic (seeded; no dataset)",
-        "config": {"workload": WORKLOADS[args.workload], "K": K, "e_ref": e_ref, "target": target,
+        "config": {"workload": WORKLOADS[args.workload], "algorithm": ALGOS[args.algo], "K": K, "e_ref": e_ref,
+                   "target": target,
                    "oracle_iterations": n_ref, "oracle_seconds": round(t_oracle, 3), "check_every": CHECK,
                    "forms": results},
     }
@@ -808,8 +818,9 @@ def main():
     ap.add_argument("--workload", default="text20ng", choices=sorted(WORKLOADS))
     ap.add_argument("--prec", default="fp32", choices=["fp32", "bf16"])
     ap.add_argument("--tile", type=int, default=0)
-    ap.add_argument("--algo", default="tiled", choices=["tiled", "alg1"],
-                    help="alg1: the updates column by column as Alg. 1 is written (comparator of the tiled form)")
+    ap.add_argument("--algo", default="tiled", choices=sorted(ALGOS),
+                    help="comparators of the tiled form: alg1 (the updates column by column as Alg. 1 is "
+                         "written), mu (multiplicative updates)")
     ap.add_argument("--cpu-iters", type=int, default=5)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--time-to-error", action="store_true",

@@ -184,6 +184,13 @@ nmf_status nmf_set_buffer(nmf_ctx* c, int32_t which, const float* src, int64_t c
  * NMF_EINVAL for n_iters < 0 or a NULL context. */
 nmf_status nmf_iterate_alg1(nmf_ctx* c, int32_t n_iters, float* step_ms);
 
+/* Multiplicative updates (Lee & Seung 2001; the simplest NMF algorithm, the
+ * paper's comparison baseline, Sec. 2): H <- H * (W^T A) / (W^T W H + eps),
+ * then W <- W * (A H^T) / (W H H^T + eps), elementwise, W not normalised;
+ * the same products, Grams and objective as nmf_iterate.  Arguments, state
+ * and step_ms as nmf_iterate_alg1. */
+nmf_status nmf_iterate_mu(nmf_ctx* c, int32_t n_iters, float* step_ms);
+
 /* Step timing (tracing): runs n_iters iterations eagerly (no graph) with a
  * CUDA event between consecutive steps on the context stream and writes the
  * mean milliseconds per iteration of each step to step_ms[0..6]:

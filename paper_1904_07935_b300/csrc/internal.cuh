@@ -176,6 +176,11 @@ cudaError_t alg1_update_h(float* Ht, const float* R, const float* S, int D, int 
 cudaError_t alg1_update_w(float* W, const float* P, const float* Q, int V, int K, int Kp, float eps, float* part,
                           int* status, cudaStream_t s, int* launches);
 
+// Multiplicative update of the tall factor X (N x Kp): X <- X * B / (X G + delta)
+// for the K valid columns (G symmetric K x K Gram); scratch: N x Kp.
+cudaError_t mu_update(float* X, const float* B, const float* G, float* scratch, int N, int K, int Kp, float delta,
+                      cudaStream_t s, int* launches);
+
 // Persistent, cooperative W update (one launch per update): cluster 0 runs the
 // column chain over all tiles, the other clusters compute the tile bases.
 struct WPersistConfig {

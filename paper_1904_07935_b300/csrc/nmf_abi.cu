@@ -72,6 +72,8 @@ struct nmf_ctx {
   float* alg1_part = nullptr;
   cudaGraph_t graph_alg1 = nullptr;
   cudaGraphExec_t graph_alg1_exec = nullptr;
+  cudaGraph_t graph_mu = nullptr;           // nmf_iterate_mu
+  cudaGraphExec_t graph_mu_exec = nullptr;
 };
 
 namespace {
@@ -318,6 +320,10 @@ void destroy_graph(nmf_ctx* c) {
   if (c->graph_alg1) cudaGraphDestroy(c->graph_alg1);
   c->graph_alg1_exec = nullptr;
   c->graph_alg1 = nullptr;
+  if (c->graph_mu_exec) cudaGraphExecDestroy(c->graph_mu_exec);
+  if (c->graph_mu) cudaGraphDestroy(c->graph_mu);
+  c->graph_mu_exec = nullptr;
+  c->graph_mu = nullptr;
 }
 
 nmf_status validate_and_copy_csr(const nmf_problem* p, std::vector<int>& rp, std::vector<int>& ci,
@@ -853,24 +859,33 @@ nmf_status nmf_iterate(nmf_ctx* c, int32_t n_iters) {
   return NMF_OK;
 }
 
-// One iteration of Alg. 1 as written: the same products as enq_iteration,
-// the two updates column by column (alg1.cu), steps in sequence.  Entry and
-// exit invariant as enq_iteration: S = W^T W and R = A^T W for the current W.
-cudaError_t enq_alg1_iteration(nmf_ctx* c) {
+// Comparator forms of one iteration (same products and objective as
+// enq_iteration, other updates; same entry/exit invariant: S = W^T W and
+// R = A^T W for the current W):
+//   FORM_ALG1: Alg. 1 as written, the updates column by column (alg1.cu);
+//   FORM_MU:   multiplicative updates (mu.cu), H then W.
+enum AltForm { FORM_ALG1 = 0, FORM_MU = 1 };
+
+cudaError_t enq_update_alt(nmf_ctx* c, AltForm f, bool is_w, cudaStream_t s, int* launches) {
+  if (f == FORM_ALG1)
+    return is_w ? alg1_update_w(c->W, c->P, c->Q, c->V, c->K, c->Kp, c->eps, c->alg1_part, c->d_status, s, launches)
+                : alg1_update_h(c->Ht, c->R, c->S, c->D, c->K, c->Kp, c->eps, s, launches);
+  return is_w ? mu_update(c->W, c->P, c->Q, c->Y, c->V, c->K, c->Kp, c->eps, s, launches)
+              : mu_update(c->Ht, c->R, c->S, c->Y, c->D, c->K, c->Kp, c->eps, s, launches);
+}
+
+cudaError_t enq_alt_iteration(nmf_ctx* c, AltForm f) {
   cudaError_t e;
-  if ((e = alg1_update_h(c->Ht, c->R, c->S, c->D, c->K, c->Kp, c->eps, c->stream, &c->launch_count)) != cudaSuccess)
-    return e;
+  if ((e = enq_update_alt(c, f, false, c->stream, &c->launch_count)) != cudaSuccess) return e;
   if ((e = enq_product_P(c)) != cudaSuccess) return e;
   if ((e = enq_gram(c, c->gramH, c->Ht, c->Q)) != cudaSuccess) return e;
-  if ((e = alg1_update_w(c->W, c->P, c->Q, c->V, c->K, c->Kp, c->eps, c->alg1_part, c->d_status, c->stream,
-                         &c->launch_count)) != cudaSuccess)
-    return e;
+  if ((e = enq_update_alt(c, f, true, c->stream, &c->launch_count)) != cudaSuccess) return e;
   if ((e = enq_product_R(c)) != cudaSuccess) return e;
   if ((e = enq_gram(c, c->gramW, c->W, c->S)) != cudaSuccess) return e;
   return enq_objective(c);
 }
 
-nmf_status nmf_iterate_alg1(nmf_ctx* c, int32_t n_iters, float* step_ms) {
+nmf_status iterate_alt(nmf_ctx* c, AltForm f, int32_t n_iters, float* step_ms) {
   if (!c || n_iters < 0) return NMF_EINVAL;
   if (n_iters == 0) return NMF_OK;
   CK(ensure_entry(c));
@@ -883,14 +898,13 @@ nmf_status nmf_iterate_alg1(nmf_ctx* c, int32_t n_iters, float* step_ms) {
     for (int it = 0; it < n_iters && e == cudaSuccess; ++it) {
       cudaStream_t s = c->stream;
       e = cudaEventRecord(ev[0], s);                                           // H
-      if (e == cudaSuccess) e = alg1_update_h(c->Ht, c->R, c->S, c->D, c->K, c->Kp, c->eps, s, nullptr);
+      if (e == cudaSuccess) e = enq_update_alt(c, f, false, s, nullptr);
       if (e == cudaSuccess) e = cudaEventRecord(ev[1], s);                     // P
       if (e == cudaSuccess) e = enq_product_P(c);
       if (e == cudaSuccess) e = cudaEventRecord(ev[2], s);                     // Q
       if (e == cudaSuccess) e = enq_gram(c, c->gramH, c->Ht, c->Q);
       if (e == cudaSuccess) e = cudaEventRecord(ev[3], s);                     // W
-      if (e == cudaSuccess)
-        e = alg1_update_w(c->W, c->P, c->Q, c->V, c->K, c->Kp, c->eps, c->alg1_part, c->d_status, s, nullptr);
+      if (e == cudaSuccess) e = enq_update_alt(c, f, true, s, nullptr);
       if (e == cudaSuccess) e = cudaEventRecord(ev[4], s);                     // R
       if (e == cudaSuccess) e = enq_product_R(c);
       if (e == cudaSuccess) e = cudaEventRecord(ev[5], s);                     // S
@@ -912,22 +926,32 @@ nmf_status nmf_iterate_alg1(nmf_ctx* c, int32_t n_iters, float* step_ms) {
     c->iters_run += n_iters;
     return read_status(c);
   }
-  if (!c->graph_alg1_exec) {
+  cudaGraph_t& graph = f == FORM_ALG1 ? c->graph_alg1 : c->graph_mu;
+  cudaGraphExec_t& exec = f == FORM_ALG1 ? c->graph_alg1_exec : c->graph_mu_exec;
+  if (!exec) {
     c->launch_count = 0;
     CK(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
-    cudaError_t e = enq_alg1_iteration(c);
+    cudaError_t e = enq_alt_iteration(c, f);
     cudaGraph_t g = nullptr;
     cudaError_t e2 = cudaStreamEndCapture(c->stream, &g);
     if (e != cudaSuccess || e2 != cudaSuccess) {
       if (g) cudaGraphDestroy(g);
       return from_cuda(e != cudaSuccess ? e : e2);
     }
-    c->graph_alg1 = g;
-    CK(cudaGraphInstantiate(&c->graph_alg1_exec, g, 0));
+    graph = g;
+    CK(cudaGraphInstantiate(&exec, g, 0));
   }
-  for (int i = 0; i < n_iters; ++i) CK(cudaGraphLaunch(c->graph_alg1_exec, c->stream));
+  for (int i = 0; i < n_iters; ++i) CK(cudaGraphLaunch(exec, c->stream));
   c->iters_run += n_iters;
   return NMF_OK;
+}
+
+nmf_status nmf_iterate_alg1(nmf_ctx* c, int32_t n_iters, float* step_ms) {
+  return iterate_alt(c, FORM_ALG1, n_iters, step_ms);
+}
+
+nmf_status nmf_iterate_mu(nmf_ctx* c, int32_t n_iters, float* step_ms) {
+  return iterate_alt(c, FORM_MU, n_iters, step_ms);
 }
 
 nmf_status nmf_warm_h(nmf_ctx* c, nmf_mlp* mlp, const nmf_problem* nd, float tol, int32_t max_sweeps,

@@ -62,6 +62,7 @@ _SIGS = {
     "nmf_query": ([_vp, ctypes.POINTER(_i32), ctypes.POINTER(_i32), ctypes.POINTER(_i32)], _i32),
     "nmf_profile": ([_vp, _i32, _vp], _i32),
     "nmf_iterate_alg1": ([_vp, _i32, _vp], _i32),
+    "nmf_iterate_mu": ([_vp, _i32, _vp], _i32),
     "nmf_destroy": ([_vp], None),
     "nmf_gram_noalloc": ([_vp, _i32, _i32, _i64, _vp, _vp], _i32),
     "nmf_gemm": ([_i32, _i32, _i32, _vp, _i64, _i32, _vp, _i64, _vp, _i64, _i32, _vp], _i32),
@@ -239,6 +240,15 @@ class Nmf:
             check(lib.nmf_iterate_alg1(self.h, n, out.ctypes.data), "nmf_iterate_alg1")
             return dict(zip(self.PROFILE_STEPS, out.tolist()))
         check(lib.nmf_iterate_alg1(self.h, n, None), "nmf_iterate_alg1")
+
+    def iterate_mu(self, n=1, profile=False):
+        """n multiplicative-update iterations (Lee & Seung); with profile=True
+        the mean ms of each step (as profile())."""
+        if profile:
+            out = np.zeros(len(self.PROFILE_STEPS), dtype=np.float32)
+            check(lib.nmf_iterate_mu(self.h, n, out.ctypes.data), "nmf_iterate_mu")
+            return dict(zip(self.PROFILE_STEPS, out.tolist()))
+        check(lib.nmf_iterate_mu(self.h, n, None), "nmf_iterate_mu")
 
     def query(self):
         t, c, l = _i32(), _i32(), _i32()

@@ -359,3 +359,51 @@ def test_operand_rounding_hook_is_identity_when_unset():
     a = fh.iteration(A, W, H, EPS)
     b = fh.iteration(A, W, H, EPS, operand_round=lambda x: x)
     assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
+
+
+# --- multiplicative updates (MU comparator) ---------------------------------
+
+def test_mu_k1_h_step_is_least_squares():
+    """K = 1: one MU H step gives h_j = w^T a_j / w^T w for every positive
+    h_j, the unconstrained least-squares minimiser (non-negative for A >= 0)."""
+    from oracle import mu
+    rng = np.random.default_rng(3)
+    A = rng.random((40, 30))
+    w = rng.random((40, 1))
+    h0 = rng.random((1, 30)) + 0.1
+    h1 = mu.update_h(A, w, h0, delta=0.0)
+    np.testing.assert_allclose(h1[0], (w[:, 0] @ A) / (w[:, 0] @ w[:, 0]), rtol=1e-13)
+
+
+def test_mu_exact_factorisation_is_fixed_point():
+    from oracle import mu
+    rng = np.random.default_rng(4)
+    W = rng.random((50, 6)) + 0.05
+    H = rng.random((6, 35)) + 0.05
+    A = W @ H
+    W1, H1 = mu.iteration(A, W, H, delta=0.0)
+    np.testing.assert_allclose(H1, H, rtol=1e-12)
+    np.testing.assert_allclose(W1, W, rtol=1e-12)
+
+
+def test_mu_objective_non_increasing_and_order():
+    """Lee & Seung's monotonicity, on dense and sparse inputs; and the order
+    of the two updates (H first, with the current W) matters."""
+    from oracle import mu
+    for A in (synth.planted_dense(60, 45, 5, 9).A.astype(np.float64),
+              synth.sparse_termdoc(300, 120, 5, mean_terms=12).A):
+        V, D = (A.n_rows, A.n_cols) if hasattr(A, "n_rows") else A.shape
+        W0, H0 = synth.init_factors(11, V, D, 4)
+        W, H = mu.normalize_init(W0), H0.astype(np.float64)
+        f_prev = np.inf
+        for _ in range(30):
+            W, H = mu.iteration(A, W, H)
+            f = ob.frob2_direct(A, W, H)
+            assert f <= f_prev * (1 + 1e-12)
+            f_prev = f
+    A = synth.planted_dense(60, 45, 5, 9).A.astype(np.float64)
+    W0, H0 = synth.init_factors(12, 60, 45, 4)
+    W, H = mu.normalize_init(W0), H0.astype(np.float64)
+    Wa, Ha = mu.iteration(A, W, H)
+    Wb = mu.update_w(A, W, H)                          # W first: a different iterate
+    assert not np.allclose(Wa, Wb)
