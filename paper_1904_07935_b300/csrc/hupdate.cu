@@ -467,7 +467,7 @@ __global__ void __launch_bounds__(256) h_update_warp_kernel(float* __restrict__ 
 __global__ void __launch_bounds__(HTHREADS) w_prep_kernel(const float* __restrict__ X, const float* __restrict__ B,
                                                           const float* __restrict__ G, float* __restrict__ Y,
                                                           float* __restrict__ Ylo, int N, int K, int Kp, int lo,
-                                                          int new_end, int* status) {
+                                                          int new_end, int T, int* status) {
   // Shared memory: Gc (Kr x HT) = G[j][lo + c], zero beyond K; Xs = the CTA's
   // rows of X (row stride Kp + 4, see h_update_kernel).
   extern __shared__ __align__(16) float smem[];
@@ -476,7 +476,7 @@ __global__ void __launch_bounds__(HTHREADS) w_prep_kernel(const float* __restric
   const int ldx = Kp + 4;
   float* Gc = smem;
   float* Xs = smem + Kr * HT;
-  const int hi = min(K, lo + HT);
+  const int hi = min(K, lo + T);                          // tile [lo, hi), T <= HT columns
   const int tid = threadIdx.x;
   const int sub = tid & (HL - 1);
   const int row0 = blockIdx.x * HROWS;
@@ -525,7 +525,7 @@ __global__ void __launch_bounds__(HTHREADS) w_prep_kernel(const float* __restric
     }
   };
   outside(0, new_end);
-  outside(lo + HT < Kp ? lo + HT : Kp, Kp);
+  outside(lo + T < Kp ? lo + T : Kp, Kp);
   // Old in-tile columns j > c: one more block.
   float xo[HT];
 #pragma unroll
@@ -539,7 +539,7 @@ __global__ void __launch_bounds__(HTHREADS) w_prep_kernel(const float* __restric
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
       const int cl = 4 * sub + q;
-      if (j > cl) blk[q] = fmaf(Gc[(lo + j) * HT + cl], xo[j], blk[q]);
+      if (j > cl && j < T) blk[q] = fmaf(Gc[(lo + j) * HT + cl], xo[j], blk[q]);
     }
   }
 #pragma unroll
@@ -561,12 +561,13 @@ __global__ void __launch_bounds__(HTHREADS) w_prep_kernel(const float* __restric
 }  // namespace
 
 cudaError_t w_prep_run(const float* X, const float* B, const float* G, float* Y, int N, int K, int Kp, int lo,
-                       int new_end, int* status, cudaStream_t s, float* Ylo) {
+                       int new_end, int* status, cudaStream_t s, int T, float* Ylo) {
+  if (T < 1 || T > HT) return cudaErrorInvalidValue;
   const size_t smem = sizeof(float) * ((size_t)((Kp + HT - 1) / HT * HT) * HT + (size_t)HROWS * (Kp + 4));
   cudaError_t e = cudaFuncSetAttribute(w_prep_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   const int blocks = (N + HROWS - 1) / HROWS;
-  w_prep_kernel<<<blocks, HTHREADS, smem, s>>>(X, B, G, Y, B ? nullptr : Ylo, N, K, Kp, lo, new_end, status);
+  w_prep_kernel<<<blocks, HTHREADS, smem, s>>>(X, B, G, Y, B ? nullptr : Ylo, N, K, Kp, lo, new_end, T, status);
   return cudaGetLastError();
 }
 

@@ -157,13 +157,14 @@ bool chain_config_cluster(int N, int T, int cl, ChainConfig* cfg);
 // place, B = R, G = S.
 cudaError_t h_update_run(float* X, const float* B, const float* G, int N, int K, int Kp, float eps,
                          int* status, cudaStream_t s);
-// Base of W tile [lo, lo + 16) for the chain: Y[:, tile] from B = P, G = Q and
-// the current (partly updated) factor X, with the new columns [0, new_end).
+// Base of W tile [lo, lo + T) (T <= 16) for the chain: Y[:, tile] from B = P,
+// G = Q and the current (partly updated) factor X, with the new columns
+// [0, new_end).
 // B == nullptr leaves the data term out; then, with Ylo (N x 16) given, the
 // compensated sum is returned unrounded as Y[:, tile] + Ylo (the caller adds
 // P to Y first: the two cancel, so the early rounding would be magnified).
 cudaError_t w_prep_run(const float* X, const float* B, const float* G, float* Y, int N, int K, int Kp, int lo,
-                       int new_end, int* status, cudaStream_t s, float* Ylo = nullptr);
+                       int new_end, int* status, cudaStream_t s, int T, float* Ylo = nullptr);
 constexpr int kRowTile = 16;   // tile width of the row-parallel update kernels
 
 // Alg. 1 as written (no column tiling): the H and W updates column by

@@ -208,7 +208,8 @@ cudaError_t enq_update(nmf_ctx* c, float* X, const float* G, const float* B, int
   // W: tile tau's base without tile tau-1 ("main") runs on the side stream
   // while the chain of tile tau-1 runs; the chain of tile tau adds tile
   // tau-1 itself.  Events: fork, base_done[tau], chain_done[tau].
-  const int nt = (K + kRowTile - 1) / kRowTile;
+  const int T = c->T;                                   // tile width of this path (<= 16)
+  const int nt = (K + T - 1) / T;
   cudaEvent_t* ev = c->ev.data();
   cudaEvent_t fork = ev[0];
   cudaEvent_t* base_done = ev + 1;
@@ -219,20 +220,21 @@ cudaError_t enq_update(nmf_ctx* c, float* X, const float* G, const float* B, int
   // An event wait orders against the event's latest record *in enqueue
   // order*, so every base is enqueued after the chain it depends on.
   auto base = [&](int tau) -> cudaError_t {
-    const int lo = tau * kRowTile;
-    const int new_end = tau >= 1 ? lo - kRowTile : 0;    // new columns [0, lo - 16)
+    const int lo = tau * T;
+    const int new_end = tau >= 1 ? lo - T : 0;           // new columns [0, lo - T)
     cudaError_t err;
     if (tau >= 2 && (err = cudaStreamWaitEvent(c->side, chain_done[tau - 2], 0)) != cudaSuccess) return err;
-    if ((err = w_prep_run(X, B, G, c->Y, N, K, Kp, lo, new_end, c->d_status, c->side)) != cudaSuccess) return err;
+    if ((err = w_prep_run(X, B, G, c->Y, N, K, Kp, lo, new_end, c->d_status, c->side, T)) != cudaSuccess)
+      return err;
     c->launch_count += 1;
     return cudaEventRecord(base_done[tau], c->side);
   };
   if ((e = base(0)) != cudaSuccess) return e;
   if (nt > 1 && (e = base(1)) != cudaSuccess) return e;
   for (int tau = 0; tau < nt; ++tau) {
-    const int lo = tau * kRowTile, hi = std::min(K, lo + kRowTile);
+    const int lo = tau * T, hi = std::min(K, lo + T);
     if ((e = cudaStreamWaitEvent(c->stream, base_done[tau], 0)) != cudaSuccess) return e;
-    e = chain_run(c->Y, X, G, N, Kp, lo, hi, tau >= 1 ? lo - kRowTile : -1, c->eps, true, c->chainW, c->d_status,
+    e = chain_run(c->Y, X, G, N, Kp, lo, hi, tau >= 1 ? lo - T : -1, c->eps, true, c->chainW, c->d_status,
                   c->stream);
     c->launch_count += 1;
     if (e != cudaSuccess) return e;
@@ -269,7 +271,8 @@ cudaError_t enq_iteration(nmf_ctx* c) {
   const bool pre0 = c->w_persistent;
   if (pre0) {
     c->launch_count += 1;
-    if ((e = w_prep_run(c->W, nullptr, c->Q, c->Y, c->V, c->K, c->Kp, 0, 0, c->d_status, b, c->Y0lo)) != cudaSuccess)
+    if ((e = w_prep_run(c->W, nullptr, c->Q, c->Y, c->V, c->K, c->Kp, 0, 0, c->d_status, b, kRowTile, c->Y0lo)) !=
+        cudaSuccess)
       return e;
   }
   if ((e = cudaEventRecord(c->evx[1], b)) != cudaSuccess) return e;
@@ -368,16 +371,19 @@ nmf_status init_impl(const nmf_problem* p, nmf_ctx* c) {
     c->own_stream = true;
   }
   // Tile width T of the regrouped updates: 16 columns (the register tile of
-  // the column chain).  A requested tile_T other than 16 is accepted only as
-  // a request for the library choice.
-  const int T = kRowTile;
+  // the column chain).  With the per-tile W launches (NMF_FLAG_MULTI_LAUNCH_W)
+  // a requested tile_T of 1..16 sets the W update's tile width (the tile-size
+  // study; the H update keeps 16); otherwise a request is taken as one for
+  // the library choice.
+  const int T = (p->flags & NMF_FLAG_MULTI_LAUNCH_W) && p->tile_T >= 1 && p->tile_T <= kRowTile ? p->tile_T
+                                                                                              : kRowTile;
   if (!chain_config_for(V, true, T, &c->chainW)) return NMF_EUNSUPPORTED;
   if (!chain_config_for(D, false, T, &c->chainH)) return NMF_EUNSUPPORTED;
   c->T = T;
 
   CK(cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking));
   {
-    const int nt = (c->K + kRowTile - 1) / kRowTile;
+    const int nt = (c->K + T - 1) / T;
     c->ev.assign(1 + 2 * nt, nullptr);
     for (auto& e : c->ev) CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
     for (auto& e : c->evx) CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));

@@ -225,6 +225,20 @@ def test_one_iteration_sparse_k_sweep(nmf, K):
     assert rel_w(Wg, Wr) < TOL_ITER
 
 
+@pytest.mark.parametrize("T", [4, 8, 12, 16])
+def test_one_iteration_per_tile_w_width(nmf, T):
+    """The per-tile W path at tile widths 4 .. 16 (the tile-size study; K = 21
+    and 48 are multiples of none of them but 4 / 12 / 16 for 48), one
+    iteration against the oracle."""
+    for (V, D, seed, K) in [(2500, 1300, 51, 21), (6000, 3000, 61, 48)]:
+        sp = synth.sparse_termdoc(V, D, seed, mean_terms=30)
+        W0, H0 = synth.init_factors(seed + 1, V, D, K)
+        ctx = _sparse_ctx(nmf, sp, K, W0, H0, tile_T=T, flags=nmf.FLAG_MULTI_LAUNCH_W)
+        assert ctx.query()["tile_T"] == T
+        Wg, Hg, Wr, Hr = _one_iteration(nmf, sp.A, ctx, W0, H0)
+        assert rel_h(Hg, Hr) < TOL_ITER and rel_w(Wg, Wr) < TOL_ITER, (V, K, T)
+
+
 @pytest.fixture(scope="module")
 def text_full():
     return synth.text_20ng_like()
