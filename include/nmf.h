@@ -60,7 +60,11 @@ typedef enum { NMF_PREC_FP32 = 0, NMF_PREC_BF16 = 1 } nmf_precision;
  *                seed ^ 0x5757.. for W, seed ^ 0x4848.. for H).  Either way
  *                the columns of W are then scaled to unit L2 norm.
  *   eps          clamp floor of Alg. 1 (paper leaves it unset; 0 -> 1e-16).
- *   tile_T       column-tile width T of Alg. 2; 0 -> library choice.
+ *   tile_T       column-tile width T of Alg. 2; 0 -> library choice (16, the
+ *                register tile of the column chain).  Honoured (1..16) for the
+ *                W update when flags has NMF_FLAG_MULTI_LAUNCH_W (per-tile
+ *                launches); otherwise any value means the library choice.
+ *                nmf_query reports the width in use.
  *   prec         NMF_PREC_FP32 (all FP32) or NMF_PREC_BF16 (dense A only:
  *                products A H^T, A^T W and the Gram matrices on the tensor
  *                cores with BF16 operands and FP32 accumulation; column
