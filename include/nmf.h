@@ -110,7 +110,8 @@ typedef struct {
 
 typedef struct nmf_ctx nmf_ctx;
 
-/* Validates the problem (shapes, CSR structure, A >= 0 and finite), builds
+/* Validates the problem (shapes, CSR structure, A >= 0 and finite, A not
+ * identically zero: the relative error is defined only for ||A|| > 0), builds
  * the transposed CSR of A and the SpMM work plans, computes ||A||_F^2 in
  * FP64, allocates W, H and all intermediates and initialises the factors.
  * On success *out owns every device buffer it allocated.  Synchronous. */
