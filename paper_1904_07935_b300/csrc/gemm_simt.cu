@@ -172,67 +172,85 @@ __global__ void __launch_bounds__(256) gemm_kernel(GemmArgs g) {
   }
 }
 
-// Split-N Gram for Kp <= 176: CTA z computes the whole Kp8 x Kp8 Gram of its
-// row chunk (Kp8 = Kp rounded up to 8), one 8 x 8 register micro-tile per
-// thread ((Kp8 / 8)^2 threads), rows of X staged GB at a time in shared
-// memory and read as 16-byte broadcasts (16 multiply-adds per load).
-constexpr int GB = 16;
-constexpr int kGramFullMaxKp = 176;               // (176 / 8)^2 = 484 threads
-constexpr int kGramFullMinKp = 64;                // >= 64 threads: <= 4 staged float4 each
-__global__ void __launch_bounds__(512) gram_full_kernel(const float* __restrict__ X, int N, int Kp, int Kp8,
-                                                        int chunk, float* __restrict__ part) {
-  extern __shared__ __align__(16) float xs[];      // 2 x GB x Kp8
-  const int nt = blockDim.x;
-  const int tpr = Kp8 / 8;                         // threads per output row of micro-tiles
-  const int tx = threadIdx.x % tpr, ty = threadIdx.x / tpr;
+// Split-N Gram for 64 <= Kp <= 176: CTA z computes the upper triangle of
+// the Kp8 x Kp8 Gram of its row chunk (Kp8 = Kp rounded up to 8).  The Kp8
+// indices form m = Kp8 / 8 groups of 8, group g = {4g .. 4g+3} together with
+// {Kh + 4g .. Kh + 4g+3} (Kh = Kp8 / 2), so that consecutive groups are
+// consecutive 16-byte words of a staged row (conflict-free loads).  Every
+// pair of groups a <= b is one 8 x 8 register tile (m (m + 1) / 2 tiles),
+// which covers every unordered index pair once (both orders for a = b); a
+// value for (i, j) is stored at (min(i, j), max(i, j)) of the partial, the
+// upper triangle that gram_reduce reads.  Two threads share a tile: rows of
+// X are staged GR at a time in shared memory (double-buffered through
+// registers) and thread half h multiplies rows [h GR/2, (h+1) GR/2) of each
+// staged block; at the end half 1's tile goes through shared memory and half
+// 0 adds it (fixed order).
+constexpr int GR = 16;                            // rows per staged block
+constexpr int kGramFullMaxKp = 176;               // m = 22: 253 tiles, 506 threads
+constexpr int kGramFullMinKp = 64;                // m = 8: 36 tiles, 72 threads
+__host__ __device__ constexpr int gram_tri_tiles(int Kp8) { return (Kp8 / 8) * (Kp8 / 8 + 1) / 2; }
+constexpr int kTriStride = 256;                   // >= gram_tri_tiles(176); compile-time offsets
+__host__ __device__ constexpr int gram_tri_smem_floats(int Kp8) {
+  return 2 * GR * Kp8 > 64 * kTriStride ? 2 * GR * Kp8 : 64 * kTriStride;
+}
+static_assert(gram_tri_tiles(kGramFullMaxKp) <= kTriStride, "tile stride");
+__global__ void __launch_bounds__(512) gram_tri_kernel(const float* __restrict__ X, int N, int Kp, int Kp8,
+                                                       int chunk, float* __restrict__ part) {
+  extern __shared__ __align__(16) float xs[];      // staging 2 x GR x Kp8; afterwards half 1's tiles
+  const int m = Kp8 / 8, Kh = Kp8 / 2;
+  const int nT = m * (m + 1) / 2;
+  const int h = threadIdx.x >= nT ? 1 : 0;
+  const int u = threadIdx.x - h * nT;
+  // Tile u -> (ty, tx), ty <= tx, row-major over the upper triangle.
+  int ty = 0, rem = u;
+  while (rem >= m - ty) {
+    rem -= m - ty;
+    ++ty;
+  }
+  const int tx = ty + rem;
   const int r0 = blockIdx.x * chunk, r1 = min(N, r0 + chunk);
   float acc[8][8];
 #pragma unroll
   for (int i = 0; i < 8; ++i)
 #pragma unroll
     for (int j = 0; j < 8; ++j) acc[i][j] = 0.f;
-  const int kq = Kp8 / 4;                          // float4 per staged row
-  // Staging of a GB-row block: GB * Kp8 / 4 float4 over (Kp8 / 8)^2 threads,
-  // at most 256 / Kp8 <= 4 per thread for Kp8 >= 64; loaded into registers
-  // before the current block is multiplied, stored after it.
-  constexpr int MAXE = 4;
-  const int total = GB * kq;
-  auto load = [&](int rb, int e) {
-    float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-    if (e < total) {
+  // Staging by 16-byte cp.async copies (L2 only; rows past the chunk and
+  // columns past Kp zero-filled by the copy), the next block in flight while
+  // the current one is multiplied.
+  const int nt = blockDim.x;
+  const int kq = Kp8 / 4;                          // 16-byte words per staged row
+  const int total = GR * kq;
+  auto stage = [&](int buf, int rb) {
+    for (int e = threadIdx.x; e < total; e += nt) {
       const int r = e / kq, q = e % kq;
       const int row = rb + r;
-      if (row < r1 && 4 * q < Kp) v = __ldg(reinterpret_cast<const float4*>(X + (int64_t)row * Kp) + q);
+      const bool ok = row < r1 && 4 * q < Kp;
+      const float* src = ok ? X + (int64_t)row * Kp + 4 * q : X;
+      asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(smem_u32(xs + buf * GR * Kp8 + 4 * e)),
+                   "l"(src), "r"(ok ? 16 : 0)
+                   : "memory");
     }
-    return v;
-  };
-  auto store = [&](int buf, int e, float4 v) {
-    if (e < total) {
-      const int r = e / kq, q = e % kq;
-      *reinterpret_cast<float4*>(xs + buf * GB * Kp8 + r * Kp8 + 4 * q) = v;
-    }
+    asm volatile("cp.async.commit_group;" ::: "memory");
   };
   int buf = 0;
-  {
-    float4 v[MAXE];
-#pragma unroll
-    for (int u = 0; u < MAXE; ++u) v[u] = load(r0, threadIdx.x + u * nt);
-#pragma unroll
-    for (int u = 0; u < MAXE; ++u) store(0, threadIdx.x + u * nt, v[u]);
-  }
-  __syncthreads();
-  for (int rb = r0; rb < r1; rb += GB) {
-    const bool more = rb + GB < r1;
-    float4 pre[MAXE];
-#pragma unroll
-    for (int u = 0; u < MAXE; ++u) pre[u] = more ? load(rb + GB, threadIdx.x + u * nt) : make_float4(0.f, 0.f, 0.f, 0.f);
-    const float* src = xs + buf * GB * Kp8;
+  stage(0, r0);
+  for (int rb = r0; rb < r1; rb += GR) {
+    const bool more = rb + GR < r1;
+    if (more) {
+      stage(buf ^ 1, rb + GR);
+      asm volatile("cp.async.wait_group 1;" ::: "memory");
+    } else {
+      asm volatile("cp.async.wait_group 0;" ::: "memory");
+    }
+    __syncthreads();                               // block rb landed for every thread
+    const float* src = xs + buf * GR * Kp8 + h * (GR / 2) * Kp8;
 #pragma unroll 2
-    for (int r = 0; r < GB; ++r) {
-      const float4 a0 = *reinterpret_cast<const float4*>(src + r * Kp8 + 8 * ty);
-      const float4 a1 = *reinterpret_cast<const float4*>(src + r * Kp8 + 8 * ty + 4);
-      const float4 b0 = *reinterpret_cast<const float4*>(src + r * Kp8 + 8 * tx);
-      const float4 b1 = *reinterpret_cast<const float4*>(src + r * Kp8 + 8 * tx + 4);
+    for (int r = 0; r < GR / 2; ++r) {
+      const float* row = src + r * Kp8;
+      const float4 a0 = *reinterpret_cast<const float4*>(row + 4 * ty);
+      const float4 a1 = *reinterpret_cast<const float4*>(row + Kh + 4 * ty);
+      const float4 b0 = *reinterpret_cast<const float4*>(row + 4 * tx);
+      const float4 b1 = *reinterpret_cast<const float4*>(row + Kh + 4 * tx);
       const float av[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
       const float bv[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
 #pragma unroll
@@ -240,23 +258,33 @@ __global__ void __launch_bounds__(512) gram_full_kernel(const float* __restrict_
 #pragma unroll
         for (int j = 0; j < 8; ++j) acc[i][j] = fmaf(av[i], bv[j], acc[i][j]);
     }
-    if (more) {
-#pragma unroll
-      for (int u = 0; u < MAXE; ++u) store(buf ^ 1, threadIdx.x + u * nt, pre[u]);
-    }
-    __syncthreads();
+    __syncthreads();                               // buf is free for the copies two blocks on
     buf ^= 1;
   }
+  // Half 1 hands its tile to half 0 (entry-major with a fixed stride, so a
+  // warp's accesses are consecutive words); the staging buffers are no longer
+  // read.
+  if (h == 1) {
+#pragma unroll
+    for (int i = 0; i < 8; ++i)
+#pragma unroll
+      for (int j = 0; j < 8; ++j) xs[(i * 8 + j) * kTriStride + u] = acc[i][j];
+  }
+  __syncthreads();
+  if (h == 1) return;
   float* out = part + (int64_t)blockIdx.x * Kp * Kp;
 #pragma unroll
   for (int i = 0; i < 8; ++i) {
-    const int m = 8 * ty + i;
-    if (m >= Kp) continue;
+    const int ri = i < 4 ? 4 * ty + i : Kh + 4 * ty + i - 4;
 #pragma unroll
     for (int j = 0; j < 8; ++j) {
-      const int n = 8 * tx + j;
-      if (n < Kp) out[(int64_t)m * Kp + n] = acc[i][j];
+      const int cj = j < 4 ? 4 * tx + j : Kh + 4 * tx + j - 4;
+      const float v = acc[i][j] + xs[(i * 8 + j) * kTriStride + u];
+      if (ri < Kp && cj < Kp) out[(int64_t)min(ri, cj) * Kp + max(ri, cj)] = v;
     }
+    // One tile row at a time: keeps the compiler from hoisting all 64
+    // shared-memory reads above the stores (register spills).
+    asm volatile("" ::: "memory");
   }
 }
 
@@ -587,9 +615,8 @@ cudaError_t gram_setup(GramWork& g, int N, int Kp) {
   g.N = N;
   g.Kp = Kp;
   if (Kp >= kGramFullMinKp && Kp <= kGramFullMaxKp) {
-    // gram_full_kernel: one CTA per SM.
-    int chunk = (N + 147) / 148;
-    chunk = std::max(GB, (chunk + GB - 1) / GB * GB);
+    // gram_tri_kernel: one CTA per SM (chunks of at least GR rows).
+    const int chunk = std::max(GR, (N + 147) / 148);
     g.chunk = chunk;
     g.n_chunks = (N + chunk - 1) / chunk;
     return cudaMalloc(&g.d_part, sizeof(float) * (size_t)g.n_chunks * Kp * Kp);
@@ -685,9 +712,13 @@ void gram_free(GramWork& g) {
 cudaError_t gram_run(const GramWork& g, const float* X, float* S, int K, cudaStream_t s) {
   if (g.Kp >= kGramFullMinKp && g.Kp <= kGramFullMaxKp) {
     const int Kp8 = (g.Kp + 7) / 8 * 8;
-    const int threads = (Kp8 / 8) * (Kp8 / 8);
-    const size_t smem = sizeof(float) * 2 * GB * Kp8;
-    gram_full_kernel<<<g.n_chunks, threads, smem, s>>>(X, g.N, g.Kp, Kp8, g.chunk, g.d_part);
+    const int threads = 2 * gram_tri_tiles(Kp8);
+    const size_t smem = sizeof(float) * gram_tri_smem_floats(Kp8);
+    static const cudaError_t attr = cudaFuncSetAttribute(
+        gram_tri_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        (int)(sizeof(float) * gram_tri_smem_floats((kGramFullMaxKp + 7) / 8 * 8)));
+    if (attr != cudaSuccess) return attr;
+    gram_tri_kernel<<<g.n_chunks, threads, smem, s>>>(X, g.N, g.Kp, Kp8, g.chunk, g.d_part);
     cudaError_t err = cudaGetLastError();
     if (err != cudaSuccess) return err;
     return gram_reduce(g.d_part, g.n_chunks, g.Kp, K, S, s);
