@@ -35,6 +35,10 @@ struct SpmmPlan {
   int4* d_items = nullptr;
   int4* d_combine = nullptr;  // {row, first_slot, n_slots, 0}
   float* d_partial = nullptr; // n_slots x Kp
+  // Column indices carry a tag in bit 31 (set: a frequently gathered row of
+  // X, kept in L1 with evict_last; clear: streamed past L1).  Only for index
+  // arrays the library builds itself (CSR of A^T).
+  bool tagged = false;
 };
 
 // Builds the plan from host CSR row pointers.  seg = max nnz per item.

@@ -18,6 +18,21 @@
 namespace plnmf {
 namespace {
 
+// Gathers of X rows: plain read-only loads, or (tagged plans) rows marked
+// hot kept in L1 with high priority and the others not allocated in L1.
+template <bool TAG>
+__device__ __forceinline__ float4 gather(const float4* p, bool hot) {
+  if (!TAG) return __ldg(p);
+  float4 v;
+  asm(
+      "{\n\t.reg .pred h;\n\tsetp.ne.u32 h, %5, 0;\n\t"
+      "@h ld.global.nc.L1::evict_last.v4.f32 {%0, %1, %2, %3}, [%4];\n\t"
+      "@!h ld.global.nc.L1::no_allocate.v4.f32 {%0, %1, %2, %3}, [%4];\n\t}"
+      : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+      : "l"(p), "r"((unsigned)hot));
+  return v;
+}
+
 __device__ __forceinline__ void fma4(float4& acc, float a, const float4& x) {
   acc.x = fmaf(a, x.x, acc.x);
   acc.y = fmaf(a, x.y, acc.y);
@@ -30,8 +45,17 @@ __device__ __forceinline__ void fma4(float4& acc, float a, const float4& x) {
 // lanes owns C float4 chunks of the output row (L * C * 4 >= Kp), so one step
 // gathers G rows of X at once with 16-byte loads (two steps in flight).  At
 // the end the G group sums are added with shuffles in a fixed tree order.
-template <int L, int C>
-__global__ void __launch_bounds__(256) spmm_items_kernel(const int4* __restrict__ items, int n_items,
+// Minimum resident CTAs per SM the compiler plans registers for (it bounds
+// the registers and so how many gathers a thread keeps in flight), measured
+// on the text-like matrix at K = 80 / 160 / 240 / 400: three CTAs up to
+// 5 chunks per lane (K <= 160: P 79 -> 53 us, R 82 -> 71 us at K = 160
+// against the default), two for wider rows of tagged plans (R at K = 240:
+// 96 us against 152 with three) and for 8 chunks untagged (P at K = 400:
+// 112 us against 128).
+constexpr int spmm_min_blocks(int C, bool tag) { return C <= 5 ? 3 : (tag || C >= 8 ? 2 : 3); }
+
+template <int L, int C, bool TAG>
+__global__ void __launch_bounds__(256, spmm_min_blocks(C, TAG)) spmm_items_kernel(const int4* __restrict__ items, int n_items,
                                                          const int* __restrict__ col_idx,
                                                          const float* __restrict__ val,
                                                          const float4* __restrict__ X, int Kp4,
@@ -50,7 +74,8 @@ __global__ void __launch_bounds__(256) spmm_items_kernel(const int4* __restrict_
 
   int e = it.y + g;
   for (; e + G < it.z; e += 2 * G) {               // two non-zeros per group in flight
-    const int c0 = __ldg(col_idx + e), c1 = __ldg(col_idx + e + G);
+    const int t0 = __ldg(col_idx + e), t1 = __ldg(col_idx + e + G);
+    const int c0 = TAG ? (t0 & 0x7fffffff) : t0, c1 = TAG ? (t1 & 0x7fffffff) : t1;
     const float a0 = __ldg(val + e), a1 = __ldg(val + e + G);
     const float4* x0 = X + (size_t)c0 * Kp4;
     const float4* x1 = X + (size_t)c1 * Kp4;
@@ -58,8 +83,8 @@ __global__ void __launch_bounds__(256) spmm_items_kernel(const int4* __restrict_
 #pragma unroll
     for (int q = 0; q < C; ++q) {
       const int k = sub + L * q;
-      v0[q] = k < Kp4 ? __ldg(x0 + k) : make_float4(0.f, 0.f, 0.f, 0.f);
-      v1[q] = k < Kp4 ? __ldg(x1 + k) : make_float4(0.f, 0.f, 0.f, 0.f);
+      v0[q] = k < Kp4 ? gather<TAG>(x0 + k, t0 < 0) : make_float4(0.f, 0.f, 0.f, 0.f);
+      v1[q] = k < Kp4 ? gather<TAG>(x1 + k, t1 < 0) : make_float4(0.f, 0.f, 0.f, 0.f);
     }
 #pragma unroll
     for (int q = 0; q < C; ++q) {
@@ -68,13 +93,14 @@ __global__ void __launch_bounds__(256) spmm_items_kernel(const int4* __restrict_
     }
   }
   if (e < it.z) {
-    const int c0 = __ldg(col_idx + e);
+    const int t0 = __ldg(col_idx + e);
+    const int c0 = TAG ? (t0 & 0x7fffffff) : t0;
     const float a0 = __ldg(val + e);
     const float4* x0 = X + (size_t)c0 * Kp4;
 #pragma unroll
     for (int q = 0; q < C; ++q) {
       const int k = sub + L * q;
-      if (k < Kp4) fma4(acc[q], a0, __ldg(x0 + k));
+      if (k < Kp4) fma4(acc[q], a0, gather<TAG>(x0 + k, t0 < 0));
     }
   }
   // Add the group sums: xor-shuffles over the group index bits.
@@ -121,9 +147,10 @@ cudaError_t launch_items(const SpmmPlan& p, const int* ci, const float* va, cons
   const int warps_per_block = 8;
   const int blocks = (p.n_items + warps_per_block - 1) / warps_per_block;
   if (blocks > 0) {
-    spmm_items_kernel<L, C><<<blocks, 32 * warps_per_block, 0, s>>>(
-        p.d_items, p.n_items, ci, va, reinterpret_cast<const float4*>(X), Kp4,
-        reinterpret_cast<float4*>(Y), reinterpret_cast<float4*>(p.d_partial));
+    auto kern = p.tagged ? spmm_items_kernel<L, C, true> : spmm_items_kernel<L, C, false>;
+    kern<<<blocks, 32 * warps_per_block, 0, s>>>(p.d_items, p.n_items, ci, va, reinterpret_cast<const float4*>(X),
+                                                 Kp4, reinterpret_cast<float4*>(Y),
+                                                 reinterpret_cast<float4*>(p.d_partial));
   }
   return cudaGetLastError();
 }
