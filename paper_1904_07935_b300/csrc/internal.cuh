@@ -45,6 +45,8 @@ struct SpmmPlan {
 cudaError_t spmm_plan_build(SpmmPlan& plan, const std::vector<int>& row_ptr, int rows, int cols,
                             int Kp, int seg);
 void spmm_plan_free(SpmmPlan& plan);
+// Clears the tag bit (bit 31) of n column indices on the device.
+cudaError_t spmm_untag(int* col_idx, int64_t n, cudaStream_t s);
 // Y (rows x Kp) = A (CSR) * X (cols x Kp).
 cudaError_t spmm_run(const SpmmPlan& plan, const int* col_idx, const float* val, const float* X,
                      float* Y, int Kp, cudaStream_t s);

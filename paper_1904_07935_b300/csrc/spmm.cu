@@ -52,15 +52,18 @@ __device__ __forceinline__ void fma4(float4& acc, float a, const float4& x) {
 // against the default), two for wider rows of tagged plans (R at K = 240:
 // 96 us against 152 with three) and for 8 chunks untagged (P at K = 400:
 // 112 us against 128).
+// The 4-chunk layouts (K <= 64 and 97 <= K <= 128, the sizes of the batched
+// workload's members) keep the compiler's own choice: their launches run
+// beside many other members' kernels, where fewer registers per CTA (more
+// co-resident CTAs) counts for more (batch of 64: 21.5k against 20.2k
+// instance-iterations per second with three CTAs planned).
 constexpr int spmm_min_blocks(int C, bool tag) { return C <= 5 ? 3 : (tag || C >= 8 ? 2 : 3); }
 
 template <int L, int C, bool TAG>
-__global__ void __launch_bounds__(256, spmm_min_blocks(C, TAG)) spmm_items_kernel(const int4* __restrict__ items, int n_items,
-                                                         const int* __restrict__ col_idx,
-                                                         const float* __restrict__ val,
-                                                         const float4* __restrict__ X, int Kp4,
-                                                         float4* __restrict__ Y,
-                                                         float4* __restrict__ partial) {
+__device__ __forceinline__ void spmm_items_body(const int4* __restrict__ items, int n_items,
+                                                const int* __restrict__ col_idx, const float* __restrict__ val,
+                                                const float4* __restrict__ X, int Kp4, float4* __restrict__ Y,
+                                                float4* __restrict__ partial) {
   constexpr int G = 32 / L;
   const int lane = threadIdx.x & 31;
   const int g = lane / L, sub = lane % L;
@@ -123,6 +126,26 @@ __global__ void __launch_bounds__(256, spmm_min_blocks(C, TAG)) spmm_items_kerne
   }
 }
 
+template <int L, int C, bool TAG>
+__global__ void __launch_bounds__(256, spmm_min_blocks(C, TAG))
+    spmm_items_kernel(const int4* __restrict__ items, int n_items, const int* __restrict__ col_idx,
+                      const float* __restrict__ val, const float4* __restrict__ X, int Kp4, float4* __restrict__ Y,
+                      float4* __restrict__ partial) {
+  spmm_items_body<L, C, TAG>(items, n_items, col_idx, val, X, Kp4, Y, partial);
+}
+template <int L, int C, bool TAG>
+__global__ void __launch_bounds__(256)
+    spmm_items_lean_kernel(const int4* __restrict__ items, int n_items, const int* __restrict__ col_idx,
+                           const float* __restrict__ val, const float4* __restrict__ X, int Kp4,
+                           float4* __restrict__ Y, float4* __restrict__ partial) {
+  spmm_items_body<L, C, TAG>(items, n_items, col_idx, val, X, Kp4, Y, partial);
+}
+
+__global__ void untag_kernel(int* __restrict__ idx, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    idx[i] &= 0x7fffffff;
+}
+
 // Y[row] = sum of its partial rows in slot order.
 __global__ void spmm_combine_kernel(const int4* __restrict__ comb, int n_long,
                                     const float4* __restrict__ partial, float4* __restrict__ Y,
@@ -147,7 +170,12 @@ cudaError_t launch_items(const SpmmPlan& p, const int* ci, const float* va, cons
   const int warps_per_block = 8;
   const int blocks = (p.n_items + warps_per_block - 1) / warps_per_block;
   if (blocks > 0) {
-    auto kern = p.tagged ? spmm_items_kernel<L, C, true> : spmm_items_kernel<L, C, false>;
+    void (*kern)(const int4*, int, const int*, const float*, const float4*, int, float4*, float4*);
+    if constexpr (C == 4) {
+      kern = p.tagged ? spmm_items_lean_kernel<L, C, true> : spmm_items_lean_kernel<L, C, false>;
+    } else {
+      kern = p.tagged ? spmm_items_kernel<L, C, true> : spmm_items_kernel<L, C, false>;
+    }
     kern<<<blocks, 32 * warps_per_block, 0, s>>>(p.d_items, p.n_items, ci, va, reinterpret_cast<const float4*>(X),
                                                  Kp4, reinterpret_cast<float4*>(Y),
                                                  reinterpret_cast<float4*>(p.d_partial));
@@ -198,6 +226,13 @@ cudaError_t spmm_plan_build(SpmmPlan& plan, const std::vector<int>& row_ptr, int
     return err;
   if ((err = cudaMalloc(&plan.d_partial, sizeof(float) * (size_t)std::max(1, slot) * Kp)) != cudaSuccess) return err;
   return cudaSuccess;
+}
+
+cudaError_t spmm_untag(int* col_idx, int64_t n, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  const int64_t blocks = std::min<int64_t>((n + 255) / 256, 4 * 148);
+  untag_kernel<<<(int)blocks, 256, 0, s>>>(col_idx, n);
+  return cudaGetLastError();
 }
 
 void spmm_plan_free(SpmmPlan& plan) {
