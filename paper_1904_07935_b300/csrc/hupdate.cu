@@ -116,9 +116,13 @@ constexpr int HROWS = 64;         // rows per CTA
 constexpr int HTHREADS = HROWS * HL;
 
 // R rows per lane group: each group of 4 lanes owns R rows (4 tile columns per
-// lane), so a 16-byte load of S's column block serves R rows.
+// lane), so a 16-byte load of S's column block serves R rows.  The grid
+// leaves few CTAs per SM (D / 32 R of them), so registers are not what limits
+// occupancy: planning for two CTAs per SM lets the compiler keep more loads
+// in flight (120 registers at R = 1 instead of 60; text-like K = 160:
+// 69.8 -> 66.1 us).
 template <int R>
-__global__ void __launch_bounds__(128) h_update_kernel(float* __restrict__ X, const float* __restrict__ B,
+__global__ void __launch_bounds__(128, 2) h_update_kernel(float* __restrict__ X, const float* __restrict__ B,
                                                        const float* __restrict__ G, int N, int K, int Kp, float eps,
                                                        int* status) {
   // Shared memory: two Gc buffers (Kr x HT each) = G[j][lo + c] for the
