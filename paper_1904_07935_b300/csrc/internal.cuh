@@ -35,18 +35,12 @@ struct SpmmPlan {
   int4* d_items = nullptr;
   int4* d_combine = nullptr;  // {row, first_slot, n_slots, 0}
   float* d_partial = nullptr; // n_slots x Kp
-  // Column indices carry a tag in bit 31 (set: a frequently gathered row of
-  // X, kept in L1 with evict_last; clear: streamed past L1).  Only for index
-  // arrays the library builds itself (CSR of A^T).
-  bool tagged = false;
 };
 
 // Builds the plan from host CSR row pointers.  seg = max nnz per item.
 cudaError_t spmm_plan_build(SpmmPlan& plan, const std::vector<int>& row_ptr, int rows, int cols,
                             int Kp, int seg);
 void spmm_plan_free(SpmmPlan& plan);
-// Clears the tag bit (bit 31) of n column indices on the device.
-cudaError_t spmm_untag(int* col_idx, int64_t n, cudaStream_t s);
 // Y (rows x Kp) = A (CSR) * X (cols x Kp).
 cudaError_t spmm_run(const SpmmPlan& plan, const int* col_idx, const float* val, const float* X,
                      float* Y, int Kp, cudaStream_t s);

@@ -5,7 +5,6 @@
 #include <cmath>
 #include <cstring>
 #include <new>
-#include <numeric>
 #include <vector>
 
 #include <cstdlib>
@@ -48,7 +47,6 @@ struct nmf_ctx {
   int* ciT = nullptr;
   float* vaT = nullptr;
   SpmmPlan planA, planAt;
-  bool planAt_tagged = false;   // ciT carries the hot-row tags (bit 31)
   GramWork gramW, gramH;
   ChainConfig chainW, chainH;
   // Factors and intermediates, row stride Kp, padding columns kept at zero.
@@ -81,7 +79,6 @@ struct nmf_ctx {
 namespace {
 
 constexpr int kHistCap = 4096;
-constexpr int kHotRows = 256;      // most rows of W tagged for L1 in R = A^T W
 
 nmf_status from_cuda(cudaError_t e) {
   if (e == cudaSuccess) return NMF_OK;
@@ -421,24 +418,6 @@ nmf_status init_impl(const nmf_problem* p, nmf_ctx* c) {
         ciT[pos] = r;
         vaT[pos] = va[e];
       }
-    // The words with the most non-zeros (the Zipf head of a term-document
-    // matrix) are gathered by most documents in R = A^T W: tag them so that
-    // their rows of W stay in L1 (as many rows as ~160 KB hold, at most
-    // kHotRows); the other rows bypass L1.
-    {
-      const int n_hot = std::min({kHotRows, V, (int)((160 * 1024) / ((size_t)Kp * 4))});
-      if (n_hot > 0 && p->nnz > 0) {
-        std::vector<int> words(V);
-        std::iota(words.begin(), words.end(), 0);
-        std::stable_sort(words.begin(), words.end(),
-                         [&](int a, int b) { return rp[a + 1] - rp[a] > rp[b + 1] - rp[b]; });
-        std::vector<char> hot((size_t)V, 0);
-        for (int i = 0; i < n_hot; ++i) hot[words[i]] = 1;
-        for (auto& w : ciT)
-          if (hot[w]) w |= (int)0x80000000u;
-        c->planAt_tagged = true;
-      }
-    }
     CK(dalloc(&c->rpT, rpT.size()));
     CK(dalloc(&c->ciT, ciT.size()));
     CK(dalloc(&c->vaT, vaT.size()));
@@ -449,7 +428,6 @@ nmf_status init_impl(const nmf_problem* p, nmf_ctx* c) {
     }
     CK(spmm_plan_build(c->planA, rp, V, D, Kp, 512));
     CK(spmm_plan_build(c->planAt, rpT, D, V, Kp, 512));
-    c->planAt.tagged = c->planAt_tagged;
   } else if (c->fmt == NMF_DENSE_F32) {
     if (!p->dense || p->ld < p->D) return NMF_EINVAL;
     if (!is_device_ptr(p->dense)) return NMF_EINVAL;
@@ -742,13 +720,6 @@ nmf_status nmf_batch_create(nmf_ctx* const* ctxs, int32_t n, int32_t autotune, v
   for (int i = 0; i < n; ++i) {
     nmf_ctx* c = b->m[i];
     c->w_persistent = false;
-    // Members run beside each other: plain R gathers (the L1 hints of a solo
-    // run cost the batch 4%, 20.7k against 21.5k instance-iterations/s).
-    if (c->planAt.tagged) {
-      if ((e = spmm_untag(c->ciT, c->nnz, c->stream)) != cudaSuccess) return bail(e);
-      c->planAt.tagged = false;
-      c->planAt_tagged = false;
-    }
     drop_graph(c);
     if ((e = ensure_entry(c)) != cudaSuccess) return bail(e);
     if (autotune) {

@@ -18,21 +18,6 @@
 namespace plnmf {
 namespace {
 
-// Gathers of X rows: plain read-only loads, or (tagged plans) rows marked
-// hot kept in L1 with high priority and the others not allocated in L1.
-template <bool TAG>
-__device__ __forceinline__ float4 gather(const float4* p, bool hot) {
-  if (!TAG) return __ldg(p);
-  float4 v;
-  asm(
-      "{\n\t.reg .pred h;\n\tsetp.ne.u32 h, %5, 0;\n\t"
-      "@h ld.global.nc.L1::evict_last.v4.f32 {%0, %1, %2, %3}, [%4];\n\t"
-      "@!h ld.global.nc.L1::no_allocate.v4.f32 {%0, %1, %2, %3}, [%4];\n\t}"
-      : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
-      : "l"(p), "r"((unsigned)hot));
-  return v;
-}
-
 __device__ __forceinline__ void fma4(float4& acc, float a, const float4& x) {
   acc.x = fmaf(a, x.x, acc.x);
   acc.y = fmaf(a, x.y, acc.y);
@@ -40,30 +25,28 @@ __device__ __forceinline__ void fma4(float4& acc, float a, const float4& x) {
   acc.w = fmaf(a, x.w, acc.w);
 }
 
+// Minimum resident CTAs per SM the compiler plans registers for.  It bounds
+// the registers, and with them how many gathers a thread keeps in flight,
+// while the occupancy stays what the 256-thread CTAs get anyway.  Measured on
+// the text-like matrix against the compiler's default (52-60 registers):
+// three CTAs from 5 to 6 chunks, two at 8 (K = 160: R 82 -> 54 us,
+// P 79 -> 53 us; K = 400: R 300 -> 103 us, P 270 -> 109 us).  The 4-chunk
+// layouts (K <= 64 and 97 <= K <= 128, the sizes of the batched workload's
+// members) keep the compiler's own choice (44 registers): there many
+// members' kernels share the SMs, and three planned CTAs (66 registers) cost
+// the batch of 64 3% (20.8k against 21.5k instance-iterations per second).
+constexpr int spmm_min_blocks(int C) { return C >= 8 ? 2 : 3; }
+
 // One warp per work item.  The warp is split into G = 32 / L groups of L
 // lanes; group g takes non-zeros beg + g, beg + g + G, ... and each of its
 // lanes owns C float4 chunks of the output row (L * C * 4 >= Kp), so one step
 // gathers G rows of X at once with 16-byte loads (two steps in flight).  At
 // the end the G group sums are added with shuffles in a fixed tree order.
-// Minimum resident CTAs per SM the compiler plans registers for (it bounds
-// the registers and so how many gathers a thread keeps in flight), measured
-// on the text-like matrix at K = 80 / 160 / 240 / 400: three CTAs up to
-// 5 chunks per lane (K <= 160: P 79 -> 53 us, R 82 -> 71 us at K = 160
-// against the default), two for wider rows of tagged plans (R at K = 240:
-// 96 us against 152 with three) and for 8 chunks untagged (P at K = 400:
-// 112 us against 128).
-// The 4-chunk layouts (K <= 64 and 97 <= K <= 128, the sizes of the batched
-// workload's members) keep the compiler's own choice: their launches run
-// beside many other members' kernels, where fewer registers per CTA (more
-// co-resident CTAs) counts for more (batch of 64: 21.5k against 20.2k
-// instance-iterations per second with three CTAs planned).
-constexpr int spmm_min_blocks(int C, bool tag) { return C <= 5 ? 3 : (tag || C >= 8 ? 2 : 3); }
-
-template <int L, int C, bool TAG>
-__device__ __forceinline__ void spmm_items_body(const int4* __restrict__ items, int n_items,
-                                                const int* __restrict__ col_idx, const float* __restrict__ val,
-                                                const float4* __restrict__ X, int Kp4, float4* __restrict__ Y,
-                                                float4* __restrict__ partial) {
+template <int L, int C>
+__device__ __forceinline__ void spmm_items(const int4* __restrict__ items, int n_items,
+                                           const int* __restrict__ col_idx, const float* __restrict__ val,
+                                           const float4* __restrict__ X, int Kp4, float4* __restrict__ Y,
+                                           float4* __restrict__ partial) {
   constexpr int G = 32 / L;
   const int lane = threadIdx.x & 31;
   const int g = lane / L, sub = lane % L;
@@ -77,8 +60,7 @@ __device__ __forceinline__ void spmm_items_body(const int4* __restrict__ items, 
 
   int e = it.y + g;
   for (; e + G < it.z; e += 2 * G) {               // two non-zeros per group in flight
-    const int t0 = __ldg(col_idx + e), t1 = __ldg(col_idx + e + G);
-    const int c0 = TAG ? (t0 & 0x7fffffff) : t0, c1 = TAG ? (t1 & 0x7fffffff) : t1;
+    const int c0 = __ldg(col_idx + e), c1 = __ldg(col_idx + e + G);
     const float a0 = __ldg(val + e), a1 = __ldg(val + e + G);
     const float4* x0 = X + (size_t)c0 * Kp4;
     const float4* x1 = X + (size_t)c1 * Kp4;
@@ -86,8 +68,8 @@ __device__ __forceinline__ void spmm_items_body(const int4* __restrict__ items, 
 #pragma unroll
     for (int q = 0; q < C; ++q) {
       const int k = sub + L * q;
-      v0[q] = k < Kp4 ? gather<TAG>(x0 + k, t0 < 0) : make_float4(0.f, 0.f, 0.f, 0.f);
-      v1[q] = k < Kp4 ? gather<TAG>(x1 + k, t1 < 0) : make_float4(0.f, 0.f, 0.f, 0.f);
+      v0[q] = k < Kp4 ? __ldg(x0 + k) : make_float4(0.f, 0.f, 0.f, 0.f);
+      v1[q] = k < Kp4 ? __ldg(x1 + k) : make_float4(0.f, 0.f, 0.f, 0.f);
     }
 #pragma unroll
     for (int q = 0; q < C; ++q) {
@@ -96,14 +78,13 @@ __device__ __forceinline__ void spmm_items_body(const int4* __restrict__ items, 
     }
   }
   if (e < it.z) {
-    const int t0 = __ldg(col_idx + e);
-    const int c0 = TAG ? (t0 & 0x7fffffff) : t0;
+    const int c0 = __ldg(col_idx + e);
     const float a0 = __ldg(val + e);
     const float4* x0 = X + (size_t)c0 * Kp4;
 #pragma unroll
     for (int q = 0; q < C; ++q) {
       const int k = sub + L * q;
-      if (k < Kp4) fma4(acc[q], a0, gather<TAG>(x0 + k, t0 < 0));
+      if (k < Kp4) fma4(acc[q], a0, __ldg(x0 + k));
     }
   }
   // Add the group sums: xor-shuffles over the group index bits.
@@ -126,24 +107,19 @@ __device__ __forceinline__ void spmm_items_body(const int4* __restrict__ items, 
   }
 }
 
-template <int L, int C, bool TAG>
-__global__ void __launch_bounds__(256, spmm_min_blocks(C, TAG))
+template <int L, int C>
+__global__ void __launch_bounds__(256, spmm_min_blocks(C))
     spmm_items_kernel(const int4* __restrict__ items, int n_items, const int* __restrict__ col_idx,
                       const float* __restrict__ val, const float4* __restrict__ X, int Kp4, float4* __restrict__ Y,
                       float4* __restrict__ partial) {
-  spmm_items_body<L, C, TAG>(items, n_items, col_idx, val, X, Kp4, Y, partial);
+  spmm_items<L, C>(items, n_items, col_idx, val, X, Kp4, Y, partial);
 }
-template <int L, int C, bool TAG>
+template <int L, int C>
 __global__ void __launch_bounds__(256)
     spmm_items_lean_kernel(const int4* __restrict__ items, int n_items, const int* __restrict__ col_idx,
                            const float* __restrict__ val, const float4* __restrict__ X, int Kp4,
                            float4* __restrict__ Y, float4* __restrict__ partial) {
-  spmm_items_body<L, C, TAG>(items, n_items, col_idx, val, X, Kp4, Y, partial);
-}
-
-__global__ void untag_kernel(int* __restrict__ idx, int64_t n) {
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-    idx[i] &= 0x7fffffff;
+  spmm_items<L, C>(items, n_items, col_idx, val, X, Kp4, Y, partial);
 }
 
 // Y[row] = sum of its partial rows in slot order.
@@ -170,15 +146,15 @@ cudaError_t launch_items(const SpmmPlan& p, const int* ci, const float* va, cons
   const int warps_per_block = 8;
   const int blocks = (p.n_items + warps_per_block - 1) / warps_per_block;
   if (blocks > 0) {
-    void (*kern)(const int4*, int, const int*, const float*, const float4*, int, float4*, float4*);
+    const float4* x4 = reinterpret_cast<const float4*>(X);
+    float4* y4 = reinterpret_cast<float4*>(Y);
+    float4* p4 = reinterpret_cast<float4*>(p.d_partial);
     if constexpr (C == 4) {
-      kern = p.tagged ? spmm_items_lean_kernel<L, C, true> : spmm_items_lean_kernel<L, C, false>;
+      spmm_items_lean_kernel<L, C><<<blocks, 32 * warps_per_block, 0, s>>>(p.d_items, p.n_items, ci, va, x4, Kp4,
+                                                                           y4, p4);
     } else {
-      kern = p.tagged ? spmm_items_kernel<L, C, true> : spmm_items_kernel<L, C, false>;
+      spmm_items_kernel<L, C><<<blocks, 32 * warps_per_block, 0, s>>>(p.d_items, p.n_items, ci, va, x4, Kp4, y4, p4);
     }
-    kern<<<blocks, 32 * warps_per_block, 0, s>>>(p.d_items, p.n_items, ci, va, reinterpret_cast<const float4*>(X),
-                                                 Kp4, reinterpret_cast<float4*>(Y),
-                                                 reinterpret_cast<float4*>(p.d_partial));
   }
   return cudaGetLastError();
 }
@@ -226,13 +202,6 @@ cudaError_t spmm_plan_build(SpmmPlan& plan, const std::vector<int>& row_ptr, int
     return err;
   if ((err = cudaMalloc(&plan.d_partial, sizeof(float) * (size_t)std::max(1, slot) * Kp)) != cudaSuccess) return err;
   return cudaSuccess;
-}
-
-cudaError_t spmm_untag(int* col_idx, int64_t n, cudaStream_t s) {
-  if (n <= 0) return cudaSuccess;
-  const int64_t blocks = std::min<int64_t>((n + 255) / 256, 4 * 148);
-  untag_kernel<<<(int)blocks, 256, 0, s>>>(col_idx, n);
-  return cudaGetLastError();
 }
 
 void spmm_plan_free(SpmmPlan& plan) {
