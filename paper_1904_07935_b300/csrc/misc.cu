@@ -99,15 +99,28 @@ struct Dot2 {
 };
 
 // partial[b] = <a, b> over this block's grid-stride share of [0, n1), and
-// partial[nb + b] the same for <c, d> over [0, n2).
+// partial[nb + b] the same for <c, d> over [0, n2); n1 and n2 are multiples
+// of 4 and the arrays 16-byte aligned (16-byte loads, two in flight).
 __global__ void dot_partial_kernel(const float* __restrict__ a, const float* __restrict__ b, long long n1,
                                    const float* __restrict__ c, const float* __restrict__ d, long long n2,
                                    double* __restrict__ partial) {
   Dot2 s1, s2;
   const long long step = (long long)gridDim.x * blockDim.x;
   const long long i0 = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  for (long long i = i0; i < n1; i += step) s1.add(a[i], b[i]);
-  for (long long i = i0; i < n2; i += step) s2.add(c[i], d[i]);
+  auto run = [&](Dot2& acc, const float* x, const float* y, long long n) {
+    const float4* x4 = reinterpret_cast<const float4*>(x);
+    const float4* y4 = reinterpret_cast<const float4*>(y);
+#pragma unroll 2
+    for (long long i = i0; i < n / 4; i += step) {
+      const float4 u = __ldg(x4 + i), v = __ldg(y4 + i);
+      acc.add(u.x, v.x);
+      acc.add(u.y, v.y);
+      acc.add(u.z, v.z);
+      acc.add(u.w, v.w);
+    }
+  };
+  run(s1, a, b, n1);
+  run(s2, c, d, n2);
   const double t1 = block_sum_d<kObjThreads>(s1.value());
   const double t2 = block_sum_d<kObjThreads>(s2.value());
   if (threadIdx.x == 0) {
@@ -212,6 +225,7 @@ cudaError_t normalize_columns(float* X, int N, int K, int ld, cudaStream_t s) {
 cudaError_t objective_run(const float* W, const float* P, int V, int Kp, const float* S, const float* Q,
                           double normA2, double* partial, int n_partial, double* out, unsigned* d_counter,
                           int hist_cap, cudaStream_t s) {
+  if (Kp & 3) return cudaErrorInvalidValue;
   dot_partial_kernel<<<n_partial, kObjThreads, 0, s>>>(W, P, (long long)V * Kp, S, Q, (long long)Kp * Kp,
                                                       partial);
   cudaError_t e = cudaGetLastError();
