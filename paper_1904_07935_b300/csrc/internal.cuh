@@ -222,6 +222,13 @@ cudaError_t convert_bf16(const float* src, int64_t rows, int64_t cols, int64_t l
 cudaError_t objective_run(const float* W, const float* P, int V, int Kp, const float* S,
                           const float* Q, double normA2, double* partial, int n_partial,
                           double* out, unsigned* d_counter, int hist_cap, cudaStream_t s);
+// The two halves of objective_run, for callers that overlap <W, P> (needs the
+// new W and P only) with the Gram S: partials of <W, P>, then <S, Q> and the
+// history entry.
+cudaError_t objective_wp(const float* W, const float* P, int V, int Kp, double* partial, int n_partial,
+                         cudaStream_t s);
+cudaError_t objective_finish(int Kp, const float* S, const float* Q, double normA2, const double* partial,
+                             int n_partial, double* out, unsigned* d_counter, int hist_cap, cudaStream_t s);
 constexpr int kSumsqBlocks = 592;
 cudaError_t sumsq_dense_f64(const float* A, int64_t rows, int64_t cols, int64_t ld,
                             double* d_out, int* d_bad, cudaStream_t s);

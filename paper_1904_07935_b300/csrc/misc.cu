@@ -98,51 +98,50 @@ struct Dot2 {
   __device__ __forceinline__ double value() const { return (double)p + (double)c; }
 };
 
-// partial[b] = <a, b> over this block's grid-stride share of [0, n1), and
-// partial[nb + b] the same for <c, d> over [0, n2); n1 and n2 are multiples
-// of 4 and the arrays 16-byte aligned (16-byte loads, two in flight).
-__global__ void dot_partial_kernel(const float* __restrict__ a, const float* __restrict__ b, long long n1,
-                                   const float* __restrict__ c, const float* __restrict__ d, long long n2,
+// partial[b] = <a, b> over this block's grid-stride share of [0, n); n is a
+// multiple of 4 and the arrays 16-byte aligned (16-byte loads, two in flight).
+__global__ void dot_partial_kernel(const float* __restrict__ a, const float* __restrict__ b, long long n,
                                    double* __restrict__ partial) {
-  Dot2 s1, s2;
+  Dot2 acc;
   const long long step = (long long)gridDim.x * blockDim.x;
   const long long i0 = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  auto run = [&](Dot2& acc, const float* x, const float* y, long long n) {
-    const float4* x4 = reinterpret_cast<const float4*>(x);
-    const float4* y4 = reinterpret_cast<const float4*>(y);
+  const float4* x4 = reinterpret_cast<const float4*>(a);
+  const float4* y4 = reinterpret_cast<const float4*>(b);
 #pragma unroll 2
-    for (long long i = i0; i < n / 4; i += step) {
-      const float4 u = __ldg(x4 + i), v = __ldg(y4 + i);
-      acc.add(u.x, v.x);
-      acc.add(u.y, v.y);
-      acc.add(u.z, v.z);
-      acc.add(u.w, v.w);
-    }
-  };
-  run(s1, a, b, n1);
-  run(s2, c, d, n2);
-  const double t1 = block_sum_d<kObjThreads>(s1.value());
-  const double t2 = block_sum_d<kObjThreads>(s2.value());
-  if (threadIdx.x == 0) {
-    partial[blockIdx.x] = t1;
-    partial[gridDim.x + blockIdx.x] = t2;
+  for (long long i = i0; i < n / 4; i += step) {
+    const float4 u = __ldg(x4 + i), v = __ldg(y4 + i);
+    acc.add(u.x, v.x);
+    acc.add(u.y, v.y);
+    acc.add(u.z, v.z);
+    acc.add(u.w, v.w);
   }
+  const double t = block_sum_d<kObjThreads>(acc.value());
+  if (threadIdx.x == 0) partial[blockIdx.x] = t;
 }
 
-// frob2 = normA2 - 2 sum(partial[0..n)) + sum(partial[n..2n)); appended to
-// the history ring.
-__global__ void objective_final_kernel(const double* __restrict__ partial, int n_partial, double normA2,
+// frob2 = normA2 - 2 <W, P> + <S, Q>: <W, P> from the n_partial partials of
+// dot_partial_kernel, <S, Q> (Kp x Kp, a multiple of 4 entries) summed here by
+// the one block (Dot2 per thread); appended to the history ring.
+__global__ void objective_final_kernel(const double* __restrict__ partial, int n_partial, const float* __restrict__ S,
+                                       const float* __restrict__ Q, long long n2, double normA2,
                                        double* __restrict__ hist, unsigned* counter, int hist_cap) {
-  double wp = 0.0, sq = 0.0;
-  for (int i = threadIdx.x; i < n_partial; i += blockDim.x) {
-    wp += partial[i];
-    sq += partial[n_partial + i];
+  double wp = 0.0;
+  for (int i = threadIdx.x; i < n_partial; i += blockDim.x) wp += partial[i];
+  Dot2 sq;
+  const float4* s4 = reinterpret_cast<const float4*>(S);
+  const float4* q4 = reinterpret_cast<const float4*>(Q);
+  for (long long i = threadIdx.x; i < n2 / 4; i += blockDim.x) {
+    const float4 u = __ldg(s4 + i), v = __ldg(q4 + i);
+    sq.add(u.x, v.x);
+    sq.add(u.y, v.y);
+    sq.add(u.z, v.z);
+    sq.add(u.w, v.w);
   }
   wp = block_sum_d<kObjThreads>(wp);
-  sq = block_sum_d<kObjThreads>(sq);
+  const double sqv = block_sum_d<kObjThreads>(sq.value());
   if (threadIdx.x == 0) {
     const unsigned it = *counter;
-    hist[it % hist_cap] = normA2 - 2.0 * wp + sq;
+    hist[it % hist_cap] = normA2 - 2.0 * wp + sqv;
     *counter = it + 1;
   }
 }
@@ -222,16 +221,27 @@ cudaError_t normalize_columns(float* X, int N, int K, int ld, cudaStream_t s) {
   return cudaGetLastError();
 }
 
+cudaError_t objective_wp(const float* W, const float* P, int V, int Kp, double* partial, int n_partial,
+                         cudaStream_t s) {
+  if (Kp & 3) return cudaErrorInvalidValue;
+  dot_partial_kernel<<<n_partial, kObjThreads, 0, s>>>(W, P, (long long)V * Kp, partial);
+  return cudaGetLastError();
+}
+
+cudaError_t objective_finish(int Kp, const float* S, const float* Q, double normA2, const double* partial,
+                             int n_partial, double* out, unsigned* d_counter, int hist_cap, cudaStream_t s) {
+  if (Kp & 3) return cudaErrorInvalidValue;
+  objective_final_kernel<<<1, kObjThreads, 0, s>>>(partial, n_partial, S, Q, (long long)Kp * Kp, normA2, out,
+                                                   d_counter, hist_cap);
+  return cudaGetLastError();
+}
+
 cudaError_t objective_run(const float* W, const float* P, int V, int Kp, const float* S, const float* Q,
                           double normA2, double* partial, int n_partial, double* out, unsigned* d_counter,
                           int hist_cap, cudaStream_t s) {
-  if (Kp & 3) return cudaErrorInvalidValue;
-  dot_partial_kernel<<<n_partial, kObjThreads, 0, s>>>(W, P, (long long)V * Kp, S, Q, (long long)Kp * Kp,
-                                                      partial);
-  cudaError_t e = cudaGetLastError();
+  cudaError_t e = objective_wp(W, P, V, Kp, partial, n_partial, s);
   if (e != cudaSuccess) return e;
-  objective_final_kernel<<<1, kObjThreads, 0, s>>>(partial, n_partial, normA2, out, d_counter, hist_cap);
-  return cudaGetLastError();
+  return objective_finish(Kp, S, Q, normA2, partial, n_partial, out, d_counter, hist_cap, s);
 }
 
 // d_out must hold kSumsqBlocks doubles; the host adds them in order.

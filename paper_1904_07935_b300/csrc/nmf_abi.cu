@@ -32,6 +32,7 @@ struct nmf_ctx {
   cudaStream_t stream = nullptr;
   bool own_stream = false;
   cudaStream_t side = nullptr;          // second stream for the W tile bases
+  cudaStream_t side2 = nullptr;         // third stream: <W, P> of the objective beside S and R
   bool w_persistent = false;            // whole W update as one cooperative launch
   WPersistConfig wp;
   int* d_sync = nullptr;
@@ -62,7 +63,7 @@ struct nmf_ctx {
   double normA2 = 0.0;
   bool s_valid = false;       // S == W^T W for the current W
   bool r_valid = false;       // R == A^T W for the current W
-  cudaEvent_t evx[4] = {};    // fork / join events of the overlapped step pairs
+  cudaEvent_t evx[5] = {};    // fork / join events of the overlapped steps
   long long iters_run = 0;
   int launches_per_iter = 0;
   int launch_count = 0;       // kernels issued by the last enqueue sequence
@@ -256,7 +257,9 @@ cudaError_t enq_objective(nmf_ctx* c) {
 // the end of the previous iteration, right after the W update, where it runs
 // beside S; likewise Q beside P.  Each pair is independent (same inputs,
 // disjoint outputs and work buffers), so the graph has two branches there:
-//   H update -> { P | Q } -> W update -> { S -> objective | R }.
+//   H update -> { P | Q } -> W update -> { S -> objective | R | <W, P> }
+// (the objective's <W, P> part needs only the new W and P, so it runs on a
+// third branch and the objective's last step only adds <S, Q>).
 cudaError_t enq_iteration(nmf_ctx* c) {
   cudaError_t e;
   cudaStream_t m = c->stream, b = c->side;
@@ -284,8 +287,16 @@ cudaError_t enq_iteration(nmf_ctx* c) {
   if ((e = cudaStreamWaitEvent(b, c->evx[2], 0)) != cudaSuccess) return e;
   if ((e = enq_product_R(c, b, shared_op)) != cudaSuccess) return e;
   if ((e = cudaEventRecord(c->evx[3], b)) != cudaSuccess) return e;
+  if ((e = cudaStreamWaitEvent(c->side2, c->evx[2], 0)) != cudaSuccess) return e;
+  c->launch_count += 2;
+  if ((e = objective_wp(c->W, c->P, c->V, c->Kp, c->obj_partial, c->n_obj_partial, c->side2)) != cudaSuccess)
+    return e;
+  if ((e = cudaEventRecord(c->evx[4], c->side2)) != cudaSuccess) return e;
   if ((e = enq_gram(c, c->gramW, c->W, c->S, nullptr, shared_op)) != cudaSuccess) return e;
-  if ((e = enq_objective(c)) != cudaSuccess) return e;
+  if ((e = cudaStreamWaitEvent(m, c->evx[4], 0)) != cudaSuccess) return e;
+  if ((e = objective_finish(c->Kp, c->S, c->Q, c->normA2, c->obj_partial, c->n_obj_partial, c->hist, c->d_counter,
+                            kHistCap, m)) != cudaSuccess)
+    return e;
   return cudaStreamWaitEvent(m, c->evx[3], 0);
 }
 
@@ -382,6 +393,7 @@ nmf_status init_impl(const nmf_problem* p, nmf_ctx* c) {
   c->T = T;
 
   CK(cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking));
+  CK(cudaStreamCreateWithFlags(&c->side2, cudaStreamNonBlocking));
   {
     const int nt = (c->K + T - 1) / T;
     c->ev.assign(1 + 2 * nt, nullptr);
@@ -569,6 +581,10 @@ void free_ctx(nmf_ctx* c) {
   if (c->side) {
     cudaStreamSynchronize(c->side);
     cudaStreamDestroy(c->side);
+  }
+  if (c->side2) {
+    cudaStreamSynchronize(c->side2);
+    cudaStreamDestroy(c->side2);
   }
   for (auto e : c->ev)
     if (e) cudaEventDestroy(e);
