@@ -74,6 +74,7 @@ __global__ void normalize_columns_kernel(float* X, int N, int K, int ld) {
 }
 
 constexpr int kObjThreads = 256;
+constexpr int kSqBlocks = 64;          // blocks of the <S, Q> partials (partial[n_wp .. n_wp + 64))
 
 // Error-free transformations (Knuth TwoSum; TwoProduct through fma) and the
 // compensated dot product Dot2 of Ogita, Rump & Oishi, "Accurate sum and dot
@@ -119,29 +120,19 @@ __global__ void dot_partial_kernel(const float* __restrict__ a, const float* __r
   if (threadIdx.x == 0) partial[blockIdx.x] = t;
 }
 
-// frob2 = normA2 - 2 <W, P> + <S, Q>: <W, P> from the n_partial partials of
-// dot_partial_kernel, <S, Q> (Kp x Kp, a multiple of 4 entries) summed here by
-// the one block (Dot2 per thread); appended to the history ring.
-__global__ void objective_final_kernel(const double* __restrict__ partial, int n_partial, const float* __restrict__ S,
-                                       const float* __restrict__ Q, long long n2, double normA2,
+// frob2 = normA2 - 2 sum(partial[0..n_wp)) + sum(partial[n_wp..n_wp + n_sq))
+// (<W, P> and <S, Q> partials of dot_partial_kernel, added in a fixed order);
+// appended to the history ring.
+__global__ void objective_final_kernel(const double* __restrict__ partial, int n_wp, int n_sq, double normA2,
                                        double* __restrict__ hist, unsigned* counter, int hist_cap) {
-  double wp = 0.0;
-  for (int i = threadIdx.x; i < n_partial; i += blockDim.x) wp += partial[i];
-  Dot2 sq;
-  const float4* s4 = reinterpret_cast<const float4*>(S);
-  const float4* q4 = reinterpret_cast<const float4*>(Q);
-  for (long long i = threadIdx.x; i < n2 / 4; i += blockDim.x) {
-    const float4 u = __ldg(s4 + i), v = __ldg(q4 + i);
-    sq.add(u.x, v.x);
-    sq.add(u.y, v.y);
-    sq.add(u.z, v.z);
-    sq.add(u.w, v.w);
-  }
+  double wp = 0.0, sq = 0.0;
+  for (int i = threadIdx.x; i < n_wp; i += blockDim.x) wp += partial[i];
+  for (int i = threadIdx.x; i < n_sq; i += blockDim.x) sq += partial[n_wp + i];
   wp = block_sum_d<kObjThreads>(wp);
-  const double sqv = block_sum_d<kObjThreads>(sq.value());
+  sq = block_sum_d<kObjThreads>(sq);
   if (threadIdx.x == 0) {
     const unsigned it = *counter;
-    hist[it % hist_cap] = normA2 - 2.0 * wp + sqv;
+    hist[it % hist_cap] = normA2 - 2.0 * wp + sq;
     *counter = it + 1;
   }
 }
@@ -228,11 +219,13 @@ cudaError_t objective_wp(const float* W, const float* P, int V, int Kp, double* 
   return cudaGetLastError();
 }
 
-cudaError_t objective_finish(int Kp, const float* S, const float* Q, double normA2, const double* partial,
+cudaError_t objective_finish(int Kp, const float* S, const float* Q, double normA2, double* partial,
                              int n_partial, double* out, unsigned* d_counter, int hist_cap, cudaStream_t s) {
   if (Kp & 3) return cudaErrorInvalidValue;
-  objective_final_kernel<<<1, kObjThreads, 0, s>>>(partial, n_partial, S, Q, (long long)Kp * Kp, normA2, out,
-                                                   d_counter, hist_cap);
+  dot_partial_kernel<<<kSqBlocks, kObjThreads, 0, s>>>(S, Q, (long long)Kp * Kp, partial + n_partial);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  objective_final_kernel<<<1, kObjThreads, 0, s>>>(partial, n_partial, kSqBlocks, normA2, out, d_counter, hist_cap);
   return cudaGetLastError();
 }
 

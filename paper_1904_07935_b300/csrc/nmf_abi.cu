@@ -247,7 +247,7 @@ cudaError_t enq_update(nmf_ctx* c, float* X, const float* G, const float* B, int
 }
 
 cudaError_t enq_objective(nmf_ctx* c) {
-  c->launch_count += 2;
+  c->launch_count += 3;
   return objective_run(c->W, c->P, c->V, c->Kp, c->S, c->Q, c->normA2, c->obj_partial,
                        c->n_obj_partial, c->hist, c->d_counter, kHistCap, c->stream);
 }
@@ -288,7 +288,7 @@ cudaError_t enq_iteration(nmf_ctx* c) {
   if ((e = enq_product_R(c, b, shared_op)) != cudaSuccess) return e;
   if ((e = cudaEventRecord(c->evx[3], b)) != cudaSuccess) return e;
   if ((e = cudaStreamWaitEvent(c->side2, c->evx[2], 0)) != cudaSuccess) return e;
-  c->launch_count += 2;
+  c->launch_count += 3;
   if ((e = objective_wp(c->W, c->P, c->V, c->Kp, c->obj_partial, c->n_obj_partial, c->side2)) != cudaSuccess)
     return e;
   if ((e = cudaEventRecord(c->evx[4], c->side2)) != cudaSuccess) return e;
