@@ -206,7 +206,9 @@ nmf_status nmf_iterate_mu(nmf_ctx* c, int32_t n_iters, float* step_ms);
 nmf_status nmf_profile(nmf_ctx* c, int32_t n_iters, float* step_ms);
 
 /* Introspection: tile width in use, cluster size of the W column chain,
- * number of kernel launches one iteration makes. */
+ * number of kernel launches one iteration makes in the form run last
+ * (nmf_iterate, nmf_iterate_alg1 or nmf_iterate_mu; before any of them, the
+ * nmf_iterate form's count once its graph exists, else 0). */
 nmf_status nmf_query(nmf_ctx* c, int32_t* tile_T, int32_t* chain_ctas, int32_t* launches_per_iter);
 
 /* Dense product on the tensor cores (tcgen05), a library utility used by the

@@ -66,6 +66,8 @@ struct nmf_ctx {
   cudaEvent_t evx[5] = {};    // fork / join events of the overlapped steps
   long long iters_run = 0;
   int launches_per_iter = 0;
+  int launches_alg1 = 0, launches_mu = 0;   // per iteration of the comparator graphs
+  int last_launches = 0;                    // per iteration of the form run last
   int launch_count = 0;       // kernels issued by the last enqueue sequence
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t graph_exec = nullptr;
@@ -876,6 +878,7 @@ nmf_status nmf_iterate(nmf_ctx* c, int32_t n_iters) {
     c->launches_per_iter = c->launch_count;
     CK(cudaGraphInstantiate(&c->graph_exec, g, 0));
   }
+  c->last_launches = c->launches_per_iter;
   for (int i = 0; i < n_iters; ++i) CK(cudaGraphLaunch(c->graph_exec, c->stream));
   c->iters_run += n_iters;
   return NMF_OK;
@@ -961,8 +964,10 @@ nmf_status iterate_alt(nmf_ctx* c, AltForm f, int32_t n_iters, float* step_ms) {
       return from_cuda(e != cudaSuccess ? e : e2);
     }
     graph = g;
+    (f == FORM_ALG1 ? c->launches_alg1 : c->launches_mu) = c->launch_count;
     CK(cudaGraphInstantiate(&exec, g, 0));
   }
+  c->last_launches = f == FORM_ALG1 ? c->launches_alg1 : c->launches_mu;
   for (int i = 0; i < n_iters; ++i) CK(cudaGraphLaunch(exec, c->stream));
   c->iters_run += n_iters;
   return NMF_OK;
@@ -1264,12 +1269,12 @@ nmf_status nmf_query(nmf_ctx* c, int32_t* tile_T, int32_t* chain_ctas, int32_t* 
   if (chain_ctas && c->w_persistent) {
     *chain_ctas = c->wp.cluster;
     if (tile_T) *tile_T = c->T;
-    if (launches_per_iter) *launches_per_iter = c->launches_per_iter;
+    if (launches_per_iter) *launches_per_iter = c->last_launches ? c->last_launches : c->launches_per_iter;
     return NMF_OK;
   }
   if (tile_T) *tile_T = c->T;
   if (chain_ctas) *chain_ctas = c->chainW.cluster;
-  if (launches_per_iter) *launches_per_iter = c->launches_per_iter;
+  if (launches_per_iter) *launches_per_iter = c->last_launches ? c->last_launches : c->launches_per_iter;
   return NMF_OK;
 }
 

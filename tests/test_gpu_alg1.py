@@ -76,6 +76,11 @@ def test_alg1_matches_regrouped_form(nmf):
     Wr, Hr = fh.iteration(sp.A, fh.normalize_init(W0), H0.astype(np.float64), EPS)
     assert rel_w(Wa, Wr) < TOL and rel_h(Ha, Hr) < TOL
     assert rel_w(Wa, Wb) < 2 * TOL and rel_h(Ha, Hb) < 2 * TOL
+    # nmf_query reports the launches of the form run last: K column launches
+    # for H and 2K for W (Alg. 1 as written) against a handful for the
+    # regrouped form.
+    la, lb = a.query()["launches_per_iter"], b.query()["launches_per_iter"]
+    assert la >= 3 * 48 and 0 < lb < 48
 
 
 def test_alg1_profile_and_mixing(nmf):

@@ -65,5 +65,6 @@ def test_mu_twenty_iterations_monotone(nmf):
     Wr, Hr = omu.run(sp.A, W0, H0, 20)
     fr = ob.frob2_direct(sp.A, Wr, Hr)
     assert abs(fs[-1] - fr) <= 1e-4 * fr
+    assert ctx.query()["launches_per_iter"] > 0          # the MU graph's own count
     prof = ctx.iterate_mu(1, profile=True)
     assert all(v > 0 for v in prof.values())
