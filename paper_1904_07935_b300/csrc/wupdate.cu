@@ -641,10 +641,15 @@ bool w_persistent_config(int N, int Kp, WPersistConfig* cfg) {
     const int nrc = (N + cl - 1) / cl;
     const int rpt = (nrc + WNR - 1) / WNR;
     if (rpt > 4) continue;
+    // Rows per worker pass: as many (up to 4 lanes per thread's row, a
+    // multiple of 8) as the shared-memory budget holds, so that at large K
+    // most of the CTA's threads still have a row (K = 400: 120 rows, where
+    // halving from 128 gave 64 and left half the threads idle).
+    constexpr size_t kBudget = 220 * 1024;
     int worker_rows = WNT / 4;
-    while (worker_rows > 16 && persistent_smem(rpt, Kp, worker_rows) > 200 * 1024) worker_rows /= 2;
+    while (worker_rows > 16 && persistent_smem(rpt, Kp, worker_rows) > kBudget) worker_rows -= 8;
     const size_t smem = persistent_smem(rpt, Kp, worker_rows);
-    if (smem > 200 * 1024) continue;
+    if (smem > kBudget) continue;
     const int nc = max_clusters(rpt, cl, smem);
     if (nc < 2) continue;
     cfg->cluster = cl;
