@@ -189,6 +189,7 @@ struct WPersistConfig {
   int rpt = 1;
   int n_clusters = 0;
   int worker_rows = 128;
+  int worker_wr = 1;      // rows per worker lane group (2 for Kp >= 192)
   int chain_rows = 0;     // rows per chain CTA
   size_t smem = 0;
 };

@@ -92,6 +92,11 @@ __device__ bool wait_counter(const int* p, int target, int* status) {
 // --------------------------------------------------------------------------
 // Worker role: tile bases.
 // --------------------------------------------------------------------------
+// WR rows per lane group: group g takes rows g and (WR = 2) g + RB / 2 of
+// the pass, so that one 16-byte load of Q's block serves WR rows (long rows,
+// Kp >= 192, where the shared-memory loads bound the workers); each row's
+// arithmetic is the same either way.
+template <int WR>
 __device__ void worker_role(const WParams& p, char* smem, int wid, int n_workers) {
   const int nt = (p.K + WT - 1) / WT;
   const int Kr = (p.Kp + WT - 1) / WT * WT;
@@ -168,28 +173,55 @@ __device__ void worker_role(const WParams& p, char* smem, int wid, int n_workers
         }
         phase ^= 1u;
       }
-      if (rl < nrows) {
-        const int row = row0 + rl;
-        const float* xr = Xs + rl * ldx;
-        float acc[4];
+      const int half = WR == 1 ? nrows : (nrows + 1) / 2;  // groups with a row
+      if (rl < half) {
+        int lr[WR];
+        bool has[WR];
+        const float* xr[WR];
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          const int c = lo + 4 * sub + q;
-          acc[q] = c < hi ? __ldg(p.P + (int64_t)row * p.Kp + c) : 0.f;
+        for (int u = 0; u < WR; ++u) {
+          lr[u] = rl + u * half;
+          has[u] = lr[u] < nrows;
+          xr[u] = Xs + (has[u] ? lr[u] : rl) * ldx;
         }
-        // Blocks of WT terms folded into acc with compensation (comp_fold).
-        float cmp[4] = {0.f, 0.f, 0.f, 0.f}, blk[4] = {0.f, 0.f, 0.f, 0.f};
-        auto step = [&](int j) {
-          const float4 x4 = *reinterpret_cast<const float4*>(xr + j);
-          const float xs[4] = {x4.x, x4.y, x4.z, x4.w};
+        float acc[WR][4];
 #pragma unroll
-          for (int u = 0; u < 4; ++u) {
-            const float4 g = *reinterpret_cast<const float4*>(Gc + (j + u) * WT + 4 * sub);
-            blk[0] = fmaf(g.x, xs[u], blk[0]);
-            blk[1] = fmaf(g.y, xs[u], blk[1]);
-            blk[2] = fmaf(g.z, xs[u], blk[2]);
-            blk[3] = fmaf(g.w, xs[u], blk[3]);
+        for (int u = 0; u < WR; ++u)
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            const int c = lo + 4 * sub + q;
+            acc[u][q] = (has[u] && c < hi) ? __ldg(p.P + (int64_t)(row0 + lr[u]) * p.Kp + c) : 0.f;
           }
+        // Blocks of WT terms folded into acc with compensation (comp_fold).
+        float cmp[WR][4], blk[WR][4];
+#pragma unroll
+        for (int u = 0; u < WR; ++u)
+#pragma unroll
+          for (int q = 0; q < 4; ++q) cmp[u][q] = blk[u][q] = 0.f;
+        auto step = [&](int j) {
+          float xs[WR][4];
+#pragma unroll
+          for (int u = 0; u < WR; ++u) {
+            const float4 x4 = *reinterpret_cast<const float4*>(xr[u] + j);
+            xs[u][0] = x4.x; xs[u][1] = x4.y; xs[u][2] = x4.z; xs[u][3] = x4.w;
+          }
+#pragma unroll
+          for (int v = 0; v < 4; ++v) {
+            const float4 g = *reinterpret_cast<const float4*>(Gc + (j + v) * WT + 4 * sub);
+#pragma unroll
+            for (int u = 0; u < WR; ++u) {
+              blk[u][0] = fmaf(g.x, xs[u][v], blk[u][0]);
+              blk[u][1] = fmaf(g.y, xs[u][v], blk[u][1]);
+              blk[u][2] = fmaf(g.z, xs[u][v], blk[u][2]);
+              blk[u][3] = fmaf(g.w, xs[u][v], blk[u][3]);
+            }
+          }
+        };
+        auto fold = [&]() {
+#pragma unroll
+          for (int u = 0; u < WR; ++u)
+#pragma unroll
+            for (int q = 0; q < 4; ++q) comp_fold(acc[u][q], cmp[u][q], blk[u][q]);
         };
         // Full blocks unrolled; a ragged last block step by step.
         auto outside = [&](int j0, int j1) {
@@ -198,42 +230,44 @@ __device__ void worker_role(const WParams& p, char* smem, int wid, int n_workers
           for (; jb + WT <= j1; jb += WT) {
 #pragma unroll
             for (int jj = 0; jj < WT; jj += 4) step(jb + jj);
-#pragma unroll
-            for (int q = 0; q < 4; ++q) comp_fold(acc[q], cmp[q], blk[q]);
+            fold();
           }
           if (jb < j1) {
 #pragma unroll 1
             for (int j = jb; j < j1; j += 4) step(j);
-#pragma unroll
-            for (int q = 0; q < 4; ++q) comp_fold(acc[q], cmp[q], blk[q]);
+            fold();
           }
         };
         outside(0, new_end);
         outside(lo + WT < p.Kp ? lo + WT : p.Kp, p.Kp);
 #pragma unroll
-        for (int q = 0; q < 4; ++q) acc[q] += cmp[q];
-        float xo[WT];
+        for (int u = 0; u < WR; ++u) {
 #pragma unroll
-        for (int q = 0; q < WT / 4; ++q) {
-          float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-          if (lo + 4 * q < p.Kp) v = *reinterpret_cast<const float4*>(xr + lo + 4 * q);
-          xo[4 * q] = v.x; xo[4 * q + 1] = v.y; xo[4 * q + 2] = v.z; xo[4 * q + 3] = v.w;
-        }
+          for (int q = 0; q < 4; ++q) acc[u][q] += cmp[u][q];
+          float xo[WT];
 #pragma unroll
-        for (int j = 1; j < WT; ++j) {
-#pragma unroll
-          for (int q = 0; q < 4; ++q) {
-            const int cl = 4 * sub + q;
-            if (j > cl) acc[q] = fmaf(-Gc[(lo + j) * WT + cl], xo[j], acc[q]);
+          for (int q = 0; q < WT / 4; ++q) {
+            float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (lo + 4 * q < p.Kp) v = *reinterpret_cast<const float4*>(xr[u] + lo + 4 * q);
+            xo[4 * q] = v.x; xo[4 * q + 1] = v.y; xo[4 * q + 2] = v.z; xo[4 * q + 3] = v.w;
           }
-        }
-        float* yr = p.Y + (int64_t)row * p.Kp;
-        if (lo + 4 * sub + 3 < hi) {
-          *reinterpret_cast<float4*>(yr + lo + 4 * sub) = make_float4(acc[0], acc[1], acc[2], acc[3]);
-        } else {
 #pragma unroll
-          for (int q = 0; q < 4; ++q)
-            if (lo + 4 * sub + q < hi) yr[lo + 4 * sub + q] = acc[q];
+          for (int j = 1; j < WT; ++j) {
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+              const int cl = 4 * sub + q;
+              if (j > cl) acc[u][q] = fmaf(-Gc[(lo + j) * WT + cl], xo[j], acc[u][q]);
+            }
+          }
+          if (!has[u]) continue;
+          float* yr = p.Y + (int64_t)(row0 + lr[u]) * p.Kp;
+          if (lo + 4 * sub + 3 < hi) {
+            *reinterpret_cast<float4*>(yr + lo + 4 * sub) = make_float4(acc[u][0], acc[u][1], acc[u][2], acc[u][3]);
+          } else {
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+              if (lo + 4 * sub + q < hi) yr[lo + 4 * sub + q] = acc[u][q];
+          }
         }
       }
     }
@@ -557,13 +591,13 @@ __device__ void chain_role(const WParams& p, char* smem, int n_workers) {
   cluster_sync_all();
 }
 
-template <int RPT>
+template <int RPT, int WR>
 __global__ void __launch_bounds__(WNT, 1) w_update_persistent_kernel(WParams p) {
   extern __shared__ __align__(16) char smem[];
   const unsigned cid = cluster_id_x();
   const int n_workers = (int)gridDim.x - p.cl;
   if (cid == 0) chain_role<RPT>(p, smem, n_workers);
-  else worker_role(p, smem, (int)blockIdx.x - p.cl, n_workers);
+  else worker_role<WR>(p, smem, (int)blockIdx.x - p.cl, n_workers);
 }
 
 size_t persistent_smem(int rpt, int Kp, int worker_rows) {
@@ -572,9 +606,9 @@ size_t persistent_smem(int rpt, int Kp, int worker_rows) {
   return std::max(chain, worker);
 }
 
-template <int RPT>
+template <int RPT, int WR>
 cudaError_t launch_persistent_t(const WParams& p, int n_clusters, size_t smem, cudaStream_t s) {
-  auto kern = w_update_persistent_kernel<RPT>;
+  auto kern = w_update_persistent_kernel<RPT, WR>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   if ((e = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1)) != cudaSuccess) return e;
@@ -597,7 +631,7 @@ cudaError_t launch_persistent_t(const WParams& p, int n_clusters, size_t smem, c
 
 template <int RPT>
 int max_clusters_t(int cl, size_t smem) {
-  auto kern = w_update_persistent_kernel<RPT>;
+  auto kern = w_update_persistent_kernel<RPT, 1>;
   if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess ||
       cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess) {
     cudaGetLastError();
@@ -657,6 +691,7 @@ bool w_persistent_config(int N, int Kp, WPersistConfig* cfg) {
     cfg->chain_rows = nrc;
     cfg->n_clusters = std::min(nc, 9);
     cfg->worker_rows = worker_rows;
+    cfg->worker_wr = Kp >= 192 ? 2 : 1;
     cfg->smem = smem;
     return true;
   }
@@ -669,11 +704,16 @@ cudaError_t w_persistent_run(float* X, const float* P, const float* Q, float* Y,
   cudaError_t e = cudaMemsetAsync(d_sync, 0, sizeof(int) * w_sync_ints(K), s);
   if (e != cudaSuccess) return e;
   WParams p{X, P, Q, Y, N, K, Kp, eps, d_status, d_sync, cfg.cluster, cfg.worker_rows, cfg.chain_rows, pre0};
+  const bool two = cfg.worker_wr == 2;
   switch (cfg.rpt) {
-    case 1: return launch_persistent_t<1>(p, cfg.n_clusters, cfg.smem, s);
-    case 2: return launch_persistent_t<2>(p, cfg.n_clusters, cfg.smem, s);
-    case 3: return launch_persistent_t<3>(p, cfg.n_clusters, cfg.smem, s);
-    case 4: return launch_persistent_t<4>(p, cfg.n_clusters, cfg.smem, s);
+    case 1: return two ? launch_persistent_t<1, 2>(p, cfg.n_clusters, cfg.smem, s)
+                       : launch_persistent_t<1, 1>(p, cfg.n_clusters, cfg.smem, s);
+    case 2: return two ? launch_persistent_t<2, 2>(p, cfg.n_clusters, cfg.smem, s)
+                       : launch_persistent_t<2, 1>(p, cfg.n_clusters, cfg.smem, s);
+    case 3: return two ? launch_persistent_t<3, 2>(p, cfg.n_clusters, cfg.smem, s)
+                       : launch_persistent_t<3, 1>(p, cfg.n_clusters, cfg.smem, s);
+    case 4: return two ? launch_persistent_t<4, 2>(p, cfg.n_clusters, cfg.smem, s)
+                       : launch_persistent_t<4, 1>(p, cfg.n_clusters, cfg.smem, s);
     default: return cudaErrorInvalidValue;
   }
 }
