@@ -172,8 +172,9 @@ __global__ void __launch_bounds__(256) gemm_kernel(GemmArgs g) {
   }
 }
 
-// Split-N Gram for 64 <= Kp <= 176: CTA z computes the upper triangle of
-// the Kp8 x Kp8 Gram of its row chunk (Kp8 = Kp rounded up to 8).  The Kp8
+// Split-N Gram for 64 <= Kp <= 512: CTA (z, y) computes tile group y of the
+// upper triangle of the Kp8 x Kp8 Gram of row chunk z (Kp8 = Kp rounded up
+// to 8).  The Kp8
 // indices form m = Kp8 / 8 groups of 8, group g = {4g .. 4g+3} together with
 // {Kh + 4g .. Kh + 4g+3} (Kh = Kp8 / 2), so that consecutive groups are
 // consecutive 16-byte words of a staged row (conflict-free loads).  Every
@@ -184,25 +185,30 @@ __global__ void __launch_bounds__(256) gemm_kernel(GemmArgs g) {
 // X are staged GR at a time in shared memory (double-buffered through
 // registers) and thread half h multiplies rows [h GR/2, (h+1) GR/2) of each
 // staged block; at the end half 1's tile goes through shared memory and half
-// 0 adds it (fixed order).
+// 0 adds it (fixed order).  The tiles are numbered row-major over the
+// triangle and dealt in groups of tpg <= 253 (one group up to Kp = 176);
+// every CTA of a chunk stages the same rows.
 constexpr int GR = 16;                            // rows per staged block
-constexpr int kGramFullMaxKp = 176;               // m = 22: 253 tiles, 506 threads
+constexpr int kGramFullMaxKp = kMaxK;             // up to m = 64: 2,080 tiles in 9 groups
+constexpr int kTriGroupMax = 253;                 // tiles per CTA (506 threads)
 constexpr int kGramFullMinKp = 64;                // m = 8: 36 tiles, 72 threads
 __host__ __device__ constexpr int gram_tri_tiles(int Kp8) { return (Kp8 / 8) * (Kp8 / 8 + 1) / 2; }
-constexpr int kTriStride = 256;                   // >= gram_tri_tiles(176); compile-time offsets
+constexpr int kTriStride = 256;                   // >= kTriGroupMax; compile-time offsets
 __host__ __device__ constexpr int gram_tri_smem_floats(int Kp8) {
   return 2 * GR * Kp8 > 64 * kTriStride ? 2 * GR * Kp8 : 64 * kTriStride;
 }
-static_assert(gram_tri_tiles(kGramFullMaxKp) <= kTriStride, "tile stride");
+static_assert(kTriGroupMax <= kTriStride, "tile stride");
 __global__ void __launch_bounds__(512) gram_tri_kernel(const float* __restrict__ X, int N, int Kp, int Kp8,
-                                                       int chunk, float* __restrict__ part) {
+                                                       int chunk, int tpg, float* __restrict__ part) {
   extern __shared__ __align__(16) float xs[];      // staging 2 x GR x Kp8; afterwards half 1's tiles
   const int m = Kp8 / 8, Kh = Kp8 / 2;
   const int nT = m * (m + 1) / 2;
-  const int h = threadIdx.x >= nT ? 1 : 0;
-  const int u = threadIdx.x - h * nT;
-  // Tile u -> (ty, tx), ty <= tx, row-major over the upper triangle.
-  int ty = 0, rem = u;
+  const int h = threadIdx.x >= tpg ? 1 : 0;
+  const int ul = threadIdx.x - h * tpg;            // tile within the group
+  const int ut = blockIdx.y * tpg + ul;            // tile within the triangle
+  const bool act = ut < nT;                        // (the last group may be short)
+  // Tile ut -> (ty, tx), ty <= tx, row-major over the upper triangle.
+  int ty = 0, rem = act ? ut : 0;
   while (rem >= m - ty) {
     rem -= m - ty;
     ++ty;
@@ -268,10 +274,10 @@ __global__ void __launch_bounds__(512) gram_tri_kernel(const float* __restrict__
 #pragma unroll
     for (int i = 0; i < 8; ++i)
 #pragma unroll
-      for (int j = 0; j < 8; ++j) xs[(i * 8 + j) * kTriStride + u] = acc[i][j];
+      for (int j = 0; j < 8; ++j) xs[(i * 8 + j) * kTriStride + ul] = acc[i][j];
   }
   __syncthreads();
-  if (h == 1) return;
+  if (h == 1 || !act) return;
   float* out = part + (int64_t)blockIdx.x * Kp * Kp;
 #pragma unroll
   for (int i = 0; i < 8; ++i) {
@@ -279,7 +285,7 @@ __global__ void __launch_bounds__(512) gram_tri_kernel(const float* __restrict__
 #pragma unroll
     for (int j = 0; j < 8; ++j) {
       const int cj = j < 4 ? 4 * tx + j : Kh + 4 * tx + j - 4;
-      const float v = acc[i][j] + xs[(i * 8 + j) * kTriStride + u];
+      const float v = acc[i][j] + xs[(i * 8 + j) * kTriStride + ul];
       if (ri < Kp && cj < Kp) out[(int64_t)min(ri, cj) * Kp + max(ri, cj)] = v;
     }
     // One tile row at a time: keeps the compiler from hoisting all 64
@@ -615,8 +621,14 @@ cudaError_t gram_setup(GramWork& g, int N, int Kp) {
   g.N = N;
   g.Kp = Kp;
   if (Kp >= kGramFullMinKp && Kp <= kGramFullMaxKp) {
-    // gram_tri_kernel: one CTA per SM (chunks of at least GR rows).
-    const int chunk = std::max(GR, (N + 147) / 148);
+    // gram_tri_kernel: the triangle's tiles in groups of at most
+    // kTriGroupMax, and row chunks (of at least GR rows) such that chunks x
+    // groups is about one CTA per SM.
+    const int nT = gram_tri_tiles((Kp + 7) / 8 * 8);
+    g.groups = (nT + kTriGroupMax - 1) / kTriGroupMax;
+    g.tpg = (nT + g.groups - 1) / g.groups;
+    const int want = std::max(1, 148 / g.groups);
+    const int chunk = std::max(GR, (N + want - 1) / want);
     g.chunk = chunk;
     g.n_chunks = (N + chunk - 1) / chunk;
     return cudaMalloc(&g.d_part, sizeof(float) * (size_t)g.n_chunks * Kp * Kp);
@@ -712,13 +724,13 @@ void gram_free(GramWork& g) {
 cudaError_t gram_run(const GramWork& g, const float* X, float* S, int K, cudaStream_t s) {
   if (g.Kp >= kGramFullMinKp && g.Kp <= kGramFullMaxKp) {
     const int Kp8 = (g.Kp + 7) / 8 * 8;
-    const int threads = 2 * gram_tri_tiles(Kp8);
+    const int threads = 2 * g.tpg;
     const size_t smem = sizeof(float) * gram_tri_smem_floats(Kp8);
     static const cudaError_t attr = cudaFuncSetAttribute(
         gram_tri_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
         (int)(sizeof(float) * gram_tri_smem_floats((kGramFullMaxKp + 7) / 8 * 8)));
     if (attr != cudaSuccess) return attr;
-    gram_tri_kernel<<<g.n_chunks, threads, smem, s>>>(X, g.N, g.Kp, Kp8, g.chunk, g.d_part);
+    gram_tri_kernel<<<dim3(g.n_chunks, g.groups), threads, smem, s>>>(X, g.N, g.Kp, Kp8, g.chunk, g.tpg, g.d_part);
     cudaError_t err = cudaGetLastError();
     if (err != cudaSuccess) return err;
     return gram_reduce(g.d_part, g.n_chunks, g.Kp, K, S, s);

@@ -119,6 +119,7 @@ cudaError_t resid2_dense(const float* A, int64_t lda, const float* W, const floa
 struct GramWork {
   float* d_part = nullptr;   // n_chunks x Kp x Kp
   int n_chunks = 0, chunk = 0, N = 0, Kp = 0;
+  int groups = 1, tpg = 0;   // upper-triangle tile groups (gram_tri_kernel)
 };
 cudaError_t gram_setup(GramWork& g, int N, int Kp);
 void gram_free(GramWork& g);
