@@ -619,10 +619,23 @@ cudaError_t h_update_run(float* X, const float* B, const float* G, int N, int K,
   auto enough = [&](int R) { return (long long)(N + 32 * R - 1) / (32 * R) >= 3LL * sms; };
   if (fits(4) && enough(4)) return h_update_launch<4>(X, B, G, N, K, Kp, eps, status, s);
   if (fits(2) && enough(2)) return h_update_launch<2>(X, B, G, N, K, Kp, eps, status, s);
-  // Long rows: two rows per lane group even with few CTAs, as one 16-byte load
-  // of S's block then serves two rows (8192 x 256: 115 -> 101 us; at K = 160
-  // one row is faster, 66 against 68 us on 11,314 rows).
-  if (Kp >= 192 && fits(2)) return h_update_launch<2>(X, B, G, N, K, Kp, eps, status, s);
+  // Long rows: two or three rows per lane group even with few CTAs, as one
+  // 16-byte load of S's block then serves them all (8192 x 256: 115 -> 101 us;
+  // at K = 160 one row is faster, 66 against 68 us on 11,314 rows).  Of the
+  // two, the one with the fewer waves x rows per CTA: where a 64-row CTA
+  // needs more than half the shared memory the 2-row grid runs in two waves
+  // and the 3-row grid in one.
+  if (Kp >= 192 && fits(2)) {
+    auto cost = [&](int R) -> long long {
+      const size_t bytes = 2 * gc + per_row * 32 * R;
+      const long long per_sm = std::max<long long>(1, (long long)(227 * 1024) / (long long)bytes);
+      const long long blocks = (N + 32 * R - 1) / (32 * R);
+      return (blocks + per_sm * sms - 1) / (per_sm * sms) * R;
+    };
+    if (2 * gc + per_row * 96 <= 220 * 1024 && cost(3) < cost(2))
+      return h_update_launch<3>(X, B, G, N, K, Kp, eps, status, s);
+    return h_update_launch<2>(X, B, G, N, K, Kp, eps, status, s);
+  }
   return h_update_launch<1>(X, B, G, N, K, Kp, eps, status, s);
 }
 
