@@ -83,7 +83,7 @@ def test_dense_products_and_grams(nmf):
     _check_products(ctx, nmf, prob.A.astype(np.float64), W0, H0, 2e-6)
 
 
-@pytest.mark.parametrize("K", [37, 100, 176])
+@pytest.mark.parametrize("K", [37, 100, 176, 320])
 def test_sparse_products_with_long_and_empty_rows(nmf, K):
     sp = synth.sparse_termdoc(3000, 1400, 21, mean_terms=40)
     lens = np.diff(sp.A.row_ptr)
@@ -220,6 +220,20 @@ def test_one_iteration_sparse_k_sweep(nmf, K):
     sp = synth.sparse_termdoc(8000, 4000, 0xC2 + K, mean_terms=100)
     W0, H0 = synth.init_factors(0xC2 + K + 1, 8000, 4000, K)
     ctx = _sparse_ctx(nmf, sp, K, W0, H0)
+    Wg, Hg, Wr, Hr = _one_iteration(nmf, sp.A, ctx, W0, H0)
+    assert rel_h(Hg, Hr) < TOL_ITER
+    assert rel_w(Wg, Wr) < TOL_ITER
+
+
+def test_one_iteration_three_row_h_update(nmf):
+    """10,000 documents at K = 320: two rows per lane group would need two
+    waves of CTAs (a 64-row CTA takes more than half an SM's shared memory),
+    so the H update runs three rows per lane group; its W update takes two
+    rows per worker lane group and the Grams take the grouped upper-triangle
+    kernel.  One iteration against the FP64 oracle."""
+    sp = synth.sparse_termdoc(12000, 10000, 0xD3, mean_terms=60)
+    W0, H0 = synth.init_factors(0xD4, 12000, 10000, 320)
+    ctx = _sparse_ctx(nmf, sp, 320, W0, H0)
     Wg, Hg, Wr, Hr = _one_iteration(nmf, sp.A, ctx, W0, H0)
     assert rel_h(Hg, Hr) < TOL_ITER
     assert rel_w(Wg, Wr) < TOL_ITER
