@@ -259,10 +259,14 @@ __global__ void __launch_bounds__(4 * NG, 2) h_update_kernel(float* __restrict__
       }
 #pragma unroll
       for (int j = 1; j < HT; ++j) {
+        // The lane's four values of S's row j in one 16-byte load (four
+        // scalar loads cost as many wavefronts and four times the issue).
+        const float4 g4 = *reinterpret_cast<const float4*>(Gc + (lo + j) * HT + 4 * sub);
+        const float gv[4] = {g4.x, g4.y, g4.z, g4.w};
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
           const int cl = 4 * sub + q;
-          if (j > cl) acc[i][q] = fmaf(-Gc[(lo + j) * HT + cl], xo[j], acc[i][q]);
+          if (j > cl) acc[i][q] = fmaf(-gv[q], xo[j], acc[i][q]);
         }
       }
     }
@@ -272,6 +276,8 @@ __global__ void __launch_bounds__(4 * NG, 2) h_update_kernel(float* __restrict__
 #pragma unroll
     for (int t = 0; t < HT; ++t) {
       const int owner = t >> 2, q = t & 3;
+      const float4 g4t = *reinterpret_cast<const float4*>(Gc + (lo + t) * HT + 4 * sub);
+      const float gt[4] = {g4t.x, g4t.y, g4t.z, g4t.w};
 #pragma unroll
       for (int i = 0; i < R; ++i) {
         float v = 0.f;
@@ -283,7 +289,7 @@ __global__ void __launch_bounds__(4 * NG, 2) h_update_kernel(float* __restrict__
 #pragma unroll
         for (int q2 = 0; q2 < 4; ++q2) {
           const int c2 = 4 * sub + q2;
-          if (c2 > t) acc[i][q2] = fmaf(-Gc[(lo + t) * HT + c2], v, acc[i][q2]);
+          if (c2 > t) acc[i][q2] = fmaf(-gt[q2], v, acc[i][q2]);
         }
       }
     }
@@ -541,10 +547,12 @@ __global__ void __launch_bounds__(HTHREADS) w_prep_kernel(const float* __restric
   }
 #pragma unroll
   for (int j = 1; j < HT; ++j) {
+    const float4 g4 = *reinterpret_cast<const float4*>(Gc + (lo + j) * HT + 4 * sub);
+    const float gv[4] = {g4.x, g4.y, g4.z, g4.w};
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
       const int cl = 4 * sub + q;
-      if (j > cl && j < T) blk[q] = fmaf(Gc[(lo + j) * HT + cl], xo[j], blk[q]);
+      if (j > cl && j < T) blk[q] = fmaf(gv[q], xo[j], blk[q]);
     }
   }
 #pragma unroll

@@ -253,10 +253,12 @@ __device__ void worker_role(const WParams& p, char* smem, int wid, int n_workers
           }
 #pragma unroll
           for (int j = 1; j < WT; ++j) {
+            const float4 g4 = *reinterpret_cast<const float4*>(Gc + (lo + j) * WT + 4 * sub);
+            const float gv[4] = {g4.x, g4.y, g4.z, g4.w};
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
               const int cl = 4 * sub + q;
-              if (j > cl) acc[u][q] = fmaf(-Gc[(lo + j) * WT + cl], xo[j], acc[u][q]);
+              if (j > cl) acc[u][q] = fmaf(-gv[q], xo[j], acc[u][q]);
             }
           }
           if (!has[u]) continue;
