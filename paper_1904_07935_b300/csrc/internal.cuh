@@ -35,6 +35,8 @@ struct SpmmPlan {
   int4* d_items = nullptr;
   int4* d_combine = nullptr;  // {row, first_slot, n_slots, 0}
   float* d_partial = nullptr; // n_slots x Kp
+  int* d_slot_long = nullptr; // long-row index of each slot
+  int* d_counter = nullptr;   // per long row: items done in this launch (the last resets it)
 };
 
 // Builds the plan from host CSR row pointers.  seg = max nnz per item.

@@ -123,7 +123,7 @@ cudaError_t bf16_operand(nmf_ctx* c, bool w, cudaStream_t s) {
 cudaError_t enq_product_R(nmf_ctx* c, cudaStream_t s = nullptr, bool operand_ready = false) {   // R = A^T W
   if (!s) s = c->stream;
   if (c->fmt == NMF_CSR_F32_I32) {
-    c->launch_count += 1 + (c->planAt.n_long > 0);
+    c->launch_count += 1;
     return spmm_run(c->planAt, c->ciT, c->vaT, c->W, c->R, c->Kp, s);
   }
   GemmArgs a;
@@ -147,7 +147,7 @@ cudaError_t enq_product_R(nmf_ctx* c, cudaStream_t s = nullptr, bool operand_rea
 
 cudaError_t enq_product_P(nmf_ctx* c, bool operand_ready = false) {   // P = A H^T  (V x Kp)
   if (c->fmt == NMF_CSR_F32_I32) {
-    c->launch_count += 1 + (c->planA.n_long > 0);
+    c->launch_count += 1;
     return spmm_run(c->planA, c->ci, c->va, c->Ht, c->P, c->Kp, c->stream);
   }
   GemmArgs a;

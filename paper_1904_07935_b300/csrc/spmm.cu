@@ -6,10 +6,11 @@
 // except rows longer than `seg` non-zeros (the Zipf head words, which can hold
 // nearly every document), which are cut into items of at most `seg`
 // non-zeros.  A warp owns an item (see spmm_items_kernel for the lane
-// layout); the gathered rows of X are read as 16-byte loads.  Split rows write
-// partial rows to a scratch buffer and a second kernel adds them in a fixed
-// order, so results are bit-reproducible (no floating-point atomics).  Items
-// are ordered longest first to balance the tail.
+// layout); the gathered rows of X are read as 16-byte loads.  The items of a
+// split row write partial rows to a scratch buffer; the one that finishes
+// last (a per-row counter) adds them in slot order, so results are
+// bit-reproducible (no floating-point atomics) and no second launch is
+// needed.  Items are ordered longest first to balance the tail.
 #include <algorithm>
 #include <numeric>
 
@@ -46,7 +47,8 @@ template <int L, int C>
 __device__ __forceinline__ void spmm_items(const int4* __restrict__ items, int n_items,
                                            const int* __restrict__ col_idx, const float* __restrict__ val,
                                            const float4* __restrict__ X, int Kp4, float4* __restrict__ Y,
-                                           float4* __restrict__ partial) {
+                                           float4* __restrict__ partial, const int4* __restrict__ comb,
+                                           const int* __restrict__ slot_long, int* __restrict__ counter) {
   constexpr int G = 32 / L;
   const int lane = threadIdx.x & 31;
   const int g = lane / L, sub = lane % L;
@@ -98,45 +100,51 @@ __device__ __forceinline__ void spmm_items(const int4* __restrict__ items, int n
       acc[q].w += __shfl_xor_sync(0xffffffffu, acc[q].w, off);
     }
   }
-  if (g != 0) return;
   float4* dst = (it.w < 0) ? (Y + (size_t)it.x * Kp4) : (partial + (size_t)it.w * Kp4);
+  if (g == 0) {
 #pragma unroll
-  for (int q = 0; q < C; ++q) {
-    const int k = sub + L * q;
-    if (k < Kp4) dst[k] = acc[q];
+    for (int q = 0; q < C; ++q) {
+      const int k = sub + L * q;
+      if (k < Kp4) dst[k] = acc[q];
+    }
   }
+  if (it.w < 0) return;                            // whole warp: a row of its own
+  // Split row: the item that finishes last adds the row's partials in slot
+  // order (each partial written and fenced before its item is counted).
+  __threadfence();
+  __syncwarp();
+  const int lr = slot_long[it.w];
+  const int4 c = comb[lr];
+  int last = 0;
+  if (lane == 0) last = atomicAdd(counter + lr, 1) == c.z - 1;
+  if (!__shfl_sync(0xffffffffu, last, 0)) return;
+  __threadfence();
+  for (int k = lane; k < Kp4; k += 32) {
+    float4 sum = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int j = 0; j < c.z; ++j) {
+      const float4 v = __ldcg(partial + (size_t)(c.y + j) * Kp4 + k);
+      sum.x += v.x; sum.y += v.y; sum.z += v.z; sum.w += v.w;
+    }
+    Y[(size_t)c.x * Kp4 + k] = sum;
+  }
+  if (lane == 0) counter[lr] = 0;                  // ready for the next launch
 }
 
 template <int L, int C>
 __global__ void __launch_bounds__(256, spmm_min_blocks(C))
     spmm_items_kernel(const int4* __restrict__ items, int n_items, const int* __restrict__ col_idx,
                       const float* __restrict__ val, const float4* __restrict__ X, int Kp4, float4* __restrict__ Y,
-                      float4* __restrict__ partial) {
-  spmm_items<L, C>(items, n_items, col_idx, val, X, Kp4, Y, partial);
+                      float4* __restrict__ partial, const int4* __restrict__ comb,
+                      const int* __restrict__ slot_long, int* __restrict__ counter) {
+  spmm_items<L, C>(items, n_items, col_idx, val, X, Kp4, Y, partial, comb, slot_long, counter);
 }
 template <int L, int C>
 __global__ void __launch_bounds__(256)
     spmm_items_lean_kernel(const int4* __restrict__ items, int n_items, const int* __restrict__ col_idx,
                            const float* __restrict__ val, const float4* __restrict__ X, int Kp4,
-                           float4* __restrict__ Y, float4* __restrict__ partial) {
-  spmm_items<L, C>(items, n_items, col_idx, val, X, Kp4, Y, partial);
-}
-
-// Y[row] = sum of its partial rows in slot order.
-__global__ void spmm_combine_kernel(const int4* __restrict__ comb, int n_long,
-                                    const float4* __restrict__ partial, float4* __restrict__ Y,
-                                    int Kp4) {
-  const int i = blockIdx.x;
-  if (i >= n_long) return;
-  const int4 c = comb[i];
-  for (int k = threadIdx.x; k < Kp4; k += blockDim.x) {
-    float4 s = make_float4(0.f, 0.f, 0.f, 0.f);
-    for (int j = 0; j < c.z; ++j) {
-      const float4 p = partial[(size_t)(c.y + j) * Kp4 + k];
-      s.x += p.x; s.y += p.y; s.z += p.z; s.w += p.w;
-    }
-    Y[(size_t)c.x * Kp4 + k] = s;
-  }
+                           float4* __restrict__ Y, float4* __restrict__ partial, const int4* __restrict__ comb,
+                           const int* __restrict__ slot_long, int* __restrict__ counter) {
+  spmm_items<L, C>(items, n_items, col_idx, val, X, Kp4, Y, partial, comb, slot_long, counter);
 }
 
 template <int L, int C>
@@ -150,10 +158,11 @@ cudaError_t launch_items(const SpmmPlan& p, const int* ci, const float* va, cons
     float4* y4 = reinterpret_cast<float4*>(Y);
     float4* p4 = reinterpret_cast<float4*>(p.d_partial);
     if constexpr (C == 4) {
-      spmm_items_lean_kernel<L, C><<<blocks, 32 * warps_per_block, 0, s>>>(p.d_items, p.n_items, ci, va, x4, Kp4,
-                                                                           y4, p4);
+      spmm_items_lean_kernel<L, C><<<blocks, 32 * warps_per_block, 0, s>>>(
+          p.d_items, p.n_items, ci, va, x4, Kp4, y4, p4, p.d_combine, p.d_slot_long, p.d_counter);
     } else {
-      spmm_items_kernel<L, C><<<blocks, 32 * warps_per_block, 0, s>>>(p.d_items, p.n_items, ci, va, x4, Kp4, y4, p4);
+      spmm_items_kernel<L, C><<<blocks, 32 * warps_per_block, 0, s>>>(
+          p.d_items, p.n_items, ci, va, x4, Kp4, y4, p4, p.d_combine, p.d_slot_long, p.d_counter);
     }
   }
   return cudaGetLastError();
@@ -201,16 +210,28 @@ cudaError_t spmm_plan_build(SpmmPlan& plan, const std::vector<int>& row_ptr, int
       (err = cudaMemcpy(plan.d_combine, comb.data(), sizeof(int4) * comb.size(), cudaMemcpyHostToDevice)) != cudaSuccess)
     return err;
   if ((err = cudaMalloc(&plan.d_partial, sizeof(float) * (size_t)std::max(1, slot) * Kp)) != cudaSuccess) return err;
-  return cudaSuccess;
+  std::vector<int> slot_long((size_t)std::max(1, slot), 0);
+  for (size_t i = 0; i < comb.size(); ++i)
+    for (int j = 0; j < comb[i].z; ++j) slot_long[(size_t)comb[i].y + j] = (int)i;
+  if ((err = cudaMalloc(&plan.d_slot_long, sizeof(int) * slot_long.size())) != cudaSuccess) return err;
+  if ((err = cudaMemcpy(plan.d_slot_long, slot_long.data(), sizeof(int) * slot_long.size(),
+                        cudaMemcpyHostToDevice)) != cudaSuccess) return err;
+  if ((err = cudaMalloc(&plan.d_counter, sizeof(int) * std::max<size_t>(1, comb.size()))) != cudaSuccess) return err;
+  if ((err = cudaMemset(plan.d_counter, 0, sizeof(int) * std::max<size_t>(1, comb.size()))) != cudaSuccess) return err;
+  return cudaDeviceSynchronize();
 }
 
 void spmm_plan_free(SpmmPlan& plan) {
   cudaFree(plan.d_items);
   cudaFree(plan.d_combine);
   cudaFree(plan.d_partial);
+  cudaFree(plan.d_slot_long);
+  cudaFree(plan.d_counter);
   plan.d_items = nullptr;
   plan.d_combine = nullptr;
   plan.d_partial = nullptr;
+  plan.d_slot_long = nullptr;
+  plan.d_counter = nullptr;
 }
 
 cudaError_t spmm_run(const SpmmPlan& p, const int* ci, const float* va, const float* X, float* Y,
@@ -231,13 +252,6 @@ cudaError_t spmm_run(const SpmmPlan& p, const int* ci, const float* va, const fl
   else if (Kp4 <= 80) err = launch_items<16, 5>(p, ci, va, X, Y, Kp, s);
   else if (Kp4 <= 96) err = launch_items<16, 6>(p, ci, va, X, Y, Kp, s);
   else err = launch_items<16, 8>(p, ci, va, X, Y, Kp, s);   // Kp <= 512
-  if (err != cudaSuccess) return err;
-  if (p.n_long > 0) {
-    spmm_combine_kernel<<<p.n_long, 128, 0, s>>>(p.d_combine, p.n_long,
-                                                 reinterpret_cast<const float4*>(p.d_partial),
-                                                 reinterpret_cast<float4*>(Y), Kp4);
-    err = cudaGetLastError();
-  }
   return err;
 }
 
