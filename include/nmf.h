@@ -211,6 +211,24 @@ nmf_status nmf_profile(nmf_ctx* c, int32_t n_iters, float* step_ms);
  * nmf_iterate form's count once its graph exists, else 0). */
 nmf_status nmf_query(nmf_ctx* c, int32_t* tile_T, int32_t* chain_ctas, int32_t* launches_per_iter);
 
+/* Limits of the W update's device-side waits (the single-launch form that
+ * replaces Alg. 3's two host synchronisations per column with hand-offs
+ * between the column chain and the CTAs forming the tile bases).
+ *   wait_ns          limit of every such wait in nanoseconds; 0 restores the
+ *                    library default (200 ms).
+ *   extra_arrivals   0 in normal use.  A positive value makes the base-forming
+ *                    CTAs wait for that many more chain arrivals than will
+ *                    ever come, so that their waits run out: a way to test the
+ *                    failure path without a GPU fault.  Their waits then set
+ *                    the status word (the next nmf_error / nmf_get_factors
+ *                    returns NMF_ETIMEOUT once), and the chain computes the
+ *                    bases they left, so the factors stay those of a normal
+ *                    update.
+ * Takes effect at the next nmf_iterate (the iteration graph is re-captured).
+ * NMF_EINVAL for wait_ns < 0 or extra_arrivals < 0; NMF_EUNSUPPORTED when the
+ * context runs the per-tile W launches, which have no such waits. */
+nmf_status nmf_set_wait_limits(nmf_ctx* c, int64_t wait_ns, int32_t extra_arrivals);
+
 /* Dense product on the tensor cores (tcgen05), a library utility used by the
  * iteration and exposed for testing:  C (M x N) = op(A) (M x K) * B (K x N),
  * op(A) = A (row-major, lda) or A^T (A stored K x M row-major, lda) when

@@ -185,8 +185,10 @@ cudaError_t alg1_update_w(float* W, const float* P, const float* Q, int V, int K
 cudaError_t mu_update(float* X, const float* B, const float* G, float* scratch, int N, int K, int Kp, float delta,
                       cudaStream_t s, int* launches);
 
-// Persistent, cooperative W update (one launch per update): cluster 0 runs the
-// column chain over all tiles, the other clusters compute the tile bases.
+// Whole W update in one launch: cluster 0 runs the column chain over all
+// tiles, the other clusters compute the tile bases (blocks the chain finds
+// unclaimed it computes itself, so the result does not depend on how many
+// clusters are resident at once).
 struct WPersistConfig {
   int cluster = 16;
   int rpt = 1;
@@ -202,9 +204,13 @@ size_t w_sync_ints(int K);
 // pre0 != nullptr: Y's columns [0, 16) plus pre0 (N x 16) already hold tile
 // 0's base less P (w_prep_run with B = nullptr, lo = new_end = 0, Ylo =
 // pre0); the launch then adds P there.
+// wait_ns: limit of every device wait (0: kWaitLimitNs); extra_arrivals > 0
+// makes the workers wait for more chain arrivals than exist (tests of the
+// timeout path: the waits run out, ST_TIMEOUT is set and the chain computes
+// the remaining bases itself).
 cudaError_t w_persistent_run(float* X, const float* P, const float* Q, float* Y, int N, int K, int Kp, float eps,
                              int* d_sync, int* d_status, const WPersistConfig& cfg, cudaStream_t s,
-                             const float* pre0 = nullptr);
+                             const float* pre0 = nullptr, unsigned long long wait_ns = 0, int extra_arrivals = 0);
 
 // ---------------------------------------------------------------------------
 // Misc kernels.

@@ -33,9 +33,11 @@ struct nmf_ctx {
   bool own_stream = false;
   cudaStream_t side = nullptr;          // second stream for the W tile bases
   cudaStream_t side2 = nullptr;         // third stream: <W, P> of the objective beside S and R
-  bool w_persistent = false;            // whole W update as one cooperative launch
+  bool w_persistent = false;            // whole W update as one launch (chain cluster + workers)
   WPersistConfig wp;
   int* d_sync = nullptr;
+  unsigned long long wait_ns = 0;       // limit of the W update's device waits (0: library default)
+  int extra_arrivals = 0;               // tests of the timeout path: a hand-off count that cannot be reached
   std::vector<cudaEvent_t> ev;          // fork / join events of the W update
   // A (caller-owned) and its transpose (context-owned, CSR only).
   const float* dense = nullptr;
@@ -206,7 +208,7 @@ cudaError_t enq_update(nmf_ctx* c, float* X, const float* G, const float* B, int
   if (c->w_persistent) {
     c->launch_count += 1;
     return w_persistent_run(X, B, G, c->Y, N, K, Kp, c->eps, c->d_sync, c->d_status, c->wp, c->stream,
-                            pre0 ? c->Y0lo : nullptr);
+                            pre0 ? c->Y0lo : nullptr, c->wait_ns, c->extra_arrivals);
   }
   // W: tile tau's base without tile tau-1 ("main") runs on the side stream
   // while the chain of tile tau-1 runs; the chain of tile tau adds tile
@@ -538,27 +540,10 @@ nmf_status init_impl(const nmf_problem* p, nmf_ctx* c) {
     CK(fill_uniform_splitmix_t(c->Ht, D, p->K, Kp, sh, c->stream));
   }
   CK(normalize_columns(c->W, V, p->K, Kp, c->stream));
-  // Persistent W update: probe the cooperative cluster launch once with no
-  // rows (nothing is read or written but the hand-off flags).  Not with a
-  // CUDA tool injected into the process (a kernel profiler): the cooperative
-  // cluster launch has failed under one, taking the context with it, so the
-  // per-tile launches run instead.
-  const bool tool_attached = std::getenv("CUDA_INJECTION64_PATH") != nullptr;
-  if (!(p->flags & NMF_FLAG_MULTI_LAUNCH_W) && !tool_attached && w_persistent_config(V, Kp, &c->wp)) {
-    CK(cudaStreamSynchronize(c->stream));
-    cudaError_t e = w_persistent_run(c->W, c->P, c->Q, c->Y, 0, c->K, Kp, c->eps, c->d_sync, c->d_status, c->wp,
-                                     c->stream);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
-    if (e == cudaSuccess) {
-      int st = 0;
-      CK(cudaMemcpy(&st, c->d_status, sizeof(int), cudaMemcpyDeviceToHost));
-      c->w_persistent = (st & ST_TIMEOUT) == 0;
-      CK(cudaMemset(c->d_status, 0, sizeof(int)));
-    } else {
-      cudaGetLastError();
-      c->w_persistent = false;
-    }
-  }
+  // Whole W update in one launch wherever a 16- or 8-CTA chain cluster and at
+  // least one worker cluster fit; its result does not depend on how many of
+  // the clusters run at the same time, so no probe launch is needed.
+  c->w_persistent = !(p->flags & NMF_FLAG_MULTI_LAUNCH_W) && w_persistent_config(V, Kp, &c->wp);
   CK(enq_gram(c, c->gramW, c->W, c->S));
   c->s_valid = true;
   CK(cudaStreamSynchronize(c->stream));
@@ -1275,6 +1260,15 @@ nmf_status nmf_query(nmf_ctx* c, int32_t* tile_T, int32_t* chain_ctas, int32_t* 
   if (tile_T) *tile_T = c->T;
   if (chain_ctas) *chain_ctas = c->chainW.cluster;
   if (launches_per_iter) *launches_per_iter = c->last_launches ? c->last_launches : c->launches_per_iter;
+  return NMF_OK;
+}
+
+nmf_status nmf_set_wait_limits(nmf_ctx* c, int64_t wait_ns, int32_t extra_arrivals) {
+  if (!c || wait_ns < 0 || extra_arrivals < 0) return NMF_EINVAL;
+  if (!c->w_persistent) return NMF_EUNSUPPORTED;
+  c->wait_ns = (unsigned long long)wait_ns;
+  c->extra_arrivals = extra_arrivals;
+  drop_graph(c);
   return NMF_OK;
 }
 

@@ -7,15 +7,18 @@
 // W_old * Q_tt initialisation cancels the j = t term of Eq. 5 exactly and is
 // left out.)
 //
-// Roles inside the launch (grid = NC clusters of CL = 16 CTAs, all resident
-// at once, which the cooperative launch guarantees):
+// Roles inside the launch (grid = NC clusters of CL = 16 CTAs; an ordinary
+// cluster launch: nothing in the protocol below assumes that the clusters run
+// at the same time, only that the CTAs of one cluster do, which the hardware
+// guarantees):
 //  * cluster 0 ("chain") owns every row of W (each CTA a contiguous block of
 //    ceil(N / 16) rows): each of its row threads keeps
 //    RPT rows of the current tile in registers and finishes the tile's
 //    columns one after another; the norm of each column is reduced across
-//    the cluster through distributed shared memory (as in chain.cu: warp 0 of
-//    every CTA exchanges the CTA partials with st.async + mbarrier
-//    transaction counts, and adds the 16 partials in a fixed order).
+//    the cluster through distributed shared memory (warp 0 of every CTA
+//    sends the CTA partial to every CTA with st.async, completing the
+//    transaction count of that column's own mbarrier there, and every warp
+//    adds the 16 partials in a fixed order).
 //  * the other clusters ("workers") compute the base of each tile,
 //      Y[v, c] = P[v, c] - sum_{j < lo - 16} Q[j][c] W[v, j](new)
 //                        - sum_{j >= hi} Q[j][c] W[v, j](old)
@@ -25,10 +28,18 @@
 //    while the chain is still on tile tau - 1.  The chain adds the previous
 //    tile's contribution itself (its own rows, 16 x 16 per row), right after
 //    finishing that tile.
-// Hand-off through global memory: base_ready[tau] counts the workers that
-// wrote their rows of Y for tile tau; chain_done[tau] counts the chain CTAs
-// that stored their rows of tile tau of W.  Release/acquire ordering, and every wait is
-// bounded by the global timer (ST_TIMEOUT on expiry).
+// Hand-off through global memory.  The rows are cut into nb blocks (one per
+// worker CTA); block (tau, w) of a tile base is computed by whoever claims
+// it first (atomic compare-and-swap on its state word): normally worker w,
+// which claims it as soon as the chain has published tile tau - 2
+// (chain_done[tau]); when the chain reaches tile tau it claims every block
+// still unclaimed and computes it itself, with the same arithmetic in the
+// same order.  base_done[tau] counts finished blocks.  So the chain only ever
+// waits for blocks claimed by a CTA that is running and needs nothing more to
+// finish them, and a worker that finds the chain not yet running leaves its
+// remaining blocks to it: the update completes whatever subset of the
+// clusters is resident at a time.  Release/acquire ordering, and every wait
+// is bounded by the global timer (ST_TIMEOUT on expiry).
 #include <algorithm>
 
 #include "devutil.cuh"
@@ -41,6 +52,7 @@ constexpr int WT = kRowTile;        // tile width (16)
 constexpr int WNT = 512;            // threads per CTA
 constexpr int WNR = WNT - 32;       // row threads of a chain CTA
 constexpr int WMAXCL = 16;
+constexpr int WMAXNB = 128;         // blocks per tile (worker CTAs: at most 8 clusters of 16)
 
 struct WParams {
   float* X;            // N x Kp, old on entry, new on exit
@@ -50,11 +62,15 @@ struct WParams {
   int N, K, Kp;
   float eps;
   int* status;
-  int* sync;           // [0, nt): base_ready, [nt, 2 nt): chain_done
+  int* sync;           // hand-off words, w_sync_ints(K) ints (layout: sync_* below)
   int cl;              // CTAs per cluster (chain cluster size)
   int worker_rows;     // rows per worker pass (4 lanes per row)
   int chain_rows;      // rows per chain CTA, ceil(N / cl): CTA rank owns [rank * chain_rows, ...)
+  int nb;              // row blocks per tile base: block w = rows [w * per, min(N, (w + 1) * per))
+  int per;
   const float* pre0;   // non-null: Y's first tile + pre0 (N x 16) hold tile 0's base less P (formed before the launch)
+  unsigned long long wait_ns;  // limit of every wait
+  int extra_arrivals;  // added to the chain_done count the workers wait for (tests of the timeout path; 0)
 };
 
 __device__ __forceinline__ unsigned cluster_id_x() {
@@ -63,14 +79,35 @@ __device__ __forceinline__ unsigned cluster_id_x() {
   return r;
 }
 
-// Hand-off flags live one per 128-byte line (kSyncStride ints apart), so the
-// workers' polling and the chain's release do not share a line.
+// Hand-off counters live one per 128-byte line (kSyncStride ints apart), so
+// the workers' polling and the chain's release do not share a line:
+// line 0 counts the chain CTAs that started, lines 1 .. nt the chain CTAs
+// that stored tile tau (chain_done), lines nt + 1 .. 2 nt the finished blocks
+// of tile tau's base (base_done); then nt x WMAXNB block states (0 free,
+// 1 claimed).
 constexpr int kSyncStride = 32;
+__device__ __forceinline__ int* sync_started(const WParams& p) { return p.sync; }
+__device__ __forceinline__ int* sync_chain_done(const WParams& p, int nt, int tau) {
+  return p.sync + (1 + tau) * kSyncStride;
+}
+__device__ __forceinline__ int* sync_base_done(const WParams& p, int nt, int tau) {
+  return p.sync + (1 + nt + tau) * kSyncStride;
+}
+__device__ __forceinline__ int* sync_state(const WParams& p, int nt, int tau, int w) {
+  return p.sync + (1 + 2 * nt) * kSyncStride + tau * WMAXNB + w;
+}
 
-// Bounded spin on a global counter with exponential backoff (32 ns .. 512 ns
-// between polls, so that many waiting CTAs do not keep the line's L2 slice
-// busy); returns false on timeout.
-__device__ bool wait_counter(const int* p, int target, int* status) {
+// A worker that finds the chain cluster not yet running waits this long for
+// it before leaving its remaining blocks to the chain.
+constexpr unsigned long long kGiveUpNs = 50ull * 1000ull;
+
+// Bounded spin with exponential backoff (32 ns .. 512 ns between polls, so
+// that many waiting CTAs do not keep the line's L2 slice busy) until *p >=
+// target.  Returns 1 when reached, 0 when the wait ran out (ST_TIMEOUT set),
+// 2 when `started` (if given) showed fewer than `need` CTAs after kGiveUpNs
+// (no error: the caller leaves the work to those CTAs).
+__device__ int wait_count(const int* p, int target, const WParams& prm, const int* started = nullptr,
+                          int need = 0) {
   unsigned long long t0 = 0;
   unsigned polls = 0;
   unsigned sleep_ns = 32;
@@ -79,14 +116,114 @@ __device__ bool wait_counter(const int* p, int target, int* status) {
     if (sleep_ns < 512) sleep_ns <<= 1;
     if ((++polls & 15u) == 0) {
       const unsigned long long now = global_ns();
-      if (t0 == 0) t0 = now;
-      else if (now - t0 > kWaitLimitNs) {
-        atomicOr(status, ST_TIMEOUT);
-        return false;
+      if (t0 == 0) {
+        t0 = now;
+      } else {
+        const unsigned long long el = now - t0;
+        if (started && el > kGiveUpNs && ld_acquire_gpu(started) < need) return 2;
+        if (el > prm.wait_ns) {
+          atomicOr(prm.status, ST_TIMEOUT);
+          return 0;
+        }
       }
     }
   }
+  return 1;
+}
+
+// Bounded wait for the phase `parity` of a CTA-local mbarrier (bulk copies).
+__device__ bool wait_bar_cta(unsigned bar, unsigned parity, unsigned long long limit) {
+  unsigned long long t0 = 0;
+  unsigned polls = 0;
+  while (!mbar_try_wait_cta(bar, parity)) {
+    if ((++polls & 63u) == 0) {
+      const unsigned long long now = global_ns();
+      if (t0 == 0) t0 = now;
+      else if (now - t0 > limit) return false;
+    }
+  }
   return true;
+}
+
+// Bounded wait for the phase `parity` of a CTA's mbarrier that remote CTAs
+// of the cluster complete (the column partials).
+__device__ bool wait_bar_cluster(unsigned bar, unsigned parity, unsigned long long limit) {
+  unsigned long long t0 = 0;
+  unsigned polls = 0;
+  while (!mbar_try_wait(bar, parity)) {
+    if ((++polls & 31u) == 0) {
+      const unsigned long long now = global_ns();
+      if (t0 == 0) t0 = now;
+      else if (now - t0 > limit) return false;
+    }
+  }
+  return true;
+}
+
+// --------------------------------------------------------------------------
+// One row of a tile base from global memory (the chain's path for blocks no
+// worker claimed).  The operations and their order are those of the worker
+// below (Gc[j][c] = Q[j][lo + c], zero past K; blocks of WT terms folded with
+// comp_fold; the in-tile old terms last), so either path gives the same bits.
+// --------------------------------------------------------------------------
+__device__ __forceinline__ void base_row_global(const WParams& p, int v, int lo, int hi, int new_end) {
+  const float* xr = p.X + (int64_t)v * p.Kp;
+  auto gq = [&](int j, int c) -> float {
+    return (j < p.K && lo + c < p.K) ? __ldg(p.Q + (int64_t)j * p.Kp + lo + c) : 0.f;
+  };
+  float acc[WT], cmp[WT], blk[WT];
+#pragma unroll
+  for (int c = 0; c < WT; ++c) {
+    acc[c] = lo + c < hi ? __ldg(p.P + (int64_t)v * p.Kp + lo + c) : 0.f;
+    cmp[c] = blk[c] = 0.f;
+  }
+  auto step = [&](int j) {
+    const float4 x4 = *reinterpret_cast<const float4*>(xr + j);
+    const float xs[4] = {x4.x, x4.y, x4.z, x4.w};
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+#pragma unroll
+      for (int c = 0; c < WT; ++c) blk[c] = fmaf(gq(j + u, c), xs[u], blk[c]);
+  };
+  auto fold = [&]() {
+#pragma unroll
+    for (int c = 0; c < WT; ++c) comp_fold(acc[c], cmp[c], blk[c]);
+  };
+  auto outside = [&](int j0, int j1) {
+    int jb = j0;
+#pragma unroll 1
+    for (; jb + WT <= j1; jb += WT) {
+#pragma unroll 1
+      for (int jj = 0; jj < WT; jj += 4) step(jb + jj);
+      fold();
+    }
+    if (jb < j1) {
+#pragma unroll 1
+      for (int j = jb; j < j1; j += 4) step(j);
+      fold();
+    }
+  };
+  outside(0, new_end);
+  outside(lo + WT < p.Kp ? lo + WT : p.Kp, p.Kp);
+  float xo[WT];
+#pragma unroll
+  for (int q = 0; q < WT / 4; ++q) {
+    float4 t = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (lo + 4 * q < p.Kp) t = *reinterpret_cast<const float4*>(xr + lo + 4 * q);
+    xo[4 * q] = t.x; xo[4 * q + 1] = t.y; xo[4 * q + 2] = t.z; xo[4 * q + 3] = t.w;
+  }
+#pragma unroll
+  for (int c = 0; c < WT; ++c) acc[c] += cmp[c];
+#pragma unroll
+  for (int j = 1; j < WT; ++j) {
+#pragma unroll
+    for (int c = 0; c < WT; ++c)
+      if (j > c) acc[c] = fmaf(-gq(lo + j, c), xo[j], acc[c]);
+  }
+  float* yr = p.Y + (int64_t)v * p.Kp;
+#pragma unroll
+  for (int c = 0; c < WT; ++c)
+    if (lo + c < hi) yr[lo + c] = acc[c];
 }
 
 // --------------------------------------------------------------------------
@@ -97,40 +234,48 @@ __device__ bool wait_counter(const int* p, int target, int* status) {
 // Kp >= 192, where the shared-memory loads bound the workers); each row's
 // arithmetic is the same either way.
 template <int WR>
-__device__ void worker_role(const WParams& p, char* smem, int wid, int n_workers) {
+__device__ void worker_role(const WParams& p, char* smem, int wid) {
   const int nt = (p.K + WT - 1) / WT;
   const int Kr = (p.Kp + WT - 1) / WT * WT;
   const int ldx = p.Kp + 4;
   float* Gc = reinterpret_cast<float*>(smem);                 // Kr x WT
   float* Xs = Gc + Kr * WT;                                   // worker_rows x ldx
   __shared__ __align__(8) unsigned long long bar;
+  __shared__ int s_go[2];
   const int tid = threadIdx.x;
   const int sub = tid & 3;
   const int rl = tid >> 2;
   const int RB = p.worker_rows;
-  // This worker's rows: an equal contiguous share [wbeg, wend), in passes of
-  // RB rows (rather than RB-row blocks dealt round-robin, which left some
-  // workers a whole block more than others: text-like K = 240 W update
-  // 513 -> 421 us, K = 320 868 -> 688 us).
-  const int per = (p.N + n_workers - 1) / n_workers;
-  const int wbeg = min(p.N, wid * per), wend = min(p.N, wbeg + per);
+  // This worker's block: an equal contiguous share [wbeg, wend) of the rows,
+  // in passes of RB rows (rather than RB-row blocks dealt round-robin, which
+  // left some workers a whole block more than others: text-like K = 240 W
+  // update 513 -> 421 us, K = 320 868 -> 688 us).
+  if (wid >= p.nb) return;                                    // no rows (small N)
+  const int wbeg = wid * p.per, wend = min(p.N, wbeg + p.per);
   if (tid == 0) {
     mbar_init(smem_u32(&bar), 1);
     fence_mbar_init();
   }
   __syncthreads();
   unsigned phase = 0;
-  bool dead = false;
   for (int tau = 0; tau < nt; ++tau) {
+    if (tau == 0 && p.pre0) continue;                         // tile 0's base was formed before the launch
     const int lo = tau * WT, hi = min(p.K, lo + WT);
     const int new_end = tau >= 1 ? lo - WT : 0;
+    // go: 1 = this worker computes block (tau, wid); 2 = the chain claimed
+    // it; 0 = leave this and every later block to the chain.
     if (tid == 0) {
-      if (tau >= 2 && !dead) {
-        if (!wait_counter(p.sync + (nt + tau - 2) * kSyncStride, p.cl, p.status)) dead = true;
-      }
+      int go = 1;
+      if (tau >= 2)
+        go = wait_count(sync_chain_done(p, nt, tau - 2), p.cl + p.extra_arrivals, p, sync_started(p), p.cl) == 1;
+      if (go) go = atomicCAS(sync_state(p, nt, tau, wid), 0, 1) == 0 ? 1 : 2;
       fence_proxy_async_global();
+      s_go[tau & 1] = go;
     }
     __syncthreads();
+    const int go = s_go[tau & 1];
+    if (go == 0) break;
+    if (go == 2) continue;
     // G block of this tile: Gc[j * WT + c] = Q[j][lo + c].
     for (int base = tid; base < Kr * WT; base += 8 * WNT) {
       float v[8];
@@ -146,7 +291,7 @@ __device__ void worker_role(const WParams& p, char* smem, int wid, int n_workers
         if (e < Kr * WT) Gc[e] = v[u];
       }
     }
-    for (int row0 = (tau == 0 && p.pre0) ? wend : wbeg; row0 < wend; row0 += RB) {
+    for (int row0 = wbeg; row0 < wend; row0 += RB) {
       const int nrows = min(RB, wend - row0);
       __syncthreads();                                        // Gc staged; Xs free
       if (tid == 0) {
@@ -158,21 +303,13 @@ __device__ void worker_role(const WParams& p, char* smem, int wid, int n_workers
         bulk_g2s(smem_u32(Xs + tid * ldx), p.X + (int64_t)(row0 + tid) * p.Kp, (unsigned)p.Kp * 4u,
                  smem_u32(&bar));
       }
-      {
-        unsigned long long t0 = 0;
-        unsigned polls = 0;
-        while (!dead && !mbar_try_wait_cta(smem_u32(&bar), phase)) {
-          if ((++polls & 63u) == 0) {
-            const unsigned long long now = global_ns();
-            if (t0 == 0) t0 = now;
-            else if (now - t0 > kWaitLimitNs) {
-              atomicOr(p.status, ST_TIMEOUT);
-              dead = true;
-            }
-          }
-        }
-        phase ^= 1u;
+      // Bounded; on expiry the copies may still be in flight, so wait for
+      // them once more (bounded too) before the buffer is used or left.
+      if (!wait_bar_cta(smem_u32(&bar), phase, p.wait_ns)) {
+        if (tid == 0) atomicOr(p.status, ST_TIMEOUT);
+        wait_bar_cta(smem_u32(&bar), phase, p.wait_ns);
       }
+      phase ^= 1u;
       const int half = WR == 1 ? nrows : (nrows + 1) / 2;  // groups with a row
       if (rl < half) {
         int lr[WR];
@@ -273,103 +410,183 @@ __device__ void worker_role(const WParams& p, char* smem, int wid, int n_workers
         }
       }
     }
+    // A claimed block is always published (even after a timed-out copy), so
+    // the chain never waits for it in vain.
     __syncthreads();
-    if (tid == 0) red_release_add_gpu(p.sync + tau * kSyncStride, 1);
+    if (tid == 0) red_release_add_gpu(sync_base_done(p, nt, tau), 1);
   }
-  if (__syncthreads_or(dead ? 1 : 0)) drain_grace();   // bulk copies still in flight
 }
 
 // --------------------------------------------------------------------------
 // Chain role: the column chain over all tiles.
 // --------------------------------------------------------------------------
 template <int RPT>
-__device__ void chain_role(const WParams& p, char* smem, int n_workers) {
+__device__ void chain_role(const WParams& p, char* smem) {
   constexpr int NW = WNT / 32;
+  // The staging buffer, then one mbarrier per column (K of them, each
+  // completing once: no re-arming, so a partial that arrives late still
+  // lands on its own column's barrier).
   float* st = reinterpret_cast<float*>(smem);                 // RPT x WT x (WNR + 1)
+  unsigned long long* cbar = reinterpret_cast<unsigned long long*>(smem + sizeof(float) * RPT * WT * (WNR + 1));
   __shared__ float Gs[2][WT][WT];                             // Q[tile][tile], zero beyond the tile
   __shared__ __align__(16) float Gn[WT][WT];                  // Q[tile][next tile]
   __shared__ float wpart[NW];
   __shared__ float cpart[2][WMAXCL];
-  __shared__ __align__(8) unsigned long long mbar[2];
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int tr = tid - 32;
   const unsigned rank = cluster_ctarank();
   const int CL = p.cl;
-  // This CTA's rows: the contiguous block [row0, row0 + nloc); local row
-  // li = i * WNR + tr belongs to row thread tr, register row i.
-  const int row0 = (int)rank * p.chain_rows;
-  const int nloc = max(0, min(p.chain_rows, p.N - row0));
   const int nt = (p.K + WT - 1) / WT;
-  auto sidx = [](int i, int t, int r) { return (i * WT + t) * (WNR + 1) + r; };
 
-  if (tid == 0) {
-    mbar_init(smem_u32(&mbar[0]), 1);
-    mbar_init(smem_u32(&mbar[1]), 1);
-    mbar_arrive_expect_tx(smem_u32(&mbar[0]), CL * 4);
-    if (p.K > 1) mbar_arrive_expect_tx(smem_u32(&mbar[1]), CL * 4);
-    fence_mbar_init();
+  // Column g's barrier expects the CL partials of column g (4 bytes each).
+  for (int g = tid; g < p.K; g += WNT) {
+    mbar_init(smem_u32(&cbar[g]), 1);
+    mbar_arrive_expect_tx(smem_u32(&cbar[g]), CL * 4);
   }
+  fence_mbar_init();
   __syncthreads();
-  cluster_sync_all();
+  cluster_sync_all();                                          // every barrier initialised before any send
+  if (tid == 0) red_release_add_gpu(sync_started(p), 1);
 
-  bool valid[RPT];
+  // The two roles of a chain CTA run separate code (their block barriers
+  // match one for one): warp 0 exchanges the column partials and publishes
+  // the tiles, warps 1 .. NW-1 own the rows.  Keeping them apart leaves the
+  // row warps' column loop the whole register file.
+  if (warp == 0) {
+    for (int tau = 0; tau < nt; ++tau) {
+      const int lo = tau * WT, hi = min(p.K, lo + WT), Tw = hi - lo;
+      const unsigned cbar_tile = smem_u32(cbar + lo);
+      // Blocks of this tile's base that no worker has finished within
+      // kGiveUpNs and none has claimed (workers absent or behind): claim
+      // them (block w = rank + CL * lane) and compute them here, one row per
+      // lane.  The row warps wait for base_done meanwhile.
+      if (!(tau == 0 && p.pre0)) {
+        const int* bd = sync_base_done(p, nt, tau);
+        int need = 0;
+        if (lane == 0) {
+          const unsigned long long t0 = global_ns();
+          unsigned sleep_ns = 32;
+          need = ld_acquire_gpu(bd) < p.nb;
+          while (need && global_ns() - t0 < kGiveUpNs) {
+            __nanosleep(sleep_ns);
+            if (sleep_ns < 256) sleep_ns <<= 1;
+            need = ld_acquire_gpu(bd) < p.nb;
+          }
+        }
+        need = __shfl_sync(0xffffffffu, need, 0);
+        if (need) {
+          const int w = (int)rank + CL * lane;
+          const bool got = w < p.nb && atomicCAS(sync_state(p, nt, tau, w), 0, 1) == 0;
+          const unsigned m = __ballot_sync(0xffffffffu, got);
+          if (m) {
+            // These blocks read the new columns of tiles <= tau - 2, which
+            // every chain CTA has published by now; the acquire makes them
+            // visible to this warp.
+            if (lane == 0 && tau >= 2) wait_count(sync_chain_done(p, nt, tau - 2), CL, p);
+            __syncwarp();
+            const int ns = __popc(m);
+            for (int e = lane; e < ns * p.per; e += 32) {
+              const int i = e / p.per;
+              unsigned mm = m;
+              for (int k = 0; k < i; ++k) mm &= mm - 1;
+              const int v = ((int)rank + CL * (__ffs(mm) - 1)) * p.per + e % p.per;
+              if (v < p.N) base_row_global(p, v, lo, hi, tau >= 1 ? lo - WT : 0);
+            }
+            __threadfence();
+            __syncwarp();
+            if (lane == 0) red_release_add_gpu(sync_base_done(p, nt, tau), ns);
+          }
+        }
+      }
+      // Per column: the row warps' partials (block barrier), their sum sent
+      // to every CTA of the cluster.  Sent unconditionally (also after a
+      // timed-out wait elsewhere), so every column's barrier in every CTA
+      // completes and no partial is in flight at exit.  This warp does not
+      // need the norm, so it does not wait for the partials.
 #pragma unroll
-  for (int i = 0; i < RPT; ++i) valid[i] = warp > 0 && i * WNR + tr < nloc;
-  // y[i][0..15]: the tile's columns; between tiles y holds the previous
-  // tile's contribution to the next one (z), subtracted from the base.
-  float y[RPT][WT];
+      for (int t = 0; t < WT; ++t) {
+        if (t >= Tw) break;
+        const int b = t & 1;                                   // partial slot (lo is even)
+        __syncthreads();
+        float v = (lane >= 1 && lane < NW) ? wpart[lane] : 0.f;
+        v = warp_sum(v);
+        if (lane < CL) {
+          const unsigned raddr = mapa_u32(smem_u32(&cpart[b][rank]), lane);
+          const unsigned rbar = mapa_u32(cbar_tile + 8u * t, lane);
+          st_async_f32(raddr, v, rbar);
+        }
+      }
+      // Every CTA publishes its own rows (the workers wait for all CL): the
+      // block barrier after the row warps' stores, then one release count
+      // (cumulative), with no cluster barrier, so no CTA waits for the
+      // slowest one here.  The workers read tile tau only for the bases of
+      // tiles >= tau + 2.
+      __syncthreads();
+      if (lane == 0 && tau + 2 < nt) red_release_add_gpu(sync_chain_done(p, nt, tau), 1);
+    }
+  } else {
+    const int tr = tid - 32;
+    // This CTA's rows: the contiguous block [row0, row0 + nloc); local row
+    // li = i * WNR + tr belongs to row thread tr, register row i.
+    const int row0 = (int)rank * p.chain_rows;
+    const int nloc = max(0, min(p.chain_rows, p.N - row0));
+    auto sidx = [](int i, int t, int r) { return (i * WT + t) * (WNR + 1) + r; };
+    bool valid[RPT];
 #pragma unroll
-  for (int i = 0; i < RPT; ++i)
+    for (int i = 0; i < RPT; ++i) valid[i] = i * WNR + tr < nloc;
+    // y[i][0..15]: the tile's columns; between tiles y holds the previous
+    // tile's contribution to the next one (z), subtracted from the base.
+    float y[RPT][WT];
 #pragma unroll
-    for (int s = 0; s < WT; ++s) y[i][s] = 0.f;
+    for (int i = 0; i < RPT; ++i)
+#pragma unroll
+      for (int s = 0; s < WT; ++s) y[i][s] = 0.f;
 
-  // Barrier of the row warps only (warps 1 .. NW-1): warp 0 may meanwhile be
-  // publishing the previous tile.  The compiler's named-barrier intrinsic
-  // (not inline asm), after an explicit warp reconvergence: a hardware
-  // barrier counts a whole warp as arrived when any of its lanes executes
-  // it, so a warp split by a divergent wait (thread 32 polls the base
-  // flag) would otherwise complete a barrier without its waiting lane.
-  auto row_bar = []() {
-    __syncwarp();
-    __barrier_sync_count(1, WNR);
-  };
-  // The Q blocks a tile needs are copied asynchronously by the row threads
-  // (cp.async, zero-filled outside the blocks) one tile ahead, off the tile
-  // transitions: Gs of tile tq into Gs[tq & 1]; Gn of tile tq.
-  auto fetch_gs = [&](int tq) {
-    const int qlo = tq * WT, qw = min(p.K, qlo + WT) - qlo;
-    for (int e = tr; e < WT * WT; e += WNR) {
-      const int i = e / WT, j = e % WT;
-      const bool in = i < qw && j < qw;
-      cp_async4(&Gs[tq & 1][i][j], p.Q + (in ? (int64_t)(qlo + i) * p.Kp + qlo + j : 0), in);
-    }
-  };
-  auto fetch_gn = [&](int tq) {
-    const int qlo = tq * WT, qw = min(p.K, qlo + WT) - qlo;
-    const int nlo = qlo + qw, nw = min(p.K, nlo + WT) - nlo;
-    for (int e = tr; e < WT * WT; e += WNR) {
-      const int i = e / WT, j = e % WT;
-      const bool in = i < qw && j < nw;
-      cp_async4(&Gn[i][j], p.Q + (in ? (int64_t)(qlo + i) * p.Kp + nlo + j : 0), in);
-    }
-  };
-  if (warp > 0) {
+    // Barrier of the row warps only.  The compiler's named-barrier intrinsic
+    // (not inline asm), after an explicit warp reconvergence: a hardware
+    // barrier counts a whole warp as arrived when any of its lanes executes
+    // it, so a warp split by a divergent wait (thread 32 polls the base
+    // flag) would otherwise complete a barrier without its waiting lane.
+    auto row_bar = []() {
+      __syncwarp();
+      __barrier_sync_count(1, WNR);
+    };
+    // The Q blocks a tile needs are copied asynchronously (cp.async,
+    // zero-filled outside the blocks) one tile ahead, off the tile
+    // transitions: Gs of tile tq into Gs[tq & 1]; Gn of tile tq.
+    auto fetch_gs = [&](int tq) {
+      const int qlo = tq * WT, qw = min(p.K, qlo + WT) - qlo;
+      for (int e = tr; e < WT * WT; e += WNR) {
+        const int i = e / WT, j = e % WT;
+        const bool in = i < qw && j < qw;
+        cp_async4(&Gs[tq & 1][i][j], p.Q + (in ? (int64_t)(qlo + i) * p.Kp + qlo + j : 0), in);
+      }
+    };
+    auto fetch_gn = [&](int tq) {
+      const int qlo = tq * WT, qw = min(p.K, qlo + WT) - qlo;
+      const int nlo = qlo + qw, nw = min(p.K, nlo + WT) - nlo;
+      for (int e = tr; e < WT * WT; e += WNR) {
+        const int i = e / WT, j = e % WT;
+        const bool in = i < qw && j < nw;
+        cp_async4(&Gn[i][j], p.Q + (in ? (int64_t)(qlo + i) * p.Kp + nlo + j : 0), in);
+      }
+    };
     fetch_gs(0);
     cp_async_commit();
-  }
 
-  bool dead = false;
-  int gcol = 0;                                                // global column index
-  for (int tau = 0; tau < nt; ++tau) {
-    const int lo = tau * WT, hi = min(p.K, lo + WT), Tw = hi - lo;
-    const float(*G)[WT] = Gs[tau & 1];
-    // The row warps start the tile on their own; warp 0 joins at the first
-    // column's barrier.
-    if (warp > 0) {
-      cp_async_wait_all();                                       // Gs of this tile (issued a tile ahead)
-      if (tid == 32 && !dead) {
-        if (!wait_counter(p.sync + tau * kSyncStride, n_workers, p.status)) dead = true;
+    bool dead = false;       // a column exchange timed out: skip later exchange waits
+    bool base_dead = false;  // a base wait timed out (thread 32): skip later base waits
+    for (int tau = 0; tau < nt; ++tau) {
+      const int lo = tau * WT, hi = min(p.K, lo + WT), Tw = hi - lo;
+      const float(*G)[WT] = Gs[tau & 1];
+      const unsigned cbar_tile = smem_u32(cbar + lo);             // column lo + t: cbar_tile + 8 t
+      cp_async_wait_all();                                         // Gs of this tile (issued a tile ahead)
+      // Every block of this tile's base is claimed by a worker that is running
+      // and needs nothing more to finish it, or by warp 0 of a chain CTA.  (A
+      // timed-out wait is recorded in the status word; later tiles do not
+      // wait again.)
+      if (tid == 32 && !(tau == 0 && p.pre0) && !base_dead) {
+        if (wait_count(sync_base_done(p, nt, tau), p.nb, p) != 1) base_dead = true;
       }
       row_bar();
       // Gn of this tile and Gs of the next: the buffers are free (tile tau - 1
@@ -380,51 +597,53 @@ __device__ void chain_role(const WParams& p, char* smem, int n_workers) {
       // Base of the tile for this CTA's rows (4 lanes per row, 16 bytes each),
       // staged through st (8 loads in flight per thread); each row thread
       // then takes its own rows.
-      constexpr int SU = 8;
-      const int total = nloc * 4;
-      for (int base = tr; base < total; base += SU * WNR) {
-        float4 v[SU];
+      {
+        constexpr int SU = 8;
+        const int total = nloc * 4;
+        for (int base = tr; base < total; base += SU * WNR) {
+          float4 v[SU];
 #pragma unroll
-        for (int u = 0; u < SU; ++u) {
-          const int e = base + u * WNR;
-          const int row = row0 + (e >> 2), q = e & 3;
-          v[u] = make_float4(0.f, 0.f, 0.f, 0.f);
-          if (e >= total) continue;
-          const int64_t off = (int64_t)row * p.Kp + lo + 4 * q;
-          const bool pre = tau == 0 && p.pre0 != nullptr;
-          if (4 * q + 3 < Tw) {
-            v[u] = *reinterpret_cast<const float4*>(p.Y + off);
-            if (pre) {                                          // tile 0's base less P: add P here
-              // P and the early base cancel: P + hi first (nearly exact),
-              // then the early base's compensation.
-              const float4 pp = *reinterpret_cast<const float4*>(p.P + off);
-              const float4 cc = *reinterpret_cast<const float4*>(p.pre0 + (int64_t)row * WT + 4 * q);
-              v[u] = make_float4((pp.x + v[u].x) + cc.x, (pp.y + v[u].y) + cc.y, (pp.z + v[u].z) + cc.z,
-                                 (pp.w + v[u].w) + cc.w);
-            }
-          } else {
-            float w[4];
-#pragma unroll
-            for (int j = 0; j < 4; ++j) {
-              w[j] = 0.f;
-              if (4 * q + j < Tw) {
-                w[j] = p.Y[off + j];
-                if (pre) w[j] = (p.P[off + j] + w[j]) + p.pre0[(int64_t)row * WT + 4 * q + j];
+          for (int u = 0; u < SU; ++u) {
+            const int e = base + u * WNR;
+            const int row = row0 + (e >> 2), q = e & 3;
+            v[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (e >= total) continue;
+            const int64_t off = (int64_t)row * p.Kp + lo + 4 * q;
+            const bool pre = tau == 0 && p.pre0 != nullptr;
+            if (4 * q + 3 < Tw) {
+              v[u] = *reinterpret_cast<const float4*>(p.Y + off);
+              if (pre) {                                          // tile 0's base less P: add P here
+                // P and the early base cancel: P + hi first (nearly exact),
+                // then the early base's compensation.
+                const float4 pp = *reinterpret_cast<const float4*>(p.P + off);
+                const float4 cc = *reinterpret_cast<const float4*>(p.pre0 + (int64_t)row * WT + 4 * q);
+                v[u] = make_float4((pp.x + v[u].x) + cc.x, (pp.y + v[u].y) + cc.y, (pp.z + v[u].z) + cc.z,
+                                   (pp.w + v[u].w) + cc.w);
               }
-            }
-            v[u] = make_float4(w[0], w[1], w[2], w[3]);
-          }
-        }
+            } else {
+              float w[4];
 #pragma unroll
-        for (int u = 0; u < SU; ++u) {
-          const int e = base + u * WNR;
-          if (e >= total) continue;
-          const int li = e >> 2, q = e & 3;
-          const int i = li / WNR, r = li - i * WNR;
-          st[sidx(i, 4 * q, r)] = v[u].x;
-          st[sidx(i, 4 * q + 1, r)] = v[u].y;
-          st[sidx(i, 4 * q + 2, r)] = v[u].z;
-          st[sidx(i, 4 * q + 3, r)] = v[u].w;
+              for (int j = 0; j < 4; ++j) {
+                w[j] = 0.f;
+                if (4 * q + j < Tw) {
+                  w[j] = p.Y[off + j];
+                  if (pre) w[j] = (p.P[off + j] + w[j]) + p.pre0[(int64_t)row * WT + 4 * q + j];
+                }
+              }
+              v[u] = make_float4(w[0], w[1], w[2], w[3]);
+            }
+          }
+#pragma unroll
+          for (int u = 0; u < SU; ++u) {
+            const int e = base + u * WNR;
+            if (e >= total) continue;
+            const int li = e >> 2, q = e & 3;
+            const int i = li / WNR, r = li - i * WNR;
+            st[sidx(i, 4 * q, r)] = v[u].x;
+            st[sidx(i, 4 * q + 1, r)] = v[u].y;
+            st[sidx(i, 4 * q + 2, r)] = v[u].z;
+            st[sidx(i, 4 * q + 3, r)] = v[u].w;
+          }
         }
       }
       row_bar();
@@ -432,21 +651,19 @@ __device__ void chain_role(const WParams& p, char* smem, int n_workers) {
       for (int i = 0; i < RPT; ++i)
 #pragma unroll
         for (int t = 0; t < WT; ++t) y[i][t] = valid[i] ? st[sidx(i, t, tr)] - y[i][t] : 0.f;
-    }
 
-    // Columns t = 0 .. Tw-1 of the tile, unrolled so that every register slot
-    // is static: column t is finished, the previous column's contribution is
-    // pushed into columns t+1.. (column t already has it), and every fourth
-    // column the last four finished ones go to global memory, off the
-    // critical path.
-    float xp[RPT];
+      // Columns t = 0 .. Tw-1 of the tile, unrolled so that every register
+      // slot is static: column t is finished, the previous column's
+      // contribution is pushed into columns t+1.. (column t already has it),
+      // and every fourth column the last four finished ones go to global
+      // memory, off the critical path.
+      float xp[RPT];
 #pragma unroll
-    for (int i = 0; i < RPT; ++i) xp[i] = 0.f;
+      for (int i = 0; i < RPT; ++i) xp[i] = 0.f;
 #pragma unroll
-    for (int t = 0; t < WT; ++t) {
-      if (t >= Tw) break;
-      const int b = gcol & 1;
-      if (warp > 0) {
+      for (int t = 0; t < WT; ++t) {
+        if (t >= Tw) break;
+        const int b = t & 1;                                     // partial slot (lo is even)
         // The clamped column goes to this thread's slots of st (normalised
         // there after the exchange), keeping registers free across the wait.
         float ss = 0.f;
@@ -458,9 +675,7 @@ __device__ void chain_role(const WParams& p, char* smem, int n_workers) {
         }
         ss = warp_sum(ss);
         if (lane == 0) wpart[warp] = ss;
-      }
-      __syncthreads();
-      if (warp > 0) {
+        __syncthreads();
         if (t > 0) {
 #pragma unroll
           for (int s2 = t + 1; s2 < WT; ++s2) {
@@ -478,51 +693,38 @@ __device__ void chain_role(const WParams& p, char* smem, int n_workers) {
             *reinterpret_cast<float4*>(p.X + (int64_t)(row0 + i * WNR + tr) * p.Kp + lo + t - 4) = v;
           }
         }
-      } else {
-        float v = (lane >= 1 && lane < NW) ? wpart[lane] : 0.f;
-        v = warp_sum(v);
-        if (lane < CL && !dead) {
-          const unsigned raddr = mapa_u32(smem_u32(&cpart[b][rank]), lane);
-          const unsigned rbar = mapa_u32(smem_u32(&mbar[b]), lane);
-          st_async_f32(raddr, v, rbar);
-        }
-      }
-      // Every warp waits for the column's CL partials itself and adds them in
-      // the same fixed order (no second block barrier): the partials of
-      // column gcol + 2 cannot arrive before every warp here has sent
-      // column gcol + 1, which it does only after reading these.
-      if (!dead) {
-        const unsigned bar = smem_u32(&mbar[b]);
-        const unsigned parity = (gcol >> 1) & 1;
-        unsigned long long t0 = 0;
-        unsigned polls = 0;
-        while (!mbar_try_wait(bar, parity)) {
-          if ((++polls & 31u) == 0) {
-            const unsigned long long now = global_ns();
-            if (t0 == 0) {
-              t0 = now;
-            } else if (now - t0 > kWaitLimitNs) {
-              dead = true;
-              if (lane == 0) atomicOr(p.status, ST_TIMEOUT);
-              break;
+        // Every row warp waits for the column's CL partials itself and adds
+        // them in the same fixed order (no second block barrier): the
+        // partials of column lo + t + 2 cannot arrive before every warp here
+        // has passed the next column's block barrier, which it does only
+        // after reading these.
+        if (!dead) {
+          const unsigned bar = cbar_tile + 8u * t;
+          unsigned long long t0 = 0;
+          unsigned polls = 0;
+          while (!mbar_try_wait(bar, 0)) {
+            if ((++polls & 31u) == 0) {
+              const unsigned long long now = global_ns();
+              if (t0 == 0) {
+                t0 = now;
+              } else if (now - t0 > p.wait_ns) {
+                dead = true;
+                if (lane == 0) atomicOr(p.status, ST_TIMEOUT);
+                break;
+              }
             }
           }
         }
-      }
-      dead = __any_sync(0xffffffffu, dead);
-      // The CL partials summed by an xor butterfly over lanes 0..15 (lanes
-      // 16..31 mirror them): each step adds the same two operands in every
-      // lane it pairs, so every lane of every CTA gets the same squared norm.
-      float tot = (lane & 15) < CL ? cpart[b][lane & 15] : 0.f;
+        dead = __any_sync(0xffffffffu, dead);
+        // The CL partials summed by an xor butterfly over lanes 0..15 (lanes
+        // 16..31 mirror them): each step adds the same two operands in every
+        // lane it pairs, so every lane of every CTA gets the same squared
+        // norm.
+        float tot = (lane & 15) < CL ? cpart[b][lane & 15] : 0.f;
 #pragma unroll
-      for (int o = 8; o > 0; o >>= 1) tot += __shfl_xor_sync(0xffffffffu, tot, o);
-      const float inv = rsqrtf(tot);                           // 1 / ||column||
-      if (tid == 0) {
-        // Re-arm this parity for column gcol + 2 (before this warp's next send).
-        if (gcol + 2 < p.K && !dead) mbar_arrive_expect_tx(smem_u32(&mbar[b]), CL * 4);
-        if (rank == 0 && (!(tot > 0.f) || !(tot < INFINITY))) atomicOr(p.status, ST_NUMERIC);
-      }
-      if (warp > 0) {
+        for (int o = 8; o > 0; o >>= 1) tot += __shfl_xor_sync(0xffffffffu, tot, o);
+        const float inv = rsqrtf(tot);                           // 1 / ||column||
+        if (tid == 32 && rank == 0 && (!(tot > 0.f) || !(tot < INFINITY))) atomicOr(p.status, ST_NUMERIC);
         const float g1 = t + 1 < WT ? G[t][t + 1] : 0.f;
 #pragma unroll
         for (int i = 0; i < RPT; ++i) {
@@ -532,13 +734,11 @@ __device__ void chain_role(const WParams& p, char* smem, int n_workers) {
           xp[i] = x;
         }
       }
-      ++gcol;
-    }
-    // The columns not yet stored, then the tile is published (below), then
-    // the contribution of this tile to the next one, z = x_tile * Q[tile][next]
-    // for this CTA's rows (kept in y until the next base is loaded).
-    const int nlo = hi, nhi = min(p.K, nlo + WT), Tn = nhi - nlo;
-    if (warp > 0) {
+      // The columns not yet stored, then the tile is published (warp 0,
+      // after the block barrier), then the contribution of this tile to the
+      // next one, z = x_tile * Q[tile][next] for this CTA's rows (kept in y
+      // until the next base is loaded).
+      const int nlo = hi, nhi = min(p.K, nlo + WT), Tn = nhi - nlo;
       const int sdone = 4 * ((Tw - 1) / 4);                    // columns [0, sdone) already stored
 #pragma unroll
       for (int i = 0; i < RPT; ++i) {
@@ -551,15 +751,7 @@ __device__ void chain_role(const WParams& p, char* smem, int n_workers) {
           for (int c = sdone; c < Tw; ++c) dst[c] = st[sidx(i, c, tr)];
         }
       }
-    }
-    // Every CTA publishes its own rows (the workers wait for all CL): a
-    // block barrier, then one thread's release count (cumulative), with no
-    // cluster barrier, so no CTA waits for the slowest one here.  Warp 0
-    // publishes while the row warps compute z and start the next tile.  The
-    // workers read tile tau only for the bases of tiles >= tau + 2.
-    __syncthreads();
-    if (tid == 0 && tau + 2 < nt) red_release_add_gpu(p.sync + (nt + tau) * kSyncStride, 1);
-    if (warp > 0) {
+      __syncthreads();
       cp_async_wait_all();                                     // Gn of this tile, Gs of the next
       row_bar();
 #pragma unroll
@@ -587,23 +779,27 @@ __device__ void chain_role(const WParams& p, char* smem, int n_workers) {
       }
     }
   }
-  // A timed-out wait anywhere: let remote stores still in flight land before
-  // any CTA of the cluster leaves.
-  if (__syncthreads_or(dead ? 1 : 0)) drain_grace();
+  // Every CTA has sent every column's partial once it reaches the cluster
+  // barrier; each then waits (bounded) until all partials addressed to it
+  // have landed, so no remote store is in flight when the cluster leaves.
+  __syncthreads();
   cluster_sync_all();
+  for (int g = tid; g < p.K; g += WNT) {
+    if (!wait_bar_cluster(smem_u32(&cbar[g]), 0, p.wait_ns)) atomicOr(p.status, ST_TIMEOUT);
+  }
+  __syncthreads();
 }
 
 template <int RPT, int WR>
 __global__ void __launch_bounds__(WNT, 1) w_update_persistent_kernel(WParams p) {
   extern __shared__ __align__(16) char smem[];
   const unsigned cid = cluster_id_x();
-  const int n_workers = (int)gridDim.x - p.cl;
-  if (cid == 0) chain_role<RPT>(p, smem, n_workers);
-  else worker_role<WR>(p, smem, (int)blockIdx.x - p.cl, n_workers);
+  if (cid == 0) chain_role<RPT>(p, smem);
+  else worker_role<WR>(p, smem, (int)blockIdx.x - p.cl);
 }
 
 size_t persistent_smem(int rpt, int Kp, int worker_rows) {
-  const size_t chain = sizeof(float) * (size_t)rpt * WT * (WNR + 1);
+  const size_t chain = sizeof(unsigned long long) * (size_t)Kp + sizeof(float) * (size_t)rpt * WT * (WNR + 1);
   const size_t worker = sizeof(float) * ((size_t)(Kp + WT - 1) / WT * WT * WT + (size_t)worker_rows * (Kp + 4));
   return std::max(chain, worker);
 }
@@ -619,15 +815,14 @@ cudaError_t launch_persistent_t(const WParams& p, int n_clusters, size_t smem, c
   cfg.blockDim = dim3(WNT, 1, 1);
   cfg.dynamicSmemBytes = smem;
   cfg.stream = s;
-  cudaLaunchAttribute attr[2];
+  // An ordinary cluster launch (no co-residency of the clusters is assumed).
+  cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeClusterDimension;
   attr[0].val.clusterDim.x = p.cl;
   attr[0].val.clusterDim.y = 1;
   attr[0].val.clusterDim.z = 1;
-  attr[1].id = cudaLaunchAttributeCooperative;
-  attr[1].val.cooperative = 1;
   cfg.attrs = attr;
-  cfg.numAttrs = 2;
+  cfg.numAttrs = 1;
   return cudaLaunchKernelEx(&cfg, kern, p);
 }
 
@@ -670,7 +865,10 @@ int max_clusters(int rpt, int cl, size_t smem) {
 
 }  // namespace
 
-size_t w_sync_ints(int K) { return (size_t)2 * ((K + WT - 1) / WT) * kSyncStride; }
+size_t w_sync_ints(int K) {
+  const size_t nt = (size_t)(K + WT - 1) / WT;
+  return (1 + 2 * nt) * kSyncStride + nt * WMAXNB;
+}
 
 bool w_persistent_config(int N, int Kp, WPersistConfig* cfg) {
   for (int cl : {16, 8}) {
@@ -681,7 +879,7 @@ bool w_persistent_config(int N, int Kp, WPersistConfig* cfg) {
     // multiple of 8) as the shared-memory budget holds, so that at large K
     // most of the CTA's threads still have a row (K = 400: 120 rows, where
     // halving from 128 gave 64 and left half the threads idle).
-    constexpr size_t kBudget = 220 * 1024;
+    constexpr size_t kBudget = 216 * 1024;
     int worker_rows = WNT / 4;
     while (worker_rows > 16 && persistent_smem(rpt, Kp, worker_rows) > kBudget) worker_rows -= 8;
     const size_t smem = persistent_smem(rpt, Kp, worker_rows);
@@ -691,7 +889,7 @@ bool w_persistent_config(int N, int Kp, WPersistConfig* cfg) {
     cfg->cluster = cl;
     cfg->rpt = rpt;
     cfg->chain_rows = nrc;
-    cfg->n_clusters = std::min(nc, 9);
+    cfg->n_clusters = std::min(nc, 1 + WMAXNB / cl);
     cfg->worker_rows = worker_rows;
     cfg->worker_wr = Kp >= 192 ? 2 : 1;
     cfg->smem = smem;
@@ -702,10 +900,16 @@ bool w_persistent_config(int N, int Kp, WPersistConfig* cfg) {
 
 cudaError_t w_persistent_run(float* X, const float* P, const float* Q, float* Y, int N, int K, int Kp, float eps,
                              int* d_sync, int* d_status, const WPersistConfig& cfg, cudaStream_t s,
-                             const float* pre0) {
+                             const float* pre0, unsigned long long wait_ns, int extra_arrivals) {
+  if (N <= 0 || K <= 0) return cudaSuccess;
   cudaError_t e = cudaMemsetAsync(d_sync, 0, sizeof(int) * w_sync_ints(K), s);
   if (e != cudaSuccess) return e;
-  WParams p{X, P, Q, Y, N, K, Kp, eps, d_status, d_sync, cfg.cluster, cfg.worker_rows, cfg.chain_rows, pre0};
+  const int n_workers = (cfg.n_clusters - 1) * cfg.cluster;
+  if (n_workers < 1 || n_workers > WMAXNB) return cudaErrorInvalidValue;
+  const int per = (N + n_workers - 1) / n_workers;
+  const int nb = (N + per - 1) / per;
+  WParams p{X, P, Q, Y, N, K, Kp, eps, d_status, d_sync, cfg.cluster, cfg.worker_rows, (N + cfg.cluster - 1) / cfg.cluster,
+            nb, per, pre0, wait_ns ? wait_ns : kWaitLimitNs, extra_arrivals};
   const bool two = cfg.worker_wr == 2;
   switch (cfg.rpt) {
     case 1: return two ? launch_persistent_t<1, 2>(p, cfg.n_clusters, cfg.smem, s)

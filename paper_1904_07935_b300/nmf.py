@@ -60,6 +60,7 @@ _SIGS = {
     "nmf_get_buffer": ([_vp, _i32, _vp, _i64], _i32),
     "nmf_set_buffer": ([_vp, _i32, _vp, _i64], _i32),
     "nmf_query": ([_vp, ctypes.POINTER(_i32), ctypes.POINTER(_i32), ctypes.POINTER(_i32)], _i32),
+    "nmf_set_wait_limits": ([_vp, _i64, _i32], _i32),
     "nmf_profile": ([_vp, _i32, _vp], _i32),
     "nmf_iterate_alg1": ([_vp, _i32, _vp], _i32),
     "nmf_iterate_mu": ([_vp, _i32, _vp], _i32),
@@ -254,6 +255,12 @@ class Nmf:
         t, c, l = _i32(), _i32(), _i32()
         check(lib.nmf_query(self.h, ctypes.byref(t), ctypes.byref(c), ctypes.byref(l)), "nmf_query")
         return {"tile_T": t.value, "chain_ctas": c.value, "launches_per_iter": l.value}
+
+    def set_wait_limits(self, wait_ns=0, extra_arrivals=0):
+        """Limit of the W update's device waits (0: library default) and, for
+        tests of the failure path, extra chain arrivals the base-forming CTAs
+        wait for (include/nmf.h, nmf_set_wait_limits)."""
+        check(lib.nmf_set_wait_limits(self.h, int(wait_ns), int(extra_arrivals)), "nmf_set_wait_limits")
 
 
 def gemm(A, B, C, *, transA=False, prec=PREC_FP32, stream=None):

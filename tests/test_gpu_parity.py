@@ -362,7 +362,7 @@ def test_invalid_inputs_rejected(nmf):
 
 @pytest.mark.parametrize("K", [16, 37, 160])
 def test_w_update_persistent_and_multi_launch_agree_with_alg1(nmf, K):
-    """The persistent (one cooperative launch) and the per-tile multi-launch W
+    """The single-launch (chain cluster + base workers) and the per-tile W
     updates both match Alg. 1 on a ragged K."""
     V = 3000 if K < 100 else 9000
     prob = synth.planted_dense(V, 400, 8, 101 + K)
