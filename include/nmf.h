@@ -68,7 +68,8 @@ typedef enum { NMF_PREC_FP32 = 0, NMF_PREC_BF16 = 1 } nmf_precision;
  *   prec         NMF_PREC_FP32 (all FP32) or NMF_PREC_BF16 (dense A only:
  *                products A H^T, A^T W and the Gram matrices on the tensor
  *                cores with BF16 operands and FP32 accumulation; column
- *                updates and norms FP32; A is copied to BF16 once).
+ *                updates and norms FP32; A is copied once to a BF16 pair
+ *                A_hi + A_lo, see NMF_FLAG_BF16_SINGLE_A).
  *   stream       cudaStream_t to run on (NULL -> the context creates one).
  */
 typedef struct {
@@ -98,15 +99,26 @@ typedef struct {
  * to the tensor cores (3xTF32) anyway.  The BF16 precision form always uses
  * the tensor cores. */
 #define NMF_FLAG_TC_GRAMS 1
-/* Run the W update as separate launches per column tile instead of one
- * persistent cooperative launch (the default where the GPU supports it and
- * no CUDA tool such as a kernel profiler is injected into the process:
- * with CUDA_INJECTION64_PATH set the per-tile launches are always used). */
+/* Run the W update as separate launches per column tile instead of one launch
+ * holding the column chain and the tile-base workers (the default wherever a
+ * chain cluster of 16 or 8 CTAs and at least one worker cluster fit). */
 #define NMF_FLAG_MULTI_LAUNCH_W 2
 /* BF16 form (NMF_PREC_BF16): take the dense products A^T W and A H^T through
  * the SIMT-staged tensor-core kernel instead of the TMA-fed one (the default
- * where the driver exposes tensor-map encoding).  Same arithmetic. */
+ * where the driver exposes tensor-map encoding).  That kernel rounds A to BF16
+ * once (as NMF_FLAG_BF16_SINGLE_A). */
 #define NMF_FLAG_NO_TMA 4
+/* BF16 form, operand precision.  By default every tensor-core operand is
+ * carried as a BF16 pair, X = X_hi + X_lo with X_hi = bf16(X) and
+ * X_lo = bf16(X - X_hi) (about 16 significant bits): the products use
+ * A_hi F_hi + A_lo F_hi + A_hi F_lo and the Grams F_hi F_hi + F_lo F_hi +
+ * F_hi F_lo, three BF16 MMAs per tile with FP32 accumulation (F = the factor
+ * operand).  NMF_FLAG_BF16_SINGLE_FACTORS rounds the factor operands to BF16
+ * once (two MMAs per product tile, one per Gram tile); NMF_FLAG_BF16_SINGLE_A
+ * rounds A once as well (one MMA per tile; the fit is then to bf16(A), whose
+ * error is about 2^-9 / sqrt(3) of A). */
+#define NMF_FLAG_BF16_SINGLE_A 8
+#define NMF_FLAG_BF16_SINGLE_FACTORS 16
 
 typedef struct nmf_ctx nmf_ctx;
 

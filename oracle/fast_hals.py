@@ -71,20 +71,24 @@ def update_w(P: np.ndarray, Q: np.ndarray, W: np.ndarray, eps: float = DEFAULT_E
 
 
 def iteration(A, W: np.ndarray, H: np.ndarray, eps: float = DEFAULT_EPS, trace: dict | None = None,
-              operand_round=None):
+              operand_round=None, a_round=None):
     """One REPEAT body of Alg. 1: update H, then W.  Returns (W, H).
 
     If ``trace`` is a dict it receives the intermediates R, S, H, P, Q, W.
     ``operand_round`` (e.g. bf16.round_bf16) rounds the operands of the four
     matrix products (lines 4, 5, 10, 11) before they are multiplied exactly
     (FP64): the definition of a reduced-precision-product form of Alg. 1.
-    The k loops stay FP64.
+    ``a_round``, if given, is used for A instead (e.g. bf16.round_bf16_split,
+    A carried as a BF16 pair).  The k loops stay FP64.
     """
     Aop = _as_operator(A)
     W = np.asarray(W, dtype=np.float64)
     H = np.asarray(H, dtype=np.float64)
     rnd = operand_round if operand_round is not None else (lambda x: x)
-    Ar = Aop if operand_round is None else rnd(Aop)
+    if a_round is not None:
+        Ar = a_round(Aop)
+    else:
+        Ar = Aop if operand_round is None else rnd(Aop)
     # Updating H
     Wr = rnd(W)
     R = np.asarray(Ar.T @ Wr)
@@ -101,7 +105,7 @@ def iteration(A, W: np.ndarray, H: np.ndarray, eps: float = DEFAULT_EPS, trace: 
 
 
 def run(A, W0: np.ndarray, H0: np.ndarray, n_iter: int, eps: float = DEFAULT_EPS,
-        normalize: bool = True, objective_every: int = 0, operand_round=None):
+        normalize: bool = True, objective_every: int = 0, operand_round=None, a_round=None):
     """Alg. 1 for a fixed number of iterations from (W0, H0).
 
     Returns (W, H, history) where history lists the relative objective
@@ -113,7 +117,7 @@ def run(A, W0: np.ndarray, H0: np.ndarray, n_iter: int, eps: float = DEFAULT_EPS
     H = np.array(H0, dtype=np.float64)
     hist = []
     for it in range(n_iter):
-        W, H = iteration(A, W, H, eps, operand_round=operand_round)
+        W, H = iteration(A, W, H, eps, operand_round=operand_round, a_round=a_round)
         if objective_every and (it + 1) % objective_every == 0:
             hist.append(obj.relative_error(A, W, H))
     return W, H, hist

@@ -90,13 +90,18 @@ int tc_pick_bn(int N);
 // BF16 products with TMA-fed tcgen05 MMAs: C (M x N, FP32) = A (M x Kd) B (N x Kd)^T,
 // A and B BF16, K-major, row strides lda / ldb multiples of 8 elements.
 bool tma_available();
+// A_lo != nullptr: A split, C = (A + A_lo) B^T with A_lo of A's layout (A =
+// bf16 of the FP32 values, A_lo = bf16 of the remainder); B_lo != nullptr as
+// well: C = A B^T + A_lo B^T + A B_lo^T.
 cudaError_t tc_bf16_tma_gemm(const void* A, int64_t lda, const void* B, int64_t ldb, float* C, int64_t ldc, int M,
-                             int N, int Kd, int* d_status, cudaStream_t s);
+                             int N, int Kd, int* d_status, cudaStream_t s, const void* A_lo = nullptr,
+                             const void* B_lo = nullptr);
 // Split-K partial Grams of X (N x Kp) given X^T in BF16 (Kp x ldx, ldx a
 // multiple of 8): part[z] (Kp x Kp) = X^T X over the z-th K slice,
 // z < splits (tma_gram_splits gives a full-GPU count); sum with gram_reduce.
+// Xt_lo != nullptr: the factor split (X_hi X_hi^T + X_lo X_hi^T + X_hi X_lo^T).
 cudaError_t tc_bf16_tma_gram_partials(const void* Xt, int64_t ldx, int Kp, int N, float* part, int splits,
-                                      int* d_status, cudaStream_t s);
+                                      int* d_status, cudaStream_t s, const void* Xt_lo = nullptr);
 int tma_gram_splits(int Kp, int N);
 // S (Kp x Kp, pads zero) = sum of n_chunks partial Grams, FP64 in a fixed
 // order, upper triangle mirrored.
@@ -107,8 +112,9 @@ cudaError_t gram_reduce(const float* part, int n_chunks, int Kp, int K, float* S
 int splitk_chunks(int M, int N, int Kin);
 cudaError_t gemm_run_split(GemmArgs a, float* part, int n_chunks, cudaStream_t s);
 // dst (cols x ldd, BF16) = transpose of src (rows x cols FP32, row stride lds); rows..ldd zero.
+// lo != nullptr: also lo = bf16(src - dst) in dst's layout (split form).
 cudaError_t transpose_to_bf16(const float* src, int rows, int cols, int64_t lds, void* dst, int64_t ldd,
-                              cudaStream_t s);
+                              cudaStream_t s, void* lo = nullptr);
 
 // sum_{v,d} (A[v][d] - (W Ht^T)[v][d])^2: Eq. 2 evaluated directly for dense A
 // (FP32 products, FP64 sum of the squared residuals).  dpart: scratch of
@@ -225,7 +231,7 @@ cudaError_t normalize_columns(float* X, int N, int K, int ld, cudaStream_t s);
 // dst (rows x ld, BF16, round to nearest) = src (rows x cols, row stride ld), pads zero.
 // dst (rows x ldd, BF16 round-to-nearest-even) = src (rows x cols, row stride lds); columns cols..ldd zero.
 cudaError_t convert_bf16(const float* src, int64_t rows, int64_t cols, int64_t lds, void* dst, int64_t ldd,
-                         cudaStream_t s);
+                         cudaStream_t s, void* lo = nullptr);
 // frob2 = normA2 - 2 <W, P> + <S, Q>, appended to the history ring.  The
 // dot products use compensated FP32 arithmetic (Dot2) per thread and FP64
 // across threads; `partial` holds 2 * n_partial doubles.

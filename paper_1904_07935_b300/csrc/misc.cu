@@ -172,20 +172,26 @@ __global__ void transpose_kernel(const float* __restrict__ src, int rows, int co
   }
 }
 
+// dst = bf16(src) (round to nearest even); with lo != nullptr also
+// lo = bf16(src - dst), the split form's low part.
 __global__ void convert_bf16_kernel(const float* __restrict__ src, long long rows, long long cols, long long lds,
-                                    __nv_bfloat16* __restrict__ dst, long long ldd) {
+                                    __nv_bfloat16* __restrict__ dst, long long ldd, __nv_bfloat16* __restrict__ lo) {
   const long long n = rows * ldd;
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
     const long long r = e / ldd, c = e - r * ldd;
-    dst[e] = __float2bfloat16_rn(c < cols ? src[r * lds + c] : 0.f);
+    const float x = c < cols ? src[r * lds + c] : 0.f;
+    const __nv_bfloat16 h = __float2bfloat16_rn(x);
+    dst[e] = h;
+    if (lo) lo[e] = __float2bfloat16_rn(x - __bfloat162float(h));
   }
 }
 
 }  // namespace
 
 cudaError_t convert_bf16(const float* src, int64_t rows, int64_t cols, int64_t lds, void* dst, int64_t ldd,
-                         cudaStream_t s) {
-  convert_bf16_kernel<<<1184, 256, 0, s>>>(src, rows, cols, lds, static_cast<__nv_bfloat16*>(dst), ldd);
+                         cudaStream_t s, void* lo) {
+  convert_bf16_kernel<<<1184, 256, 0, s>>>(src, rows, cols, lds, static_cast<__nv_bfloat16*>(dst), ldd,
+                                           static_cast<__nv_bfloat16*>(lo));
   return cudaGetLastError();
 }
 

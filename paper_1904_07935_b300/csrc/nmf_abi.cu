@@ -21,7 +21,10 @@ struct nmf_ctx {
   bool tma = false;         // BF16 products through the TMA-fed kernel
   void* Ab8 = nullptr;      // BF16 A, V x ld8D (row stride a multiple of 8)
   void* ATb8 = nullptr;     // BF16 A^T, D x ld8V
+  void* Ab8lo = nullptr;    // split form: bf16(A - Ab8), same layout (null: A rounded once)
+  void* ATb8lo = nullptr;   // split form: bf16(A^T - ATb8)
   void* Fb8 = nullptr;      // BF16 transposed factor, Kp x max(ld8V, ld8D)
+  void* Fb8lo = nullptr;    // split factor: bf16(factor - Fb8), same layout (null: factor rounded once)
   int64_t ld8V = 0, ld8D = 0;
   float* gpart = nullptr;   // BF16 form: split-K partial Grams, gsplits x Kp x Kp
   float* ppart = nullptr;   // dense FP32 products: split-K partials
@@ -118,8 +121,8 @@ bool is_device_ptr(const void* p) {
 // means the iteration already made it for both branches.
 cudaError_t bf16_operand(nmf_ctx* c, bool w, cudaStream_t s) {
   c->launch_count += 1;
-  return w ? transpose_to_bf16(c->W, c->V, c->Kp, c->Kp, c->Fb8, c->ld8V, s)
-           : transpose_to_bf16(c->Ht, c->D, c->Kp, c->Kp, c->Fb8, c->ld8D, s);
+  return w ? transpose_to_bf16(c->W, c->V, c->Kp, c->Kp, c->Fb8, c->ld8V, s, c->Fb8lo)
+           : transpose_to_bf16(c->Ht, c->D, c->Kp, c->Kp, c->Fb8, c->ld8D, s, c->Fb8lo);
 }
 
 cudaError_t enq_product_R(nmf_ctx* c, cudaStream_t s = nullptr, bool operand_ready = false) {   // R = A^T W
@@ -140,7 +143,8 @@ cudaError_t enq_product_R(nmf_ctx* c, cudaStream_t s = nullptr, bool operand_rea
       cudaError_t e = bf16_operand(c, true, s);
       if (e != cudaSuccess) return e;
     }
-    return tc_bf16_tma_gemm(c->ATb8, c->ld8V, c->Fb8, c->ld8V, c->R, c->Kp, c->D, c->Kp, c->V, c->d_status, s);
+    return tc_bf16_tma_gemm(c->ATb8, c->ld8V, c->Fb8, c->ld8V, c->R, c->Kp, c->D, c->Kp, c->V, c->d_status, s,
+                            c->ATb8lo, c->Fb8lo);
   }
   if (c->bf16) return tc_gemm_run(a, TC_BF16, c->A_bf16, c->Kp > 128 ? 128 : 0, c->d_status, s);
   c->launch_count += c->splitR > 1;
@@ -165,7 +169,7 @@ cudaError_t enq_product_P(nmf_ctx* c, bool operand_ready = false) {   // P = A H
       if (e != cudaSuccess) return e;
     }
     return tc_bf16_tma_gemm(c->Ab8, c->ld8D, c->Fb8, c->ld8D, c->P, c->Kp, c->V, c->Kp, c->D, c->d_status,
-                            c->stream);
+                            c->stream, c->Ab8lo, c->Fb8lo);
   }
   if (c->bf16) return tc_gemm_run(a, TC_BF16, c->A_bf16, c->Kp > 128 ? 128 : 0, c->d_status, c->stream);
   c->launch_count += c->splitP > 1;
@@ -184,7 +188,8 @@ cudaError_t enq_gram(nmf_ctx* c, const GramWork& g, const float* X, float* out, 
     const int N = w ? c->V : c->D;
     const int splits = tma_gram_splits(c->Kp, N);
     c->launch_count += 2;
-    if ((e = tc_bf16_tma_gram_partials(c->Fb8, w ? c->ld8V : c->ld8D, c->Kp, N, c->gpart, splits, c->d_status, s)) !=
+    if ((e = tc_bf16_tma_gram_partials(c->Fb8, w ? c->ld8V : c->ld8D, c->Kp, N, c->gpart, splits, c->d_status, s,
+                                       c->Fb8lo)) !=
         cudaSuccess)
       return e;
     return gram_reduce(c->gpart, splits, c->Kp, c->K, out, s);
@@ -506,12 +511,18 @@ nmf_status init_impl(const nmf_problem* p, nmf_ctx* c) {
       c->ld8D = (D + 7) / 8 * 8;
       CK(cudaMalloc(&c->Ab8, sizeof(uint16_t) * (size_t)V * c->ld8D));
       CK(cudaMalloc(&c->ATb8, sizeof(uint16_t) * (size_t)D * c->ld8V));
+      if (!(p->flags & NMF_FLAG_BF16_SINGLE_A)) {
+        CK(cudaMalloc(&c->Ab8lo, sizeof(uint16_t) * (size_t)V * c->ld8D));
+        CK(cudaMalloc(&c->ATb8lo, sizeof(uint16_t) * (size_t)D * c->ld8V));
+      }
       CK(cudaMalloc(&c->Fb8, sizeof(uint16_t) * (size_t)Kp * std::max(c->ld8V, c->ld8D)));
+      if (c->Ab8lo && !(p->flags & NMF_FLAG_BF16_SINGLE_FACTORS))
+        CK(cudaMalloc(&c->Fb8lo, sizeof(uint16_t) * (size_t)Kp * std::max(c->ld8V, c->ld8D)));
       c->gsplits = std::max(tma_gram_splits(Kp, V), tma_gram_splits(Kp, D));
       CK(cudaMalloc(&c->gpart, sizeof(float) * (size_t)c->gsplits * Kp * Kp));
       // A (V x D) -> BF16 with row stride ld8D, and A^T (D x V) with ld8V.
-      CK(convert_bf16(c->dense, V, D, c->lda, c->Ab8, c->ld8D, c->stream));
-      CK(transpose_to_bf16(c->dense, V, D, c->lda, c->ATb8, c->ld8V, c->stream));
+      CK(convert_bf16(c->dense, V, D, c->lda, c->Ab8, c->ld8D, c->stream, c->Ab8lo));
+      CK(transpose_to_bf16(c->dense, V, D, c->lda, c->ATb8, c->ld8V, c->stream, c->ATb8lo));
     }
   }
   if (c->fmt == NMF_DENSE_F32) CK(dalloc(&c->resid_part, (size_t)resid2_partials(V, D)));
@@ -560,7 +571,7 @@ void free_ctx(nmf_ctx* c) {
   gram_free(c->gramW);
   gram_free(c->gramH);
 
-  for (void* p : {(void*)c->A_bf16, c->Ab8, c->ATb8, c->Fb8, (void*)c->gpart, (void*)c->ppart, (void*)c->resid_part,
+  for (void* p : {(void*)c->A_bf16, c->Ab8, c->ATb8, c->Ab8lo, c->ATb8lo, c->Fb8, c->Fb8lo, (void*)c->gpart, (void*)c->ppart, (void*)c->resid_part,
                   (void*)c->d_sync, (void*)c->rpT, (void*)c->ciT, (void*)c->vaT, (void*)c->W, (void*)c->Ht, (void*)c->R,
                   (void*)c->P, (void*)c->S, (void*)c->Q, (void*)c->Y, (void*)c->stage, (void*)c->Y0lo, (void*)c->alg1_part,
                   (void*)c->obj_partial, (void*)c->hist, (void*)c->d_counter, (void*)c->d_status})

@@ -5,15 +5,15 @@ iteration on the GPU against the FP64 oracle at full size.
 The first W updates of these near-square factorisations (AT&T: 400 images)
 cancel heavily, so each case starts from an early oracle iterate where the
 FP32 storage floor d32 (`fp32_storage_sensitivity`) is below 3e-6, checked
-in the test, and holds the strict 1e-5.  The BF16 form is compared with the
-BF16-operand oracle (Alg. 1 with the operands of its products rounded to
-BF16) within 2e-2."""
+in the test, and holds the strict 1e-5.  The BF16 form is compared with its
+definition, Alg. 1 with the operands of its products carried as BF16 pairs
+(hi = bf16(x), lo = bf16(x - hi)), within 2e-2."""
 
 import numpy as np
 import pytest
 
 from oracle import fast_hals as fh
-from oracle.bf16 import round_bf16
+from oracle.bf16 import round_bf16_split
 from paper_1904_07935_b300 import synth
 
 from ._parity import f32, fp32_storage_sensitivity, rel_h, rel_w
@@ -68,6 +68,6 @@ def test_bf16_one_iteration_pie(nmf):
     W0, H0, W, H = _start(prob, K, 1)
     W64, H64 = W.astype(np.float64), H.astype(np.float64)
     Wg, Hg = _gpu_iteration(nmf, prob.A, K, W0, H0, W, H, nmf.PREC_BF16)
-    Wb, Hb = fh.iteration(prob.A, W64, H64, EPS, operand_round=round_bf16)
+    Wb, Hb = fh.iteration(prob.A, W64, H64, EPS, operand_round=round_bf16_split)
     print("pie bf16 W", rel_w(Wg, Wb), "H", rel_h(Hg, Hb))
     assert rel_w(Wg, Wb) < 2e-2 and rel_h(Hg, Hb) < 2e-2

@@ -352,6 +352,63 @@ def test_round_bf16_definition_and_library_agree():
     assert round_bf16(np.array([1.0 + 3 * 2 ** -8]))[0] == 1.0 + 2 ** -6
 
 
+def test_round_bf16_split_bound_exactness_and_library():
+    """The BF16 pair (hi, lo) of the split form: exact for values whose binary32
+    significand fits in the two BF16 significands, within 2^-16 |x| always,
+    and hi, lo are the library's BF16 roundings of x and of x - hi."""
+    import torch
+    from oracle.bf16 import round_bf16, round_bf16_split
+    rng = np.random.default_rng(11)
+    # exactly representable pairs: an 8-bit significand plus one 8 binades lower
+    hi = round_bf16(rng.random(4000) + 0.5)
+    # |lo| in [2^-11, 2^-10): below half a BF16 ulp of hi, and hi + lo spans
+    # at most 19 significant bits
+    lo = round_bf16(np.where(rng.random(4000) < 0.5, -1.0, 1.0) * (1.0 + rng.random(4000)) * 2.0 ** -11)
+    x = (hi + lo).astype(np.float32).astype(np.float64)
+    assert np.array_equal(x, hi + lo)                    # the pair is a binary32 value
+    assert np.array_equal(round_bf16_split(x), x)
+    # bound on arbitrary binary32 values over many binades
+    y = (rng.random(200000) * 10.0 ** rng.integers(-8, 8, size=200000)).astype(np.float32).astype(np.float64)
+    err = np.abs(round_bf16_split(y) - y)
+    assert np.all(err <= 2.0 ** -16 * np.abs(y))
+    assert np.max(err / y) > 2.0 ** -20                  # not exact in general: the bound is not vacuous
+    # the two parts against the library's conversion
+    t = torch.from_numpy(y.astype(np.float32))
+    th = t.to(torch.bfloat16).to(torch.float32)
+    tl = (t - th).to(torch.bfloat16).to(torch.float64)
+    assert np.array_equal(round_bf16_split(y), th.double().numpy() + tl.numpy())
+    # planted mistake: lo rounded from x instead of from x - hi breaks the bound
+    bad = round_bf16(y) + round_bf16(y)
+    assert np.max(np.abs(bad - y) / y) > 0.5
+
+
+def test_adam_later_steps_match_expanded_moments():
+    """Adam over four steps with varying gradients against the moments
+    written out as weighted sums, m_t = (1 - b1) sum_s b1^(t-s) g_s and
+    v_t = (1 - b2) sum_s b2^(t-s) g_s^2, each step p -= lr mhat / (sqrt(vhat) + eps).
+    An oracle that failed to carry m or v between steps passes the first
+    step (where the step is lr g / (|g| + eps) whatever they hold) but not this."""
+    b1, b2, lr, eps = 0.9, 0.999, 0.05, 1e-8
+    gs = [np.array([0.5, -4.0, 1e-3]), np.array([-1.0, 2.0, 3.0]), np.array([0.25, 0.0, -2.0]),
+          np.array([2.0, -1.0, 0.5])]
+    p = [np.array([1.0, -2.0, 3.0])]
+    m, v = [np.zeros(3)], [np.zeros(3)]
+    expect = np.array([1.0, -2.0, 3.0])
+    for t in range(1, len(gs) + 1):
+        p, m, v = mlp.adam_step(p, [gs[t - 1]], m, v, t, lr=lr, b1=b1, b2=b2, eps=eps)
+        mt = (1 - b1) * sum(b1 ** (t - s) * gs[s - 1] for s in range(1, t + 1))
+        vt = (1 - b2) * sum(b2 ** (t - s) * gs[s - 1] ** 2 for s in range(1, t + 1))
+        expect = expect - lr * (mt / (1 - b1 ** t)) / (np.sqrt(vt / (1 - b2 ** t)) + eps)
+        assert np.allclose(m[0], mt, rtol=1e-14, atol=1e-16)
+        assert np.allclose(v[0], vt, rtol=1e-14, atol=1e-16)
+        assert np.allclose(p[0], expect, rtol=1e-13, atol=1e-15)
+    # planted mistake: moments restarted every step -> the fourth parameter set differs
+    q = [np.array([1.0, -2.0, 3.0])]
+    for t in range(1, len(gs) + 1):
+        q, _, _ = mlp.adam_step(q, [gs[t - 1]], [np.zeros(3)], [np.zeros(3)], t, lr=lr, b1=b1, b2=b2, eps=eps)
+    assert np.max(np.abs(q[0] - expect)) > 1e-3
+
+
 def test_operand_rounding_hook_is_identity_when_unset():
     A = _dense(30, 20, 3, 4)
     W0, H0 = synth.init_factors(5, 30, 20, 4)
