@@ -283,6 +283,32 @@ def dense_costs(V, D, K, bf16):
             "objective": 8 * V * K}, prod_flops
 
 
+def iteration_bytes(V, D, a_bytes, K):
+    """Whole-iteration algorithmic bytes as the scope table defines them:
+    2 |A| + 16 (V + D) K (A read by both products; each factor and its data
+    term read and written once)."""
+    return 2 * a_bytes + 16 * (V + D) * K
+
+
+def step_bounds(ab, prof, V, D, K, peak, fpeak):
+    """Per-step roofline fractions: HBM-bound steps (products, column updates,
+    objective) against the measured copy bandwidth, the Grams' (N K (K+1))
+    flops against the FP32 SIMT peak."""
+    out = {}
+    for k, ms in prof.items():
+        if ms <= 0:
+            continue
+        if k in ("S", "Q"):
+            N = V if k == "S" else D
+            tf = N * K * (K + 1) / (ms * 1e-3) / 1e12
+            out[k] = {"ms": round(ms, 5), "bound": "fp32-simt", "achieved_tflops": round(tf, 3),
+                      "frac": round(tf / fpeak, 5)}
+        else:
+            gbs = ab[k] / (ms * 1e-3) / 1e9
+            out[k] = {"ms": round(ms, 5), "bound": "hbm", "achieved_gbs": round(gbs, 2), "frac": round(gbs / peak, 5)}
+    return out
+
+
 def alg_bytes(V, D, nnz, K):
     """Algorithmic bytes of one iteration (each operand moved once):
     SpMM: nnz*8 + (rows+1)*4 + 4*cols*K + 4*rows*K, twice; column updates:
@@ -391,16 +417,29 @@ def run_gpu(args):
                     "unit": "TFLOP/s", "frac": round(tflops / tpeak, 5), "traffic": None,
                     "step": "P (A H^T)", "peak_source": tkind, "dominant_step": dom,
                     "step_ms": {k: round(v, 5) for k, v in prof.items()}}
+        # A's bytes as the products read them: FP32, or the BF16 pair (4 bytes).
+        it_bytes = iteration_bytes(V, D, 4 * V * D, K)
+        roofline["alg_bytes_per_iter"] = int(it_bytes)
+        roofline["alg_bytes_definition"] = "2|A| + 16 (V + D) K, |A| = 4 V D bytes (FP32 A or its BF16 pair)"
+        roofline["iteration_frac_of_hbm"] = round(it_bytes / (ms * 1e-3) / 1e9 / peak, 5)
     else:
         ab = alg_bytes(V, D, nnz, K)
         dom = max(prof, key=prof.get)
         achieved = ab[dom] / (prof[dom] * 1e-3) / 1e9
+        it_bytes = iteration_bytes(V, D, nnz * 8 + (V + 1) * 4, K)
+        fpeak, _ = _tensor_peak(False)
         roofline = {"bound": "hbm", "achieved": round(achieved, 2), "peak": peak, "unit": "GB/s",
                     "frac": round(achieved / peak, 5), "traffic": None, "step": dom,
                     "peak_source": peak_kind,
                     "step_ms": {k: round(v, 5) for k, v in prof.items()},
-                    "alg_bytes_per_iter": int(sum(ab.values())),
-                    "iteration_frac_of_hbm": round(sum(ab.values()) / (ms * 1e-3) / 1e9 / peak, 5)}
+                    "steps": step_bounds(ab, prof, V, D, K, peak, fpeak),
+                    "alg_bytes_per_iter": int(it_bytes),
+                    "alg_bytes_definition": "2|A| + 16 (V + D) K, |A| = CSR bytes (nnz * 8 + (V + 1) * 4)",
+                    "iteration_frac_of_hbm": round(it_bytes / (ms * 1e-3) / 1e9 / peak, 5),
+                    "step_bytes_sum": int(sum(ab.values()))}
+        if dom == "update_W":
+            roofline["traffic_source"] = ("none: the single-launch W update is timed with CUDA events only and "
+                                          "not run under ncu (its earlier cooperative form faulted under a profiler)")
 
     # Latency floor of the W update (K sequential cluster-wide column norms):
     # the same update on a 512 x 512 problem at the same K, where the rows'

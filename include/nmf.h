@@ -355,8 +355,10 @@ nmf_status nmf_gemm_bf16(int32_t M, int32_t N, int32_t K, const uint16_t* A, int
  * by its own pool allocator, or code running where an allocation's implicit
  * synchronisation is not allowed).
  *   S (K x K, row-major, device) = X^T X for X (N x K, device, row stride
- *   ldx >= K), FP32 on the SIMT pipes with fixed-order FP64 combination of
- *   the partial sums, asynchronous on `stream`.
+ *   ldx >= K), FP32 on the SIMT pipes over row chunks; the chunks' partial
+ *   sums are combined in a fixed order, with compensated FP32 additions
+ *   (TwoSum) for up to 256 chunks and in FP64 beyond; asynchronous on
+ *   `stream`.
  * The partial sums use one file-scope device array of
  * NMF_NOALLOC_SCRATCH_FLOATS floats (16 MiB) that every GPU loading the
  * library holds until the process exits.  The first call on a device looks

@@ -1,16 +1,19 @@
-// Alg. 1 as written: the H and W updates column by column, with no column
-// tiling (the form the paper's regrouping, Alg. 2, is measured against,
-// Sec. 5 / Table 5).  One warp per row of the tall factor; column k is one
-// grid-wide step (W: a second step normalises the column before the next
-// one reads it), so an update is K (H) or 2K (W) dependent launches.
-//
-//   H: h_k <- max(eps, h_k + R_k - H^T S_k)           (Alg. 1 lines 6-8)
-//   W: w_k <- max(eps, w_k Q_kk + P_k - W Q_k),
-//      w_k <- w_k / ||w_k||                            (lines 12-16)
-//
-// H^T S_k and W Q_k use the current factor (columns < k already new) and
-// include the j = k term, exactly as the algorithm is written.  S and Q are
-// symmetric, so column k is read as row k (contiguous).
+// Comparator: HALS without column tiling (Sec. 3).  Each factor is updated
+// one column at a time, every column being the exact non-negative minimiser
+// of the objective in that column with all others fixed, and columns taken in
+// ascending order so that column k sees the new values of columns < k.  For
+// the tall factor X with data term B and Gram G (H: X = H^T, B = R, G = S;
+// W: X = W, B = P, G = Q):
+//   x_k <- max(eps, x_k G_kk + B_k - X G_k)     (W; then x_k <- x_k / ||x_k||)
+//   x_k <- max(eps, x_k + B_k - X G_k)          (H, where G_kk = 1 by the unit
+//                                                 columns of W)
+// X G_k is the product with the current X (columns < k already new,
+// including the k-th term).  Without tiling there is no cheaper way to form
+// it than a pass over the whole factor per column: one warp per row, column
+// k one grid-wide launch (W: a second launch normalises the column before
+// the next one reads it), K (H) or 2K (W) dependent launches per update.
+// This is what the tiled order of Sec. 4 (Eqs. 4-6) is measured against.
+// G is symmetric, so column k is read as row k (contiguous).
 #include "devutil.cuh"
 #include "internal.cuh"
 

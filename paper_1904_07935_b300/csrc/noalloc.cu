@@ -6,6 +6,7 @@
 // stand-in for the symbol), so the first call on each device asks the
 // runtime for the address with cudaGetSymbolAddress while that device is
 // current, and every call passes that address to the kernels.
+#include <algorithm>
 #include <mutex>
 
 #include "internal.cuh"
@@ -58,14 +59,12 @@ extern "C" nmf_status nmf_gram_noalloc(const float* X, int32_t N, int32_t K, int
   if (want < 1) want = 1;
   const long long max_chunks = NMF_NOALLOC_SCRATCH_FLOATS / kk;
   if (want > max_chunks) want = (int)max_chunks;
-  int chunk = (N + want - 1) / want;
-  chunk = ((chunk + 15) / 16) * 16;
-  if (chunk < 16) chunk = 16;
-  int n_chunks = (N + chunk - 1) / chunk;
-  while (n_chunks > max_chunks) {
-    chunk += 16;
-    n_chunks = (N + chunk - 1) / chunk;
-  }
-  err = gram_run_scratch(X, N, K, ldx, part, n_chunks, chunk, S, static_cast<cudaStream_t>(stream));
+  // Rows per chunk: a multiple of 16, at least N / max_chunks so that the
+  // chunks' partials fit the array.
+  const long long need = ((long long)N + max_chunks - 1) / max_chunks;
+  long long chunk = std::max<long long>(((long long)N + want - 1) / want, need);
+  chunk = std::max<long long>(16, (chunk + 15) / 16 * 16);
+  const int n_chunks = (int)((N + chunk - 1) / chunk);
+  err = gram_run_scratch(X, N, K, ldx, part, n_chunks, (int)chunk, S, static_cast<cudaStream_t>(stream));
   return err == cudaSuccess ? NMF_OK : NMF_ECUDA;
 }
