@@ -611,6 +611,8 @@ def run_batch(args):
     stream = torch.cuda.Stream()
     bt = nmf.Batch(ctxs, autotune=True, stream=stream)
     sizes = [bt.query(i)[0] for i in range(n)]
+    sched = [bt.schedule(i) for i in range(n)]
+    tally = lambda key: {str(v): [s[key] for s in sched].count(v) for v in sorted({s[key] for s in sched})}
     bt.iterate(args.warmup)
     torch.cuda.synchronize()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -660,6 +662,7 @@ def run_batch(args):
                    "sequential_iter_per_s": round(n / seq_s, 3),
                    "speedup_vs_sequential": round((n * 1000.0 / ms) / (n / seq_s), 3),
                    "chain_cluster_sizes": {str(s): sizes.count(s) for s in sorted(set(sizes))},
+                   "tile_T": tally("tile_T"), "spmm_seg_P": tally("spmm_seg_P"), "spmm_seg_R": tally("spmm_seg_R"),
                    "rel_err_median": float(np.median(rels))},
         "e2e": {"value": round(n / t_e2e, 3), "unit": "iter/s", "h2d_bytes_per_step": fac,
                 "d2h_bytes_per_step": fac + 16 * n},

@@ -260,20 +260,26 @@ nmf_status nmf_gemm(int32_t M, int32_t N, int32_t K, const float* A, int64_t lda
  * nmf_batch_create: members must be distinct contexts on distinct streams,
  *   and `stream` (the batch's launch stream; NULL = a new one owned by the
  *   batch) must differ from all of them (NMF_EINVAL otherwise, and for
- *   n < 1).  Members switch to the per-tile W launches (the persistent W
- *   launch occupies every SM); a member's own single-problem graph is
- *   re-captured on its next nmf_iterate.  autotune != 0: for each member
- *   the W column chain's cluster size (4, 8 or 16 CTAs, where the rows fit)
- *   is chosen by timing three W updates per size and keeping the least
- *   SM-time (CTAs x time); W is restored, so tuning does not advance the
- *   factorisation.  Synchronous.  The batch does not own the members:
- *   destroy the batch before them.
+ *   n < 1).  Members switch to the per-tile W launches (the single-launch W
+ *   update holds every SM); a member's own single-problem graph is
+ *   re-captured on its next nmf_iterate.  autotune != 0: for each member,
+ *   timed with CUDA events from the same start: (1) sparse A: the SpMM
+ *   schedule of each product, rows longer than seg non-zeros split into
+ *   seg-long items (seg in 128, 256, 512, 1024) or no split, fastest of
+ *   three runs; (2) the W update's column-tile width T (8, 12 or 16) and its
+ *   column chain's cluster size (4, 8 or 16 CTAs, where the rows fit), least
+ *   SM-time (chain CTAs x time of three updates).  W is restored, so tuning
+ *   does not advance the factorisation.  Synchronous.  The batch does not
+ *   own the members: destroy the batch before them.
  * nmf_batch_iterate: n_iters iterations of every member, asynchronous on the
  *   batch stream; ordered after all work already queued on the members'
  *   streams, and each member's stream is made to wait for the batch, so
  *   nmf_error / nmf_get_factors on a member see the result.
  * nmf_batch_query: member i's chain cluster size and, if autotuned, the
  *   measured W-update time (microseconds) of the chosen size.
+ * nmf_batch_query_schedule: member i's W tile width and the SpMM split
+ *   lengths of the products P = A H^T and R = A^T W (0 for dense A; 2^30:
+ *   no row is split).
  * nmf_batch_submit: nmf_init of ps[0..n) (each ps[i].stream NULL or
  *   distinct), an autotuned batch, n_iters iterations; the contexts are
  *   returned in outs (caller destroys them); on failure none is returned.
@@ -282,6 +288,8 @@ typedef struct nmf_batch nmf_batch;
 nmf_status nmf_batch_create(nmf_ctx* const* ctxs, int32_t n, int32_t autotune, void* stream, nmf_batch** out);
 nmf_status nmf_batch_iterate(nmf_batch* b, int32_t n_iters);
 nmf_status nmf_batch_query(nmf_batch* b, int32_t i, int32_t* chain_ctas, float* w_update_us);
+nmf_status nmf_batch_query_schedule(nmf_batch* b, int32_t i, int32_t* tile_T, int32_t* spmm_seg_P,
+                                    int32_t* spmm_seg_R);
 void nmf_batch_destroy(nmf_batch* b);
 nmf_status nmf_batch_submit(const nmf_problem* ps, int32_t n, int32_t n_iters, nmf_ctx** outs);
 

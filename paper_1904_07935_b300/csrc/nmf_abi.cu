@@ -53,6 +53,8 @@ struct nmf_ctx {
   int* ciT = nullptr;
   float* vaT = nullptr;
   SpmmPlan planA, planAt;
+  std::vector<int> h_rp, h_rpT;   // host row pointers of A and A^T (re-planning by the batch autotuner)
+  int segA = 512, segAt = 512;    // SpMM schedule: rows longer than seg non-zeros split into seg-long items
   GramWork gramW, gramH;
   ChainConfig chainW, chainH;
   // Factors and intermediates, row stride Kp, padding columns kept at zero.
@@ -447,8 +449,10 @@ nmf_status init_impl(const nmf_problem* p, nmf_ctx* c) {
       CK(cudaMemcpy(c->ciT, ciT.data(), sizeof(int) * ciT.size(), cudaMemcpyHostToDevice));
       CK(cudaMemcpy(c->vaT, vaT.data(), sizeof(float) * vaT.size(), cudaMemcpyHostToDevice));
     }
-    CK(spmm_plan_build(c->planA, rp, V, D, Kp, 512));
-    CK(spmm_plan_build(c->planAt, rpT, D, V, Kp, 512));
+    CK(spmm_plan_build(c->planA, rp, V, D, Kp, c->segA));
+    CK(spmm_plan_build(c->planAt, rpT, D, V, Kp, c->segAt));
+    c->h_rp = std::move(rp);
+    c->h_rpT = std::move(rpT);
   } else if (c->fmt == NMF_DENSE_F32) {
     if (!p->dense || p->ld < p->D) return NMF_EINVAL;
     if (!is_device_ptr(p->dense)) return NMF_EINVAL;
@@ -636,12 +640,21 @@ void drop_graph(nmf_ctx* c) {
   c->graph = nullptr;
 }
 
-// Autotuner for a batch member: the W update's column chain runs on one
-// cluster of 4, 8 or 16 CTAs; a wider cluster finishes the chain sooner but
-// holds more SMs, which the other members could use.  Each fitting size is
-// timed (three W updates from the same start, CUDA events) and the one with
-// the least SM-time (CTAs x microseconds) is kept.  W is restored afterwards,
-// so tuning does not advance the factorisation.
+// Autotuner for a batch member (Sec. 1's repeated factorisation: many small
+// problems of uneven shape, each with its own best schedule).  Three choices
+// are timed per member with CUDA events, each from the same start:
+//  * the SpMM schedule of each product (CSR SpMM of A for P, of A^T for R):
+//    rows longer than `seg` non-zeros are split into seg-long items whose
+//    partial rows the last item sums; seg in {128, 256, 512, 1024} or no
+//    split at all (one item per row); the fastest of three runs each wins;
+//  * the W update's column-tile width T in {8, 12, 16} (Alg. 2's T; each tile
+//    costs a base launch and a chain launch, each column a cluster-wide norm)
+//    and the chain's cluster size (4, 8 or 16 CTAs: a wider cluster finishes
+//    the chain sooner but holds more SMs the other members could use): the
+//    pair with the least chain SM-time (CTAs x microseconds of three
+//    updates) wins.
+// W is restored afterwards and R is recomputed for the current W, so tuning
+// does not advance the factorisation.
 cudaError_t autotune_member(nmf_ctx* c, float* w_us_out) {
   const size_t bytes = sizeof(float) * (size_t)c->V * c->Kp;
   float* saved = nullptr;
@@ -655,37 +668,91 @@ cudaError_t autotune_member(nmf_ctx* c, float* w_us_out) {
     return err;
   };
   if ((e = cudaEventCreate(&t0)) != cudaSuccess || (e = cudaEventCreate(&t1)) != cudaSuccess) return fail(e);
+  auto elapsed_us = [&](int reps, float* us) -> cudaError_t {
+    cudaError_t err;
+    if ((err = cudaEventRecord(t1, c->stream)) != cudaSuccess) return err;
+    if ((err = cudaEventSynchronize(t1)) != cudaSuccess) return err;
+    float ms = 0.f;
+    if ((err = cudaEventElapsedTime(&ms, t0, t1)) != cudaSuccess) return err;
+    *us = ms * 1000.f / (float)reps;
+    return cudaSuccess;
+  };
+  // SpMM schedules (sparse A only).
+  if (c->fmt == NMF_CSR_F32_I32) {
+    const int segs[] = {128, 256, 512, 1024, 1 << 30};
+    for (int which = 0; which < 2; ++which) {
+      SpmmPlan& plan = which == 0 ? c->planA : c->planAt;
+      const std::vector<int>& rp = which == 0 ? c->h_rp : c->h_rpT;
+      const int rows = which == 0 ? c->V : c->D, cols = which == 0 ? c->D : c->V;
+      const int* ci = which == 0 ? c->ci : c->ciT;
+      const float* va = which == 0 ? c->va : c->vaT;
+      const float* X = which == 0 ? c->Ht : c->W;
+      float* Y = which == 0 ? c->P : c->R;
+      int best_seg = which == 0 ? c->segA : c->segAt;
+      float best = INFINITY;
+      for (int seg : segs) {
+        spmm_plan_free(plan);
+        if ((e = spmm_plan_build(plan, rp, rows, cols, c->Kp, seg)) != cudaSuccess) return fail(e);
+        for (int rep = 0; rep < 4; ++rep) {
+          if (rep == 1 && (e = cudaEventRecord(t0, c->stream)) != cudaSuccess) return fail(e);
+          if ((e = spmm_run(plan, ci, va, X, Y, c->Kp, c->stream)) != cudaSuccess) return fail(e);
+        }
+        float us = 0.f;
+        if ((e = elapsed_us(3, &us)) != cudaSuccess) return fail(e);
+        if (us < best) {
+          best = us;
+          best_seg = seg;
+        }
+      }
+      spmm_plan_free(plan);
+      if ((e = spmm_plan_build(plan, rp, rows, cols, c->Kp, best_seg)) != cudaSuccess) return fail(e);
+      (which == 0 ? c->segA : c->segAt) = best_seg;
+    }
+  }
   if ((e = cudaMemcpyAsync(saved, c->W, bytes, cudaMemcpyDeviceToDevice, c->stream)) != cudaSuccess) return fail(e);
   // P and Q of the current H: the W update's inputs.
   if ((e = enq_product_P(c)) != cudaSuccess) return fail(e);
   if ((e = enq_gram(c, c->gramH, c->Ht, c->Q)) != cudaSuccess) return fail(e);
   ChainConfig best = c->chainW;
+  int best_T = c->T;
   float best_cost = INFINITY, best_us = 0.f;
-  for (int cl : {16, 8, 4}) {
-    ChainConfig cfg;
-    if (!chain_config_cluster(c->V, kRowTile, cl, &cfg)) continue;
-    c->chainW = cfg;
-    // warm-up, then three timed updates
-    for (int rep = 0; rep < 4; ++rep) {
-      if ((e = cudaMemcpyAsync(c->W, saved, bytes, cudaMemcpyDeviceToDevice, c->stream)) != cudaSuccess) return fail(e);
-      if (rep == 1 && (e = cudaEventRecord(t0, c->stream)) != cudaSuccess) return fail(e);
-      if ((e = enq_update(c, c->W, c->Q, c->P, c->V, true)) != cudaSuccess) return fail(e);
+  for (int T : {16, 12, 8}) {
+    // Events of the per-tile launches: 1 + 2 * ceil(K / T).
+    const size_t need = 1 + 2 * (size_t)((c->K + T - 1) / T);
+    while (c->ev.size() < need) {
+      cudaEvent_t ev = nullptr;
+      if ((e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming)) != cudaSuccess) return fail(e);
+      c->ev.push_back(ev);
     }
-    if ((e = cudaEventRecord(t1, c->stream)) != cudaSuccess) return fail(e);
-    if ((e = cudaEventSynchronize(t1)) != cudaSuccess) return fail(e);
-    float ms = 0.f;
-    if ((e = cudaEventElapsedTime(&ms, t0, t1)) != cudaSuccess) return fail(e);
-    const float us = ms * 1000.f / 3.f;       // includes the three restoring copies (same for every size)
-    const float cost = us * (float)cl;
-    if (cost < best_cost) {
-      best_cost = cost;
-      best = cfg;
-      best_us = us;
+    for (int cl : {16, 8, 4}) {
+      ChainConfig cfg;
+      if (!chain_config_cluster(c->V, T, cl, &cfg)) continue;
+      c->chainW = cfg;
+      c->T = T;
+      // warm-up, then three timed updates
+      for (int rep = 0; rep < 4; ++rep) {
+        if ((e = cudaMemcpyAsync(c->W, saved, bytes, cudaMemcpyDeviceToDevice, c->stream)) != cudaSuccess)
+          return fail(e);
+        if (rep == 1 && (e = cudaEventRecord(t0, c->stream)) != cudaSuccess) return fail(e);
+        if ((e = enq_update(c, c->W, c->Q, c->P, c->V, true)) != cudaSuccess) return fail(e);
+      }
+      float us = 0.f;      // includes the three restoring copies (the same for every choice)
+      if ((e = elapsed_us(3, &us)) != cudaSuccess) return fail(e);
+      const float cost = us * (float)cl;
+      if (cost < best_cost) {
+        best_cost = cost;
+        best = cfg;
+        best_T = T;
+        best_us = us;
+      }
     }
   }
   c->chainW = best;
+  c->T = best_T;
   *w_us_out = best_us;
   if ((e = cudaMemcpyAsync(c->W, saved, bytes, cudaMemcpyDeviceToDevice, c->stream)) != cudaSuccess) return fail(e);
+  // R = A^T W of the restored W (the iteration's entry state).
+  if ((e = enq_product_R(c)) != cudaSuccess) return fail(e);
   if ((e = cudaStreamSynchronize(c->stream)) != cudaSuccess) return fail(e);
   return fail(cudaSuccess);
 }
@@ -789,6 +856,17 @@ nmf_status nmf_batch_query(nmf_batch* b, int32_t i, int32_t* chain_ctas, float* 
   if (!b || i < 0 || i >= (int)b->m.size()) return NMF_EINVAL;
   if (chain_ctas) *chain_ctas = b->m[i]->chainW.cluster;
   if (w_update_us) *w_update_us = b->w_us[i];
+  return NMF_OK;
+}
+
+nmf_status nmf_batch_query_schedule(nmf_batch* b, int32_t i, int32_t* tile_T, int32_t* spmm_seg_P,
+                                    int32_t* spmm_seg_R) {
+  if (!b || i < 0 || i >= (int)b->m.size()) return NMF_EINVAL;
+  const nmf_ctx* c = b->m[i];
+  const bool sparse = c->fmt == NMF_CSR_F32_I32;
+  if (tile_T) *tile_T = c->T;
+  if (spmm_seg_P) *spmm_seg_P = sparse ? c->segA : 0;
+  if (spmm_seg_R) *spmm_seg_R = sparse ? c->segAt : 0;
   return NMF_OK;
 }
 

@@ -73,6 +73,7 @@ _SIGS = {
     "nmf_batch_create": ([_vp, _i32, _i32, _vp, _vp], _i32),
     "nmf_batch_iterate": ([_vp, _i32], _i32),
     "nmf_batch_query": ([_vp, _i32, _vp, _vp], _i32),
+    "nmf_batch_query_schedule": ([_vp, _i32, _vp, _vp, _vp], _i32),
     "nmf_batch_destroy": ([_vp], None),
     "nmf_batch_submit": ([_vp, _i32, _i32, _vp], _i32),
     "nmf_mlp_create": ([_i32, _i32, ctypes.c_uint64, _vp], _i32),
@@ -292,6 +293,13 @@ class Batch:
         cl, us = ctypes.c_int32(), ctypes.c_float()
         check(lib.nmf_batch_query(self.h, i, ctypes.byref(cl), ctypes.byref(us)), "nmf_batch_query")
         return cl.value, us.value
+
+    def schedule(self, i):
+        """Member i's autotuned W tile width and SpMM split lengths (P, R)."""
+        t, sp, sr = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+        check(lib.nmf_batch_query_schedule(self.h, i, ctypes.byref(t), ctypes.byref(sp), ctypes.byref(sr)),
+              "nmf_batch_query_schedule")
+        return {"tile_T": t.value, "spmm_seg_P": sp.value, "spmm_seg_R": sr.value}
 
     def close(self):
         if getattr(self, "h", None):

@@ -2,8 +2,9 @@
 (nmf_batch_*).  The batch adds no arithmetic, so each member must equal the
 same problem run alone: bit-exact when the configuration is the same (the
 kernels are deterministic), and within the one-iteration FP32 tolerance of
-the FP64 oracle (Alg. 1) when the autotuner changed the chain's cluster
-size (a different but fixed order of the column-norm partial sums)."""
+the FP64 oracle (Alg. 1) when the autotuner changed a member's schedule
+(the chain's cluster size, the W tile width, the SpMM split lengths: each a
+different but fixed order of the same sums)."""
 
 import numpy as np
 import pytest
@@ -68,6 +69,10 @@ def test_batch_autotuned_one_iteration_against_oracle(nmf, problems):
     b = nmf.Batch(members, autotune=True)
     sizes = [b.query(i)[0] for i in range(len(members))]
     assert all(s in (4, 8, 16) for s in sizes)
+    segs = (128, 256, 512, 1024, 1 << 30)
+    for i in range(len(members)):
+        s = b.schedule(i)
+        assert s["tile_T"] in (8, 12, 16) and s["spmm_seg_P"] in segs and s["spmm_seg_R"] in segs
     b.iterate(1)
     for m, (sp, K, W0, H0) in zip(members, problems):
         Wg, Hg = m.get_factors()
