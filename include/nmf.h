@@ -119,6 +119,14 @@ typedef struct {
  * error is about 2^-9 / sqrt(3) of A). */
 #define NMF_FLAG_BF16_SINGLE_A 8
 #define NMF_FLAG_BF16_SINGLE_FACTORS 16
+/* Form the factor updates' off-tile sums (Eqs. 4 and 6: new columns left of
+ * each tile, old columns right of it) on the tensor cores, in the H update
+ * and in the W update's tile bases: both operands split into TF32 pairs
+ * (hi + lo, three kind::tf32 MMAs per K step, about 2^-21 relative per
+ * product), each 32-column plane accumulated on its own and the planes' sums
+ * folded with compensation.  The in-tile column chains stay on the CUDA
+ * cores. */
+#define NMF_FLAG_TC_UPDATES 32
 
 typedef struct nmf_ctx nmf_ctx;
 

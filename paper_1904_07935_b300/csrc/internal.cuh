@@ -166,6 +166,11 @@ bool chain_config_cluster(int N, int T, int cl, ChainConfig* cfg);
 // place, B = R, G = S.
 cudaError_t h_update_run(float* X, const float* B, const float* G, int N, int K, int Kp, float eps,
                          int* status, cudaStream_t s);
+// The same update with the off-tile sums on the tensor cores (3xTF32 with
+// per-plane compensated folds); supported for 16 <= Kp <= 512.
+bool h_update_tc_supported(int Kp);
+cudaError_t h_update_tc_run(float* X, const float* B, const float* G, int N, int K, int Kp, float eps,
+                            int* status, cudaStream_t s);
 // Base of W tile [lo, lo + T) (T <= 16) for the chain: Y[:, tile] from B = P,
 // G = Q and the current (partly updated) factor X, with the new columns
 // [0, new_end).
@@ -203,8 +208,10 @@ struct WPersistConfig {
   int worker_wr = 1;      // rows per worker lane group (2 for Kp >= 192)
   int chain_rows = 0;     // rows per chain CTA
   size_t smem = 0;
+  bool tc = false;        // worker clusters form the tile bases on the tensor cores
 };
-bool w_persistent_config(int N, int Kp, WPersistConfig* cfg);
+// tc: the workers form the tile bases on the tensor cores (TF32 pairs).
+bool w_persistent_config(int N, int Kp, WPersistConfig* cfg, bool tc = false);
 // d_sync: w_sync_ints(K) ints (zeroed by the call, on the stream).
 size_t w_sync_ints(int K);
 // pre0 != nullptr: Y's columns [0, 16) plus pre0 (N x 16) already hold tile

@@ -16,6 +16,7 @@ using namespace plnmf;
 struct nmf_ctx {
   int V = 0, D = 0, K = 0, Kp = 0, T = 16, fmt = 0, prec = 0;
   bool use_tc = false;      // FP32 Grams on the tensor cores (3xTF32)
+  bool tc_updates = false;  // off-tile sums of the factor updates on the tensor cores
   bool bf16 = false;        // precision form: BF16 tensor-core products and Grams
   void* A_bf16 = nullptr;   // BF16 copy of dense A (V x lda)
   bool tma = false;         // BF16 products through the TMA-fed kernel
@@ -210,6 +211,7 @@ cudaError_t enq_update(nmf_ctx* c, float* X, const float* G, const float* B, int
   const int K = c->K, Kp = c->Kp;
   if (!is_w) {
     c->launch_count += 1;
+    if (c->tc_updates) return h_update_tc_run(X, B, G, N, K, Kp, c->eps, c->d_status, c->stream);
     return h_update_run(X, B, G, N, K, Kp, c->eps, c->d_status, c->stream);
   }
   if (c->w_persistent) {
@@ -502,6 +504,7 @@ nmf_status init_impl(const nmf_problem* p, nmf_ctx* c) {
   CK(cudaMemsetAsync(c->R, 0, sizeof(float) * nD, c->stream));
   CK(cudaMemsetAsync(c->Y, 0, sizeof(float) * nMax, c->stream));
   c->use_tc = (p->flags & NMF_FLAG_TC_GRAMS) != 0;
+  c->tc_updates = (p->flags & NMF_FLAG_TC_UPDATES) && h_update_tc_supported(Kp) && tma_available();
   c->bf16 = c->prec == NMF_PREC_BF16;
   if (c->bf16) {
     // BF16 copy of A for the tensor-core products; FP32 Grams and buffers for
@@ -558,7 +561,7 @@ nmf_status init_impl(const nmf_problem* p, nmf_ctx* c) {
   // Whole W update in one launch wherever a 16- or 8-CTA chain cluster and at
   // least one worker cluster fit; its result does not depend on how many of
   // the clusters run at the same time, so no probe launch is needed.
-  c->w_persistent = !(p->flags & NMF_FLAG_MULTI_LAUNCH_W) && w_persistent_config(V, Kp, &c->wp);
+  c->w_persistent = !(p->flags & NMF_FLAG_MULTI_LAUNCH_W) && w_persistent_config(V, Kp, &c->wp, c->tc_updates);
   CK(enq_gram(c, c->gramW, c->W, c->S));
   c->s_valid = true;
   CK(cudaStreamSynchronize(c->stream));

@@ -27,6 +27,7 @@
 
 #include "devutil.cuh"
 #include "internal.cuh"
+#include "tcutil.cuh"
 
 namespace plnmf {
 namespace {
@@ -256,6 +257,19 @@ __global__ void transpose_bf16_kernel(const float* __restrict__ src, int rows, i
 }
 
 }  // namespace
+
+bool tma_map_f32(CUtensorMap* map, const float* base, int64_t rows, int64_t cols, int64_t ld, int box_cols,
+                 int box_rows) {
+  auto enc = get_encode();
+  if (!enc || ((ld * 4) & 15) || (reinterpret_cast<uintptr_t>(base) & 15)) return false;
+  cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+  cuuint64_t strides[1] = {(cuuint64_t)(ld * 4)};
+  cuuint32_t box[2] = {(cuuint32_t)box_cols, (cuuint32_t)box_rows};
+  cuuint32_t es[2] = {1, 1};
+  return enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(base), dims, strides, box, es,
+             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
 
 // Tensor-map encoding reachable and the kernels' shared-memory opt-in done
 // (once per process, outside any stream capture).

@@ -44,6 +44,7 @@
 
 #include "devutil.cuh"
 #include "internal.cuh"
+#include "tcutil.cuh"
 
 namespace plnmf {
 namespace {
@@ -415,6 +416,248 @@ __device__ void worker_role(const WParams& p, char* smem, int wid) {
     __syncthreads();
     if (tid == 0) red_release_add_gpu(sync_base_done(p, nt, tau), 1);
   }
+}
+
+// --------------------------------------------------------------------------
+// Worker role on the tensor cores: the same tile bases with the off-tile sums
+// (Eqs. 4 and 6) as a [128 rows x Kp] x [Kp x 16] product on tcgen05.  The
+// operands are split into TF32 pairs (hi = tf32(x), lo = tf32(x - hi); three
+// kind::tf32 MMAs per K step, about 2^-21 relative per product); each
+// 32-column plane of the rows accumulates in its own 16-column slice of
+// tensor memory and the slices are folded into the running value with
+// compensation, plane by plane.  The B operand of tile tau is Q[lo + c][j]
+// for the columns the base needs (new j < lo - 16, old j >= lo + 16), zero
+// elsewhere.  Roles: warps 0-3 one row each (split, fold, epilogue); thread
+// 128 streams the planes of 128-row passes (TMA, 128-byte swizzle); thread
+// 160 issues the MMAs into one of two halves of tensor memory (pass parity);
+// every thread builds B at the start of a tile.
+// --------------------------------------------------------------------------
+constexpr int WPW = 32;               // FP32 columns per plane
+constexpr int WTM = 128;              // rows per pass (TMEM lanes)
+constexpr int WPLANE = WTM * 128;     // 16 KB
+constexpr int WBPLANE = WT * 128;     // 2 KB
+constexpr int WNSMAX = 6;
+
+__host__ __device__ constexpr int wtc_planes(int Kp) { return (Kp + WPW - 1) / WPW; }
+__host__ __device__ constexpr int wtc_slots(int Kp) {
+  return (200 * 1024 - 4 * wtc_planes(Kp) * WBPLANE) / (2 * WPLANE) > WNSMAX
+             ? WNSMAX
+             : ((200 * 1024 - 4 * wtc_planes(Kp) * WBPLANE) / (2 * WPLANE) < 2
+                    ? 2
+                    : (200 * 1024 - 4 * wtc_planes(Kp) * WBPLANE) / (2 * WPLANE));
+}
+__host__ __device__ constexpr unsigned wtc_tmem_cols(int Kp) {
+  return 2 * wtc_planes(Kp) * WT <= 32    ? 32u
+         : 2 * wtc_planes(Kp) * WT <= 64  ? 64u
+         : 2 * wtc_planes(Kp) * WT <= 128 ? 128u
+         : 2 * wtc_planes(Kp) * WT <= 256 ? 256u
+                                           : 512u;
+}
+size_t wtc_smem(int Kp) {
+  return (size_t)2 * wtc_slots(Kp) * WPLANE + (size_t)2 * wtc_planes(Kp) * WBPLANE + 1024;
+}
+
+__device__ void worker_role_tc(const WParams& p, char* smem_raw, int wid, const CUtensorMap* mapX) {
+  if (wid >= p.nb) return;                                    // no rows (small N)
+  char* smem = reinterpret_cast<char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  const int nt = (p.K + WT - 1) / WT;
+  const int P = wtc_planes(p.Kp), NS = wtc_slots(p.Kp);
+  const unsigned cols = wtc_tmem_cols(p.Kp);
+  char* ahi = smem;
+  char* alo = smem + NS * WPLANE;
+  char* bhi = smem + 2 * NS * WPLANE;
+  char* blo = bhi + P * WBPLANE;
+  __shared__ __align__(8) unsigned long long full[WNSMAX], loready[WNSMAX], empty[WNSMAX];
+  __shared__ __align__(8) unsigned long long done[2], tfree[2], fin;
+  __shared__ unsigned tmem_slot;
+  __shared__ int s_go[2];
+  const int tid = threadIdx.x, warp = tid >> 5;
+  const int wbeg = wid * p.per, wend = min(p.N, wbeg + p.per);
+  const int npass = (wend - wbeg + WTM - 1) / WTM;
+  if (tid == 0) {
+    for (int s = 0; s < NS; ++s) {
+      mbar_init(smem_u32(&full[s]), 1);
+      mbar_init(smem_u32(&loready[s]), WTM);
+      mbar_init(smem_u32(&empty[s]), 1);
+    }
+    for (int h = 0; h < 2; ++h) {
+      mbar_init(smem_u32(&done[h]), 1);
+      mbar_init(smem_u32(&tfree[h]), WTM);
+    }
+    mbar_init(smem_u32(&fin), 1);
+    fence_mbar_init();
+  }
+  if (warp == 0) tc::tmem_alloc(&tmem_slot, cols);
+  tc::fence_before();
+  __syncthreads();
+  tc::fence_after();
+  const unsigned tmem = tmem_slot;
+  bool dead = false;
+  auto bwait = [&](unsigned long long* bar, unsigned parity) {
+    if (dead) return;
+    if (!tc::wait(smem_u32(bar), parity, p.wait_ns)) {
+      atomicOr(p.status, ST_TIMEOUT);
+      dead = true;
+    }
+  };
+  int gp = 0, gc = 0;                                         // passes / planes streamed so far
+  int issued[WNSMAX] = {0, 0, 0, 0, 0, 0};
+  for (int tau = 0; tau < nt; ++tau) {
+    if (tau == 0 && p.pre0) continue;                         // tile 0's base was formed before the launch
+    const int lo = tau * WT, hi = min(p.K, lo + WT), w = hi - lo;
+    const int new_end = tau >= 1 ? lo - WT : 0;
+    if (tid == 0) {
+      int go = 1;
+      if (tau >= 2)
+        go = wait_count(sync_chain_done(p, nt, tau - 2), p.cl + p.extra_arrivals, p, sync_started(p), p.cl) == 1;
+      if (go) go = atomicCAS(sync_state(p, nt, tau, wid), 0, 1) == 0 ? 1 : 2;
+      fence_proxy_async_global();
+      s_go[tau & 1] = go;
+    }
+    __syncthreads();
+    const int go = s_go[tau & 1];
+    if (go == 0) break;
+    if (go == 2) continue;
+    // B operand of this tile (every thread; the previous tile's MMAs are
+    // complete: its last pass was read before the barrier above).
+    for (int e = tid; e < WT * P * WPW; e += WNT) {
+      const int c = e / (P * WPW), j = e % (P * WPW);
+      const bool in = j < p.K && lo + c < p.K && (j < new_end || j >= lo + WT);
+      const float v = in ? __ldg(p.Q + (int64_t)(lo + c) * p.Kp + j) : 0.f;
+      const float h = tc::tf32_rn(v), l = tc::tf32_rn(v - h);
+      const unsigned off = (unsigned)((j / WPW) * WBPLANE) + tc::sw128_off(c, (j % WPW) * 4);
+      *reinterpret_cast<float*>(bhi + off) = h;
+      *reinterpret_cast<float*>(blo + off) = l;
+    }
+    tc::fence_async_smem();
+    __syncthreads();
+    if (tid < WTM) {
+      // ---- rows: split the planes, fold the slices, form and store the base
+      const unsigned lane_base = (unsigned)(warp * 32) << 16;
+      for (int k = 0; k < npass; ++k) {
+        const int gpk = gp + k, half = gpk & 1;
+        for (int q = 0; q < P; ++q) {
+          const int g = gc + k * P + q, s = g % NS;
+          bwait(&full[s], (unsigned)(g / NS) & 1u);
+          char* ph = ahi + s * WPLANE;
+          char* pl = alo + s * WPLANE;
+#pragma unroll
+          for (int u = 0; u < 8; ++u) {
+            const unsigned off = tc::sw128_off(tid, u * 16);
+            const float4 v = *reinterpret_cast<const float4*>(ph + off);
+            float4 h4, l4;
+            h4.x = tc::tf32_rn(v.x); l4.x = tc::tf32_rn(v.x - h4.x);
+            h4.y = tc::tf32_rn(v.y); l4.y = tc::tf32_rn(v.y - h4.y);
+            h4.z = tc::tf32_rn(v.z); l4.z = tc::tf32_rn(v.z - h4.z);
+            h4.w = tc::tf32_rn(v.w); l4.w = tc::tf32_rn(v.w - h4.w);
+            *reinterpret_cast<float4*>(ph + off) = h4;
+            *reinterpret_cast<float4*>(pl + off) = l4;
+          }
+          tc::fence_async_smem();
+          mbar_arrive(smem_u32(&loready[s]));
+        }
+        const int v = wbeg + k * WTM + tid;
+        const bool valid = v < wend;
+        float acc[WT], cmp[WT];
+#pragma unroll
+        for (int c = 0; c < WT; ++c) {
+          acc[c] = valid && c < w ? __ldg(p.P + (int64_t)v * p.Kp + lo + c) : 0.f;
+          cmp[c] = 0.f;
+        }
+        bwait(&done[half], (unsigned)(gpk >> 1) & 1u);
+        tc::fence_after();
+        for (int q = 0; q < P; ++q) {
+          float blk[WT];
+          tc::tmem_ld16(tmem + lane_base + (unsigned)((half * P + q) * WT), blk);
+#pragma unroll
+          for (int c = 0; c < WT; ++c) comp_fold(acc[c], cmp[c], blk[c]);
+        }
+        tc::fence_before();
+        mbar_arrive(smem_u32(&tfree[half]));
+#pragma unroll
+        for (int c = 0; c < WT; ++c) acc[c] += cmp[c];
+        if (valid) {
+          // Old in-tile columns j > c.
+          const float* xr = p.X + (int64_t)v * p.Kp + lo;
+          float xo[WT];
+#pragma unroll
+          for (int c = 0; c < WT; ++c) xo[c] = c < w ? xr[c] : 0.f;
+          const float* gt = p.Q + (int64_t)lo * p.Kp + lo;
+#pragma unroll
+          for (int j = 1; j < WT; ++j)
+#pragma unroll
+            for (int c = 0; c < WT; ++c)
+              if (j > c && j < w) acc[c] = fmaf(-__ldg(gt + (int64_t)j * p.Kp + c), xo[j], acc[c]);
+          float* yr = p.Y + (int64_t)v * p.Kp + lo;
+          if (w == WT) {
+#pragma unroll
+            for (int q = 0; q < WT / 4; ++q)
+              *reinterpret_cast<float4*>(yr + 4 * q) = make_float4(acc[4 * q], acc[4 * q + 1], acc[4 * q + 2], acc[4 * q + 3]);
+          } else {
+            for (int c = 0; c < w; ++c) yr[c] = acc[c];
+          }
+        }
+      }
+    } else if (tid == 128) {
+      // ---- planes of every pass through the ring
+      for (int k = 0; k < npass && !dead; ++k) {
+        const int row0 = wbeg + k * WTM;
+        for (int q = 0; q < P && !dead; ++q) {
+          const int g = gc + k * P + q, s = g % NS;
+          if (g >= NS) bwait(&empty[s], (unsigned)(g / NS - 1) & 1u);
+          if (dead) break;
+          mbar_arrive_expect_tx(smem_u32(&full[s]), WPLANE);
+          tc::tma_load_2d(smem_u32(ahi + s * WPLANE), mapX, q * WPW, row0, smem_u32(&full[s]));
+          ++issued[s];
+        }
+      }
+    } else if (tid == 160) {
+      // ---- MMAs of every pass into tensor-memory half (pass parity)
+      constexpr unsigned id = tc::idesc(WTM, WT, 2);
+      for (int k = 0; k < npass && !dead; ++k) {
+        const int gpk = gp + k, half = gpk & 1;
+        if (gpk >= 2) bwait(&tfree[half], (unsigned)((gpk - 2) >> 1) & 1u);
+        tc::fence_after();
+        for (int q = 0; q < P && !dead; ++q) {
+          const int g = gc + k * P + q, s = g % NS;
+          bwait(&loready[s], (unsigned)(g / NS) & 1u);
+          if (dead) break;
+          tc::fence_after();
+          const unsigned a_h = smem_u32(ahi + s * WPLANE), a_l = smem_u32(alo + s * WPLANE);
+          const unsigned b_h = smem_u32(bhi + q * WBPLANE), b_l = smem_u32(blo + q * WBPLANE);
+          const unsigned d = tmem + (unsigned)((half * P + q) * WT);
+#pragma unroll
+          for (int kk = 0; kk < WPW / 8; ++kk) {
+            const unsigned ko = (unsigned)kk * 32u;
+            tc::mma_tf32(d, tc::desc_sw128(a_h + ko), tc::desc_sw128(b_h + ko), id, kk > 0 ? 1u : 0u);
+            tc::mma_tf32(d, tc::desc_sw128(a_l + ko), tc::desc_sw128(b_h + ko), id, 1u);
+            tc::mma_tf32(d, tc::desc_sw128(a_h + ko), tc::desc_sw128(b_l + ko), id, 1u);
+          }
+          tc::commit(smem_u32(&empty[s]));
+        }
+        tc::commit(smem_u32(&done[half]));
+      }
+    }
+    gp += npass;
+    gc += npass * P;
+    // A claimed block is always published (even after a timed-out wait).
+    tc::fence_before();
+    __syncthreads();
+    tc::fence_after();
+    if (tid == 0) red_release_add_gpu(sync_base_done(p, nt, tau), 1);
+  }
+  // Copies and MMAs still in flight complete before the CTA leaves (bounded).
+  if (tid == 128)
+    for (int s = 0; s < NS; ++s)
+      if (issued[s] > 0) tc::wait(smem_u32(&full[s]), (unsigned)(issued[s] - 1) & 1u, p.wait_ns);
+  if (tid == 160) {
+    tc::commit(smem_u32(&fin));
+    tc::wait(smem_u32(&fin), 0u, p.wait_ns);
+  }
+  tc::fence_before();
+  __syncthreads();
+  tc::fence_after();
+  if (warp == 0) tc::tmem_dealloc(tmem, cols);
 }
 
 // --------------------------------------------------------------------------
@@ -790,11 +1033,12 @@ __device__ void chain_role(const WParams& p, char* smem) {
   __syncthreads();
 }
 
-template <int RPT, int WR>
-__global__ void __launch_bounds__(WNT, 1) w_update_persistent_kernel(WParams p) {
+template <int RPT, int WR, bool TCW>
+__global__ void __launch_bounds__(WNT, 1) w_update_persistent_kernel(WParams p, const __grid_constant__ CUtensorMap mapX) {
   extern __shared__ __align__(16) char smem[];
   const unsigned cid = cluster_id_x();
   if (cid == 0) chain_role<RPT>(p, smem);
+  else if (TCW) worker_role_tc(p, smem, (int)blockIdx.x - p.cl, &mapX);
   else worker_role<WR>(p, smem, (int)blockIdx.x - p.cl);
 }
 
@@ -804,9 +1048,10 @@ size_t persistent_smem(int rpt, int Kp, int worker_rows) {
   return std::max(chain, worker);
 }
 
-template <int RPT, int WR>
-cudaError_t launch_persistent_t(const WParams& p, int n_clusters, size_t smem, cudaStream_t s) {
-  auto kern = w_update_persistent_kernel<RPT, WR>;
+template <int RPT, int WR, bool TCW>
+cudaError_t launch_persistent_t(const WParams& p, const CUtensorMap& map, int n_clusters, size_t smem,
+                                cudaStream_t s) {
+  auto kern = w_update_persistent_kernel<RPT, WR, TCW>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   if ((e = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1)) != cudaSuccess) return e;
@@ -823,12 +1068,12 @@ cudaError_t launch_persistent_t(const WParams& p, int n_clusters, size_t smem, c
   attr[0].val.clusterDim.z = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, kern, p);
+  return cudaLaunchKernelEx(&cfg, kern, p, map);
 }
 
 template <int RPT>
 int max_clusters_t(int cl, size_t smem) {
-  auto kern = w_update_persistent_kernel<RPT, 1>;
+  auto kern = w_update_persistent_kernel<RPT, 1, false>;
   if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess ||
       cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess) {
     cudaGetLastError();
@@ -870,7 +1115,7 @@ size_t w_sync_ints(int K) {
   return (1 + 2 * nt) * kSyncStride + nt * WMAXNB;
 }
 
-bool w_persistent_config(int N, int Kp, WPersistConfig* cfg) {
+bool w_persistent_config(int N, int Kp, WPersistConfig* cfg, bool tc) {
   for (int cl : {16, 8}) {
     const int nrc = (N + cl - 1) / cl;
     const int rpt = (nrc + WNR - 1) / WNR;
@@ -882,7 +1127,8 @@ bool w_persistent_config(int N, int Kp, WPersistConfig* cfg) {
     constexpr size_t kBudget = 216 * 1024;
     int worker_rows = WNT / 4;
     while (worker_rows > 16 && persistent_smem(rpt, Kp, worker_rows) > kBudget) worker_rows -= 8;
-    const size_t smem = persistent_smem(rpt, Kp, worker_rows);
+    size_t smem = persistent_smem(rpt, Kp, worker_rows);
+    if (tc) smem = std::max(smem, wtc_smem(Kp));        // tensor-core workers: plane ring and B operand
     if (smem > kBudget) continue;
     const int nc = max_clusters(rpt, cl, smem);
     if (nc < 2) continue;
@@ -893,6 +1139,7 @@ bool w_persistent_config(int N, int Kp, WPersistConfig* cfg) {
     cfg->worker_rows = worker_rows;
     cfg->worker_wr = Kp >= 192 ? 2 : 1;
     cfg->smem = smem;
+    cfg->tc = tc;
     return true;
   }
   return false;
@@ -910,16 +1157,27 @@ cudaError_t w_persistent_run(float* X, const float* P, const float* Q, float* Y,
   const int nb = (N + per - 1) / per;
   WParams p{X, P, Q, Y, N, K, Kp, eps, d_status, d_sync, cfg.cluster, cfg.worker_rows, (N + cfg.cluster - 1) / cfg.cluster,
             nb, per, pre0, wait_ns ? wait_ns : kWaitLimitNs, extra_arrivals};
+  CUtensorMap map = {};
+  if (cfg.tc) {
+    if (!tma_map_f32(&map, X, N, Kp, Kp, WPW, WTM)) return cudaErrorNotSupported;
+    switch (cfg.rpt) {
+      case 1: return launch_persistent_t<1, 1, true>(p, map, cfg.n_clusters, cfg.smem, s);
+      case 2: return launch_persistent_t<2, 1, true>(p, map, cfg.n_clusters, cfg.smem, s);
+      case 3: return launch_persistent_t<3, 1, true>(p, map, cfg.n_clusters, cfg.smem, s);
+      case 4: return launch_persistent_t<4, 1, true>(p, map, cfg.n_clusters, cfg.smem, s);
+      default: return cudaErrorInvalidValue;
+    }
+  }
   const bool two = cfg.worker_wr == 2;
   switch (cfg.rpt) {
-    case 1: return two ? launch_persistent_t<1, 2>(p, cfg.n_clusters, cfg.smem, s)
-                       : launch_persistent_t<1, 1>(p, cfg.n_clusters, cfg.smem, s);
-    case 2: return two ? launch_persistent_t<2, 2>(p, cfg.n_clusters, cfg.smem, s)
-                       : launch_persistent_t<2, 1>(p, cfg.n_clusters, cfg.smem, s);
-    case 3: return two ? launch_persistent_t<3, 2>(p, cfg.n_clusters, cfg.smem, s)
-                       : launch_persistent_t<3, 1>(p, cfg.n_clusters, cfg.smem, s);
-    case 4: return two ? launch_persistent_t<4, 2>(p, cfg.n_clusters, cfg.smem, s)
-                       : launch_persistent_t<4, 1>(p, cfg.n_clusters, cfg.smem, s);
+    case 1: return two ? launch_persistent_t<1, 2, false>(p, map, cfg.n_clusters, cfg.smem, s)
+                       : launch_persistent_t<1, 1, false>(p, map, cfg.n_clusters, cfg.smem, s);
+    case 2: return two ? launch_persistent_t<2, 2, false>(p, map, cfg.n_clusters, cfg.smem, s)
+                       : launch_persistent_t<2, 1, false>(p, map, cfg.n_clusters, cfg.smem, s);
+    case 3: return two ? launch_persistent_t<3, 2, false>(p, map, cfg.n_clusters, cfg.smem, s)
+                       : launch_persistent_t<3, 1, false>(p, map, cfg.n_clusters, cfg.smem, s);
+    case 4: return two ? launch_persistent_t<4, 2, false>(p, map, cfg.n_clusters, cfg.smem, s)
+                       : launch_persistent_t<4, 1, false>(p, map, cfg.n_clusters, cfg.smem, s);
     default: return cudaErrorInvalidValue;
   }
 }

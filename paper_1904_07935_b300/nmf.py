@@ -48,6 +48,7 @@ FLAG_MULTI_LAUNCH_W = 2
 FLAG_NO_TMA = 4
 FLAG_BF16_SINGLE_A = 8
 FLAG_BF16_SINGLE_FACTORS = 16
+FLAG_TC_UPDATES = 32
 
 
 _vp, _i32, _i64, _dp = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.POINTER(ctypes.c_double)
