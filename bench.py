@@ -338,7 +338,7 @@ def run_gpu(args):
     dense = args.workload != "text20ng"
     bf16 = args.prec == "bf16"
     stream = torch.cuda.Stream(device=dev)
-    flags = nmf.FLAG_MULTI_LAUNCH_W if args.w_multi_launch else 0
+    flags = (nmf.FLAG_MULTI_LAUNCH_W if args.w_multi_launch else 0) | (nmf.FLAG_TC_UPDATES if args.tc_updates else 0)
     prec = nmf.PREC_BF16 if bf16 else nmf.PREC_FP32
     if dense:
         V, D = prob.A.shape
@@ -485,7 +485,8 @@ def run_gpu(args):
                    "tile_T": q["tile_T"], "chain_ctas": q["chain_ctas"], "precision": args.prec,
                    "l2": "flushed between steps (256 MB write)", "parallelism": "replicas" if world > 1 else "single",
                    "ms_per_step_warm_l2": round(ms_warm, 5), "rel_err_final": rel,
-                   "algorithm": ALGOS[args.algo]},
+                   "algorithm": ALGOS[args.algo],
+                   "update_off_tile_sums": "tensor cores (TF32 pairs)" if args.tc_updates else "SIMT FP32"},
         "e2e": {"value": round(1.0 / t_e2e, 3), "unit": "iter/s", "h2d_bytes_per_step": fac_bytes,
                 "d2h_bytes_per_step": fac_bytes + 16},
         "gpu_launches": int(q["launches_per_iter"]) * args.steps,
@@ -871,8 +872,9 @@ def main():
     ap.add_argument("--ws-eval", type=int, default=100000, help="warmstart: evaluation documents")
     ap.add_argument("--ws-epochs", type=int, default=20, help="warmstart: training epochs")
     ap.add_argument("--w-multi-launch", action="store_true",
-                    help="W update as per-tile launches instead of one cooperative launch "
-                         "(for per-kernel profiling)")
+                    help="W update as per-tile launches instead of one launch (for per-kernel profiling)")
+    ap.add_argument("--tc-updates", action="store_true",
+                    help="the factor updates' off-tile sums on the tensor cores (NMF_FLAG_TC_UPDATES)")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3
