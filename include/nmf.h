@@ -166,13 +166,13 @@ nmf_status nmf_get_factors(nmf_ctx* c, float* W, float* H);
 nmf_status nmf_set_factors(nmf_ctx* c, const float* W, const float* H);
 
 /* Individual steps of one iteration, for per-step parity and timing
- * (Alg. 1 lines noted; all asynchronous on the context stream):
- *   NMF_STEP_R        R = A^T W                    (line 4)
- *   NMF_STEP_S        S = W^T W                    (line 5)
- *   NMF_STEP_UPDATE_H H update with R, S           (lines 6-8, Alg. 2 order)
- *   NMF_STEP_P        P = A H^T                    (line 10)
- *   NMF_STEP_Q        Q = H H^T                    (line 11)
- *   NMF_STEP_UPDATE_W W update with P, Q           (lines 12-16, Alg. 2 order)
+ * (the steps of Alg. 1; all asynchronous on the context stream):
+ *   NMF_STEP_R        R = A^T W
+ *   NMF_STEP_S        S = W^T W
+ *   NMF_STEP_UPDATE_H H update with R, S           (Alg. 2 order)
+ *   NMF_STEP_P        P = A H^T
+ *   NMF_STEP_Q        Q = H H^T
+ *   NMF_STEP_UPDATE_W W update with P, Q           (Alg. 2 order)
  *   NMF_STEP_OBJECTIVE objective of current W, H using the current P and the
  *                     Gram of the current W (recomputed) and Q. */
 typedef enum {
@@ -199,7 +199,7 @@ nmf_status nmf_set_buffer(nmf_ctx* c, int32_t which, const float* src, int64_t c
  * the H and W updates run column by column, each column one grid-wide step
  * (W: two, the second normalising the column before the next one reads it),
  * so an iteration is 3K + O(1) dependent launches.  H^T S_k and W Q_k use
- * the current factor and include the j = k term (Alg. 1 lines 6-8, 12-16);
+ * the current factor and include the j = k term (Alg. 1's H and W loops);
  * FP32 with FP32 dot products (no compensation).  n_iters iterations of
  * the context's factors (same entry/exit state as nmf_iterate, so the two
  * can be mixed).  step_ms: NULL -> the iterations run as a CUDA graph
@@ -302,7 +302,7 @@ void nmf_batch_destroy(nmf_batch* b);
 nmf_status nmf_batch_submit(const nmf_problem* ps, int32_t n, int32_t n_iters, nmf_ctx** outs);
 
 /* Learned warm start for new documents with W fixed (fixed-W H subproblem).
- * With W fixed, repeating the H loop of Alg. 1 (lines 4-8; S = W^T W) is
+ * With W fixed, repeating the H loop of Alg. 1 (S = W^T W) is
  * exact coordinate descent on min_{h >= eps} ||a - W h||^2 per document and
  * converges to the unique optimum h*.  A small network predicts a starting
  * h from r = W^T a so that fewer sweeps are needed.  The network (not in the
@@ -355,7 +355,7 @@ nmf_status nmf_warm_h(nmf_ctx* fixedW, nmf_mlp* mlp, const nmf_problem* new_docs
                       const float* H_ref, float* H_out, float* R_out, int32_t* sweeps_out, double* trace);
 
 /* BF16 product with TMA-fed tensor-core MMAs (the kernel of the BF16 form,
- * Alg. 1 lines 4 and 10): C (M x N, FP32, row-major, ldc) = A B^T with
+ * the products R and P of Alg. 1): C (M x N, FP32, row-major, ldc) = A B^T with
  * A row-major M x K (lda) and B row-major N x K (ldb): both operands K-major
  * bfloat16 (uint16 bit patterns), FP32 accumulation in tensor memory.  A and
  * B must start on 16-byte boundaries and lda, ldb be multiples of 8;

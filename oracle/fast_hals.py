@@ -76,7 +76,7 @@ def iteration(A, W: np.ndarray, H: np.ndarray, eps: float = DEFAULT_EPS, trace: 
 
     If ``trace`` is a dict it receives the intermediates R, S, H, P, Q, W.
     ``operand_round`` (e.g. bf16.round_bf16) rounds the operands of the four
-    matrix products (lines 4, 5, 10, 11) before they are multiplied exactly
+    matrix products (R, S, P, Q) before they are multiplied exactly
     (FP64): the definition of a reduced-precision-product form of Alg. 1.
     ``a_round``, if given, is used for A instead (e.g. bf16.round_bf16_split,
     A carried as a BF16 pair).  The k loops stay FP64.

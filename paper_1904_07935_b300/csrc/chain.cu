@@ -7,7 +7,7 @@
 // (phase 1 and the phase-3 updates of earlier tiles).  The kernel adds the
 // remaining contributions of new columns inside the tile, clamps at eps and,
 // for W, divides every finished column by its L2 norm before the next column
-// uses it (Alg. 1 lines 13-15).  Each thread keeps its rows' tile of Y in
+// uses it (Alg. 1's W loop).  Each thread keeps its rows' tile of Y in
 // registers; when column t is final its value is pushed into the later
 // columns of the tile ("right-looking"), so a column costs one clamp, one
 // square and the norm reduction on the critical path.

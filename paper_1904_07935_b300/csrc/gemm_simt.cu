@@ -1,6 +1,6 @@
 // FP32 SIMT GEMM family used by the FP32 path: dense products A H^T and
-// A^T W (Alg. 1 lines 4/10 for dense A), the Gram matrices W^T W and H H^T
-// (lines 5/11), phase 1 of the regrouped factor update (Eq. 4 plus the old
+// A^T W (Alg. 1 for dense A), the Gram matrices W^T W and H H^T (Alg. 1),
+// phase 1 of the regrouped factor update (Eq. 4 plus the old
 // half of Eq. 5, as one strictly-upper masked GEMM) and phase 3 (Eq. 6).
 //
 // 64 x 64 output tile per 256-thread CTA, 4 x 4 register micro-tile per

@@ -1,4 +1,4 @@
-// Fused H update (Alg. 1 lines 6-8 in the tiled order of Alg. 2).
+// Fused H update (Alg. 1's H loop in the tiled order of Alg. 2).
 //
 // H carries no normalisation, so every document (row of H^T) is updated
 // independently of the others (Sec. 4.1, last sentence) and the whole update

@@ -265,8 +265,8 @@ cudaError_t enq_objective(nmf_ctx* c) {
                        c->n_obj_partial, c->hist, c->d_counter, kHistCap, c->stream);
 }
 
-// One iteration.  On entry S = W^T W and R = A^T W for the current W (Alg. 1
-// lines 4-5); on exit the same holds for the new W.  R is therefore formed at
+// One iteration.  On entry S = W^T W and R = A^T W for the current W (the
+// first two products of Alg. 1); on exit the same holds for the new W.  R is therefore formed at
 // the end of the previous iteration, right after the W update, where it runs
 // beside S; likewise Q beside P.  Each pair is independent (same inputs,
 // disjoint outputs and work buffers), so the graph has two branches there:

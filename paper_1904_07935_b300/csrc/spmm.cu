@@ -1,4 +1,4 @@
-// CSR SpMM for the products P = A H^T and R = A^T W (Alg. 1, lines 4 and 10)
+// CSR SpMM for the products P = A H^T and R = A^T W (the products of Alg. 1)
 // when A is a sparse term-document matrix (the paper calls a library CSR
 // routine there, Sec. 4.1 / 4.2).
 //

@@ -1,7 +1,7 @@
 // Tensor-core GEMM on the 5th-generation tensor cores (tcgen05) for the dense
-// contractions of the iteration: the Gram matrices W^T W and H H^T (Alg. 1
-// lines 5 and 11), phase 1 / phase 3 of the regrouped W update (Eqs. 4, 6)
-// and the dense products A H^T, A^T W (lines 4, 10).
+// contractions of the iteration (Alg. 1): the Gram matrices W^T W and H H^T,
+// phase 1 / phase 3 of the regrouped W update (Eqs. 4, 6) and the dense
+// products A H^T, A^T W.
 //
 // C (M x N) = op(A) (M x K) * B (K x N) with the GemmArgs epilogues of the
 // SIMT family.  One CTA computes a 128 x BN tile (BN <= 256, a multiple of

@@ -1,7 +1,7 @@
 // BF16 products of the precision form on the tensor cores with TMA operand
 // loads: C (M x N, FP32, row-major) = A (M x Kd) * B (N x Kd)^T, both operands
 // K-major BF16 in global memory (A = the BF16 copy of A or of A^T, B = the
-// BF16 transposed factor, Alg. 1 lines 4 and 10).  Split forms: an operand
+// BF16 transposed factor; the products R and P of Alg. 1).  Split forms: an operand
 // X is given as two BF16 arrays, X_hi = bf16(X) and X_lo = bf16(X - X_hi),
 // whose sum carries X to about 16 significant bits.  With A split each stage
 // holds both A tiles and C = A_hi B^T + A_lo B^T (two MMAs per K step, twice

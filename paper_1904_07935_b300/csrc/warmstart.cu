@@ -1,6 +1,6 @@
 // Learned warm start for the fixed-W H subproblem: a small network maps a new
-// document's data term r = W^T a (one row of R = A^T W, Alg. 1 line 4) to an
-// initial h, from which the H loop of Alg. 1 (lines 6-8, S = W^T W fixed) is
+// document's data term r = W^T a (one row of R = A^T W, Alg. 1) to an
+// initial h, from which the H loop of Alg. 1 (S = W^T W fixed) is
 // repeated.  The paper has no learned component; the network is fixed here:
 //   z1 = x W1 + b1, a1 = GELU(z1), z2 = a1 W2 + b2, a2 = GELU(z2),
 //   z3 = a2 W3 + b3, y = softplus(z3)       (Wl stored n_in x n_out)

@@ -1,5 +1,5 @@
-// The whole W update (Alg. 1 lines 12-16 in the tiled order of Alg. 2) as
-// one persistent, cooperative launch.
+// The whole W update (Alg. 1's W loop in the tiled order of Alg. 2) as
+// one persistent launch.
 //
 // W is updated in tiles of 16 columns.  Column t of tile [lo, hi) is
 //   w_t = max(eps, P_t - sum_{j < t} Q[j][t] w_j(new) - sum_{j > t} Q[j][t] w_j(old)),
@@ -82,8 +82,8 @@ __device__ __forceinline__ unsigned cluster_id_x() {
 
 // Hand-off counters live one per 128-byte line (kSyncStride ints apart), so
 // the workers' polling and the chain's release do not share a line:
-// line 0 counts the chain CTAs that started, lines 1 .. nt the chain CTAs
-// that stored tile tau (chain_done), lines nt + 1 .. 2 nt the finished blocks
+// counter 0 counts the chain CTAs that started, counters 1 .. nt the chain
+// CTAs that stored tile tau (chain_done), counters nt + 1 .. 2 nt the finished blocks
 // of tile tau's base (base_done); then nt x WMAXNB block states (0 free,
 // 1 claimed).
 constexpr int kSyncStride = 32;

@@ -135,7 +135,7 @@ def test_bf16_rejected_for_sparse(nmf):
     assert e.value.status == nmf.NMF_EUNSUPPORTED
 
 
-# --- the TMA-fed BF16 product (Alg. 1 lines 4 and 10 of the BF16 form) -----
+# --- the TMA-fed BF16 product (R = A^T W and P = A H^T of Alg. 1, BF16 form)
 
 def _bf16_bound(a64, b64):
     """|C - A B^T| bound: BF16 x BF16 products are exact in FP32, so only the

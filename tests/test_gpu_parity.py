@@ -115,6 +115,30 @@ def test_update_h_matches_alg1(nmf, K, T):
     assert forward_error_ratio(got, ref, h_update_scale(R, S, Hin, ref)) < 1e-6
 
 
+@pytest.mark.parametrize("K,D", [(64, 1500), (160, 11314), (176, 3001), (37, 149)])
+def test_update_h_row_counts_and_wide_ranks(nmf, K, D):
+    """The H update alone at the text-like document count (11,314 rows, one
+    row per group of four lanes), at K = 176 (11 tiles, S's blocks fetched
+    tile by tile) and on 149 rows with K = 37 (fewer rows than SMs, a ragged
+    last block of the off-tile sums)."""
+    V = 300
+    prob = synth.planted_dense(V, D, 6, 53 + K)
+    W0, H0 = synth.init_factors(54 + K, V, D, K)
+    W, H = _oracle_start(W0, H0)
+    A = prob.A.astype(np.float64)
+    R, S = f32(A.T @ W), f32(W.T @ W)
+    Hin = f32(H)
+    ctx = _dense_ctx(nmf, prob.A, K, W0, H0)
+    ctx.set_buffer(nmf.BUF_R, R)
+    ctx.set_buffer(nmf.BUF_S, S)
+    ctx.set_buffer(nmf.BUF_HT, np.ascontiguousarray(Hin.T))
+    ctx.run_step(nmf.STEP_UPDATE_H)
+    got = ctx.get_buffer(nmf.BUF_HT).T
+    ref = fh.update_h(R.astype(np.float64), S.astype(np.float64), Hin, EPS)
+    assert rel_h(got, ref) < TOL_ITER
+    assert forward_error_ratio(got, ref, h_update_scale(R, S, Hin, ref)) < 1e-6
+
+
 @pytest.mark.parametrize("K,T", [(16, 16), (16, 1), (20, 3), (37, 16), (48, 8)])
 def test_update_w_matches_alg1(nmf, K, T):
     prob = synth.planted_dense(900, 300, 6, 41)
