@@ -165,6 +165,28 @@ nmf_status nmf_get_factors(nmf_ctx* c, float* W, float* H);
  * normalisation).  Synchronous. */
 nmf_status nmf_set_factors(nmf_ctx* c, const float* W, const float* H);
 
+/* One iteration (Alg. 1, factor updates in the order of Alg. 2) on factors
+ * held by the caller: the same as nmf_set_factors(W_in, H_in),
+ * nmf_iterate(1), nmf_error(frob2), nmf_get_factors(W_out, H_out), with the
+ * copies overlapped with the iteration.
+ *   W_in, W_out  V x K, H_in, H_out  K x D, row-major FP32; any may be NULL
+ *                (that factor is neither loaded nor returned).  W_in may
+ *                equal W_out and H_in H_out (each input is read before its
+ *                output is written).  W_in is used as given (no
+ *                normalisation).
+ *   frob2        NULL or the objective ||A - W H||_F^2 after the iteration
+ *                (as nmf_error reports it).
+ * When every buffer given is pinned host memory (cudaHostAlloc,
+ * cudaHostRegister) or device memory, the copies and the iteration run as one
+ * CUDA graph (captured on the first call, reused while the pointers stay the
+ * same): H_in is copied while R = A^T W and S = W^T W of the new W run, H_out
+ * while P, Q and the W update run, W_out beside the objective.  R of the new
+ * W is not formed (a following nmf_iterate forms it).  Other host memory is
+ * copied before and after, without overlap.  Synchronous; returns the
+ * iteration's device status like nmf_error. */
+nmf_status nmf_iterate_host(nmf_ctx* c, const float* W_in, const float* H_in, float* W_out, float* H_out,
+                            double* frob2);
+
 /* Individual steps of one iteration, for per-step parity and timing
  * (the steps of Alg. 1; all asynchronous on the context stream):
  *   NMF_STEP_R        R = A^T W

@@ -248,11 +248,13 @@ cudaError_t objective_run(const float* W, const float* P, int V, int Kp, const f
 // The two halves of objective_run, for callers that overlap <W, P> (needs the
 // new W and P only) with the Gram S: partials of <W, P> (partial[0..n)), then
 // the <S, Q> partials (partial[n..n + 64)) and the history entry.  partial
-// holds at least n + 64 doubles.
+// holds at least n + 64 doubles.  `last` (optional, device) receives the
+// new history entry as well.
 cudaError_t objective_wp(const float* W, const float* P, int V, int Kp, double* partial, int n_partial,
                          cudaStream_t s);
 cudaError_t objective_finish(int Kp, const float* S, const float* Q, double normA2, double* partial,
-                             int n_partial, double* out, unsigned* d_counter, int hist_cap, cudaStream_t s);
+                             int n_partial, double* out, unsigned* d_counter, int hist_cap, cudaStream_t s,
+                             double* last = nullptr);
 constexpr int kSumsqBlocks = 592;
 cudaError_t sumsq_dense_f64(const float* A, int64_t rows, int64_t cols, int64_t ld,
                             double* d_out, int* d_bad, cudaStream_t s);

@@ -124,7 +124,8 @@ __global__ void dot_partial_kernel(const float* __restrict__ a, const float* __r
 // (<W, P> and <S, Q> partials of dot_partial_kernel, added in a fixed order);
 // appended to the history ring.
 __global__ void objective_final_kernel(const double* __restrict__ partial, int n_wp, int n_sq, double normA2,
-                                       double* __restrict__ hist, unsigned* counter, int hist_cap) {
+                                       double* __restrict__ hist, unsigned* counter, int hist_cap,
+                                       double* __restrict__ last) {
   double wp = 0.0, sq = 0.0;
   for (int i = threadIdx.x; i < n_wp; i += blockDim.x) wp += partial[i];
   for (int i = threadIdx.x; i < n_sq; i += blockDim.x) sq += partial[n_wp + i];
@@ -132,8 +133,10 @@ __global__ void objective_final_kernel(const double* __restrict__ partial, int n
   sq = block_sum_d<kObjThreads>(sq);
   if (threadIdx.x == 0) {
     const unsigned it = *counter;
-    hist[it % hist_cap] = normA2 - 2.0 * wp + sq;
+    const double f = normA2 - 2.0 * wp + sq;
+    hist[it % hist_cap] = f;
     *counter = it + 1;
+    if (last) *last = f;
   }
 }
 
@@ -226,12 +229,14 @@ cudaError_t objective_wp(const float* W, const float* P, int V, int Kp, double* 
 }
 
 cudaError_t objective_finish(int Kp, const float* S, const float* Q, double normA2, double* partial,
-                             int n_partial, double* out, unsigned* d_counter, int hist_cap, cudaStream_t s) {
+                             int n_partial, double* out, unsigned* d_counter, int hist_cap, cudaStream_t s,
+                             double* last) {
   if (Kp & 3) return cudaErrorInvalidValue;
   dot_partial_kernel<<<kSqBlocks, kObjThreads, 0, s>>>(S, Q, (long long)Kp * Kp, partial + n_partial);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  objective_final_kernel<<<1, kObjThreads, 0, s>>>(partial, n_partial, kSqBlocks, normA2, out, d_counter, hist_cap);
+  objective_final_kernel<<<1, kObjThreads, 0, s>>>(partial, n_partial, kSqBlocks, normA2, out, d_counter, hist_cap,
+                                                    last);
   return cudaGetLastError();
 }
 

@@ -85,6 +85,15 @@ struct nmf_ctx {
   cudaGraphExec_t graph_alg1_exec = nullptr;
   cudaGraph_t graph_mu = nullptr;           // nmf_iterate_mu
   cudaGraphExec_t graph_mu_exec = nullptr;
+  // nmf_iterate_host: copies of host factors overlapped with the iteration.
+  cudaStream_t side3 = nullptr;             // host copies beside the iteration
+  cudaEvent_t evio[6] = {};
+  cudaGraph_t graph_io = nullptr;
+  cudaGraphExec_t graph_io_exec = nullptr;
+  const void* io_key[5] = {};               // W_in, H_in, W_out, H_out, objective wanted
+  double* d_obj_last = nullptr;             // objective of the last iteration (device)
+  double* h_obj = nullptr;                  // its pinned host copy
+  int* h_status = nullptr;                  // pinned copy of the status word after the iteration
 };
 
 namespace {
@@ -273,11 +282,31 @@ cudaError_t enq_objective(nmf_ctx* c) {
 //   H update -> { P | Q } -> W update -> { S -> objective | R | <W, P> }
 // (the objective's <W, P> part needs only the new W and P, so it runs on a
 // third branch and the objective's last step only adds <S, Q>).
-cudaError_t enq_iteration(nmf_ctx* c) {
+// Host copies folded into one iteration (nmf_iterate_host): the new H is
+// copied out on side3 while P, Q and the W update run, the new W once the W
+// update is done (beside S and the objective), and the objective after it;
+// R of the new W, which the next iteration would need, is not formed (the
+// caller brings a new W).
+struct IoHooks {
+  float* H_out = nullptr;      // host, K x D
+  float* W_out = nullptr;      // host, V x K
+  double* obj_host = nullptr;  // pinned host scalar
+};
+
+cudaError_t enq_iteration(nmf_ctx* c, const IoHooks* io = nullptr) {
   cudaError_t e;
   cudaStream_t m = c->stream, b = c->side;
   const bool shared_op = c->bf16 && c->tma;      // one BF16 factor operand for both branches
   if ((e = enq_update(c, c->Ht, c->S, c->R, c->D, false)) != cudaSuccess) return e;
+  if (io && io->H_out) {
+    if ((e = cudaEventRecord(c->evio[0], m)) != cudaSuccess) return e;
+    if ((e = cudaStreamWaitEvent(c->side3, c->evio[0], 0)) != cudaSuccess) return e;
+    c->launch_count += 1;
+    if ((e = transpose_f32(c->Ht, c->D, c->K, c->Kp, c->stage, c->D, c->side3)) != cudaSuccess) return e;
+    if ((e = cudaMemcpyAsync(io->H_out, c->stage, sizeof(float) * (size_t)c->K * c->D, cudaMemcpyDefault,
+                             c->side3)) != cudaSuccess)
+      return e;
+  }
   if (shared_op && (e = bf16_operand(c, false, m)) != cudaSuccess) return e;
   if ((e = cudaEventRecord(c->evx[0], m)) != cudaSuccess) return e;
   if ((e = cudaStreamWaitEvent(b, c->evx[0], 0)) != cudaSuccess) return e;
@@ -297,9 +326,16 @@ cudaError_t enq_iteration(nmf_ctx* c) {
   if ((e = enq_update(c, c->W, c->Q, c->P, c->V, true, pre0)) != cudaSuccess) return e;
   if (shared_op && (e = bf16_operand(c, true, m)) != cudaSuccess) return e;
   if ((e = cudaEventRecord(c->evx[2], m)) != cudaSuccess) return e;
-  if ((e = cudaStreamWaitEvent(b, c->evx[2], 0)) != cudaSuccess) return e;
-  if ((e = enq_product_R(c, b, shared_op)) != cudaSuccess) return e;
-  if ((e = cudaEventRecord(c->evx[3], b)) != cudaSuccess) return e;
+  if (!io) {
+    if ((e = cudaStreamWaitEvent(b, c->evx[2], 0)) != cudaSuccess) return e;
+    if ((e = enq_product_R(c, b, shared_op)) != cudaSuccess) return e;
+    if ((e = cudaEventRecord(c->evx[3], b)) != cudaSuccess) return e;
+  } else if (io->W_out) {
+    if ((e = cudaStreamWaitEvent(c->side3, c->evx[2], 0)) != cudaSuccess) return e;
+    if ((e = cudaMemcpy2DAsync(io->W_out, sizeof(float) * c->K, c->W, sizeof(float) * c->Kp, sizeof(float) * c->K,
+                               c->V, cudaMemcpyDefault, c->side3)) != cudaSuccess)
+      return e;
+  }
   if ((e = cudaStreamWaitEvent(c->side2, c->evx[2], 0)) != cudaSuccess) return e;
   c->launch_count += 3;
   if ((e = objective_wp(c->W, c->P, c->V, c->Kp, c->obj_partial, c->n_obj_partial, c->side2)) != cudaSuccess)
@@ -308,9 +344,14 @@ cudaError_t enq_iteration(nmf_ctx* c) {
   if ((e = enq_gram(c, c->gramW, c->W, c->S, nullptr, shared_op)) != cudaSuccess) return e;
   if ((e = cudaStreamWaitEvent(m, c->evx[4], 0)) != cudaSuccess) return e;
   if ((e = objective_finish(c->Kp, c->S, c->Q, c->normA2, c->obj_partial, c->n_obj_partial, c->hist, c->d_counter,
-                            kHistCap, m)) != cudaSuccess)
+                            kHistCap, m, io ? c->d_obj_last : nullptr)) != cudaSuccess)
     return e;
-  return cudaStreamWaitEvent(m, c->evx[3], 0);
+  if (!io) return cudaStreamWaitEvent(m, c->evx[3], 0);
+  if (io->obj_host &&
+      (e = cudaMemcpyAsync(io->obj_host, c->d_obj_last, sizeof(double), cudaMemcpyDeviceToHost, m)) != cudaSuccess)
+    return e;
+  if ((e = cudaEventRecord(c->evio[1], c->side3)) != cudaSuccess) return e;
+  return cudaStreamWaitEvent(m, c->evio[1], 0);
 }
 
 // Establish the iteration's entry state (S and R of the current W).
@@ -351,6 +392,10 @@ void destroy_graph(nmf_ctx* c) {
   if (c->graph_mu) cudaGraphDestroy(c->graph_mu);
   c->graph_mu_exec = nullptr;
   c->graph_mu = nullptr;
+  if (c->graph_io_exec) cudaGraphExecDestroy(c->graph_io_exec);
+  if (c->graph_io) cudaGraphDestroy(c->graph_io);
+  c->graph_io_exec = nullptr;
+  c->graph_io = nullptr;
 }
 
 nmf_status validate_and_copy_csr(const nmf_problem* p, std::vector<int>& rp, std::vector<int>& ci,
@@ -407,12 +452,17 @@ nmf_status init_impl(const nmf_problem* p, nmf_ctx* c) {
 
   CK(cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking));
   CK(cudaStreamCreateWithFlags(&c->side2, cudaStreamNonBlocking));
+  CK(cudaStreamCreateWithFlags(&c->side3, cudaStreamNonBlocking));
   {
     const int nt = (c->K + T - 1) / T;
     c->ev.assign(1 + 2 * nt, nullptr);
     for (auto& e : c->ev) CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
     for (auto& e : c->evx) CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    for (auto& e : c->evio) CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
   }
+  CK(dalloc(&c->d_obj_last, 1));
+  CK(cudaHostAlloc(reinterpret_cast<void**>(&c->h_obj), sizeof(double), cudaHostAllocDefault));
+  CK(cudaHostAlloc(reinterpret_cast<void**>(&c->h_status), sizeof(int), cudaHostAllocDefault));
   CK(dalloc(&c->d_status, 1));
   CK(cudaMemset(c->d_status, 0, sizeof(int)));
   CK(dalloc(&c->d_sync, w_sync_ints(c->K)));
@@ -581,8 +631,17 @@ void free_ctx(nmf_ctx* c) {
   for (void* p : {(void*)c->A_bf16, c->Ab8, c->ATb8, c->Ab8lo, c->ATb8lo, c->Fb8, c->Fb8lo, (void*)c->gpart, (void*)c->ppart, (void*)c->resid_part,
                   (void*)c->d_sync, (void*)c->rpT, (void*)c->ciT, (void*)c->vaT, (void*)c->W, (void*)c->Ht, (void*)c->R,
                   (void*)c->P, (void*)c->S, (void*)c->Q, (void*)c->Y, (void*)c->stage, (void*)c->Y0lo, (void*)c->alg1_part,
-                  (void*)c->obj_partial, (void*)c->hist, (void*)c->d_counter, (void*)c->d_status})
+                  (void*)c->obj_partial, (void*)c->hist, (void*)c->d_counter, (void*)c->d_status,
+                  (void*)c->d_obj_last})
     if (p) cudaFree(p);
+  if (c->h_obj) cudaFreeHost(c->h_obj);
+  if (c->h_status) cudaFreeHost(c->h_status);
+  if (c->side3) {
+    cudaStreamSynchronize(c->side3);
+    cudaStreamDestroy(c->side3);
+  }
+  for (auto e : c->evio)
+    if (e) cudaEventDestroy(e);
   if (c->side) {
     cudaStreamSynchronize(c->side);
     cudaStreamDestroy(c->side);
@@ -641,6 +700,10 @@ void drop_graph(nmf_ctx* c) {
   if (c->graph) cudaGraphDestroy(c->graph);
   c->graph_exec = nullptr;
   c->graph = nullptr;
+  if (c->graph_io_exec) cudaGraphExecDestroy(c->graph_io_exec);
+  if (c->graph_io) cudaGraphDestroy(c->graph_io);
+  c->graph_io_exec = nullptr;
+  c->graph_io = nullptr;
 }
 
 // Autotuner for a batch member (Sec. 1's repeated factorisation: many small
@@ -1198,6 +1261,120 @@ nmf_status nmf_objective_history(nmf_ctx* c, double* out, int32_t n) {
   CK(cudaMemcpy(h.data(), c->hist, sizeof(double) * kHistCap, cudaMemcpyDeviceToHost));
   for (int i = 0; i < n; ++i) out[i] = h[(cnt - n + i) % kHistCap];
   return read_status(c);
+}
+
+// One iteration on host-held factors.  With host buffers the runtime can
+// copy asynchronously (pinned, or device memory) the copies are captured
+// with the iteration into one graph (cached for the last pointer set):
+//   main:  W_in -> W | R = A^T W | (S, H_in landed) H update | P | W update | S, objective | objective -> host
+//   side2:            S = W^T W                                                <W, P>
+//   side3:            H_in -> stage -> H^T   H^T -> stage -> H_out    W -> W_out
+// W comes in first, at the link's full rate, since R and S need it; H's copy
+// in then runs beside R and S, its copy out beside P, Q and the W update,
+// and W's copy out beside S and the objective.  The status word comes back
+// with the outputs.  Other host memory is copied before and after one
+// nmf_iterate, without overlap.
+nmf_status nmf_iterate_host(nmf_ctx* c, const float* W_in, const float* H_in, float* W_out, float* H_out,
+                            double* frob2) {
+  if (!c) return NMF_EINVAL;
+  auto async_ok = [](const void* p) {
+    if (!p) return true;
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+      cudaGetLastError();
+      return false;
+    }
+    return a.type == cudaMemoryTypeHost || a.type == cudaMemoryTypeDevice;
+  };
+  const bool dense = c->fmt == NMF_DENSE_F32;
+  if (!async_ok(W_in) || !async_ok(H_in) || !async_ok(W_out) || !async_ok(H_out)) {
+    nmf_status st = nmf_set_factors(c, W_in, H_in);
+    if (st != NMF_OK) return st;
+    if ((st = nmf_iterate(c, 1)) != NMF_OK) return st;
+    double f = 0.0;
+    if (frob2 && (st = nmf_error(c, &f, nullptr)) != NMF_OK) return st;
+    if (frob2) *frob2 = f;
+    return nmf_get_factors(c, W_out, H_out);
+  }
+  const void* key[5] = {W_in, H_in, W_out, H_out, (frob2 && !dense) ? c : nullptr};
+  if (c->graph_io_exec && std::memcmp(key, c->io_key, sizeof(key)) != 0) {
+    cudaGraphExecDestroy(c->graph_io_exec);
+    cudaGraphDestroy(c->graph_io);
+    c->graph_io_exec = nullptr;
+    c->graph_io = nullptr;
+  }
+  if (!c->graph_io_exec) {
+    cudaStream_t m = c->stream;
+    const int K = c->K, Kp = c->Kp;
+    c->launch_count = 0;
+    CK(cudaStreamBeginCapture(m, cudaStreamCaptureModeThreadLocal));
+    auto body = [&]() -> cudaError_t {
+      cudaError_t e;
+      // W first at the link's full rate (R and S wait for it), then H while
+      // they run.
+      if (W_in && (e = cudaMemcpy2DAsync(c->W, sizeof(float) * Kp, W_in, sizeof(float) * K, sizeof(float) * K, c->V,
+                                         cudaMemcpyDefault, m)) != cudaSuccess)
+        return e;
+      if ((e = cudaEventRecord(c->evio[2], m)) != cudaSuccess) return e;
+      if ((e = cudaStreamWaitEvent(c->side3, c->evio[2], 0)) != cudaSuccess) return e;
+      if (H_in) {
+        if ((e = cudaMemcpyAsync(c->stage, H_in, sizeof(float) * (size_t)K * c->D, cudaMemcpyDefault, c->side3)) !=
+            cudaSuccess)
+          return e;
+        c->launch_count += 1;
+        if ((e = transpose_f32(c->stage, K, c->D, c->D, c->Ht, Kp, c->side3)) != cudaSuccess) return e;
+        if ((e = cudaEventRecord(c->evio[3], c->side3)) != cudaSuccess) return e;
+      }
+      // Entry state of the iteration for this W: S beside R (in the BF16
+      // form both read one BF16 operand of W, made first).
+      const bool shared_op = c->bf16 && c->tma;
+      if (shared_op && (e = bf16_operand(c, true, m)) != cudaSuccess) return e;
+      if ((e = cudaEventRecord(c->evio[4], m)) != cudaSuccess) return e;
+      if ((e = cudaStreamWaitEvent(c->side2, c->evio[4], 0)) != cudaSuccess) return e;
+      if ((e = enq_gram(c, c->gramW, c->W, c->S, c->side2, shared_op)) != cudaSuccess) return e;
+      if ((e = cudaEventRecord(c->evio[5], c->side2)) != cudaSuccess) return e;
+      if ((e = enq_product_R(c, m, shared_op)) != cudaSuccess) return e;
+      if ((e = cudaStreamWaitEvent(m, c->evio[5], 0)) != cudaSuccess) return e;
+      if (H_in && (e = cudaStreamWaitEvent(m, c->evio[3], 0)) != cudaSuccess) return e;
+      IoHooks io;
+      io.H_out = H_out;
+      io.W_out = W_out;
+      io.obj_host = key[4] ? c->h_obj : nullptr;
+      if ((e = enq_iteration(c, &io)) != cudaSuccess) return e;
+      return cudaMemcpyAsync(c->h_status, c->d_status, sizeof(int), cudaMemcpyDeviceToHost, m);
+    };
+    const cudaError_t e = body();
+    cudaGraph_t g = nullptr;
+    const cudaError_t e2 = cudaStreamEndCapture(m, &g);
+    if (e != cudaSuccess || e2 != cudaSuccess) {
+      if (g) cudaGraphDestroy(g);
+      cudaGetLastError();
+      return from_cuda(e != cudaSuccess ? e : e2);
+    }
+    c->graph_io = g;
+    const cudaError_t e3 = cudaGraphInstantiate(&c->graph_io_exec, g, 0);
+    if (e3 != cudaSuccess) {
+      cudaGraphDestroy(g);
+      c->graph_io = nullptr;
+      c->graph_io_exec = nullptr;
+      return from_cuda(e3);
+    }
+    std::memcpy(c->io_key, key, sizeof(key));
+  }
+  CK(cudaGraphLaunch(c->graph_io_exec, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  c->iters_run += 1;
+  c->s_valid = true;      // S of the new W was formed for the objective
+  c->r_valid = false;     // R of the new W was not
+  if (*c->h_status != 0) {
+    nmf_status st = read_status(c);       // reports and clears it
+    if (st != NMF_OK) return st;
+  }
+  if (frob2) {
+    if (dense) return nmf_error(c, frob2, nullptr);
+    *frob2 = *c->h_obj;
+  }
+  return NMF_OK;
 }
 
 nmf_status nmf_get_factors(nmf_ctx* c, float* W, float* H) {

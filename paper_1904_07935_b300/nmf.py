@@ -59,6 +59,7 @@ _SIGS = {
     "nmf_objective_history": ([_vp, _vp, _i32], _i32),
     "nmf_get_factors": ([_vp, _vp, _vp], _i32),
     "nmf_set_factors": ([_vp, _vp, _vp], _i32),
+    "nmf_iterate_host": ([_vp, _vp, _vp, _vp, _vp, _dp], _i32),
     "nmf_run_step": ([_vp, _i32], _i32),
     "nmf_get_buffer": ([_vp, _i32, _vp, _i64], _i32),
     "nmf_set_buffer": ([_vp, _i32, _vp, _i64], _i32),
@@ -205,6 +206,15 @@ class Nmf:
 
     def set_factors(self, W=None, H=None):
         check(lib.nmf_set_factors(self.h, ptr(W), ptr(H)), "nmf_set_factors")
+
+    def iterate_host(self, W_in=None, H_in=None, W_out=None, H_out=None):
+        """One iteration on caller-held factors (W V x K, H K x D; pinned
+        host or device buffers overlap the copies with the iteration); the
+        outputs may be the inputs.  Returns the objective after it."""
+        f = ctypes.c_double()
+        check(lib.nmf_iterate_host(self.h, ptr(W_in), ptr(H_in), ptr(W_out), ptr(H_out), ctypes.byref(f)),
+              "nmf_iterate_host")
+        return f.value
 
     def run_step(self, step):
         check(lib.nmf_run_step(self.h, step), "nmf_run_step")
