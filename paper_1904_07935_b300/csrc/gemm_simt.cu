@@ -199,8 +199,12 @@ __host__ __device__ constexpr int gram_tri_smem_floats(int Kp8) {
 }
 static_assert(kTriGroupMax <= kTriStride, "tile stride");
 __global__ void __launch_bounds__(512) gram_tri_kernel(const float* __restrict__ X, int N, int Kp, int Kp8,
-                                                       int chunk, int tpg, float* __restrict__ part) {
+                                                       int chunk, int tpg, float* __restrict__ part,
+                                                       const int* __restrict__ skip_count, int skip_need) {
   extern __shared__ __align__(16) float xs[];      // staging 2 x GR x Kp8; afterwards half 1's tiles
+  // The partials are already there (formed in the same order by the W
+  // update's workers): nothing to do.
+  if (skip_count && *skip_count >= skip_need) return;
   const int m = Kp8 / 8, Kh = Kp8 / 2;
   const int nT = m * (m + 1) / 2;
   const int h = threadIdx.x >= tpg ? 1 : 0;
@@ -716,12 +720,30 @@ cudaError_t gram_run_scratch(const float* X, int N, int K, int64_t ldx, float* p
   return gram_reduce(part, n_chunks, K, K, S, s);
 }
 
+void gram_rechunk(GramWork& g, int chunk, int n_chunks) {
+  g.chunk = chunk;
+  g.n_chunks = n_chunks;
+  if (!(g.Kp >= kGramFullMinKp && g.Kp <= kGramFullMaxKp)) return;
+  // Tile groups so that chunks x groups covers the SMs about twice (the
+  // order of each entry's sum does not depend on the grouping).
+  const int nT = gram_tri_tiles((g.Kp + 7) / 8 * 8);
+  int groups = std::max((nT + kTriGroupMax - 1) / kTriGroupMax, (2 * 148 + n_chunks - 1) / std::max(1, n_chunks));
+  groups = std::min(groups, std::max(1, nT / 32));
+  g.groups = groups;
+  g.tpg = (nT + groups - 1) / groups;
+}
+
+bool gram_tri_single_group(const GramWork& g) {
+  return g.Kp >= kGramFullMinKp && g.Kp <= kGramFullMaxKp && g.groups == 1;
+}
+
 void gram_free(GramWork& g) {
   cudaFree(g.d_part);
   g.d_part = nullptr;
 }
 
-cudaError_t gram_run(const GramWork& g, const float* X, float* S, int K, cudaStream_t s) {
+cudaError_t gram_run(const GramWork& g, const float* X, float* S, int K, cudaStream_t s, const int* skip_count,
+                     int skip_need) {
   if (g.Kp >= kGramFullMinKp && g.Kp <= kGramFullMaxKp) {
     const int Kp8 = (g.Kp + 7) / 8 * 8;
     const int threads = 2 * g.tpg;
@@ -730,11 +752,13 @@ cudaError_t gram_run(const GramWork& g, const float* X, float* S, int K, cudaStr
         gram_tri_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
         (int)(sizeof(float) * gram_tri_smem_floats((kGramFullMaxKp + 7) / 8 * 8)));
     if (attr != cudaSuccess) return attr;
-    gram_tri_kernel<<<dim3(g.n_chunks, g.groups), threads, smem, s>>>(X, g.N, g.Kp, Kp8, g.chunk, g.tpg, g.d_part);
+    gram_tri_kernel<<<dim3(g.n_chunks, g.groups), threads, smem, s>>>(X, g.N, g.Kp, Kp8, g.chunk, g.tpg, g.d_part,
+                                                                     skip_count, skip_need);
     cudaError_t err = cudaGetLastError();
     if (err != cudaSuccess) return err;
     return gram_reduce(g.d_part, g.n_chunks, g.Kp, K, S, s);
   }
+  if (skip_count) return cudaErrorInvalidValue;      // partials of the W update's workers: gram_tri_kernel's order only
   GemmArgs a;
   a.M = g.Kp;
   a.N = g.Kp;

@@ -131,7 +131,17 @@ struct GramWork {
 };
 cudaError_t gram_setup(GramWork& g, int N, int Kp);
 void gram_free(GramWork& g);
-cudaError_t gram_run(const GramWork& g, const float* X, float* S, int K, cudaStream_t s);
+// skip_count (gram_tri_kernel shapes only): when *skip_count >= skip_need
+// the chunk partials are taken as already formed (by the W update's workers,
+// in this kernel's order) and only the reduction runs.
+cudaError_t gram_run(const GramWork& g, const float* X, float* S, int K, cudaStream_t s,
+                     const int* skip_count = nullptr, int skip_need = 0);
+// The chunked Gram applies (gram_tri_kernel with one tile group): the shapes
+// for which the W update's workers can form the partials.
+bool gram_tri_single_group(const GramWork& g);
+// Re-chunk a GramWork (chunk rows per partial, n_chunks <= the chunks its
+// buffer was set up for); the tile grouping follows.
+void gram_rechunk(GramWork& g, int chunk, int n_chunks);
 // S (K x K) = X^T X for X (N x K, row stride ldx) with caller-provided
 // partial storage: n_chunks * K * K floats, chunk rows per partial.
 cudaError_t gram_run_scratch(const float* X, int N, int K, int64_t ldx, float* part, int n_chunks, int chunk,
@@ -207,6 +217,7 @@ struct WPersistConfig {
   int worker_rows = 128;
   int worker_wr = 1;      // rows per worker lane group (2 for Kp >= 192)
   int chain_rows = 0;     // rows per chain CTA
+  int stage_rows = 128;   // rows a worker stages at once (its whole block where it fits)
   size_t smem = 0;
   bool tc = false;        // worker clusters form the tile bases on the tensor cores
 };
@@ -221,9 +232,19 @@ size_t w_sync_ints(int K);
 // makes the workers wait for more chain arrivals than exist (tests of the
 // timeout path: the waits run out, ST_TIMEOUT is set and the chain computes
 // the remaining bases itself).
+// spart != nullptr (SIMT workers, Kp <= 256): the workers also form the Gram
+// partials of the new factor for the row chunks of w_persistent_blocks (chunk
+// w = worker w's rows, Kp x Kp each, upper triangle), in gram_tri_kernel's
+// order for those chunks, and count the finished block columns at
+// d_sync[w_sync_sdone_offset(K)] (nb x ceil(K / 16) when all are done).
 cudaError_t w_persistent_run(float* X, const float* P, const float* Q, float* Y, int N, int K, int Kp, float eps,
                              int* d_sync, int* d_status, const WPersistConfig& cfg, cudaStream_t s,
-                             const float* pre0 = nullptr, unsigned long long wait_ns = 0, int extra_arrivals = 0);
+                             const float* pre0 = nullptr, unsigned long long wait_ns = 0, int extra_arrivals = 0,
+                             float* spart = nullptr);
+// Row blocks of the single-launch W update: nb blocks of per rows (the last
+// shorter), one per worker CTA.
+void w_persistent_blocks(int N, const WPersistConfig& cfg, int* nb, int* per);
+size_t w_sync_sdone_offset(int K);
 
 // ---------------------------------------------------------------------------
 // Misc kernels.

@@ -39,6 +39,12 @@ struct nmf_ctx {
   cudaStream_t side2 = nullptr;         // third stream: <W, P> of the objective beside S and R
   bool w_persistent = false;            // whole W update as one launch (chain cluster + workers)
   WPersistConfig wp;
+  // The single-launch W update's workers also form the chunk partials of
+  // S = W^T W of the new W (gramW chunked by the workers' row blocks); the
+  // Gram kernel after it only reduces them, or forms any the workers left.
+  bool ws_gram = false;
+  int ws_need = 0;                      // finished block columns when the workers formed all partials
+  GramWork gramW0;                      // gramW's own chunking (restored when ws_gram is turned off)
   int* d_sync = nullptr;
   unsigned long long wait_ns = 0;       // limit of the W update's device waits (0: library default)
   int extra_arrivals = 0;               // tests of the timeout path: a hand-off count that cannot be reached
@@ -211,12 +217,22 @@ cudaError_t enq_gram(nmf_ctx* c, const GramWork& g, const float* X, float* out, 
   return gram_run(g, X, out, c->K, s);
 }
 
+// S = W^T W right after a W update enqueued with with_s: where the update's
+// workers formed the chunk partials the Gram kernel only checks their count
+// and the partials are reduced; otherwise the Gram as usual.
+cudaError_t enq_gram_after_w(nmf_ctx* c, cudaStream_t s, bool shared_op) {
+  if (!c->ws_gram) return enq_gram(c, c->gramW, c->W, c->S, s, shared_op);
+  c->launch_count += 2;
+  return gram_run(c->gramW, c->W, c->S, c->K, s ? s : c->stream, c->d_sync + w_sync_sdone_offset(c->K), c->ws_need);
+}
+
 // Regrouped update of one tall factor X (N x Kp) with Gram G and data term B.
 //  H: rows are independent; one kernel runs every tile (base, chain, write).
 //  W: per tile of 16 columns, a full-grid kernel forms the tile's base from the
 //     current rows (new columns left of the tile, old ones right of it), then
 //     the cluster kernel finishes the tile's columns with their norms.
-cudaError_t enq_update(nmf_ctx* c, float* X, const float* G, const float* B, int N, bool is_w, bool pre0 = false) {
+cudaError_t enq_update(nmf_ctx* c, float* X, const float* G, const float* B, int N, bool is_w, bool pre0 = false,
+                       bool with_s = false) {
   const int K = c->K, Kp = c->Kp;
   if (!is_w) {
     c->launch_count += 1;
@@ -226,7 +242,8 @@ cudaError_t enq_update(nmf_ctx* c, float* X, const float* G, const float* B, int
   if (c->w_persistent) {
     c->launch_count += 1;
     return w_persistent_run(X, B, G, c->Y, N, K, Kp, c->eps, c->d_sync, c->d_status, c->wp, c->stream,
-                            pre0 ? c->Y0lo : nullptr, c->wait_ns, c->extra_arrivals);
+                            pre0 ? c->Y0lo : nullptr, c->wait_ns, c->extra_arrivals,
+                            with_s && c->ws_gram ? c->gramW.d_part : nullptr);
   }
   // W: tile tau's base without tile tau-1 ("main") runs on the side stream
   // while the chain of tile tau-1 runs; the chain of tile tau adds tile
@@ -323,7 +340,7 @@ cudaError_t enq_iteration(nmf_ctx* c, const IoHooks* io = nullptr) {
   if ((e = cudaEventRecord(c->evx[1], b)) != cudaSuccess) return e;
   if ((e = enq_product_P(c, shared_op)) != cudaSuccess) return e;
   if ((e = cudaStreamWaitEvent(m, c->evx[1], 0)) != cudaSuccess) return e;
-  if ((e = enq_update(c, c->W, c->Q, c->P, c->V, true, pre0)) != cudaSuccess) return e;
+  if ((e = enq_update(c, c->W, c->Q, c->P, c->V, true, pre0, true)) != cudaSuccess) return e;
   if (shared_op && (e = bf16_operand(c, true, m)) != cudaSuccess) return e;
   if ((e = cudaEventRecord(c->evx[2], m)) != cudaSuccess) return e;
   if (!io) {
@@ -341,7 +358,7 @@ cudaError_t enq_iteration(nmf_ctx* c, const IoHooks* io = nullptr) {
   if ((e = objective_wp(c->W, c->P, c->V, c->Kp, c->obj_partial, c->n_obj_partial, c->side2)) != cudaSuccess)
     return e;
   if ((e = cudaEventRecord(c->evx[4], c->side2)) != cudaSuccess) return e;
-  if ((e = enq_gram(c, c->gramW, c->W, c->S, nullptr, shared_op)) != cudaSuccess) return e;
+  if ((e = enq_gram_after_w(c, nullptr, shared_op)) != cudaSuccess) return e;
   if ((e = cudaStreamWaitEvent(m, c->evx[4], 0)) != cudaSuccess) return e;
   if ((e = objective_finish(c->Kp, c->S, c->Q, c->normA2, c->obj_partial, c->n_obj_partial, c->hist, c->d_counter,
                             kHistCap, m, io ? c->d_obj_last : nullptr)) != cudaSuccess)
@@ -612,6 +629,19 @@ nmf_status init_impl(const nmf_problem* p, nmf_ctx* c) {
   // least one worker cluster fit; its result does not depend on how many of
   // the clusters run at the same time, so no probe launch is needed.
   c->w_persistent = !(p->flags & NMF_FLAG_MULTI_LAUNCH_W) && w_persistent_config(V, Kp, &c->wp, c->tc_updates);
+  c->gramW0 = c->gramW;
+  if (c->w_persistent && !c->wp.tc && !c->use_tc && !c->bf16 && Kp <= 256 && gram_tri_single_group(c->gramW) &&
+      (size_t)c->wp.worker_rows * (Kp + 4) >= 16 * 256) {
+    int nb = 0, per = 0;
+    w_persistent_blocks(V, c->wp, &nb, &per);
+    if (nb >= 1 && nb <= c->gramW0.n_chunks) {
+      // gramW chunked by the workers' row blocks (its partial buffer holds
+      // gramW0.n_chunks >= nb chunks).
+      gram_rechunk(c->gramW, per, nb);
+      c->ws_gram = true;
+      c->ws_need = nb * ((c->K + kRowTile - 1) / kRowTile);
+    }
+  }
   CK(enq_gram(c, c->gramW, c->W, c->S));
   c->s_valid = true;
   CK(cudaStreamSynchronize(c->stream));
@@ -867,6 +897,8 @@ nmf_status nmf_batch_create(nmf_ctx* const* ctxs, int32_t n, int32_t autotune, v
   for (int i = 0; i < n; ++i) {
     nmf_ctx* c = b->m[i];
     c->w_persistent = false;
+    c->ws_gram = false;                       // the per-tile W update forms no Gram partials
+    c->gramW = c->gramW0;
     drop_graph(c);
     if ((e = ensure_entry(c)) != cudaSuccess) return bail(e);
     if (autotune) {
@@ -1495,9 +1527,9 @@ nmf_status nmf_profile(nmf_ctx* c, int32_t n_iters, float* step_ms) {
     if (e == cudaSuccess) e = cudaEventRecord(ev[3], c->stream);
     if (e == cudaSuccess) e = enq_gram(c, c->gramH, c->Ht, c->Q);
     if (e == cudaSuccess) e = cudaEventRecord(ev[4], c->stream);
-    if (e == cudaSuccess) e = enq_update(c, c->W, c->Q, c->P, c->V, true);
+    if (e == cudaSuccess) e = enq_update(c, c->W, c->Q, c->P, c->V, true, false, true);
     if (e == cudaSuccess) e = cudaEventRecord(ev[5], c->stream);
-    if (e == cudaSuccess) e = enq_gram(c, c->gramW, c->W, c->S);
+    if (e == cudaSuccess) e = enq_gram_after_w(c, nullptr, false);
     if (e == cudaSuccess) e = cudaEventRecord(ev[6], c->stream);
     if (e == cudaSuccess) e = enq_objective(c);
     if (e == cudaSuccess) e = cudaEventRecord(ev[7], c->stream);

@@ -72,6 +72,9 @@ struct WParams {
   const float* pre0;   // non-null: Y's first tile + pre0 (N x 16) hold tile 0's base less P (formed before the launch)
   unsigned long long wait_ns;  // limit of every wait
   int extra_arrivals;  // added to the chain_done count the workers wait for (tests of the timeout path; 0)
+  float* spart;        // non-null: chunk w (w < nb) of the Gram partials S_w = X_w^T X_w of the new factor,
+                       // Kp x Kp each, upper triangle (the rows of worker w are the chunk)
+  int stage_rows;      // rows a worker stages at once (>= worker_rows; per: its whole block)
 };
 
 __device__ __forceinline__ unsigned cluster_id_x() {
@@ -96,6 +99,11 @@ __device__ __forceinline__ int* sync_base_done(const WParams& p, int nt, int tau
 }
 __device__ __forceinline__ int* sync_state(const WParams& p, int nt, int tau, int w) {
   return p.sync + (1 + 2 * nt) * kSyncStride + tau * WMAXNB + w;
+}
+// Block columns of the Gram partials finished by the workers (nb x nt when
+// complete).
+__device__ __forceinline__ int* sync_sdone(const WParams& p, int nt) {
+  return p.sync + (1 + 2 * nt) * kSyncStride + nt * WMAXNB;
 }
 
 // A worker that finds the chain cluster not yet running waits this long for
@@ -247,6 +255,8 @@ __device__ void worker_role(const WParams& p, char* smem, int wid) {
   const int sub = tid & 3;
   const int rl = tid >> 2;
   const int RB = p.worker_rows;
+  const int SR = p.stage_rows;
+  const bool s_after = SR >= p.per;                           // the whole block staged at once
   // This worker's block: an equal contiguous share [wbeg, wend) of the rows,
   // in passes of RB rows (rather than RB-row blocks dealt round-robin, which
   // left some workers a whole block more than others: text-like K = 240 W
@@ -259,6 +269,115 @@ __device__ void worker_role(const WParams& p, char* smem, int wid) {
   }
   __syncthreads();
   unsigned phase = 0;
+  // Rows [row0, row0 + nrows) of the factor into Xs (one bulk copy per row),
+  // bounded wait; on expiry the copies may still be in flight, so wait for
+  // them once more (bounded too) before the buffer is used or left.
+  auto stage_pass = [&](int row0, int nrows) {
+    __syncthreads();                                          // Xs free
+    if (tid == 0) mbar_arrive_expect_tx(smem_u32(&bar), (unsigned)nrows * p.Kp * 4u);
+    __syncthreads();
+    if (tid < nrows) {
+      fence_proxy_async_global();
+      bulk_g2s(smem_u32(Xs + tid * ldx), p.X + (int64_t)(row0 + tid) * p.Kp, (unsigned)p.Kp * 4u, smem_u32(&bar));
+    }
+    if (!wait_bar_cta(smem_u32(&bar), phase, p.wait_ns)) {
+      if (tid == 0) atomicOr(p.status, ST_TIMEOUT);
+      wait_bar_cta(smem_u32(&bar), phase, p.wait_ns);
+    }
+    phase ^= 1u;
+  };
+  // Gram partial of this worker's rows (WParams::spart), block column sc:
+  // entries (i, j), j in [16 sc, 16 sc + 16), i <= j, as 4 x 4 tiles
+  // (s_st = tile); each tile has two threads in the two half-warps of one
+  // warp, the first taking the 8-row groups 0, 2, 4, ... of the chunk and the
+  // second 1, 3, 5, ..., each adding its rows in order (the chunk's rows are
+  // final in every column up to the block column once chain_done[sc] is
+  // seen); the two sums are then added, the first's plus the second's.  This
+  // is the order of gram_tri_kernel's chunk partials, so with the same chunks
+  // the two agree bit for bit and either can stand for the other.
+  const int s_h = (tid >> 4) & 1;
+  const int s_st = (tid & 15) + 16 * (tid >> 5);
+  float sacc[4][4];
+  auto s_tile = [&](int sc, int* i0, int* j0) -> bool {
+    const int slo = sc * WT, shi = min(p.K, slo + WT);
+    const int nj = (min(p.Kp, slo + WT) - slo) / 4, niq = (shi + 3) / 4;
+    if (s_st >= niq * nj) return false;
+    *i0 = 4 * (s_st / nj);
+    *j0 = slo + 4 * (s_st % nj);
+    return *i0 <= *j0 + 3;                                    // not entirely below the diagonal
+  };
+  auto s_begin = [&]() {
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+#pragma unroll
+      for (int v = 0; v < 4; ++v) sacc[u][v] = 0.f;
+  };
+  auto s_rows = [&](int sc, int row0, int nrows) {
+    int i0, j0;
+    if (!s_tile(sc, &i0, &j0)) return;
+    // This half's rows in order: groups g0, g0 + 2, ... of 8 rows; full
+    // groups with all eight rows' operands loaded first.
+    for (int g = (((row0 - wbeg) >> 3) ^ s_h) & 1; 8 * g < nrows; g += 2) {
+      const float* xr = Xs + 8 * g * ldx;
+      if (8 * g + 8 <= nrows) {
+        float4 a4[8], b4[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+          a4[q] = *reinterpret_cast<const float4*>(xr + q * ldx + i0);
+          b4[q] = *reinterpret_cast<const float4*>(xr + q * ldx + j0);
+        }
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+          const float a[4] = {a4[q].x, a4[q].y, a4[q].z, a4[q].w}, b[4] = {b4[q].x, b4[q].y, b4[q].z, b4[q].w};
+#pragma unroll
+          for (int u = 0; u < 4; ++u)
+#pragma unroll
+            for (int v = 0; v < 4; ++v) sacc[u][v] = fmaf(a[u], b[v], sacc[u][v]);
+        }
+      } else {
+        for (int q = 0; 8 * g + q < nrows; ++q) {
+          const float4 a4 = *reinterpret_cast<const float4*>(xr + q * ldx + i0);
+          const float4 b4 = *reinterpret_cast<const float4*>(xr + q * ldx + j0);
+          const float a[4] = {a4.x, a4.y, a4.z, a4.w}, b[4] = {b4.x, b4.y, b4.z, b4.w};
+#pragma unroll
+          for (int u = 0; u < 4; ++u)
+#pragma unroll
+            for (int v = 0; v < 4; ++v) sacc[u][v] = fmaf(a[u], b[v], sacc[u][v]);
+        }
+      }
+    }
+  };
+  auto s_finish = [&](int sc) {
+    int i0 = 0, j0 = 0;
+    const bool own = s_tile(sc, &i0, &j0);                    // the same for both half-warps of a tile
+    float* out = p.spart + (int64_t)wid * p.Kp * p.Kp;
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+#pragma unroll
+      for (int v = 0; v < 4; ++v) {
+        const float o = __shfl_xor_sync(0xffffffffu, sacc[u][v], 16);
+        const int i = i0 + u, j = j0 + v;
+        if (own && s_h == 0 && i <= j && j < p.K) out[(int64_t)i * p.Kp + j] = sacc[u][v] + o;
+      }
+    __syncthreads();                                          // the block column's partial is written
+    if (tid == 0) atomicAdd(sync_sdone(p, nt), 1);
+  };
+  // Columns [c0, c1) of the staged rows from the factor in global memory (the
+  // rest of each row is staged already): the last block columns need only
+  // their own tiles again.
+  auto reload_cols = [&](int c0, int c1) {
+    __syncthreads();
+    const int q4 = (c1 - c0) / 4, n = wend - wbeg;
+    for (int e = tid; e < n * q4; e += WNT) {
+      const int r = e / q4, q = e % q4;
+      *reinterpret_cast<float4*>(Xs + r * ldx + c0 + 4 * q) =
+          __ldcg(reinterpret_cast<const float4*>(p.X + (int64_t)(wbeg + r) * p.Kp + c0 + 4 * q));
+    }
+    __syncthreads();
+  };
+  // Tiles [0, xs_final) of the staged rows are final (whole-block staging).
+  int xs_final = -1;
+  bool gave_up = false;
   for (int tau = 0; tau < nt; ++tau) {
     if (tau == 0 && p.pre0) continue;                         // tile 0's base was formed before the launch
     const int lo = tau * WT, hi = min(p.K, lo + WT);
@@ -275,8 +394,15 @@ __device__ void worker_role(const WParams& p, char* smem, int wid) {
     }
     __syncthreads();
     const int go = s_go[tau & 1];
-    if (go == 0) break;
+    if (go == 0) {
+      gave_up = true;
+      break;
+    }
     if (go == 2) continue;
+    // Block column tau - 2 of the Gram partial rides on this tile's passes
+    // (its columns are final: chain_done[tau - 2] was seen above).
+    const int scol = p.spart && tau >= 2 ? tau - 2 : -1;
+    if (scol >= 0) s_begin();
     // G block of this tile: Gc[j * WT + c] = Q[j][lo + c].
     for (int base = tid; base < Kr * WT; base += 8 * WNT) {
       float v[8];
@@ -292,25 +418,17 @@ __device__ void worker_role(const WParams& p, char* smem, int wid) {
         if (e < Kr * WT) Gc[e] = v[u];
       }
     }
-    for (int row0 = wbeg; row0 < wend; row0 += RB) {
-      const int nrows = min(RB, wend - row0);
-      __syncthreads();                                        // Gc staged; Xs free
-      if (tid == 0) {
-        mbar_arrive_expect_tx(smem_u32(&bar), (unsigned)nrows * p.Kp * 4u);
-      }
-      __syncthreads();
-      if (tid < nrows) {
-        fence_proxy_async_global();
-        bulk_g2s(smem_u32(Xs + tid * ldx), p.X + (int64_t)(row0 + tid) * p.Kp, (unsigned)p.Kp * 4u,
-                 smem_u32(&bar));
-      }
-      // Bounded; on expiry the copies may still be in flight, so wait for
-      // them once more (bounded too) before the buffer is used or left.
-      if (!wait_bar_cta(smem_u32(&bar), phase, p.wait_ns)) {
-        if (tid == 0) atomicOr(p.status, ST_TIMEOUT);
-        wait_bar_cta(smem_u32(&bar), phase, p.wait_ns);
-      }
-      phase ^= 1u;
+    // Rows staged stage_rows at a time (normally the whole block, which
+    // then stays in shared memory for the Gram partial below), the base
+    // formed in passes of RB rows over them.
+    for (int srow0 = wbeg; srow0 < wend; srow0 += SR) {
+     const int snrows = min(SR, wend - srow0);
+     stage_pass(srow0, snrows);                               // (after Gc is staged)
+     xs_final = s_after ? max(0, tau - 1) : -1;
+     for (int prow = 0; prow < snrows; prow += RB) {
+      const int nrows = min(RB, snrows - prow);
+      const int row0 = srow0 + prow;
+      const float* Xq = Xs + prow * ldx;
       const int half = WR == 1 ? nrows : (nrows + 1) / 2;  // groups with a row
       if (rl < half) {
         int lr[WR];
@@ -320,7 +438,7 @@ __device__ void worker_role(const WParams& p, char* smem, int wid) {
         for (int u = 0; u < WR; ++u) {
           lr[u] = rl + u * half;
           has[u] = lr[u] < nrows;
-          xr[u] = Xs + (has[u] ? lr[u] : rl) * ldx;
+          xr[u] = Xq + (has[u] ? lr[u] : rl) * ldx;
         }
         float acc[WR][4];
 #pragma unroll
@@ -410,11 +528,51 @@ __device__ void worker_role(const WParams& p, char* smem, int wid) {
           }
         }
       }
+     }
+     if (scol >= 0 && !s_after) s_rows(scol, srow0, snrows);   // block larger than one staging
     }
     // A claimed block is always published (even after a timed-out copy), so
     // the chain never waits for it in vain.
     __syncthreads();
     if (tid == 0) red_release_add_gpu(sync_base_done(p, nt, tau), 1);
+    // The Gram partial's block column from the rows still staged: after the
+    // base is published, so the chain does not wait for it.
+    if (scol >= 0) {
+      if (s_after) s_rows(scol, wbeg, wend - wbeg);
+      s_finish(scol);
+    }
+  }
+  // The last block columns of the Gram partial (those no later tile's passes
+  // carried), each once its tile is final; a worker that gave up, or whose
+  // wait runs out here, leaves its remaining columns to the Gram kernel that
+  // follows the launch (the completion count falls short).
+  if (p.spart && !gave_up) {
+    for (int sc = nt >= 2 ? nt - 2 : 0; sc < nt; ++sc) {
+      if (tid == 0) {
+        const int ok =
+            wait_count(sync_chain_done(p, nt, sc), p.cl + p.extra_arrivals, p, sync_started(p), p.cl) == 1;
+        fence_proxy_async_global();
+        s_go[sc & 1] = ok;
+      }
+      __syncthreads();
+      if (!s_go[sc & 1]) break;
+      s_begin();
+      if (s_after && xs_final >= 0 && xs_final <= sc) {
+        // The block is staged with tiles [0, xs_final) final: fetch tiles
+        // xs_final .. sc again.
+        reload_cols(xs_final * WT, min(p.Kp, (sc + 1) * WT));
+        xs_final = sc + 1;
+        s_rows(sc, wbeg, wend - wbeg);
+      } else {
+        for (int row0 = wbeg; row0 < wend; row0 += SR) {
+          const int nrows = min(SR, wend - row0);
+          stage_pass(row0, nrows);
+          s_rows(sc, row0, nrows);
+        }
+        xs_final = s_after ? sc + 1 : -1;
+      }
+      s_finish(sc);
+    }
   }
 }
 
@@ -765,7 +923,7 @@ __device__ void chain_role(const WParams& p, char* smem) {
       // slowest one here.  The workers read tile tau only for the bases of
       // tiles >= tau + 2.
       __syncthreads();
-      if (lane == 0 && tau + 2 < nt) red_release_add_gpu(sync_chain_done(p, nt, tau), 1);
+      if (lane == 0 && (tau + 2 < nt || p.spart)) red_release_add_gpu(sync_chain_done(p, nt, tau), 1);
     }
   } else {
     const int tr = tid - 32;
@@ -1112,7 +1270,18 @@ int max_clusters(int rpt, int cl, size_t smem) {
 
 size_t w_sync_ints(int K) {
   const size_t nt = (size_t)(K + WT - 1) / WT;
+  return (1 + 2 * nt) * kSyncStride + nt * WMAXNB + kSyncStride;
+}
+
+size_t w_sync_sdone_offset(int K) {
+  const size_t nt = (size_t)(K + WT - 1) / WT;
   return (1 + 2 * nt) * kSyncStride + nt * WMAXNB;
+}
+
+void w_persistent_blocks(int N, const WPersistConfig& cfg, int* nb, int* per) {
+  const int n_workers = (cfg.n_clusters - 1) * cfg.cluster;
+  *per = (N + n_workers - 1) / n_workers;
+  *nb = (N + *per - 1) / *per;
 }
 
 bool w_persistent_config(int N, int Kp, WPersistConfig* cfg, bool tc) {
@@ -1137,6 +1306,20 @@ bool w_persistent_config(int N, int Kp, WPersistConfig* cfg, bool tc) {
     cfg->chain_rows = nrc;
     cfg->n_clusters = std::min(nc, 1 + WMAXNB / cl);
     cfg->worker_rows = worker_rows;
+    // A worker stages its whole row block at once where it fits (the base
+    // is then formed in passes of worker_rows over it, and the block stays
+    // in shared memory for the Gram partial).
+    {
+      const int n_workers = (cfg->n_clusters - 1) * cl;
+      const int per = (N + n_workers - 1) / n_workers;
+      const size_t whole = sizeof(float) * ((size_t)(Kp + WT - 1) / WT * WT * WT + (size_t)per * (Kp + 4));
+      cfg->stage_rows = worker_rows;
+      if (!tc && per > worker_rows && whole <= kBudget &&
+          max_clusters(rpt, cl, std::max(smem, whole)) >= cfg->n_clusters) {
+        cfg->stage_rows = per;
+        smem = std::max(smem, whole);
+      }
+    }
     cfg->worker_wr = Kp >= 192 ? 2 : 1;
     cfg->smem = smem;
     cfg->tc = tc;
@@ -1147,7 +1330,7 @@ bool w_persistent_config(int N, int Kp, WPersistConfig* cfg, bool tc) {
 
 cudaError_t w_persistent_run(float* X, const float* P, const float* Q, float* Y, int N, int K, int Kp, float eps,
                              int* d_sync, int* d_status, const WPersistConfig& cfg, cudaStream_t s,
-                             const float* pre0, unsigned long long wait_ns, int extra_arrivals) {
+                             const float* pre0, unsigned long long wait_ns, int extra_arrivals, float* spart) {
   if (N <= 0 || K <= 0) return cudaSuccess;
   cudaError_t e = cudaMemsetAsync(d_sync, 0, sizeof(int) * w_sync_ints(K), s);
   if (e != cudaSuccess) return e;
@@ -1155,8 +1338,10 @@ cudaError_t w_persistent_run(float* X, const float* P, const float* Q, float* Y,
   if (n_workers < 1 || n_workers > WMAXNB) return cudaErrorInvalidValue;
   const int per = (N + n_workers - 1) / n_workers;
   const int nb = (N + per - 1) / per;
+  if (spart && (cfg.tc || Kp > 256 || (size_t)cfg.worker_rows * (Kp + 4) < 16 * 256)) return cudaErrorInvalidValue;
   WParams p{X, P, Q, Y, N, K, Kp, eps, d_status, d_sync, cfg.cluster, cfg.worker_rows, (N + cfg.cluster - 1) / cfg.cluster,
-            nb, per, pre0, wait_ns ? wait_ns : kWaitLimitNs, extra_arrivals};
+            nb, per, pre0, wait_ns ? wait_ns : kWaitLimitNs, extra_arrivals, spart,
+            std::max(cfg.worker_rows, std::min(cfg.stage_rows, per))};
   CUtensorMap map = {};
   if (cfg.tc) {
     if (!tma_map_f32(&map, X, N, Kp, Kp, WPW, WTM)) return cudaErrorNotSupported;

@@ -406,6 +406,29 @@ def test_invalid_inputs_rejected(nmf):
                 col_idx=torch.from_numpy(sp.A.col_idx).cuda(), val=torch.from_numpy(sp.A.val).cuda())
 
 
+
+@pytest.mark.parametrize("K", [64, 80, 160, 37])
+def test_gram_partials_of_the_w_update_match_the_gram_kernel(nmf, K):
+    """Within an iteration the single-launch W update's worker CTAs form the
+    chunk partials of S = W^T W of the new W while the column chain runs, and
+    the Gram kernel after it only reduces them.  Those partials follow the
+    Gram kernel's own order for the same row chunks, so S is bit-identical to
+    the Gram of the same W formed on its own (STEP_S), and within FP32
+    rounding of the FP64 Gram.  K = 37 takes the ordinary Gram path (the
+    chunked Gram kernel needs K >= 64)."""
+    import torch
+    sp = synth.sparse_termdoc(9000, 2500, 81 + K, mean_terms=50)
+    W0, H0 = synth.init_factors(82 + K, 9000, 2500, K)
+    ctx = nmf.from_sparse(sp, K, W0=torch.from_numpy(W0).cuda(), H0=torch.from_numpy(H0).cuda())
+    ctx.iterate(2)
+    S_iter = ctx.get_buffer(nmf.BUF_S)
+    ctx.run_step(nmf.STEP_S)
+    S_own = ctx.get_buffer(nmf.BUF_S)
+    assert np.array_equal(S_iter, S_own)
+    W, _ = ctx.get_factors()
+    S64 = W.astype(np.float64).T @ W.astype(np.float64)
+    assert np.max(np.abs(S_iter - S64)) <= 1e-6 * np.max(np.abs(S64))
+
 @pytest.mark.parametrize("K", [16, 37, 160])
 def test_w_update_persistent_and_multi_launch_agree_with_alg1(nmf, K):
     """The single-launch (chain cluster + base workers) and the per-tile W
