@@ -290,15 +290,23 @@ def iteration_bytes(V, D, a_bytes, K):
     return 2 * a_bytes + 16 * (V + D) * K
 
 
-def step_bounds(ab, prof, V, D, K, peak, fpeak):
+def step_bounds(ab, prof, V, D, K, peak, fpeak, s_in_w=False, s_chunks=0):
     """Per-step roofline fractions: HBM-bound steps (products, column updates,
     objective) against the measured copy bandwidth, the Grams' (N K (K+1))
-    flops against the FP32 SIMT peak."""
+    flops against the FP32 SIMT peak.  Where the W update's workers form S's
+    chunk partials (s_in_w), the S step is their reduction (s_chunks partials
+    of K (K+1) / 2 entries read once, against the copy bandwidth) and the
+    W step carries the Gram's flops as well."""
     out = {}
     for k, ms in prof.items():
         if ms <= 0:
             continue
-        if k in ("S", "Q"):
+        if k == "S" and s_in_w:
+            b = s_chunks * K * (K + 1) // 2 * 4 + 4 * K * K
+            gbs = b / (ms * 1e-3) / 1e9
+            out[k] = {"ms": round(ms, 5), "bound": "hbm", "achieved_gbs": round(gbs, 2), "frac": round(gbs / peak, 5),
+                      "what": "reduction of the chunk partials formed in the W update"}
+        elif k in ("S", "Q"):
             N = V if k == "S" else D
             tf = N * K * (K + 1) / (ms * 1e-3) / 1e12
             out[k] = {"ms": round(ms, 5), "bound": "fp32-simt", "achieved_tflops": round(tf, 3),
@@ -306,6 +314,8 @@ def step_bounds(ab, prof, V, D, K, peak, fpeak):
         else:
             gbs = ab[k] / (ms * 1e-3) / 1e9
             out[k] = {"ms": round(ms, 5), "bound": "hbm", "achieved_gbs": round(gbs, 2), "frac": round(gbs / peak, 5)}
+            if k == "update_W" and s_in_w:
+                out[k]["also_forms"] = "the row-chunk partials of S = W^T W (V K (K+1) flops)"
     return out
 
 
@@ -432,7 +442,8 @@ def run_gpu(args):
                     "frac": round(achieved / peak, 5), "traffic": None, "step": dom,
                     "peak_source": peak_kind,
                     "step_ms": {k: round(v, 5) for k, v in prof.items()},
-                    "steps": step_bounds(ab, prof, V, D, K, peak, fpeak),
+                    "steps": step_bounds(ab, prof, V, D, K, peak, fpeak, q.get("s_in_w_update", False),
+                                         q.get("s_chunks", 0)),
                     "alg_bytes_per_iter": int(it_bytes),
                     "alg_bytes_definition": "2|A| + 16 (V + D) K, |A| = CSR bytes (nnz * 8 + (V + 1) * 4)",
                     "iteration_frac_of_hbm": round(it_bytes / (ms * 1e-3) / 1e9 / peak, 5),

@@ -253,6 +253,17 @@ nmf_status nmf_profile(nmf_ctx* c, int32_t n_iters, float* step_ms);
  * nmf_iterate form's count once its graph exists, else 0). */
 nmf_status nmf_query(nmf_ctx* c, int32_t* tile_T, int32_t* chain_ctas, int32_t* launches_per_iter);
 
+/* How the context runs the W side of an iteration (any output may be NULL):
+ *   w_single_launch  1: the whole W update is one launch (a column-chain
+ *                    cluster and base-forming worker CTAs), 0: per-tile
+ *                    launches.
+ *   s_in_w_update    1: within nmf_iterate / nmf_profile the worker CTAs of
+ *                    that launch also form the row-chunk partials of
+ *                    S = W^T W of the new W (in the Gram kernel's order), so
+ *                    the S step that follows only reduces them.
+ *   s_chunks         the number of those row-chunk partials (0 if none). */
+nmf_status nmf_query_form(nmf_ctx* c, int32_t* w_single_launch, int32_t* s_in_w_update, int32_t* s_chunks);
+
 /* Limits of the W update's device-side waits (the single-launch form that
  * replaces Alg. 3's two host synchronisations per column with hand-offs
  * between the column chain and the CTAs forming the tile bases).

@@ -1564,6 +1564,14 @@ nmf_status nmf_query(nmf_ctx* c, int32_t* tile_T, int32_t* chain_ctas, int32_t* 
   return NMF_OK;
 }
 
+nmf_status nmf_query_form(nmf_ctx* c, int32_t* w_single_launch, int32_t* s_in_w_update, int32_t* s_chunks) {
+  if (!c) return NMF_EINVAL;
+  if (w_single_launch) *w_single_launch = c->w_persistent ? 1 : 0;
+  if (s_in_w_update) *s_in_w_update = c->ws_gram ? 1 : 0;
+  if (s_chunks) *s_chunks = c->ws_gram ? c->gramW.n_chunks : 0;
+  return NMF_OK;
+}
+
 nmf_status nmf_set_wait_limits(nmf_ctx* c, int64_t wait_ns, int32_t extra_arrivals) {
   if (!c || wait_ns < 0 || extra_arrivals < 0) return NMF_EINVAL;
   if (!c->w_persistent) return NMF_EUNSUPPORTED;

@@ -65,6 +65,7 @@ _SIGS = {
     "nmf_set_buffer": ([_vp, _i32, _vp, _i64], _i32),
     "nmf_query": ([_vp, ctypes.POINTER(_i32), ctypes.POINTER(_i32), ctypes.POINTER(_i32)], _i32),
     "nmf_set_wait_limits": ([_vp, _i64, _i32], _i32),
+    "nmf_query_form": ([_vp, ctypes.POINTER(_i32), ctypes.POINTER(_i32), ctypes.POINTER(_i32)], _i32),
     "nmf_profile": ([_vp, _i32, _vp], _i32),
     "nmf_iterate_alg1": ([_vp, _i32, _vp], _i32),
     "nmf_iterate_mu": ([_vp, _i32, _vp], _i32),
@@ -268,7 +269,10 @@ class Nmf:
     def query(self):
         t, c, l = _i32(), _i32(), _i32()
         check(lib.nmf_query(self.h, ctypes.byref(t), ctypes.byref(c), ctypes.byref(l)), "nmf_query")
-        return {"tile_T": t.value, "chain_ctas": c.value, "launches_per_iter": l.value}
+        w1, sw, sn = _i32(), _i32(), _i32()
+        check(lib.nmf_query_form(self.h, ctypes.byref(w1), ctypes.byref(sw), ctypes.byref(sn)), "nmf_query_form")
+        return {"tile_T": t.value, "chain_ctas": c.value, "launches_per_iter": l.value,
+                "w_single_launch": bool(w1.value), "s_in_w_update": bool(sw.value), "s_chunks": sn.value}
 
     def set_wait_limits(self, wait_ns=0, extra_arrivals=0):
         """Limit of the W update's device waits (0: library default) and, for
