@@ -1160,7 +1160,10 @@ __device__ void chain_role(const WParams& p, char* smem) {
 #pragma unroll
         for (int s2 = 0; s2 < WT; ++s2) y[i][s2] = 0.f;
       if (Tn > 0) {                                            // then Tw == WT (only the last tile is partial)
-#pragma unroll 4
+        // (Unrolled by two: at 4 rows per thread the 4-way unroll spilled
+        // 46 / 96 bytes, this 16 / 16, and the text-like K = 160 W update
+        // went 298 -> 285 us.)
+#pragma unroll 2
         for (int j = 0; j < WT; ++j) {
           float xv[RPT];
 #pragma unroll
