@@ -909,8 +909,11 @@ __device__ void chain_role(const WParams& p, char* smem) {
         if (t >= Tw) break;
         const int b = t & 1;                                   // partial slot (lo is even)
         __syncthreads();
+        // The row warps' partials sit in lanes 1 .. NW - 1 < 16: a butterfly
+        // over the low four lane bits gives lanes 0 .. 15 their sum.
         float v = (lane >= 1 && lane < NW) ? wpart[lane] : 0.f;
-        v = warp_sum(v);
+#pragma unroll
+        for (int o = 8; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
         if (lane < CL) {
           const unsigned raddr = mapa_u32(smem_u32(&cpart[b][rank]), lane);
           const unsigned rbar = mapa_u32(cbar_tile + 8u * t, lane);
