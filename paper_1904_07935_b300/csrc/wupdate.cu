@@ -1057,10 +1057,9 @@ __device__ void chain_role(const WParams& p, char* smem) {
         for (int t = 0; t < WT; ++t) y[i][t] = valid[i] ? st[sidx(i, t, tr)] - y[i][t] : 0.f;
 
       // Columns t = 0 .. Tw-1 of the tile, unrolled so that every register
-      // slot is static: column t is finished, the previous column's
-      // contribution is pushed into columns t+1.. (column t already has it),
-      // and every fourth column the last four finished ones go to global
-      // memory, off the critical path.
+      // slot is static: column t is finished and the previous column's
+      // contribution is pushed into columns t+1.. (column t already has it);
+      // the finished columns wait in st until the tile's end.
       float xp[RPT];
 #pragma unroll
       for (int i = 0; i < RPT; ++i) xp[i] = 0.f;
@@ -1086,15 +1085,6 @@ __device__ void chain_role(const WParams& p, char* smem) {
             const float g = G[t - 1][s2];
 #pragma unroll
             for (int i = 0; i < RPT; ++i) y[i][s2] = fmaf(-xp[i], g, y[i][s2]);
-          }
-        }
-        if (t >= 4 && (t & 3) == 0) {
-#pragma unroll
-          for (int i = 0; i < RPT; ++i) {
-            if (!valid[i]) continue;
-            const float4 v = make_float4(st[sidx(i, t - 4, tr)], st[sidx(i, t - 3, tr)], st[sidx(i, t - 2, tr)],
-                                         st[sidx(i, t - 1, tr)]);
-            *reinterpret_cast<float4*>(p.X + (int64_t)(row0 + i * WNR + tr) * p.Kp + lo + t - 4) = v;
           }
         }
         // Every row warp waits for the column's CL partials itself and adds
@@ -1138,21 +1128,29 @@ __device__ void chain_role(const WParams& p, char* smem) {
           xp[i] = x;
         }
       }
-      // The columns not yet stored, then the tile is published (warp 0,
+      // The tile's columns stored, then the tile is published (warp 0,
       // after the block barrier), then the contribution of this tile to the
       // next one, z = x_tile * Q[tile][next] for this CTA's rows (kept in y
       // until the next base is loaded).
       const int nlo = hi, nhi = min(p.K, nlo + WT), Tn = nhi - nlo;
-      const int sdone = 4 * ((Tw - 1) / 4);                    // columns [0, sdone) already stored
-#pragma unroll
-      for (int i = 0; i < RPT; ++i) {
-        if (!valid[i]) continue;
-        float* dst = p.X + (int64_t)(row0 + i * WNR + tr) * p.Kp + lo;
-        if (Tw - sdone == 4) {
-          *reinterpret_cast<float4*>(dst + sdone) = make_float4(st[sidx(i, sdone, tr)], st[sidx(i, sdone + 1, tr)],
-                                                                st[sidx(i, sdone + 2, tr)], st[sidx(i, sdone + 3, tr)]);
-        } else {
-          for (int c = sdone; c < Tw; ++c) dst[c] = st[sidx(i, c, tr)];
+      // The tile's columns stored once, at its end: four lanes per row, so
+      // one warp instruction writes eight whole 64-byte row segments
+      // (storing four columns of each thread's rows every fourth column
+      // wrote a 16-byte piece of 32 rows per instruction and made those
+      // columns 2.5x slower: text-like K = 160 W update 283 -> 258 us).
+      row_bar();
+      {
+        const int nq = (Tw + 3) / 4;
+        for (int e = tr; e < nloc * nq; e += WNR) {
+          const int li = e / nq, cq = e - (e / nq) * nq;
+          const int i = li / WNR, r = li - i * WNR;
+          float* dst = p.X + (int64_t)(row0 + li) * p.Kp + lo + 4 * cq;
+          if (4 * cq + 3 < Tw) {
+            *reinterpret_cast<float4*>(dst) = make_float4(st[sidx(i, 4 * cq, r)], st[sidx(i, 4 * cq + 1, r)],
+                                                          st[sidx(i, 4 * cq + 2, r)], st[sidx(i, 4 * cq + 3, r)]);
+          } else {
+            for (int c = 4 * cq; c < Tw; ++c) dst[c - 4 * cq] = st[sidx(i, c, r)];
+          }
         }
       }
       __syncthreads();
