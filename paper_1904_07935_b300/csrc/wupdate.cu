@@ -1139,18 +1139,21 @@ __device__ void chain_role(const WParams& p, char* smem) {
       // wrote a 16-byte piece of 32 rows per instruction and made those
       // columns 2.5x slower: text-like K = 160 W update 283 -> 258 us).
       row_bar();
-      {
-        const int nq = (Tw + 3) / 4;
-        for (int e = tr; e < nloc * nq; e += WNR) {
-          const int li = e / nq, cq = e - (e / nq) * nq;
+      if (Tw == WT) {
+        // Item e: row li = e / 4 (register row i, thread r), columns 4 (e % 4) ..
+#pragma unroll 4
+        for (int e = tr; e < nloc * 4; e += WNR) {
+          const int li = e >> 2, cq = e & 3;
           const int i = li / WNR, r = li - i * WNR;
-          float* dst = p.X + (int64_t)(row0 + li) * p.Kp + lo + 4 * cq;
-          if (4 * cq + 3 < Tw) {
-            *reinterpret_cast<float4*>(dst) = make_float4(st[sidx(i, 4 * cq, r)], st[sidx(i, 4 * cq + 1, r)],
-                                                          st[sidx(i, 4 * cq + 2, r)], st[sidx(i, 4 * cq + 3, r)]);
-          } else {
-            for (int c = 4 * cq; c < Tw; ++c) dst[c - 4 * cq] = st[sidx(i, c, r)];
-          }
+          *reinterpret_cast<float4*>(p.X + (int64_t)(row0 + li) * p.Kp + lo + 4 * cq) =
+              make_float4(st[sidx(i, 4 * cq, r)], st[sidx(i, 4 * cq + 1, r)], st[sidx(i, 4 * cq + 2, r)],
+                          st[sidx(i, 4 * cq + 3, r)]);
+        }
+      } else {
+        for (int e = tr; e < nloc * Tw; e += WNR) {
+          const int li = e / Tw, c = e - li * Tw;
+          const int i = li / WNR, r = li - i * WNR;
+          p.X[(int64_t)(row0 + li) * p.Kp + lo + c] = st[sidx(i, c, r)];
         }
       }
       __syncthreads();
