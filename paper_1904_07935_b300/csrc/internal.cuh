@@ -211,15 +211,16 @@ cudaError_t mu_update(float* X, const float* B, const float* G, float* scratch, 
 // unclaimed it computes itself, so the result does not depend on how many
 // clusters are resident at once).
 struct WPersistConfig {
-  int cluster = 16;
+  int cluster = 16;       // chain CTAs (one cluster)
   int rpt = 1;
-  int n_clusters = 0;
+  int n_workers = 0;      // worker CTAs (one per SM outside the chain)
   int worker_rows = 128;
   int worker_wr = 1;      // rows per worker lane group (2 for Kp >= 192)
   int chain_rows = 0;     // rows per chain CTA
   int stage_rows = 128;   // rows a worker stages at once (its whole block where it fits)
-  size_t smem = 0;
-  bool tc = false;        // worker clusters form the tile bases on the tensor cores
+  size_t chain_smem = 0;
+  size_t worker_smem = 0;
+  bool tc = false;        // the workers form the tile bases on the tensor cores
 };
 // tc: the workers form the tile bases on the tensor cores (TF32 pairs).
 bool w_persistent_config(int N, int Kp, WPersistConfig* cfg, bool tc = false);

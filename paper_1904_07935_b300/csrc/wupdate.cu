@@ -7,27 +7,14 @@
 // W_old * Q_tt initialisation cancels the j = t term of Eq. 5 exactly and is
 // left out.)
 //
-// Roles inside the launch (grid = NC clusters of CL = 16 CTAs; an ordinary
-// cluster launch: nothing in the protocol below assumes that the clusters run
-// at the same time, only that the CTAs of one cluster do, which the hardware
-// guarantees):
-//  * cluster 0 ("chain") owns every row of W (each CTA a contiguous block of
-//    ceil(N / 16) rows): each of its row threads keeps
-//    RPT rows of the current tile in registers and finishes the tile's
-//    columns one after another; the norm of each column is reduced across
-//    the cluster through distributed shared memory (warp 0 of every CTA
-//    sends the CTA partial to every CTA with st.async, completing the
-//    transaction count of that column's own mbarrier there, and every warp
-//    adds the 16 partials in a fixed order).
-//  * the other clusters ("workers") compute the base of each tile,
-//      Y[v, c] = P[v, c] - sum_{j < lo - 16} Q[j][c] W[v, j](new)
-//                        - sum_{j >= hi} Q[j][c] W[v, j](old)
-//                        - sum_{c < j < hi} Q[j][c] W[v, j](old),
-//    i.e. everything except the previous tile, which is not final yet: the
-//    base of tile tau only needs tiles <= tau - 2, so the workers compute it
-//    while the chain is still on tile tau - 1.  The chain adds the previous
-//    tile's contribution itself (its own rows, 16 x 16 per row), right after
-//    finishing that tile.
+// Two grids run side by side: the chain grid (one cluster of CL = 16 CTAs,
+// whose CTAs the hardware runs together) and the worker grid (one CTA per
+// remaining SM, no clusters, so every SM outside the chain's cluster takes
+// a share of the bases; a single launch would need clusters of 16 for the
+// workers too, and only 7 such clusters fit on the 148 SMs).  The worker
+// grid is launched after the chain grid as a programmatic dependent: it may
+// start once every chain CTA is running, and nothing below assumes that it
+// runs at the same time as the chain, or at all:
 // Hand-off through global memory.  The rows are cut into nb blocks (one per
 // worker CTA); block (tau, w) of a tile base is computed by whoever claims
 // it first (atomic compare-and-swap on its state word): normally worker w,
@@ -38,8 +25,11 @@
 // waits for blocks claimed by a CTA that is running and needs nothing more to
 // finish them, and a worker that finds the chain not yet running leaves its
 // remaining blocks to it: the update completes whatever subset of the
-// clusters is resident at a time.  Release/acquire ordering, and every wait
-// is bounded by the global timer (ST_TIMEOUT on expiry).
+// worker CTAs is resident at a time.  The worker grid ends only after the
+// chain has finished (a release count of the chain CTAs that every worker
+// CTA waits for), so work ordered after the two launches sees the whole
+// update.  Release/acquire ordering, and every wait is bounded by the global
+// timer (ST_TIMEOUT on expiry).
 #include <algorithm>
 
 #include "devutil.cuh"
@@ -53,7 +43,7 @@ constexpr int WT = kRowTile;        // tile width (16)
 constexpr int WNT = 512;            // threads per CTA
 constexpr int WNR = WNT - 32;       // row threads of a chain CTA
 constexpr int WMAXCL = 16;
-constexpr int WMAXNB = 128;         // blocks per tile (worker CTAs: at most 8 clusters of 16)
+constexpr int WMAXNB = 160;         // blocks per tile (worker CTAs: one per SM outside the chain)
 
 struct WParams {
   float* X;            // N x Kp, old on entry, new on exit
@@ -104,6 +94,10 @@ __device__ __forceinline__ int* sync_state(const WParams& p, int nt, int tau, in
 // complete).
 __device__ __forceinline__ int* sync_sdone(const WParams& p, int nt) {
   return p.sync + (1 + 2 * nt) * kSyncStride + nt * WMAXNB;
+}
+// Chain CTAs that have finished (every store released).
+__device__ __forceinline__ int* sync_finished(const WParams& p, int nt) {
+  return p.sync + (2 + 2 * nt) * kSyncStride + nt * WMAXNB;
 }
 
 // A worker that finds the chain cluster not yet running waits this long for
@@ -1195,37 +1189,54 @@ __device__ void chain_role(const WParams& p, char* smem) {
   for (int g = tid; g < p.K; g += WNT) {
     if (!wait_bar_cluster(smem_u32(&cbar[g]), 0, p.wait_ns)) atomicOr(p.status, ST_TIMEOUT);
   }
+  // Finished: every row warp's stores precede the block barrier and the
+  // release (the worker grid waits for all CL before it ends).
   __syncthreads();
+  if (tid == 0) red_release_add_gpu(sync_finished(p, nt), 1);
 }
 
-template <int RPT, int WR, bool TCW>
-__global__ void __launch_bounds__(WNT, 1) w_update_persistent_kernel(WParams p, const __grid_constant__ CUtensorMap mapX) {
+template <int RPT>
+__global__ void __launch_bounds__(WNT, 1) w_chain_kernel(WParams p) {
   extern __shared__ __align__(16) char smem[];
-  const unsigned cid = cluster_id_x();
-  if (cid == 0) chain_role<RPT>(p, smem);
-  else if (TCW) worker_role_tc(p, smem, (int)blockIdx.x - p.cl, &mapX);
-  else worker_role<WR>(p, smem, (int)blockIdx.x - p.cl);
+  // The worker grid (the next launch, a programmatic dependent) may be
+  // scheduled once every CTA of this grid has run this.
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+  chain_role<RPT>(p, smem);
 }
 
-size_t persistent_smem(int rpt, int Kp, int worker_rows) {
-  const size_t chain = sizeof(unsigned long long) * (size_t)Kp + sizeof(float) * (size_t)rpt * WT * (WNR + 1);
-  const size_t worker = sizeof(float) * ((size_t)(Kp + WT - 1) / WT * WT * WT + (size_t)worker_rows * (Kp + 4));
-  return std::max(chain, worker);
+template <int WR, bool TCW>
+__global__ void __launch_bounds__(WNT, 1) w_workers_kernel(WParams p, const __grid_constant__ CUtensorMap mapX) {
+  extern __shared__ __align__(16) char smem[];
+  if (TCW) worker_role_tc(p, smem, (int)blockIdx.x, &mapX);
+  else worker_role<WR>(p, smem, (int)blockIdx.x);
+  // The grid ends after the chain (bounded wait), so work ordered after it
+  // sees the finished factor whatever the two grids' scheduling was.
+  __syncthreads();
+  if (threadIdx.x == 0) wait_count(sync_finished(p, (p.K + WT - 1) / WT), p.cl, p);
 }
 
-template <int RPT, int WR, bool TCW>
-cudaError_t launch_persistent_t(const WParams& p, const CUtensorMap& map, int n_clusters, size_t smem,
-                                cudaStream_t s) {
-  auto kern = w_update_persistent_kernel<RPT, WR, TCW>;
+size_t chain_smem(int rpt, int Kp) {
+  return sizeof(unsigned long long) * (size_t)Kp + sizeof(float) * (size_t)rpt * WT * (WNR + 1);
+}
+// At least 120 KB, so that two worker CTAs never share an SM (nor a worker
+// an SM of the chain): the rows are dealt one block per CTA.
+constexpr size_t kWorkerSmemFloor = 120 * 1024;
+size_t worker_smem(int Kp, int worker_rows) {
+  return std::max(kWorkerSmemFloor,
+                  sizeof(float) * ((size_t)(Kp + WT - 1) / WT * WT * WT + (size_t)worker_rows * (Kp + 4)));
+}
+
+template <int RPT>
+cudaError_t launch_chain_t(const WParams& p, size_t smem, cudaStream_t s) {
+  auto kern = w_chain_kernel<RPT>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   if ((e = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1)) != cudaSuccess) return e;
   cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3(n_clusters * p.cl, 1, 1);
+  cfg.gridDim = dim3(p.cl, 1, 1);
   cfg.blockDim = dim3(WNT, 1, 1);
   cfg.dynamicSmemBytes = smem;
   cfg.stream = s;
-  // An ordinary cluster launch (no co-residency of the clusters is assumed).
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeClusterDimension;
   attr[0].val.clusterDim.x = p.cl;
@@ -1233,12 +1244,32 @@ cudaError_t launch_persistent_t(const WParams& p, const CUtensorMap& map, int n_
   attr[0].val.clusterDim.z = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kern, p);
+}
+
+template <int WR, bool TCW>
+cudaError_t launch_workers_t(const WParams& p, const CUtensorMap& map, int n_workers, size_t smem, cudaStream_t s) {
+  auto kern = w_workers_kernel<WR, TCW>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(n_workers, 1, 1);
+  cfg.blockDim = dim3(WNT, 1, 1);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  // A programmatic dependent of the chain grid: it may begin while the
+  // chain runs (it does not wait for the chain grid's completion).
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
   return cudaLaunchKernelEx(&cfg, kern, p, map);
 }
 
 template <int RPT>
 int max_clusters_t(int cl, size_t smem) {
-  auto kern = w_update_persistent_kernel<RPT, 1, false>;
+  auto kern = w_chain_kernel<RPT>;
   if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess ||
       cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess) {
     cudaGetLastError();
@@ -1277,7 +1308,7 @@ int max_clusters(int rpt, int cl, size_t smem) {
 
 size_t w_sync_ints(int K) {
   const size_t nt = (size_t)(K + WT - 1) / WT;
-  return (1 + 2 * nt) * kSyncStride + nt * WMAXNB + kSyncStride;
+  return (1 + 2 * nt) * kSyncStride + nt * WMAXNB + 2 * kSyncStride;
 }
 
 size_t w_sync_sdone_offset(int K) {
@@ -1286,49 +1317,55 @@ size_t w_sync_sdone_offset(int K) {
 }
 
 void w_persistent_blocks(int N, const WPersistConfig& cfg, int* nb, int* per) {
-  const int n_workers = (cfg.n_clusters - 1) * cfg.cluster;
-  *per = (N + n_workers - 1) / n_workers;
+  *per = (N + cfg.n_workers - 1) / cfg.n_workers;
   *nb = (N + *per - 1) / *per;
 }
 
 bool w_persistent_config(int N, int Kp, WPersistConfig* cfg, bool tc) {
+  int dev = 0, n_sm = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
   for (int cl : {16, 8}) {
     const int nrc = (N + cl - 1) / cl;
     const int rpt = (nrc + WNR - 1) / WNR;
     if (rpt > 4) continue;
+    const int n_workers = std::min(WMAXNB, n_sm - cl);
+    if (n_workers < 1) continue;
     // Rows per worker pass: as many (up to 4 lanes per thread's row, a
     // multiple of 8) as the shared-memory budget holds, so that at large K
     // most of the CTA's threads still have a row (K = 400: 120 rows, where
     // halving from 128 gave 64 and left half the threads idle).
     constexpr size_t kBudget = 216 * 1024;
     int worker_rows = WNT / 4;
-    while (worker_rows > 16 && persistent_smem(rpt, Kp, worker_rows) > kBudget) worker_rows -= 8;
-    size_t smem = persistent_smem(rpt, Kp, worker_rows);
-    if (tc) smem = std::max(smem, wtc_smem(Kp));        // tensor-core workers: plane ring and B operand
-    if (smem > kBudget) continue;
-    const int nc = max_clusters(rpt, cl, smem);
-    if (nc < 2) continue;
+    while (worker_rows > 16 && worker_smem(Kp, worker_rows) > kBudget) worker_rows -= 8;
+    size_t wsmem = worker_smem(Kp, worker_rows);
+    if (tc) wsmem = std::max(wsmem, wtc_smem(Kp));      // tensor-core workers: plane ring and B operand
+    const size_t csmem = chain_smem(rpt, Kp);
+    if (wsmem > kBudget || csmem > kBudget) continue;
+    if (max_clusters(rpt, cl, csmem) < 1) continue;
     cfg->cluster = cl;
     cfg->rpt = rpt;
     cfg->chain_rows = nrc;
-    cfg->n_clusters = std::min(nc, 1 + WMAXNB / cl);
+    cfg->n_workers = n_workers;
     cfg->worker_rows = worker_rows;
     // A worker stages its whole row block at once where it fits (the base
     // is then formed in passes of worker_rows over it, and the block stays
     // in shared memory for the Gram partial).
     {
-      const int n_workers = (cfg->n_clusters - 1) * cl;
       const int per = (N + n_workers - 1) / n_workers;
       const size_t whole = sizeof(float) * ((size_t)(Kp + WT - 1) / WT * WT * WT + (size_t)per * (Kp + 4));
       cfg->stage_rows = worker_rows;
-      if (!tc && per > worker_rows && whole <= kBudget &&
-          max_clusters(rpt, cl, std::max(smem, whole)) >= cfg->n_clusters) {
+      if (!tc && per > worker_rows && whole <= kBudget) {
         cfg->stage_rows = per;
-        smem = std::max(smem, whole);
+        wsmem = std::max(wsmem, whole);
       }
     }
     cfg->worker_wr = Kp >= 192 ? 2 : 1;
-    cfg->smem = smem;
+    cfg->chain_smem = csmem;
+    cfg->worker_smem = wsmem;
     cfg->tc = tc;
     return true;
   }
@@ -1341,37 +1378,26 @@ cudaError_t w_persistent_run(float* X, const float* P, const float* Q, float* Y,
   if (N <= 0 || K <= 0) return cudaSuccess;
   cudaError_t e = cudaMemsetAsync(d_sync, 0, sizeof(int) * w_sync_ints(K), s);
   if (e != cudaSuccess) return e;
-  const int n_workers = (cfg.n_clusters - 1) * cfg.cluster;
-  if (n_workers < 1 || n_workers > WMAXNB) return cudaErrorInvalidValue;
-  const int per = (N + n_workers - 1) / n_workers;
-  const int nb = (N + per - 1) / per;
+  if (cfg.n_workers < 1 || cfg.n_workers > WMAXNB) return cudaErrorInvalidValue;
+  int nb = 0, per = 0;
+  w_persistent_blocks(N, cfg, &nb, &per);
   if (spart && (cfg.tc || Kp > 256 || (size_t)cfg.worker_rows * (Kp + 4) < 16 * 256)) return cudaErrorInvalidValue;
   WParams p{X, P, Q, Y, N, K, Kp, eps, d_status, d_sync, cfg.cluster, cfg.worker_rows, (N + cfg.cluster - 1) / cfg.cluster,
             nb, per, pre0, wait_ns ? wait_ns : kWaitLimitNs, extra_arrivals, spart,
             std::max(cfg.worker_rows, std::min(cfg.stage_rows, per))};
   CUtensorMap map = {};
-  if (cfg.tc) {
-    if (!tma_map_f32(&map, X, N, Kp, Kp, WPW, WTM)) return cudaErrorNotSupported;
-    switch (cfg.rpt) {
-      case 1: return launch_persistent_t<1, 1, true>(p, map, cfg.n_clusters, cfg.smem, s);
-      case 2: return launch_persistent_t<2, 1, true>(p, map, cfg.n_clusters, cfg.smem, s);
-      case 3: return launch_persistent_t<3, 1, true>(p, map, cfg.n_clusters, cfg.smem, s);
-      case 4: return launch_persistent_t<4, 1, true>(p, map, cfg.n_clusters, cfg.smem, s);
-      default: return cudaErrorInvalidValue;
-    }
-  }
-  const bool two = cfg.worker_wr == 2;
+  if (cfg.tc && !tma_map_f32(&map, X, N, Kp, Kp, WPW, WTM)) return cudaErrorNotSupported;
   switch (cfg.rpt) {
-    case 1: return two ? launch_persistent_t<1, 2, false>(p, map, cfg.n_clusters, cfg.smem, s)
-                       : launch_persistent_t<1, 1, false>(p, map, cfg.n_clusters, cfg.smem, s);
-    case 2: return two ? launch_persistent_t<2, 2, false>(p, map, cfg.n_clusters, cfg.smem, s)
-                       : launch_persistent_t<2, 1, false>(p, map, cfg.n_clusters, cfg.smem, s);
-    case 3: return two ? launch_persistent_t<3, 2, false>(p, map, cfg.n_clusters, cfg.smem, s)
-                       : launch_persistent_t<3, 1, false>(p, map, cfg.n_clusters, cfg.smem, s);
-    case 4: return two ? launch_persistent_t<4, 2, false>(p, map, cfg.n_clusters, cfg.smem, s)
-                       : launch_persistent_t<4, 1, false>(p, map, cfg.n_clusters, cfg.smem, s);
+    case 1: e = launch_chain_t<1>(p, cfg.chain_smem, s); break;
+    case 2: e = launch_chain_t<2>(p, cfg.chain_smem, s); break;
+    case 3: e = launch_chain_t<3>(p, cfg.chain_smem, s); break;
+    case 4: e = launch_chain_t<4>(p, cfg.chain_smem, s); break;
     default: return cudaErrorInvalidValue;
   }
+  if (e != cudaSuccess) return e;
+  if (cfg.tc) return launch_workers_t<1, true>(p, map, cfg.n_workers, cfg.worker_smem, s);
+  return cfg.worker_wr == 2 ? launch_workers_t<2, false>(p, map, cfg.n_workers, cfg.worker_smem, s)
+                            : launch_workers_t<1, false>(p, map, cfg.n_workers, cfg.worker_smem, s);
 }
 
 }  // namespace plnmf
