@@ -238,8 +238,11 @@ size_t w_sync_ints(int K);
 // w = worker w's rows, Kp x Kp each, upper triangle), in gram_tri_kernel's
 // order for those chunks, and count the finished block columns at
 // d_sync[w_sync_sdone_offset(K)] (nb x ceil(K / 16) when all are done).
-cudaError_t w_persistent_run(float* X, const float* P, const float* Q, float* Y, int N, int K, int Kp, float eps,
-                             int* d_sync, int* d_status, const WPersistConfig& cfg, cudaStream_t s,
+// Yc: w_chain_base_floats() floats of scratch (the tile bases in the chain's
+// register order).
+size_t w_chain_base_floats();
+cudaError_t w_persistent_run(float* X, const float* P, const float* Q, float* Y, float* Yc, int N, int K, int Kp,
+                             float eps, int* d_sync, int* d_status, const WPersistConfig& cfg, cudaStream_t s,
                              const float* pre0 = nullptr, unsigned long long wait_ns = 0, int extra_arrivals = 0,
                              float* spart = nullptr);
 // Row blocks of the single-launch W update: nb blocks of per rows (the last

@@ -69,6 +69,7 @@ struct nmf_ctx {
   float* Y = nullptr;       // phase-1 / phase-3 base, max(V, D) x Kp
   float* stage = nullptr;   // transpose staging, max(V, D) x Kp
   float* Y0lo = nullptr;    // V x 16: compensation of tile 0's early W base (persistent W update)
+  float* Yc = nullptr;      // tile bases in the chain's register order (persistent W update)
   double* obj_partial = nullptr;
   int n_obj_partial = 296;
   double* hist = nullptr;
@@ -241,7 +242,7 @@ cudaError_t enq_update(nmf_ctx* c, float* X, const float* G, const float* B, int
   }
   if (c->w_persistent) {
     c->launch_count += 1;
-    return w_persistent_run(X, B, G, c->Y, N, K, Kp, c->eps, c->d_sync, c->d_status, c->wp, c->stream,
+    return w_persistent_run(X, B, G, c->Y, c->Yc, N, K, Kp, c->eps, c->d_sync, c->d_status, c->wp, c->stream,
                             pre0 ? c->Y0lo : nullptr, c->wait_ns, c->extra_arrivals,
                             with_s && c->ws_gram ? c->gramW.d_part : nullptr);
   }
@@ -629,6 +630,10 @@ nmf_status init_impl(const nmf_problem* p, nmf_ctx* c) {
   // least one worker cluster fit; its result does not depend on how many of
   // the clusters run at the same time, so no probe launch is needed.
   c->w_persistent = !(p->flags & NMF_FLAG_MULTI_LAUNCH_W) && w_persistent_config(V, Kp, &c->wp, c->tc_updates);
+  if (c->w_persistent) {
+    CK(dalloc(&c->Yc, w_chain_base_floats()));
+    CK(cudaMemsetAsync(c->Yc, 0, sizeof(float) * w_chain_base_floats(), c->stream));
+  }
   c->gramW0 = c->gramW;
   if (c->w_persistent && !c->wp.tc && !c->use_tc && !c->bf16 && Kp <= 256 && gram_tri_single_group(c->gramW) &&
       (size_t)c->wp.worker_rows * (Kp + 4) >= 16 * 256) {
@@ -660,7 +665,7 @@ void free_ctx(nmf_ctx* c) {
 
   for (void* p : {(void*)c->A_bf16, c->Ab8, c->ATb8, c->Ab8lo, c->ATb8lo, c->Fb8, c->Fb8lo, (void*)c->gpart, (void*)c->ppart, (void*)c->resid_part,
                   (void*)c->d_sync, (void*)c->rpT, (void*)c->ciT, (void*)c->vaT, (void*)c->W, (void*)c->Ht, (void*)c->R,
-                  (void*)c->P, (void*)c->S, (void*)c->Q, (void*)c->Y, (void*)c->stage, (void*)c->Y0lo, (void*)c->alg1_part,
+                  (void*)c->P, (void*)c->S, (void*)c->Q, (void*)c->Y, (void*)c->stage, (void*)c->Y0lo, (void*)c->Yc, (void*)c->alg1_part,
                   (void*)c->obj_partial, (void*)c->hist, (void*)c->d_counter, (void*)c->d_status,
                   (void*)c->d_obj_last})
     if (p) cudaFree(p);

@@ -65,6 +65,8 @@ struct WParams {
   float* spart;        // non-null: chunk w (w < nb) of the Gram partials S_w = X_w^T X_w of the new factor,
                        // Kp x Kp each, upper triangle (the rows of worker w are the chunk)
   int stage_rows;      // rows a worker stages at once (>= worker_rows; per: its whole block)
+  float* Yc;           // tile bases in the chain's register order (yc_quad), two tile slots
+  int rpt;             // register rows per chain row thread
 };
 
 __device__ __forceinline__ unsigned cluster_id_x() {
@@ -98,6 +100,20 @@ __device__ __forceinline__ int* sync_sdone(const WParams& p, int nt) {
 // Chain CTAs that have finished (every store released).
 __device__ __forceinline__ int* sync_finished(const WParams& p, int nt) {
   return p.sync + (2 + 2 * nt) * kSyncStride + nt * WMAXNB;
+}
+
+// Tile bases in the order the chain's row threads hold them: tile tau in
+// slot tau & 1; in a slot, chain CTA c, register row i, column quad q and
+// row thread r give the 16-byte quad of row c * chain_rows + i * WNR + r,
+// columns 4 q .. 4 q + 3 of the tile (zero past K).  A row thread loads its
+// whole tile with RPT x 4 loads, each a warp's 512 consecutive bytes.  Two
+// slots suffice: the base of tile tau is written only after every chain CTA
+// has published tile tau - 2, so after it has loaded the base of tile
+// tau - 2 (the chain's own blocks of tile tau are formed at tile tau).
+__device__ __forceinline__ float4* yc_quad(const WParams& p, int tau, int v, int q) {
+  const int c = v / p.chain_rows, li = v - c * p.chain_rows;
+  const int i = li / WNR, r = li - i * WNR;
+  return reinterpret_cast<float4*>(p.Yc) + ((((int64_t)(tau & 1) * p.cl + c) * p.rpt + i) * 4 + q) * WNR + r;
 }
 
 // A worker that finds the chain cluster not yet running waits this long for
@@ -223,10 +239,10 @@ __device__ __forceinline__ void base_row_global(const WParams& p, int v, int lo,
     for (int c = 0; c < WT; ++c)
       if (j > c) acc[c] = fmaf(-gq(lo + j, c), xo[j], acc[c]);
   }
-  float* yr = p.Y + (int64_t)v * p.Kp;
+  // (acc is zero past K: so are P's term and every Q factor there.)
 #pragma unroll
-  for (int c = 0; c < WT; ++c)
-    if (lo + c < hi) yr[lo + c] = acc[c];
+  for (int q = 0; q < WT / 4; ++q)
+    *yc_quad(p, lo / WT, v, q) = make_float4(acc[4 * q], acc[4 * q + 1], acc[4 * q + 2], acc[4 * q + 3]);
 }
 
 // --------------------------------------------------------------------------
@@ -512,14 +528,8 @@ __device__ void worker_role(const WParams& p, char* smem, int wid) {
             }
           }
           if (!has[u]) continue;
-          float* yr = p.Y + (int64_t)(row0 + lr[u]) * p.Kp;
-          if (lo + 4 * sub + 3 < hi) {
-            *reinterpret_cast<float4*>(yr + lo + 4 * sub) = make_float4(acc[u][0], acc[u][1], acc[u][2], acc[u][3]);
-          } else {
-#pragma unroll
-            for (int q = 0; q < 4; ++q)
-              if (lo + 4 * sub + q < hi) yr[lo + 4 * sub + q] = acc[u][q];
-          }
+          // (Zero past K: so are P's term and every Q factor there.)
+          *yc_quad(p, tau, row0 + lr[u], sub) = make_float4(acc[u][0], acc[u][1], acc[u][2], acc[u][3]);
         }
       }
      }
@@ -740,14 +750,10 @@ __device__ void worker_role_tc(const WParams& p, char* smem_raw, int wid, const 
 #pragma unroll
             for (int c = 0; c < WT; ++c)
               if (j > c && j < w) acc[c] = fmaf(-__ldg(gt + (int64_t)j * p.Kp + c), xo[j], acc[c]);
-          float* yr = p.Y + (int64_t)v * p.Kp + lo;
-          if (w == WT) {
+          // (Zero past K: so are P's term, the B operand and the in-tile terms there.)
 #pragma unroll
-            for (int q = 0; q < WT / 4; ++q)
-              *reinterpret_cast<float4*>(yr + 4 * q) = make_float4(acc[4 * q], acc[4 * q + 1], acc[4 * q + 2], acc[4 * q + 3]);
-          } else {
-            for (int c = 0; c < w; ++c) yr[c] = acc[c];
-          }
+          for (int q = 0; q < WT / 4; ++q)
+            *yc_quad(p, tau, v, q) = make_float4(acc[4 * q], acc[4 * q + 1], acc[4 * q + 2], acc[4 * q + 3]);
         }
       }
     } else if (tid == 128) {
@@ -824,7 +830,7 @@ __device__ void chain_role(const WParams& p, char* smem) {
   float* st = reinterpret_cast<float*>(smem);                 // RPT x WT x (WNR + 1)
   unsigned long long* cbar = reinterpret_cast<unsigned long long*>(smem + sizeof(float) * RPT * WT * (WNR + 1));
   __shared__ float Gs[2][WT][WT];                             // Q[tile][tile], zero beyond the tile
-  __shared__ __align__(16) float Gn[WT][WT];                  // Q[tile][next tile]
+  __shared__ __align__(16) float Gn[2][WT][WT];               // Q[tile][next tile] of tile tq in Gn[tq & 1]
   __shared__ float wpart[NW];
   __shared__ float cpart[2][WMAXCL];
 
@@ -932,8 +938,8 @@ __device__ void chain_role(const WParams& p, char* smem) {
     bool valid[RPT];
 #pragma unroll
     for (int i = 0; i < RPT; ++i) valid[i] = i * WNR + tr < nloc;
-    // y[i][0..15]: the tile's columns; between tiles y holds the previous
-    // tile's contribution to the next one (z), subtracted from the base.
+    // y[i][0..15]: the tile's columns (loaded from the tile's base, less
+    // the previous tile's contribution).
     float y[RPT][WT];
 #pragma unroll
     for (int i = 0; i < RPT; ++i)
@@ -951,7 +957,8 @@ __device__ void chain_role(const WParams& p, char* smem) {
     };
     // The Q blocks a tile needs are copied asynchronously (cp.async,
     // zero-filled outside the blocks) one tile ahead, off the tile
-    // transitions: Gs of tile tq into Gs[tq & 1]; Gn of tile tq.
+    // transitions: Gs of tile tq into Gs[tq & 1]; Gn of tile tq (used at the
+    // start of tile tq + 1) into Gn[tq & 1].
     auto fetch_gs = [&](int tq) {
       const int qlo = tq * WT, qw = min(p.K, qlo + WT) - qlo;
       for (int e = tr; e < WT * WT; e += WNR) {
@@ -966,7 +973,7 @@ __device__ void chain_role(const WParams& p, char* smem) {
       for (int e = tr; e < WT * WT; e += WNR) {
         const int i = e / WT, j = e % WT;
         const bool in = i < qw && j < nw;
-        cp_async4(&Gn[i][j], p.Q + (in ? (int64_t)(qlo + i) * p.Kp + nlo + j : 0), in);
+        cp_async4(&Gn[tq & 1][i][j], p.Q + (in ? (int64_t)(qlo + i) * p.Kp + nlo + j : 0), in);
       }
     };
     fetch_gs(0);
@@ -978,7 +985,7 @@ __device__ void chain_role(const WParams& p, char* smem) {
       const int lo = tau * WT, hi = min(p.K, lo + WT), Tw = hi - lo;
       const float(*G)[WT] = Gs[tau & 1];
       const unsigned cbar_tile = smem_u32(cbar + lo);             // column lo + t: cbar_tile + 8 t
-      cp_async_wait_all();                                         // Gs of this tile (issued a tile ahead)
+      cp_async_wait_all();                                         // Gs of this tile, Gn of the previous one
       // Every block of this tile's base is claimed by a worker that is running
       // and needs nothing more to finish it, or by warp 0 of a chain CTA.  (A
       // timed-out wait is recorded in the status word; later tiles do not
@@ -988,14 +995,31 @@ __device__ void chain_role(const WParams& p, char* smem) {
       }
       row_bar();
       // Gn of this tile and Gs of the next: the buffers are free (tile tau - 1
-      // finished reading them before the barrier ending it).
+      // finished reading them before the barrier above).
       fetch_gn(tau);
       if (tau + 1 < nt) fetch_gs(tau + 1);
       cp_async_commit();
-      // Base of the tile for this CTA's rows (4 lanes per row, 16 bytes each),
-      // staged through st (8 loads in flight per thread); each row thread
-      // then takes its own rows.
-      {
+      if (!(tau == 0 && p.pre0)) {
+        // The tile's base for this thread's rows, in its register order: one
+        // 16-byte load per register row and column quad (a warp's 512
+        // consecutive bytes), all in flight at once.
+        const float4* yb = reinterpret_cast<const float4*>(p.Yc) +
+                           (((int64_t)(tau & 1) * p.cl + rank) * RPT * 4) * WNR + tr;
+#pragma unroll
+        for (int i = 0; i < RPT; ++i)
+#pragma unroll
+          for (int q = 0; q < WT / 4; ++q) {
+            const float4 v = valid[i] ? yb[(i * 4 + q) * WNR] : make_float4(0.f, 0.f, 0.f, 0.f);
+            y[i][4 * q] = v.x;
+            y[i][4 * q + 1] = v.y;
+            y[i][4 * q + 2] = v.z;
+            y[i][4 * q + 3] = v.w;
+          }
+      } else {
+        // Tile 0's base from the early base (Y, row-major, and its
+        // compensation pre0) and P, for this CTA's rows (4 lanes per row, 16
+        // bytes each), staged through st (8 loads in flight per thread); each
+        // row thread then takes its own rows.
         constexpr int SU = 8;
         const int total = nloc * 4;
         for (int base = tr; base < total; base += SU * WNR) {
@@ -1007,26 +1031,20 @@ __device__ void chain_role(const WParams& p, char* smem) {
             v[u] = make_float4(0.f, 0.f, 0.f, 0.f);
             if (e >= total) continue;
             const int64_t off = (int64_t)row * p.Kp + lo + 4 * q;
-            const bool pre = tau == 0 && p.pre0 != nullptr;
             if (4 * q + 3 < Tw) {
-              v[u] = *reinterpret_cast<const float4*>(p.Y + off);
-              if (pre) {                                          // tile 0's base less P: add P here
-                // P and the early base cancel: P + hi first (nearly exact),
-                // then the early base's compensation.
-                const float4 pp = *reinterpret_cast<const float4*>(p.P + off);
-                const float4 cc = *reinterpret_cast<const float4*>(p.pre0 + (int64_t)row * WT + 4 * q);
-                v[u] = make_float4((pp.x + v[u].x) + cc.x, (pp.y + v[u].y) + cc.y, (pp.z + v[u].z) + cc.z,
-                                   (pp.w + v[u].w) + cc.w);
-              }
+              // P and the early base cancel: P + hi first (nearly exact),
+              // then the early base's compensation.
+              const float4 yy = *reinterpret_cast<const float4*>(p.Y + off);
+              const float4 pp = *reinterpret_cast<const float4*>(p.P + off);
+              const float4 cc = *reinterpret_cast<const float4*>(p.pre0 + (int64_t)row * WT + 4 * q);
+              v[u] = make_float4((pp.x + yy.x) + cc.x, (pp.y + yy.y) + cc.y, (pp.z + yy.z) + cc.z,
+                                 (pp.w + yy.w) + cc.w);
             } else {
               float w[4];
 #pragma unroll
               for (int j = 0; j < 4; ++j) {
                 w[j] = 0.f;
-                if (4 * q + j < Tw) {
-                  w[j] = p.Y[off + j];
-                  if (pre) w[j] = (p.P[off + j] + w[j]) + p.pre0[(int64_t)row * WT + 4 * q + j];
-                }
+                if (4 * q + j < Tw) w[j] = (p.P[off + j] + p.Y[off + j]) + p.pre0[(int64_t)row * WT + 4 * q + j];
               }
               v[u] = make_float4(w[0], w[1], w[2], w[3]);
             }
@@ -1043,12 +1061,37 @@ __device__ void chain_role(const WParams& p, char* smem) {
             st[sidx(i, 4 * q + 3, r)] = v[u].w;
           }
         }
+        row_bar();
+#pragma unroll
+        for (int i = 0; i < RPT; ++i)
+#pragma unroll
+          for (int t = 0; t < WT; ++t) y[i][t] = valid[i] ? st[sidx(i, t, tr)] : 0.f;
       }
-      row_bar();
+      if (tau > 0) {
+        // The previous tile's contribution, y -= x_prev * Q[prev][tile], for
+        // this thread's rows (the previous tile's finished columns still wait
+        // in st).  (Unrolled by two: at 4 rows per thread the 4-way unroll
+        // spilled 46 / 96 bytes, this 16 / 16, and the text-like K = 160 W
+        // update went 298 -> 285 us.)
+        const float(*Gp)[WT] = Gn[(tau - 1) & 1];
+#pragma unroll 2
+        for (int j = 0; j < WT; ++j) {
+          float xv[RPT];
 #pragma unroll
-      for (int i = 0; i < RPT; ++i)
+          for (int i = 0; i < RPT; ++i) xv[i] = st[sidx(i, j, tr)];
 #pragma unroll
-        for (int t = 0; t < WT; ++t) y[i][t] = valid[i] ? st[sidx(i, t, tr)] - y[i][t] : 0.f;
+          for (int cq = 0; cq < WT / 4; ++cq) {
+            const float4 g = *reinterpret_cast<const float4*>(&Gp[j][4 * cq]);
+#pragma unroll
+            for (int i = 0; i < RPT; ++i) {
+              y[i][4 * cq] = fmaf(-g.x, xv[i], y[i][4 * cq]);
+              y[i][4 * cq + 1] = fmaf(-g.y, xv[i], y[i][4 * cq + 1]);
+              y[i][4 * cq + 2] = fmaf(-g.z, xv[i], y[i][4 * cq + 2]);
+              y[i][4 * cq + 3] = fmaf(-g.w, xv[i], y[i][4 * cq + 3]);
+            }
+          }
+        }
+      }
 
       // Columns t = 0 .. Tw-1 of the tile, unrolled so that every register
       // slot is static: column t is finished and the previous column's
@@ -1122,12 +1165,9 @@ __device__ void chain_role(const WParams& p, char* smem) {
           xp[i] = x;
         }
       }
-      // The tile's columns stored, then the tile is published (warp 0,
-      // after the block barrier), then the contribution of this tile to the
-      // next one, z = x_tile * Q[tile][next] for this CTA's rows (kept in y
-      // until the next base is loaded).
-      const int nlo = hi, nhi = min(p.K, nlo + WT), Tn = nhi - nlo;
-      // The tile's columns stored once, at its end: four lanes per row, so
+      // The tile's columns stored once, at its end, then the tile is
+      // published (warp 0, after the block barrier; its contribution to the
+      // next tile is subtracted at the next tile's start): four lanes per row, so
       // one warp instruction writes eight whole 64-byte row segments
       // (storing four columns of each thread's rows every fourth column
       // wrote a 16-byte piece of 32 rows per instruction and made those
@@ -1151,35 +1191,8 @@ __device__ void chain_role(const WParams& p, char* smem) {
         }
       }
       __syncthreads();
-      cp_async_wait_all();                                     // Gn of this tile, Gs of the next
-      row_bar();
-#pragma unroll
-      for (int i = 0; i < RPT; ++i)
-#pragma unroll
-        for (int s2 = 0; s2 < WT; ++s2) y[i][s2] = 0.f;
-      if (Tn > 0) {                                            // then Tw == WT (only the last tile is partial)
-        // (Unrolled by two: at 4 rows per thread the 4-way unroll spilled
-        // 46 / 96 bytes, this 16 / 16, and the text-like K = 160 W update
-        // went 298 -> 285 us.)
-#pragma unroll 2
-        for (int j = 0; j < WT; ++j) {
-          float xv[RPT];
-#pragma unroll
-          for (int i = 0; i < RPT; ++i) xv[i] = st[sidx(i, j, tr)];
-#pragma unroll
-          for (int cq = 0; cq < WT / 4; ++cq) {
-            const float4 g = *reinterpret_cast<const float4*>(&Gn[j][4 * cq]);
-#pragma unroll
-            for (int i = 0; i < RPT; ++i) {
-              y[i][4 * cq] = fmaf(g.x, xv[i], y[i][4 * cq]);
-              y[i][4 * cq + 1] = fmaf(g.y, xv[i], y[i][4 * cq + 1]);
-              y[i][4 * cq + 2] = fmaf(g.z, xv[i], y[i][4 * cq + 2]);
-              y[i][4 * cq + 3] = fmaf(g.w, xv[i], y[i][4 * cq + 3]);
-            }
-          }
-        }
-      }
     }
+    cp_async_wait_all();                                         // the last tile's Gn (unused)
   }
   // Every CTA has sent every column's partial once it reaches the cluster
   // barrier; each then waits (bounded) until all partials addressed to it
@@ -1372,10 +1385,14 @@ bool w_persistent_config(int N, int Kp, WPersistConfig* cfg, bool tc) {
   return false;
 }
 
-cudaError_t w_persistent_run(float* X, const float* P, const float* Q, float* Y, int N, int K, int Kp, float eps,
-                             int* d_sync, int* d_status, const WPersistConfig& cfg, cudaStream_t s,
+size_t w_chain_base_floats() { return (size_t)2 * WMAXCL * 4 * WNR * WT; }
+
+cudaError_t w_persistent_run(float* X, const float* P, const float* Q, float* Y, float* Yc, int N, int K, int Kp,
+                             float eps, int* d_sync, int* d_status, const WPersistConfig& cfg, cudaStream_t s,
                              const float* pre0, unsigned long long wait_ns, int extra_arrivals, float* spart) {
   if (N <= 0 || K <= 0) return cudaSuccess;
+  if (!Yc || cfg.rpt < 1 || cfg.rpt > 4 || cfg.cluster > WMAXCL || (size_t)cfg.cluster * cfg.rpt * WNR < (size_t)N)
+    return cudaErrorInvalidValue;
   cudaError_t e = cudaMemsetAsync(d_sync, 0, sizeof(int) * w_sync_ints(K), s);
   if (e != cudaSuccess) return e;
   if (cfg.n_workers < 1 || cfg.n_workers > WMAXNB) return cudaErrorInvalidValue;
@@ -1384,7 +1401,7 @@ cudaError_t w_persistent_run(float* X, const float* P, const float* Q, float* Y,
   if (spart && (cfg.tc || Kp > 256 || (size_t)cfg.worker_rows * (Kp + 4) < 16 * 256)) return cudaErrorInvalidValue;
   WParams p{X, P, Q, Y, N, K, Kp, eps, d_status, d_sync, cfg.cluster, cfg.worker_rows, (N + cfg.cluster - 1) / cfg.cluster,
             nb, per, pre0, wait_ns ? wait_ns : kWaitLimitNs, extra_arrivals, spart,
-            std::max(cfg.worker_rows, std::min(cfg.stage_rows, per))};
+            std::max(cfg.worker_rows, std::min(cfg.stage_rows, per)), Yc, cfg.rpt};
   CUtensorMap map = {};
   if (cfg.tc && !tma_map_f32(&map, X, N, Kp, Kp, WPW, WTM)) return cudaErrorNotSupported;
   switch (cfg.rpt) {
