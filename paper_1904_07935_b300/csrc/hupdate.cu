@@ -478,7 +478,7 @@ __global__ void __launch_bounds__(256) h_update_warp_kernel(float* __restrict__ 
 __global__ void __launch_bounds__(HTHREADS) w_prep_kernel(const float* __restrict__ X, const float* __restrict__ B,
                                                           const float* __restrict__ G, float* __restrict__ Y,
                                                           float* __restrict__ Ylo, int N, int K, int Kp, int lo,
-                                                          int new_end, int T, int* status) {
+                                                          int new_end, int T, int* status, ChainOrder co) {
   // Shared memory: Gc (Kr x HT) = G[j][lo + c], zero beyond K; Xs = the CTA's
   // rows of X (row stride Kp + 4, see h_update_kernel).
   extern __shared__ __align__(16) float smem[];
@@ -557,6 +557,14 @@ __global__ void __launch_bounds__(HTHREADS) w_prep_kernel(const float* __restric
   }
 #pragma unroll
   for (int q = 0; q < 4; ++q) comp_fold(acc[q], cmp[q], blk[q]);
+  if (co.base) {
+    // In the W chain's register order (lo = 0, T = 16: this lane's quad;
+    // zero past K, where every G factor is).
+    const long long qi = chain_quad(row, sub, co.chain_rows, co.rpt);
+    reinterpret_cast<float4*>(co.base)[qi] = make_float4(acc[0], acc[1], acc[2], acc[3]);
+    reinterpret_cast<float4*>(co.comp)[qi] = make_float4(cmp[0], cmp[1], cmp[2], cmp[3]);
+    return;
+  }
   float* yr = Y + (int64_t)row * Kp;
 #pragma unroll
   for (int q = 0; q < 4; ++q) {
@@ -574,13 +582,16 @@ __global__ void __launch_bounds__(HTHREADS) w_prep_kernel(const float* __restric
 }  // namespace
 
 cudaError_t w_prep_run(const float* X, const float* B, const float* G, float* Y, int N, int K, int Kp, int lo,
-                       int new_end, int* status, cudaStream_t s, int T, float* Ylo) {
+                       int new_end, int* status, cudaStream_t s, int T, float* Ylo, const ChainOrder* co) {
   if (T < 1 || T > HT) return cudaErrorInvalidValue;
+  if (co && (B || lo != 0 || new_end != 0 || T != HT || !co->base || !co->comp || co->chain_rows < 1 || co->rpt < 1))
+    return cudaErrorInvalidValue;
   const size_t smem = sizeof(float) * ((size_t)((Kp + HT - 1) / HT * HT) * HT + (size_t)HROWS * (Kp + 4));
   cudaError_t e = cudaFuncSetAttribute(w_prep_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   const int blocks = (N + HROWS - 1) / HROWS;
-  w_prep_kernel<<<blocks, HTHREADS, smem, s>>>(X, B, G, Y, B ? nullptr : Ylo, N, K, Kp, lo, new_end, T, status);
+  w_prep_kernel<<<blocks, HTHREADS, smem, s>>>(X, B, G, Y, B ? nullptr : Ylo, N, K, Kp, lo, new_end, T, status,
+                                                co ? *co : ChainOrder{});
   return cudaGetLastError();
 }
 

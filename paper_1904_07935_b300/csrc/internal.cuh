@@ -187,9 +187,33 @@ cudaError_t h_update_tc_run(float* X, const float* B, const float* G, int N, int
 // B == nullptr leaves the data term out; then, with Ylo (N x 16) given, the
 // compensated sum is returned unrounded as Y[:, tile] + Ylo (the caller adds
 // P to Y first: the two cancel, so the early rounding would be magnified).
+// With co given (B == nullptr, lo = new_end = 0, T = 16), the sum and its
+// compensation go to co->base and co->comp in the W chain's register order
+// instead of Y and Ylo.
+struct ChainOrder;
 cudaError_t w_prep_run(const float* X, const float* B, const float* G, float* Y, int N, int K, int Kp, int lo,
-                       int new_end, int* status, cudaStream_t s, int T, float* Ylo = nullptr);
+                       int new_end, int* status, cudaStream_t s, int T, float* Ylo = nullptr,
+                       const ChainOrder* co = nullptr);
 constexpr int kRowTile = 16;   // tile width of the row-parallel update kernels
+
+// The register order of the persistent W update's column chain for one
+// 16-column tile: the 16-byte quad of row v, tile columns 4 q .. 4 q + 3,
+// is quad ((c * rpt + i) * 4 + q) * kChainRowThreads + r of the buffer, with
+// chain CTA c = v / chain_rows, register row i and row thread r from
+// v - c * chain_rows = i * kChainRowThreads + r.  A chain row thread loads
+// its rows of a tile with rpt x 4 loads of a warp's 512 consecutive bytes.
+constexpr int kChainRowThreads = 480;
+struct ChainOrder {
+  float* base = nullptr;       // tile 0's early base less P
+  float* comp = nullptr;       // its compensation
+  int chain_rows = 0;
+  int rpt = 0;
+};
+__host__ __device__ __forceinline__ long long chain_quad(int v, int q, int chain_rows, int rpt) {
+  const int c = v / chain_rows, li = v - c * chain_rows;
+  const int i = li / kChainRowThreads, r = li - i * kChainRowThreads;
+  return (((long long)c * rpt + i) * 4 + q) * kChainRowThreads + r;
+}
 
 // Alg. 1 as written (no column tiling): the H and W updates column by
 // column, K (H) or 2K (W) dependent grid-wide launches; `part` holds
@@ -226,9 +250,10 @@ struct WPersistConfig {
 bool w_persistent_config(int N, int Kp, WPersistConfig* cfg, bool tc = false);
 // d_sync: w_sync_ints(K) ints (zeroed by the call, on the stream).
 size_t w_sync_ints(int K);
-// pre0 != nullptr: Y's columns [0, 16) plus pre0 (N x 16) already hold tile
-// 0's base less P (w_prep_run with B = nullptr, lo = new_end = 0, Ylo =
-// pre0); the launch then adds P there.
+// pre0 != nullptr: w_chain_order(Yc, ...) slot 0 plus its compensation
+// (pre0 = the order's comp) already hold tile 0's base less P (w_prep_run
+// with B = nullptr, lo = new_end = 0 and that ChainOrder); the launch then
+// adds P there.
 // wait_ns: limit of every device wait (0: kWaitLimitNs); extra_arrivals > 0
 // makes the workers wait for more chain arrivals than exist (tests of the
 // timeout path: the waits run out, ST_TIMEOUT is set and the chain computes
@@ -238,10 +263,13 @@ size_t w_sync_ints(int K);
 // w = worker w's rows, Kp x Kp each, upper triangle), in gram_tri_kernel's
 // order for those chunks, and count the finished block columns at
 // d_sync[w_sync_sdone_offset(K)] (nb x ceil(K / 16) when all are done).
-// Yc: w_chain_base_floats() floats of scratch (the tile bases in the chain's
-// register order).
+// Yc: w_chain_base_floats() floats of scratch (two slots of tile bases in
+// the chain's register order, then tile 0's early-base compensation).
 size_t w_chain_base_floats();
-cudaError_t w_persistent_run(float* X, const float* P, const float* Q, float* Y, float* Yc, int N, int K, int Kp,
+// Tile 0's early base and its compensation in the chain's order (for
+// w_prep_run) within Yc for this configuration.
+ChainOrder w_chain_order(float* Yc, int N, const WPersistConfig& cfg);
+cudaError_t w_persistent_run(float* X, const float* P, const float* Q, float* Yc, int N, int K, int Kp,
                              float eps, int* d_sync, int* d_status, const WPersistConfig& cfg, cudaStream_t s,
                              const float* pre0 = nullptr, unsigned long long wait_ns = 0, int extra_arrivals = 0,
                              float* spart = nullptr);

@@ -68,7 +68,6 @@ struct nmf_ctx {
   float *W = nullptr, *Ht = nullptr, *R = nullptr, *P = nullptr, *S = nullptr, *Q = nullptr;
   float* Y = nullptr;       // phase-1 / phase-3 base, max(V, D) x Kp
   float* stage = nullptr;   // transpose staging, max(V, D) x Kp
-  float* Y0lo = nullptr;    // V x 16: compensation of tile 0's early W base (persistent W update)
   float* Yc = nullptr;      // tile bases in the chain's register order (persistent W update)
   double* obj_partial = nullptr;
   int n_obj_partial = 296;
@@ -242,8 +241,8 @@ cudaError_t enq_update(nmf_ctx* c, float* X, const float* G, const float* B, int
   }
   if (c->w_persistent) {
     c->launch_count += 1;
-    return w_persistent_run(X, B, G, c->Y, c->Yc, N, K, Kp, c->eps, c->d_sync, c->d_status, c->wp, c->stream,
-                            pre0 ? c->Y0lo : nullptr, c->wait_ns, c->extra_arrivals,
+    return w_persistent_run(X, B, G, c->Yc, N, K, Kp, c->eps, c->d_sync, c->d_status, c->wp, c->stream,
+                            pre0 ? w_chain_order(c->Yc, N, c->wp).comp : nullptr, c->wait_ns, c->extra_arrivals,
                             with_s && c->ws_gram ? c->gramW.d_part : nullptr);
   }
   // W: tile tau's base without tile tau-1 ("main") runs on the side stream
@@ -334,8 +333,9 @@ cudaError_t enq_iteration(nmf_ctx* c, const IoHooks* io = nullptr) {
   const bool pre0 = c->w_persistent;
   if (pre0) {
     c->launch_count += 1;
-    if ((e = w_prep_run(c->W, nullptr, c->Q, c->Y, c->V, c->K, c->Kp, 0, 0, c->d_status, b, kRowTile, c->Y0lo)) !=
-        cudaSuccess)
+    const ChainOrder co = w_chain_order(c->Yc, c->V, c->wp);
+    if ((e = w_prep_run(c->W, nullptr, c->Q, nullptr, c->V, c->K, c->Kp, 0, 0, c->d_status, b, kRowTile, nullptr,
+                        &co)) != cudaSuccess)
       return e;
   }
   if ((e = cudaEventRecord(c->evx[1], b)) != cudaSuccess) return e;
@@ -566,7 +566,6 @@ nmf_status init_impl(const nmf_problem* p, nmf_ctx* c) {
   CK(dalloc(&c->Q, nK));
   CK(dalloc(&c->Y, nMax));
   CK(dalloc(&c->stage, nMax));
-  CK(dalloc(&c->Y0lo, (size_t)V * kRowTile));
   CK(dalloc(&c->alg1_part, (size_t)alg1_parts(V)));
   CK(cudaMemsetAsync(c->P, 0, sizeof(float) * nV, c->stream));
   CK(cudaMemsetAsync(c->R, 0, sizeof(float) * nD, c->stream));
@@ -665,7 +664,7 @@ void free_ctx(nmf_ctx* c) {
 
   for (void* p : {(void*)c->A_bf16, c->Ab8, c->ATb8, c->Ab8lo, c->ATb8lo, c->Fb8, c->Fb8lo, (void*)c->gpart, (void*)c->ppart, (void*)c->resid_part,
                   (void*)c->d_sync, (void*)c->rpT, (void*)c->ciT, (void*)c->vaT, (void*)c->W, (void*)c->Ht, (void*)c->R,
-                  (void*)c->P, (void*)c->S, (void*)c->Q, (void*)c->Y, (void*)c->stage, (void*)c->Y0lo, (void*)c->Yc, (void*)c->alg1_part,
+                  (void*)c->P, (void*)c->S, (void*)c->Q, (void*)c->Y, (void*)c->stage, (void*)c->Yc, (void*)c->alg1_part,
                   (void*)c->obj_partial, (void*)c->hist, (void*)c->d_counter, (void*)c->d_status,
                   (void*)c->d_obj_last})
     if (p) cudaFree(p);

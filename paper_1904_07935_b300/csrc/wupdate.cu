@@ -49,7 +49,6 @@ struct WParams {
   float* X;            // N x Kp, old on entry, new on exit
   const float* P;      // N x Kp
   const float* Q;      // Kp x Kp
-  float* Y;            // N x Kp scratch: tile bases
   int N, K, Kp;
   float eps;
   int* status;
@@ -59,7 +58,7 @@ struct WParams {
   int chain_rows;      // rows per chain CTA, ceil(N / cl): CTA rank owns [rank * chain_rows, ...)
   int nb;              // row blocks per tile base: block w = rows [w * per, min(N, (w + 1) * per))
   int per;
-  const float* pre0;   // non-null: Y's first tile + pre0 (N x 16) hold tile 0's base less P (formed before the launch)
+  const float* pre0;   // non-null: Yc's slot 0 + pre0 (the same order) hold tile 0's base less P (formed before the launch)
   unsigned long long wait_ns;  // limit of every wait
   int extra_arrivals;  // added to the chain_done count the workers wait for (tests of the timeout path; 0)
   float* spart;        // non-null: chunk w (w < nb) of the Gram partials S_w = X_w^T X_w of the new factor,
@@ -110,10 +109,10 @@ __device__ __forceinline__ int* sync_finished(const WParams& p, int nt) {
 // slots suffice: the base of tile tau is written only after every chain CTA
 // has published tile tau - 2, so after it has loaded the base of tile
 // tau - 2 (the chain's own blocks of tile tau are formed at tile tau).
+static_assert(WNR == kChainRowThreads, "chain register order");
 __device__ __forceinline__ float4* yc_quad(const WParams& p, int tau, int v, int q) {
-  const int c = v / p.chain_rows, li = v - c * p.chain_rows;
-  const int i = li / WNR, r = li - i * WNR;
-  return reinterpret_cast<float4*>(p.Yc) + ((((int64_t)(tau & 1) * p.cl + c) * p.rpt + i) * 4 + q) * WNR + r;
+  return reinterpret_cast<float4*>(p.Yc) + (int64_t)(tau & 1) * p.cl * p.rpt * 4 * WNR +
+         chain_quad(v, q, p.chain_rows, p.rpt);
 }
 
 // A worker that finds the chain cluster not yet running waits this long for
@@ -1016,10 +1015,9 @@ __device__ void chain_role(const WParams& p, char* smem) {
             y[i][4 * q + 3] = v.w;
           }
       } else {
-        // Tile 0's base from the early base (Y, row-major, and its
-        // compensation pre0) and P, for this CTA's rows (4 lanes per row, 16
-        // bytes each), staged through st (8 loads in flight per thread); each
-        // row thread then takes its own rows.
+        // Tile 0's base: P, staged through st for this CTA's rows (4 lanes per
+        // row, 16 bytes each, 8 loads in flight per thread), plus the early
+        // base and its compensation in this thread's register order.
         constexpr int SU = 8;
         const int total = nloc * 4;
         for (int base = tr; base < total; base += SU * WNR) {
@@ -1032,20 +1030,11 @@ __device__ void chain_role(const WParams& p, char* smem) {
             if (e >= total) continue;
             const int64_t off = (int64_t)row * p.Kp + lo + 4 * q;
             if (4 * q + 3 < Tw) {
-              // P and the early base cancel: P + hi first (nearly exact),
-              // then the early base's compensation.
-              const float4 yy = *reinterpret_cast<const float4*>(p.Y + off);
-              const float4 pp = *reinterpret_cast<const float4*>(p.P + off);
-              const float4 cc = *reinterpret_cast<const float4*>(p.pre0 + (int64_t)row * WT + 4 * q);
-              v[u] = make_float4((pp.x + yy.x) + cc.x, (pp.y + yy.y) + cc.y, (pp.z + yy.z) + cc.z,
-                                 (pp.w + yy.w) + cc.w);
+              v[u] = *reinterpret_cast<const float4*>(p.P + off);
             } else {
               float w[4];
 #pragma unroll
-              for (int j = 0; j < 4; ++j) {
-                w[j] = 0.f;
-                if (4 * q + j < Tw) w[j] = (p.P[off + j] + p.Y[off + j]) + p.pre0[(int64_t)row * WT + 4 * q + j];
-              }
+              for (int j = 0; j < 4; ++j) w[j] = 4 * q + j < Tw ? p.P[off + j] : 0.f;
               v[u] = make_float4(w[0], w[1], w[2], w[3]);
             }
           }
@@ -1062,10 +1051,24 @@ __device__ void chain_role(const WParams& p, char* smem) {
           }
         }
         row_bar();
+        // P and the early base cancel: P + early base first (nearly exact),
+        // then the early base's compensation.
+        const float4* yb = reinterpret_cast<const float4*>(p.Yc) + ((int64_t)rank * RPT * 4) * WNR + tr;
+        const float4* cb = reinterpret_cast<const float4*>(p.pre0) + ((int64_t)rank * RPT * 4) * WNR + tr;
 #pragma unroll
         for (int i = 0; i < RPT; ++i)
 #pragma unroll
-          for (int t = 0; t < WT; ++t) y[i][t] = valid[i] ? st[sidx(i, t, tr)] : 0.f;
+          for (int q = 0; q < WT / 4; ++q) {
+            float4 e = make_float4(0.f, 0.f, 0.f, 0.f), c = e;
+            if (valid[i]) {
+              e = yb[(i * 4 + q) * WNR];
+              c = cb[(i * 4 + q) * WNR];
+            }
+            const float ev[4] = {e.x, e.y, e.z, e.w}, cv[4] = {c.x, c.y, c.z, c.w};
+#pragma unroll
+            for (int j = 0; j < 4; ++j)
+              y[i][4 * q + j] = valid[i] ? (st[sidx(i, 4 * q + j, tr)] + ev[j]) + cv[j] : 0.f;
+          }
       }
       if (tau > 0) {
         // The previous tile's contribution, y -= x_prev * Q[prev][tile], for
@@ -1385,9 +1388,18 @@ bool w_persistent_config(int N, int Kp, WPersistConfig* cfg, bool tc) {
   return false;
 }
 
-size_t w_chain_base_floats() { return (size_t)2 * WMAXCL * 4 * WNR * WT; }
+size_t w_chain_base_floats() { return (size_t)3 * WMAXCL * 4 * WNR * WT; }
 
-cudaError_t w_persistent_run(float* X, const float* P, const float* Q, float* Y, float* Yc, int N, int K, int Kp,
+ChainOrder w_chain_order(float* Yc, int N, const WPersistConfig& cfg) {
+  ChainOrder co;
+  co.chain_rows = (N + cfg.cluster - 1) / cfg.cluster;
+  co.rpt = cfg.rpt;
+  co.base = Yc;
+  co.comp = Yc + (size_t)2 * cfg.cluster * cfg.rpt * WNR * WT;
+  return co;
+}
+
+cudaError_t w_persistent_run(float* X, const float* P, const float* Q, float* Yc, int N, int K, int Kp,
                              float eps, int* d_sync, int* d_status, const WPersistConfig& cfg, cudaStream_t s,
                              const float* pre0, unsigned long long wait_ns, int extra_arrivals, float* spart) {
   if (N <= 0 || K <= 0) return cudaSuccess;
@@ -1399,7 +1411,7 @@ cudaError_t w_persistent_run(float* X, const float* P, const float* Q, float* Y,
   int nb = 0, per = 0;
   w_persistent_blocks(N, cfg, &nb, &per);
   if (spart && (cfg.tc || Kp > 256 || (size_t)cfg.worker_rows * (Kp + 4) < 16 * 256)) return cudaErrorInvalidValue;
-  WParams p{X, P, Q, Y, N, K, Kp, eps, d_status, d_sync, cfg.cluster, cfg.worker_rows, (N + cfg.cluster - 1) / cfg.cluster,
+  WParams p{X, P, Q, N, K, Kp, eps, d_status, d_sync, cfg.cluster, cfg.worker_rows, (N + cfg.cluster - 1) / cfg.cluster,
             nb, per, pre0, wait_ns ? wait_ns : kWaitLimitNs, extra_arrivals, spart,
             std::max(cfg.worker_rows, std::min(cfg.stage_rows, per)), Yc, cfg.rpt};
   CUtensorMap map = {};
