@@ -901,8 +901,14 @@ nmf_status nmf_batch_create(nmf_ctx* const* ctxs, int32_t n, int32_t autotune, v
   for (int i = 0; i < n; ++i) {
     nmf_ctx* c = b->m[i];
     c->w_persistent = false;
-    c->ws_gram = false;                       // the per-tile W update forms no Gram partials
-    c->gramW = c->gramW0;
+    if (c->ws_gram) {
+      // The per-tile W update forms no Gram partials; S is formed again with
+      // the Gram's own chunking, so that a member computes exactly what a
+      // context made for the per-tile form does.
+      c->ws_gram = false;
+      c->gramW = c->gramW0;
+      c->s_valid = false;
+    }
     drop_graph(c);
     if ((e = ensure_entry(c)) != cudaSuccess) return bail(e);
     if (autotune) {

@@ -428,12 +428,21 @@ __device__ void worker_role(const WParams& p, char* smem, int wid) {
       }
     }
     // Rows staged stage_rows at a time (normally the whole block, which
-    // then stays in shared memory for the Gram partial below), the base
-    // formed in passes of RB rows over them.
+    // then stays in shared memory for the Gram partial below and for the
+    // next tiles), the base formed in passes of RB rows over them.
     for (int srow0 = wbeg; srow0 < wend; srow0 += SR) {
      const int snrows = min(SR, wend - srow0);
-     stage_pass(srow0, snrows);                               // (after Gc is staged)
-     xs_final = s_after ? max(0, tau - 1) : -1;
+     if (s_after && xs_final >= 0) {
+       // The whole block is staged with tiles [0, xs_final) final and the
+       // others old, which is what they still are in global memory: only the
+       // tiles finished since (normally tile tau - 2) are fetched again.
+       if (xs_final < tau - 1) reload_cols(xs_final * WT, (tau - 1) * WT);
+       else __syncthreads();                                  // (after Gc is staged)
+       xs_final = max(xs_final, tau - 1);
+     } else {
+       stage_pass(srow0, snrows);                             // (after Gc is staged)
+       xs_final = s_after ? max(0, tau - 1) : -1;
+     }
      for (int prow = 0; prow < snrows; prow += RB) {
       const int nrows = min(RB, snrows - prow);
       const int row0 = srow0 + prow;
