@@ -373,7 +373,10 @@ nmf_status nmf_batch_submit(const nmf_problem* ps, int32_t n, int32_t n_iters, n
  *   ||H_s - H_{s-1}||_F / ||H_{s-1}||_F.  Outputs: H_out (K x N row-major,
  *   host or device), R_out (N x K row-major, optional), *sweeps_out, and
  *   trace[s] = the stopping value after sweep s + 1 (optional, max_sweeps
- *   doubles).  W and the context's own H are not changed.  Synchronous. */
+ *   doubles).  The stopping value is formed on the device in the H update's
+ *   write-back (FP32 squares, FP64 sums) and the host reads it back once per
+ *   32 sweeps; sweeps after the one that met tol leave H as it is.  W and
+ *   the context's own H are not changed.  Synchronous. */
 typedef struct nmf_mlp nmf_mlp;
 nmf_status nmf_mlp_create(int32_t K, int32_t hidden, uint64_t seed, nmf_mlp** out);
 nmf_status nmf_mlp_set_params(nmf_mlp* n, const float* const* params);

@@ -125,7 +125,9 @@ constexpr int HTHREADS = HROWS * HL;
 template <int R, int NG>
 __global__ void __launch_bounds__(4 * NG, 2) h_update_kernel(float* __restrict__ X, const float* __restrict__ B,
                                                           const float* __restrict__ G, int N, int K, int Kp,
-                                                          float eps, int* status) {
+                                                          float eps, int* status, const int* skip,
+                                                          const float* dref, double* dpart) {
+  if (skip && *skip) return;                              // a converged sweep loop (nmf_warm_h)
   // Shared memory: two Gc buffers (Kr x HT each) = G[j][lo + c] for the
   // current and the next tile, zero beyond K; Xs (32 R x (Kp + 4)) = the CTA's
   // rows, updated in place (row stride Kp + 4 keeps the 8 rows a warp reads at
@@ -311,9 +313,44 @@ __global__ void __launch_bounds__(4 * NG, 2) h_update_kernel(float* __restrict__
   {
     const int kq = Kp / 4;
     float4* dst = reinterpret_cast<float4*>(X + (int64_t)row0 * Kp);
+    const float4* rf = dref ? reinterpret_cast<const float4*>(dref + (int64_t)row0 * Kp) : nullptr;
+    // With dpart: this CTA's sums of (new - ref)^2 and ref^2, ref = dref or
+    // the old value (read before it is overwritten): per thread in FP32 (a
+    // difference of nearby values is exact), then FP64 in a fixed order.
+    float da = 0.f, db = 0.f;
     for (int e = tid; e < nrows * kq; e += NT) {
       const int r = e / kq, q = e % kq;
-      dst[e] = *reinterpret_cast<const float4*>(Xs + r * ldx + 4 * q);
+      const float4 v = *reinterpret_cast<const float4*>(Xs + r * ldx + 4 * q);
+      if (dpart) {
+        const float4 o = rf ? rf[e] : dst[e];
+        const float d0 = v.x - o.x, d1 = v.y - o.y, d2 = v.z - o.z, d3 = v.w - o.w;
+        da = fmaf(d0, d0, fmaf(d1, d1, fmaf(d2, d2, fmaf(d3, d3, da))));
+        db = fmaf(o.x, o.x, fmaf(o.y, o.y, fmaf(o.z, o.z, fmaf(o.w, o.w, db))));
+      }
+      dst[e] = v;
+    }
+    if (dpart) {
+      __shared__ double pa[NT / 32], pb[NT / 32];
+      double xa = da, xb = db;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        xa += __shfl_xor_sync(full, xa, o);
+        xb += __shfl_xor_sync(full, xb, o);
+      }
+      if ((tid & 31) == 0) {
+        pa[tid >> 5] = xa;
+        pb[tid >> 5] = xb;
+      }
+      __syncthreads();
+      if (tid == 0) {
+        double ta = 0.0, tb = 0.0;
+        for (int w = 0; w < NT / 32; ++w) {
+          ta += pa[w];
+          tb += pb[w];
+        }
+        dpart[2 * blockIdx.x] = ta;
+        dpart[2 * blockIdx.x + 1] = tb;
+      }
     }
   }
 }
@@ -338,7 +375,8 @@ __global__ void __launch_bounds__(4 * NG, 2) h_update_kernel(float* __restrict__
 template <int M>
 __global__ void __launch_bounds__(256) h_update_warp_kernel(float* __restrict__ X, const float* __restrict__ B,
                                                             const float* __restrict__ G, int N, int K, int Kp,
-                                                            float eps) {
+                                                            float eps, const int* skip) {
+  if (skip && *skip) return;                              // a converged sweep loop (nmf_warm_h)
   constexpr int NT = 256, WARPS = NT / 32;
   // S block rows padded to 20 floats: the 32 lanes read 32 consecutive rows
   // with 16-byte loads, and an 80-byte stride puts every 8 of them on
@@ -597,35 +635,41 @@ cudaError_t w_prep_run(const float* X, const float* B, const float* G, float* Y,
 
 template <int R, int NG = 32>
 cudaError_t h_update_launch(float* X, const float* B, const float* G, int N, int K, int Kp, float eps, int* status,
-                            cudaStream_t s) {
+                            cudaStream_t s, const int* skip, const float* dref = nullptr, double* dpart = nullptr,
+                            int* nblk = nullptr) {
   const size_t smem = sizeof(float) * (2 * (size_t)((Kp + HT - 1) / HT * HT) * HT + (size_t)NG * R * (Kp + 4));
   auto kern = h_update_kernel<R, NG>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   const int blocks = (N + NG * R - 1) / (NG * R);
-  kern<<<blocks, 4 * NG, smem, s>>>(X, B, G, N, K, Kp, eps, status);
+  if (nblk) *nblk = blocks;
+  kern<<<blocks, 4 * NG, smem, s>>>(X, B, G, N, K, Kp, eps, status, skip, dref, dpart);
   return cudaGetLastError();
 }
 
 template <int M>
 cudaError_t h_update_warp_launch(float* X, const float* B, const float* G, int N, int K, int Kp, float eps,
-                                 cudaStream_t s) {
+                                 cudaStream_t s, const int* skip) {
   const size_t smem = sizeof(float) * 2 * (size_t)((Kp + HT - 1) / HT * HT) * (HT + 4);
   auto kern = h_update_warp_kernel<M>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  kern<<<(N + 7) / 8, 256, smem, s>>>(X, B, G, N, K, Kp, eps);
+  kern<<<(N + 7) / 8, 256, smem, s>>>(X, B, G, N, K, Kp, eps, skip);
   return cudaGetLastError();
 }
 
-cudaError_t h_update_run(float* X, const float* B, const float* G, int N, int K, int Kp, float eps,
-                         int* status, cudaStream_t s) {
-  if (N <= 0 || K <= 0) return cudaSuccess;
+namespace {
+cudaError_t h_update_dispatch(float* X, const float* B, const float* G, int N, int K, int Kp, float eps,
+                              int* status, cudaStream_t s, const int* skip, const float* dref, double* dpart,
+                              int* nblk) {
   // One warp per row for short rows (Kp <= 32): the row is one register per
   // lane and the warp kernel's per-row column chain is short.  For longer
   // rows the four-lanes-per-row kernel is faster: its chain runs for eight
   // rows per warp at once (measured at K = 160: 68 us against 96 us).
-  if ((Kp + 31) / 32 == 1) return h_update_warp_launch<1>(X, B, G, N, K, Kp, eps, s);
+  if ((Kp + 31) / 32 == 1) {
+    if (dpart) return cudaErrorInvalidValue;              // (h_update_sweep checks this form separately)
+    return h_update_warp_launch<1>(X, B, G, N, K, Kp, eps, s, skip);
+  }
   // Four lanes per row, rows per lane group chosen for occupancy.
   static int sms = 0;
   if (sms == 0) {
@@ -637,8 +681,8 @@ cudaError_t h_update_run(float* X, const float* B, const float* G, int N, int K,
   const size_t gc = sizeof(float) * (size_t)((Kp + HT - 1) / HT * HT) * HT;
   auto fits = [&](int R) { return 2 * gc + per_row * 32 * R <= 200 * 1024; };
   auto enough = [&](int R) { return (long long)(N + 32 * R - 1) / (32 * R) >= 3LL * sms; };
-  if (fits(4) && enough(4)) return h_update_launch<4>(X, B, G, N, K, Kp, eps, status, s);
-  if (fits(2) && enough(2)) return h_update_launch<2>(X, B, G, N, K, Kp, eps, status, s);
+  if (fits(4) && enough(4)) return h_update_launch<4>(X, B, G, N, K, Kp, eps, status, s, skip, dref, dpart, nblk);
+  if (fits(2) && enough(2)) return h_update_launch<2>(X, B, G, N, K, Kp, eps, status, s, skip, dref, dpart, nblk);
   // Long rows: two or three rows per lane group even with few CTAs, as one
   // 16-byte load of S's block then serves them all (8192 x 256: 115 -> 101 us;
   // at K = 160 one row is faster, 66 against 68 us on 11,314 rows).  Of the
@@ -653,13 +697,40 @@ cudaError_t h_update_run(float* X, const float* B, const float* G, int N, int K,
       return (blocks + per_sm * sms - 1) / (per_sm * sms) * R;
     };
     if (2 * gc + per_row * 96 <= 220 * 1024 && cost(3) < cost(2))
-      return h_update_launch<3>(X, B, G, N, K, Kp, eps, status, s);
-    return h_update_launch<2>(X, B, G, N, K, Kp, eps, status, s);
+      return h_update_launch<3>(X, B, G, N, K, Kp, eps, status, s, skip, dref, dpart, nblk);
+    return h_update_launch<2>(X, B, G, N, K, Kp, eps, status, s, skip, dref, dpart, nblk);
   }
   // One row per lane group: 16-group CTAs spread more evenly over the SMs
   // (11,314 rows: 708 CTAs, 4.8 per SM, against 354 at 2.4 per SM, where some
   // SMs carry three and others two): 66.6 -> 64.1 us at K = 160.
-  return h_update_launch<1, 16>(X, B, G, N, K, Kp, eps, status, s);
+  return h_update_launch<1, 16>(X, B, G, N, K, Kp, eps, status, s, skip, dref, dpart, nblk);
+}
+}  // namespace
+
+cudaError_t h_update_run(float* X, const float* B, const float* G, int N, int K, int Kp, float eps,
+                         int* status, cudaStream_t s, const int* skip) {
+  if (N <= 0 || K <= 0) return cudaSuccess;
+  return h_update_dispatch(X, B, G, N, K, Kp, eps, status, s, skip, nullptr, nullptr, nullptr);
+}
+
+size_t h_sweep_partials(int N) { return 2 * (size_t)((N + 15) / 16); }
+
+cudaError_t h_update_sweep(float* X, const float* B, const float* G, int N, int K, int Kp, float eps, int* status,
+                           cudaStream_t s, const float* Href, float* Hprev, double* part, float tol, int sweep,
+                           double* trace, int* state) {
+  if (N <= 0 || K <= 0) return cudaErrorInvalidValue;
+  if ((Kp + 31) / 32 == 1) {
+    // The row-per-warp form has no epilogue: the previous sweep's H is kept
+    // in Hprev and the change is formed by a pass of its own.
+    cudaError_t e;
+    if (!Href && (e = copy_unless_done(Hprev, X, (int64_t)N * Kp, state, s)) != cudaSuccess) return e;
+    if ((e = h_update_warp_launch<1>(X, B, G, N, K, Kp, eps, s, state)) != cudaSuccess) return e;
+    return diff_check(X, Href ? Href : Hprev, N, K, Kp, part, tol, sweep, trace, state, s);
+  }
+  int nblk = 0;
+  cudaError_t e = h_update_dispatch(X, B, G, N, K, Kp, eps, status, s, state, Href, part, &nblk);
+  if (e != cudaSuccess) return e;
+  return sweep_check(part, nblk, tol, sweep, trace, state, s);
 }
 
 }  // namespace plnmf

@@ -173,9 +173,10 @@ bool chain_config_for(int N, bool normalize, int T, ChainConfig* cfg);
 bool chain_config_cluster(int N, int T, int cl, ChainConfig* cfg);
 
 // Whole H update in one launch (rows independent): X (N x Kp) old -> new in
-// place, B = R, G = S.
+// place, B = R, G = S.  skip (device int, optional): when nonzero at launch
+// the kernel leaves X as it is (the converged part of a sweep loop).
 cudaError_t h_update_run(float* X, const float* B, const float* G, int N, int K, int Kp, float eps,
-                         int* status, cudaStream_t s);
+                         int* status, cudaStream_t s, const int* skip = nullptr);
 // The same update with the off-tile sums on the tensor cores (3xTF32 with
 // per-plane compensated folds); supported for 16 <= Kp <= 512.
 bool h_update_tc_supported(int Kp);
@@ -324,6 +325,27 @@ cudaError_t scale_shift(float* x, int64_t n, float a, float b, cudaStream_t s);
 cudaError_t diff_norm(const float* H, const float* Href, int rows, int K, int ld, double* d_part, double* h_out,
                       cudaStream_t s);
 size_t diff_norm_partials();
+// One sweep's check on the device, for sweep loops that read back only every
+// few sweeps: state[0] = done, state[1] = sweeps run.  Unless done, the
+// relative change sqrt(sum (H - Href)^2 / sum Href^2) (sqrt(sum H^2) when the
+// second sum is zero; Href null: H^2) is formed in FP64 from the partials of
+// d_part, written to trace[sweep - 1], state[1] = sweep, and state[0] = 1
+// when it is <= tol.  copy_unless_done copies n floats unless state[0].
+cudaError_t diff_check(const float* H, const float* Href, int rows, int K, int ld, double* d_part, float tol,
+                       int sweep, double* trace, int* state, cudaStream_t s);
+cudaError_t copy_unless_done(float* dst, const float* src, int64_t n, const int* state, cudaStream_t s);
+// The check of diff_check from nblk (sum, sum) partial pairs already formed.
+cudaError_t sweep_check(const double* d_part, int nblk, float tol, int sweep, double* trace, int* state,
+                        cudaStream_t s);
+// One sweep of a fixed-W H loop (nmf_warm_h): the H update of X in place,
+// skipped once state[0] is set, with the change against Href (or, Href null,
+// against the values it replaces) summed in the update's own write-back into
+// part (h_sweep_partials(N) doubles), then the check of diff_check.  Hprev
+// (N x Kp) is scratch for the row-per-warp form (Kp <= 32) without Href.
+size_t h_sweep_partials(int N);
+cudaError_t h_update_sweep(float* X, const float* B, const float* G, int N, int K, int Kp, float eps, int* status,
+                           cudaStream_t s, const float* Href, float* Hprev, double* part, float tol, int sweep,
+                           double* trace, int* state);
 // Network forward of `rows` inputs x (row stride ldx) into y (row stride ldy).
 cudaError_t mlp_forward_dev(nmf_mlp* n, const float* x, int64_t ldx, int rows, float* y, int64_t ldy,
                             cudaStream_t s);

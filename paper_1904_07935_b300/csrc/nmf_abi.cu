@@ -1194,11 +1194,14 @@ nmf_status nmf_warm_h(nmf_ctx* c, nmf_mlp* mlp, const nmf_problem* nd, float tol
   float* d_vaT = nullptr;
   float *Rn = nullptr, *Hn = nullptr, *Hp = nullptr, *Hr = nullptr, *tmp = nullptr;
   double* part = nullptr;
+  double* d_trace = nullptr;
+  int* d_state = nullptr;
   SpmmPlan plan;
   auto cleanup = [&](nmf_status r) {
     cudaStreamSynchronize(s);
     spmm_plan_free(plan);
-    for (void* q : {(void*)d_ciT, (void*)d_vaT, (void*)Rn, (void*)Hn, (void*)Hp, (void*)Hr, (void*)tmp, (void*)part})
+    for (void* q : {(void*)d_ciT, (void*)d_vaT, (void*)Rn, (void*)Hn, (void*)Hp, (void*)Hr, (void*)tmp, (void*)part,
+                    (void*)d_trace, (void*)d_state})
       if (q) cudaFree(q);
     return r;
   };
@@ -1221,15 +1224,15 @@ nmf_status nmf_warm_h(nmf_ctx* c, nmf_mlp* mlp, const nmf_problem* nd, float tol
   WK(cudaMalloc(&Rn, sizeof(float) * nk));
   WK(cudaMalloc(&Hn, sizeof(float) * nk));
   WK(cudaMalloc(&tmp, sizeof(float) * std::max(nk, (size_t)K * N)));
-  WK(cudaMalloc(&part, sizeof(double) * diff_norm_partials()));
+  WK(cudaMalloc(&part, sizeof(double) * std::max(diff_norm_partials(), h_sweep_partials(N))));
   WK(cudaMemsetAsync(Hn, 0, sizeof(float) * nk, s));
   if (H_ref) {
     WK(cudaMalloc(&Hr, sizeof(float) * nk));
     WK(cudaMemcpyAsync(tmp, H_ref, sizeof(float) * (size_t)K * N, cudaMemcpyDefault, s));
     WK(cudaMemsetAsync(Hr, 0, sizeof(float) * nk, s));
     WK(transpose_f32(tmp, K, N, N, Hr, Kp, s));
-  } else {
-    WK(cudaMalloc(&Hp, sizeof(float) * nk));
+  } else if ((Kp + 31) / 32 == 1) {
+    WK(cudaMalloc(&Hp, sizeof(float) * nk));              // the previous sweep's H (row-per-warp form)
   }
   // S = W^T W of the fixed W; R = A_new^T W.
   if (!c->s_valid) {
@@ -1244,17 +1247,26 @@ nmf_status nmf_warm_h(nmf_ctx* c, nmf_mlp* mlp, const nmf_problem* nd, float tol
   } else {
     WK(fill_uniform_splitmix_t(Hn, N, K, Kp, nd->seed ^ 0x4848484848484848ull, s));
   }
+  // Sweeps enqueued kSweepChunk at a time; each sweep's check runs on the
+  // device (diff_check), and once it has met tol the later sweeps of the
+  // chunk leave H as it is, so the host reads the state back once per chunk.
+  constexpr int kSweepChunk = 32;
+  WK(cudaMalloc(&d_state, sizeof(int) * 2));
+  WK(cudaMalloc(&d_trace, sizeof(double) * std::max(1, max_sweeps)));
+  WK(cudaMemsetAsync(d_state, 0, sizeof(int) * 2, s));
   int done = 0;
-  for (int sw = 1; sw <= max_sweeps; ++sw) {
-    if (!H_ref) WK(cudaMemcpyAsync(Hp, Hn, sizeof(float) * nk, cudaMemcpyDeviceToDevice, s));
-    WK(h_update_run(Hn, Rn, c->S, N, K, Kp, c->eps, c->d_status, s));
-    double o[2] = {0.0, 0.0};
-    WK(diff_norm(Hn, H_ref ? Hr : Hp, N, K, Kp, part, o, s));
-    const double val = o[1] > 0.0 ? std::sqrt(o[0] / o[1]) : std::sqrt(o[0]);
-    if (trace) trace[sw - 1] = val;
-    done = sw;
-    if (val <= (double)tol) break;
+  for (int sw0 = 1; sw0 <= max_sweeps; sw0 += kSweepChunk) {
+    const int sw1 = std::min(max_sweeps, sw0 + kSweepChunk - 1);
+    for (int sw = sw0; sw <= sw1; ++sw)
+      WK(h_update_sweep(Hn, Rn, c->S, N, K, Kp, c->eps, c->d_status, s, H_ref ? Hr : nullptr, Hp, part, tol, sw,
+                        d_trace, d_state));
+    int st[2] = {0, 0};
+    WK(cudaMemcpyAsync(st, d_state, sizeof(st), cudaMemcpyDeviceToHost, s));
+    WK(cudaStreamSynchronize(s));
+    done = st[1];
+    if (st[0]) break;
   }
+  if (trace && done > 0) WK(cudaMemcpyAsync(trace, d_trace, sizeof(double) * done, cudaMemcpyDeviceToHost, s));
   WK(transpose_f32(Hn, N, K, Kp, tmp, N, s));
   WK(cudaMemcpyAsync(H_out, tmp, sizeof(float) * (size_t)K * N, cudaMemcpyDefault, s));
   WK(cudaStreamSynchronize(s));

@@ -109,20 +109,69 @@ __global__ void adam_kernel(float* __restrict__ p, const float* __restrict__ g, 
 }
 
 // Sum of (H - Href)^2 and of Href^2 (or of H^2 when Href is null) over rows x
-// K of two row-stride-ld buffers: FP64 per thread, fixed-order tree per
-// block, one pair of partials per block.
+// K of two row-stride-ld buffers (ld a multiple of 4): a warp per row at a
+// time, 16-byte loads, each lane's squares summed in FP32 (a difference of
+// two nearby FP32 values is exact, its square within one rounding; FP64
+// arithmetic runs at a small fraction of the FP32 rate on this GPU), then
+// FP64 across lanes and warps in a fixed order, one pair of partials per
+// block.
 __global__ void diff_norm_kernel(const float* __restrict__ H, const float* __restrict__ Href, int rows, int K,
-                                 int ld, double* __restrict__ part) {
+                                 int ld, double* __restrict__ part, const int* skip) {
+  if (skip && *skip) return;
+  __shared__ double sa[8], sb[8];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int K4 = (K + 3) / 4;
+  float a = 0.f, b = 0.f;
+  for (int r = blockIdx.x * 8 + warp; r < rows; r += gridDim.x * 8) {
+    const float4* hr = reinterpret_cast<const float4*>(H + (int64_t)r * ld);
+    const float4* qr = Href ? reinterpret_cast<const float4*>(Href + (int64_t)r * ld) : nullptr;
+    for (int c4 = lane; c4 < K4; c4 += 32) {
+      const float4 h = hr[c4];
+      const float4 q = qr ? qr[c4] : make_float4(0.f, 0.f, 0.f, 0.f);
+      const float hv[4] = {h.x, h.y, h.z, h.w}, qv[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        if (4 * c4 + u >= K) break;
+        const float d = hv[u] - qv[u];
+        a = fmaf(d, d, a);
+        b = qr ? fmaf(qv[u], qv[u], b) : fmaf(hv[u], hv[u], b);
+      }
+    }
+  }
+  double da = a, db = b;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    da += __shfl_xor_sync(0xffffffffu, da, o);
+    db += __shfl_xor_sync(0xffffffffu, db, o);
+  }
+  if (lane == 0) {
+    sa[warp] = da;
+    sb[warp] = db;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double ta = 0.0, tb = 0.0;
+    for (int w = 0; w < 8; ++w) {
+      ta += sa[w];
+      tb += sb[w];
+    }
+    part[2 * blockIdx.x] = ta;
+    part[2 * blockIdx.x + 1] = tb;
+  }
+}
+
+int grid_for(int64_t n) { return (int)std::min<int64_t>(1184, std::max<int64_t>(1, (n + 255) / 256)); }
+
+// The partials summed (256 threads, each a strided subset in order, then a
+// fixed tree), the relative change recorded, the loop marked done at tol.
+__global__ void diff_check_kernel(const double* __restrict__ part, int nblk, float tol, int sweep,
+                                  double* __restrict__ trace, int* __restrict__ state) {
+  if (state[0]) return;
   __shared__ double sa[256], sb[256];
-  const int64_t total = (int64_t)rows * K;
   double a = 0.0, b = 0.0;
-  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t r = e / K;
-    const int c = (int)(e - r * K);
-    const double h = H[r * ld + c];
-    const double q = Href ? (double)Href[r * ld + c] : 0.0;
-    a += (h - q) * (h - q);
-    b += Href ? q * q : h * h;
+  for (int i = threadIdx.x; i < nblk; i += 256) {
+    a += part[2 * i];
+    b += part[2 * i + 1];
   }
   sa[threadIdx.x] = a;
   sb[threadIdx.x] = b;
@@ -134,13 +183,21 @@ __global__ void diff_norm_kernel(const float* __restrict__ H, const float* __res
     }
     __syncthreads();
   }
-  if (threadIdx.x == 0) {
-    part[2 * blockIdx.x] = sa[0];
-    part[2 * blockIdx.x + 1] = sb[0];
-  }
+  if (threadIdx.x != 0) return;
+  a = sa[0];
+  b = sb[0];
+  const double val = b > 0.0 ? sqrt(a / b) : sqrt(a);
+  trace[sweep - 1] = val;
+  state[1] = sweep;
+  if (val <= (double)tol) state[0] = 1;
 }
 
-int grid_for(int64_t n) { return (int)std::min<int64_t>(1184, std::max<int64_t>(1, (n + 255) / 256)); }
+__global__ void copy_unless_done_kernel(float4* __restrict__ dst, const float4* __restrict__ src, int64_t n4,
+                                        const int* __restrict__ state) {
+  if (state[0]) return;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n4; e += (int64_t)gridDim.x * blockDim.x)
+    dst[e] = src[e];
+}
 
 __global__ void scale_shift_kernel(float* __restrict__ x, int64_t n, float a, float b) {
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
@@ -159,7 +216,7 @@ constexpr int kDiffBlocks = 296;
 
 cudaError_t diff_norm(const float* H, const float* Href, int rows, int K, int ld, double* d_part, double* h_out,
                       cudaStream_t s) {
-  diff_norm_kernel<<<kDiffBlocks, 256, 0, s>>>(H, Href, rows, K, ld, d_part);
+  diff_norm_kernel<<<kDiffBlocks, 256, 0, s>>>(H, Href, rows, K, ld, d_part, nullptr);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   double host[2 * kDiffBlocks];
@@ -176,6 +233,27 @@ cudaError_t diff_norm(const float* H, const float* Href, int rows, int K, int ld
 }
 
 size_t diff_norm_partials() { return 2 * kDiffBlocks; }
+
+cudaError_t diff_check(const float* H, const float* Href, int rows, int K, int ld, double* d_part, float tol,
+                       int sweep, double* trace, int* state, cudaStream_t s) {
+  diff_norm_kernel<<<kDiffBlocks, 256, 0, s>>>(H, Href, rows, K, ld, d_part, state);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  return sweep_check(d_part, kDiffBlocks, tol, sweep, trace, state, s);
+}
+
+cudaError_t sweep_check(const double* d_part, int nblk, float tol, int sweep, double* trace, int* state,
+                        cudaStream_t s) {
+  diff_check_kernel<<<1, 256, 0, s>>>(d_part, nblk, tol, sweep, trace, state);
+  return cudaGetLastError();
+}
+
+cudaError_t copy_unless_done(float* dst, const float* src, int64_t n, const int* state, cudaStream_t s) {
+  if (n % 4) return cudaErrorInvalidValue;
+  copy_unless_done_kernel<<<grid_for(n / 4), 256, 0, s>>>(reinterpret_cast<float4*>(dst),
+                                                          reinterpret_cast<const float4*>(src), n / 4, state);
+  return cudaGetLastError();
+}
 
 }  // namespace plnmf
 

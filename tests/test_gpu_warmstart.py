@@ -209,3 +209,41 @@ def test_warm_h_rejects_mismatches(nmf, fixed):
     m = nmf.Mlp(K + 8, HID)
     with pytest.raises(nmf.NmfError):
         nmf.warm_h(ctx, _docs(20, 1752), mlp=m, max_sweeps=1)
+
+
+@pytest.mark.parametrize("Kw", [48, 32])
+def test_sweep_checks_on_the_device(nmf, Kw):
+    """The stopping values formed on the device (in the H update's write-back
+    for K > 32, by a pass of their own for the row-per-warp form) equal the
+    relative changes of the returned iterates, and a loop that meets tol in
+    its second chunk of 32 sweeps returns exactly the H of that sweep (the
+    later sweeps of the chunk leave it unchanged)."""
+    sp = synth.sparse_termdoc(V, D, 1731, mean_terms=30)
+    ctx = nmf.from_sparse(sp, Kw, seed=1732)
+    ctx.iterate(10)
+    docs = _docs(600, 1733)
+    Hs = [nmf.warm_h(ctx, docs, tol=0.0, max_sweeps=s, seed=79)["H"].astype(np.float64) for s in (1, 2, 3)]
+    out = nmf.warm_h(ctx, docs, tol=0.0, max_sweeps=3, seed=79)
+    assert np.array_equal(out["H"], Hs[2].astype(np.float32))
+    for s in (1, 2):
+        want = np.linalg.norm(Hs[s] - Hs[s - 1]) / np.linalg.norm(Hs[s - 1])
+        assert abs(out["trace"][s] - want) <= 1e-5 * want
+    ref = Hs[2].astype(np.float32)
+    out_r = nmf.warm_h(ctx, docs, tol=0.0, max_sweeps=2, H_ref=ref, seed=79)
+    for s in (0, 1):
+        want = np.linalg.norm(Hs[s] - Hs[2]) / np.linalg.norm(Hs[2])
+        assert abs(out_r["trace"][s] - want) <= 1e-5 * want
+    # tol = the smallest change of 60 sweeps, met in the second chunk or
+    # later: the loop stops at the first sweep whose change is <= tol
+    long = nmf.warm_h(ctx, docs, tol=0.0, max_sweeps=60, seed=79)
+    tr = long["trace"]
+    t32 = np.float32(tr[32:].min())
+    if float(t32) < tr[32:].min():
+        t32 = np.nextafter(t32, np.float32(np.inf))       # tol is passed as a float
+    tol = float(t32)
+    assert np.any(tr <= tol)
+    first = int(np.argmax(tr <= tol)) + 1
+    stop = nmf.warm_h(ctx, docs, tol=tol, max_sweeps=60, seed=79)
+    assert stop["sweeps"] == first and stop["trace"][-1] <= tol
+    again = nmf.warm_h(ctx, docs, tol=0.0, max_sweeps=first, seed=79)
+    assert np.array_equal(stop["H"], again["H"])
