@@ -449,8 +449,9 @@ def run_gpu(args):
                     "iteration_frac_of_hbm": round(it_bytes / (ms * 1e-3) / 1e9 / peak, 5),
                     "step_bytes_sum": int(sum(ab.values()))}
         if dom == "update_W":
-            roofline["traffic_source"] = ("none: the single-launch W update is timed with CUDA events only and "
-                                          "not run under ncu (its earlier cooperative form faulted under a profiler)")
+            roofline["traffic_source"] = ("cuda events only: the W update (chain cluster grid + worker grid) is not "
+                                          "run under ncu by this project (an earlier single-launch form faulted "
+                                          "under a profiler)")
 
     # Latency floor of the W update (K sequential cluster-wide column norms):
     # the same update on a 512 x 512 problem at the same K, where the rows'
