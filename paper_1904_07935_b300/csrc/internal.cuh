@@ -266,6 +266,11 @@ size_t w_sync_ints(int K);
 // d_sync[w_sync_sdone_offset(K)] (nb x ceil(K / 16) when all are done).
 // Yc: w_chain_base_floats() floats of scratch (two slots of tile bases in
 // the chain's register order, then tile 0's early-base compensation).
+// after_chain (optional) is recorded right after the chain grid's launch:
+// work that waits for it sees the whole new factor (every store of the chain
+// precedes its grid's end) while the worker grid may still be forming S's
+// last block columns.  (Within a stream capture the record adds no node, so
+// the worker grid stays the chain grid's programmatic dependent.)
 size_t w_chain_base_floats();
 // Tile 0's early base and its compensation in the chain's order (for
 // w_prep_run) within Yc for this configuration.
@@ -273,7 +278,7 @@ ChainOrder w_chain_order(float* Yc, int N, const WPersistConfig& cfg);
 cudaError_t w_persistent_run(float* X, const float* P, const float* Q, float* Yc, int N, int K, int Kp,
                              float eps, int* d_sync, int* d_status, const WPersistConfig& cfg, cudaStream_t s,
                              const float* pre0 = nullptr, unsigned long long wait_ns = 0, int extra_arrivals = 0,
-                             float* spart = nullptr);
+                             float* spart = nullptr, cudaEvent_t after_chain = nullptr);
 // Row blocks of the single-launch W update: nb blocks of per rows (the last
 // shorter), one per worker CTA.
 void w_persistent_blocks(int N, const WPersistConfig& cfg, int* nb, int* per);

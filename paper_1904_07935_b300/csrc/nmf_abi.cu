@@ -77,7 +77,7 @@ struct nmf_ctx {
   double normA2 = 0.0;
   bool s_valid = false;       // S == W^T W for the current W
   bool r_valid = false;       // R == A^T W for the current W
-  cudaEvent_t evx[5] = {};    // fork / join events of the overlapped steps
+  cudaEvent_t evx[6] = {};    // fork / join events of the overlapped steps; [5]: the W chain grid done
   long long iters_run = 0;
   int launches_per_iter = 0;
   int launches_alg1 = 0, launches_mu = 0;   // per iteration of the comparator graphs
@@ -232,7 +232,7 @@ cudaError_t enq_gram_after_w(nmf_ctx* c, cudaStream_t s, bool shared_op) {
 //     current rows (new columns left of the tile, old ones right of it), then
 //     the cluster kernel finishes the tile's columns with their norms.
 cudaError_t enq_update(nmf_ctx* c, float* X, const float* G, const float* B, int N, bool is_w, bool pre0 = false,
-                       bool with_s = false) {
+                       bool with_s = false, cudaEvent_t after_chain = nullptr) {
   const int K = c->K, Kp = c->Kp;
   if (!is_w) {
     c->launch_count += 1;
@@ -243,7 +243,7 @@ cudaError_t enq_update(nmf_ctx* c, float* X, const float* G, const float* B, int
     c->launch_count += 1;
     return w_persistent_run(X, B, G, c->Yc, N, K, Kp, c->eps, c->d_sync, c->d_status, c->wp, c->stream,
                             pre0 ? w_chain_order(c->Yc, N, c->wp).comp : nullptr, c->wait_ns, c->extra_arrivals,
-                            with_s && c->ws_gram ? c->gramW.d_part : nullptr);
+                            with_s && c->ws_gram ? c->gramW.d_part : nullptr, after_chain);
   }
   // W: tile tau's base without tile tau-1 ("main") runs on the side stream
   // while the chain of tile tau-1 runs; the chain of tile tau adds tile
@@ -341,20 +341,26 @@ cudaError_t enq_iteration(nmf_ctx* c, const IoHooks* io = nullptr) {
   if ((e = cudaEventRecord(c->evx[1], b)) != cudaSuccess) return e;
   if ((e = enq_product_P(c, shared_op)) != cudaSuccess) return e;
   if ((e = cudaStreamWaitEvent(m, c->evx[1], 0)) != cudaSuccess) return e;
-  if ((e = enq_update(c, c->W, c->Q, c->P, c->V, true, pre0, true)) != cudaSuccess) return e;
+  // The steps that read only the new W (R, <W, P>, the copy-out) start when
+  // the W update's chain grid is done, beside the workers' last block
+  // columns of S (the grid that follows it on this stream).
+  const bool early = c->w_persistent && !shared_op;
+  if ((e = enq_update(c, c->W, c->Q, c->P, c->V, true, pre0, true, early ? c->evx[5] : nullptr)) != cudaSuccess)
+    return e;
   if (shared_op && (e = bf16_operand(c, true, m)) != cudaSuccess) return e;
   if ((e = cudaEventRecord(c->evx[2], m)) != cudaSuccess) return e;
+  const cudaEvent_t w_ready = early ? c->evx[5] : c->evx[2];
   if (!io) {
-    if ((e = cudaStreamWaitEvent(b, c->evx[2], 0)) != cudaSuccess) return e;
+    if ((e = cudaStreamWaitEvent(b, w_ready, 0)) != cudaSuccess) return e;
     if ((e = enq_product_R(c, b, shared_op)) != cudaSuccess) return e;
     if ((e = cudaEventRecord(c->evx[3], b)) != cudaSuccess) return e;
   } else if (io->W_out) {
-    if ((e = cudaStreamWaitEvent(c->side3, c->evx[2], 0)) != cudaSuccess) return e;
+    if ((e = cudaStreamWaitEvent(c->side3, w_ready, 0)) != cudaSuccess) return e;
     if ((e = cudaMemcpy2DAsync(io->W_out, sizeof(float) * c->K, c->W, sizeof(float) * c->Kp, sizeof(float) * c->K,
                                c->V, cudaMemcpyDefault, c->side3)) != cudaSuccess)
       return e;
   }
-  if ((e = cudaStreamWaitEvent(c->side2, c->evx[2], 0)) != cudaSuccess) return e;
+  if ((e = cudaStreamWaitEvent(c->side2, w_ready, 0)) != cudaSuccess) return e;
   c->launch_count += 3;
   if ((e = objective_wp(c->W, c->P, c->V, c->Kp, c->obj_partial, c->n_obj_partial, c->side2)) != cudaSuccess)
     return e;

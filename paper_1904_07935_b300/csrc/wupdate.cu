@@ -1410,7 +1410,8 @@ ChainOrder w_chain_order(float* Yc, int N, const WPersistConfig& cfg) {
 
 cudaError_t w_persistent_run(float* X, const float* P, const float* Q, float* Yc, int N, int K, int Kp,
                              float eps, int* d_sync, int* d_status, const WPersistConfig& cfg, cudaStream_t s,
-                             const float* pre0, unsigned long long wait_ns, int extra_arrivals, float* spart) {
+                             const float* pre0, unsigned long long wait_ns, int extra_arrivals, float* spart,
+                             cudaEvent_t after_chain) {
   if (N <= 0 || K <= 0) return cudaSuccess;
   if (!Yc || cfg.rpt < 1 || cfg.rpt > 4 || cfg.cluster > WMAXCL || (size_t)cfg.cluster * cfg.rpt * WNR < (size_t)N)
     return cudaErrorInvalidValue;
@@ -1433,6 +1434,7 @@ cudaError_t w_persistent_run(float* X, const float* P, const float* Q, float* Yc
     default: return cudaErrorInvalidValue;
   }
   if (e != cudaSuccess) return e;
+  if (after_chain && (e = cudaEventRecord(after_chain, s)) != cudaSuccess) return e;
   if (cfg.tc) return launch_workers_t<1, true>(p, map, cfg.n_workers, cfg.worker_smem, s);
   return cfg.worker_wr == 2 ? launch_workers_t<2, false>(p, map, cfg.n_workers, cfg.worker_smem, s)
                             : launch_workers_t<1, false>(p, map, cfg.n_workers, cfg.worker_smem, s);
