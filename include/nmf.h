@@ -254,17 +254,18 @@ nmf_status nmf_profile(nmf_ctx* c, int32_t n_iters, float* step_ms);
 nmf_status nmf_query(nmf_ctx* c, int32_t* tile_T, int32_t* chain_ctas, int32_t* launches_per_iter);
 
 /* How the context runs the W side of an iteration (any output may be NULL):
- *   w_single_launch  1: the whole W update is one launch (a column-chain
- *                    cluster and base-forming worker CTAs), 0: per-tile
- *                    launches.
- *   s_in_w_update    1: within nmf_iterate / nmf_profile the worker CTAs of
- *                    that launch also form the row-chunk partials of
+ *   w_single_launch  1: the whole W update is one pair of launches (a
+ *                    column-chain cluster and, as its programmatic
+ *                    dependent, a grid of base-forming worker CTAs), 0:
+ *                    per-tile launches.
+ *   s_in_w_update    1: within nmf_iterate / nmf_profile those worker CTAs
+ *                    also form the row-chunk partials of
  *                    S = W^T W of the new W (in the Gram kernel's order), so
  *                    the S step that follows only reduces them.
  *   s_chunks         the number of those row-chunk partials (0 if none). */
 nmf_status nmf_query_form(nmf_ctx* c, int32_t* w_single_launch, int32_t* s_in_w_update, int32_t* s_chunks);
 
-/* Limits of the W update's device-side waits (the single-launch form that
+/* Limits of the W update's device-side waits (the two-grid form that
  * replaces Alg. 3's two host synchronisations per column with hand-offs
  * between the column chain and the CTAs forming the tile bases).
  *   wait_ns          limit of every such wait in nanoseconds; 0 restores the
@@ -301,7 +302,7 @@ nmf_status nmf_gemm(int32_t M, int32_t N, int32_t K, const float* A, int64_t lda
  * nmf_batch_create: members must be distinct contexts on distinct streams,
  *   and `stream` (the batch's launch stream; NULL = a new one owned by the
  *   batch) must differ from all of them (NMF_EINVAL otherwise, and for
- *   n < 1).  Members switch to the per-tile W launches (the single-launch W
+ *   n < 1).  Members switch to the per-tile W launches (the two-grid W
  *   update holds every SM); a member's own single-problem graph is
  *   re-captured on its next nmf_iterate.  autotune != 0: for each member,
  *   timed with CUDA events from the same start: (1) sparse A: the SpMM

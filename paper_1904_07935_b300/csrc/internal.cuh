@@ -279,7 +279,7 @@ cudaError_t w_persistent_run(float* X, const float* P, const float* Q, float* Yc
                              float eps, int* d_sync, int* d_status, const WPersistConfig& cfg, cudaStream_t s,
                              const float* pre0 = nullptr, unsigned long long wait_ns = 0, int extra_arrivals = 0,
                              float* spart = nullptr, cudaEvent_t after_chain = nullptr);
-// Row blocks of the single-launch W update: nb blocks of per rows (the last
+// Row blocks of the two-grid W update: nb blocks of per rows (the last
 // shorter), one per worker CTA.
 void w_persistent_blocks(int N, const WPersistConfig& cfg, int* nb, int* per);
 size_t w_sync_sdone_offset(int K);

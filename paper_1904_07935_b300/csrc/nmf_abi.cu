@@ -37,9 +37,9 @@ struct nmf_ctx {
   bool own_stream = false;
   cudaStream_t side = nullptr;          // second stream for the W tile bases
   cudaStream_t side2 = nullptr;         // third stream: <W, P> of the objective beside S and R
-  bool w_persistent = false;            // whole W update as one launch (chain cluster + workers)
+  bool w_persistent = false;            // whole W update as the chain cluster grid + the worker grid
   WPersistConfig wp;
-  // The single-launch W update's workers also form the chunk partials of
+  // The two-grid W update's workers also form the chunk partials of
   // S = W^T W of the new W (gramW chunked by the workers' row blocks); the
   // Gram kernel after it only reduces them, or forms any the workers left.
   bool ws_gram = false;

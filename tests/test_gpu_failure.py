@@ -1,6 +1,6 @@
 """Failure path of the W update's device-side waits, without a GPU fault.
 
-The single-launch W update replaces the paper's two host synchronisations per
+The two-grid W update replaces the paper's two host synchronisations per
 column (Alg. 3) with hand-offs through global memory between the column chain
 and the CTAs that form the tile bases (Alg. 2, Eqs. 4 and 6).  Every such wait
 is bounded.  Here the base-forming CTAs are told to wait for one more chain

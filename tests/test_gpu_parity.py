@@ -409,7 +409,7 @@ def test_invalid_inputs_rejected(nmf):
 
 @pytest.mark.parametrize("K", [64, 80, 160, 37])
 def test_gram_partials_of_the_w_update_match_the_gram_kernel(nmf, K):
-    """Within an iteration the single-launch W update's worker CTAs form the
+    """Within an iteration the two-grid W update's worker CTAs form the
     chunk partials of S = W^T W of the new W while the column chain runs, and
     the Gram kernel after it only reduces them.  Those partials follow the
     Gram kernel's own order for the same row chunks, so S is bit-identical to
@@ -431,7 +431,7 @@ def test_gram_partials_of_the_w_update_match_the_gram_kernel(nmf, K):
 
 @pytest.mark.parametrize("K", [16, 37, 160])
 def test_w_update_persistent_and_multi_launch_agree_with_alg1(nmf, K):
-    """The single-launch (chain cluster + base workers) and the per-tile W
+    """The two-grid (chain cluster + base workers) and the per-tile W
     updates both match Alg. 1 on a ragged K."""
     V = 3000 if K < 100 else 9000
     prob = synth.planted_dense(V, 400, 8, 101 + K)
