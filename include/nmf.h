@@ -283,6 +283,23 @@ nmf_status nmf_query_form(nmf_ctx* c, int32_t* w_single_launch, int32_t* s_in_w_
  * context runs the per-tile W launches, which have no such waits. */
 nmf_status nmf_set_wait_limits(nmf_ctx* c, int64_t wait_ns, int32_t extra_arrivals);
 
+/* Launch order of the two grids of the W update (contexts that run it as
+ * the column-chain cluster grid plus the tile-base worker grid, the form that
+ * replaces Alg. 3's two host synchronisations per column, Sec. 4.2):
+ *   on = 0  default: the worker grid is a programmatic dependent of the chain
+ *           grid and forms the tile bases while the chain runs;
+ *   on = 1  the worker grid starts only after the chain grid has finished, as
+ *           a tool that serialises kernel launches runs the two.  The chain
+ *           then claims and forms every tile base itself (after waiting
+ *           50 us per tile for workers that never come); the workers find
+ *           every base formed and only form the Gram partials of the new W.
+ *           The factors and the objective are bit-identical to on = 0, the W
+ *           update is slower.  For tests of that schedule.
+ * Takes effect at the next nmf_iterate (the iteration graph is re-captured).
+ * NMF_EINVAL for on not 0 or 1; NMF_EUNSUPPORTED when the context runs the
+ * per-tile W launches. */
+nmf_status nmf_set_w_workers_after_chain(nmf_ctx* c, int32_t on);
+
 /* Dense product on the tensor cores (tcgen05), a library utility used by the
  * iteration and exposed for testing:  C (M x N) = op(A) (M x K) * B (K x N),
  * op(A) = A (row-major, lda) or A^T (A stored K x M row-major, lda) when

@@ -246,6 +246,10 @@ struct WPersistConfig {
   size_t chain_smem = 0;
   size_t worker_smem = 0;
   bool tc = false;        // the workers form the tile bases on the tensor cores
+  // The worker grid launched in plain stream order, after the chain grid has
+  // finished (as a tool that serialises launches runs the two): the chain
+  // then forms every tile base itself.  Default: a programmatic dependent.
+  bool workers_after_chain = false;
 };
 // tc: the workers form the tile bases on the tensor cores (TF32 pairs).
 bool w_persistent_config(int N, int Kp, WPersistConfig* cfg, bool tc = false);

@@ -48,6 +48,7 @@ struct nmf_ctx {
   int* d_sync = nullptr;
   unsigned long long wait_ns = 0;       // limit of the W update's device waits (0: library default)
   int extra_arrivals = 0;               // tests of the timeout path: a hand-off count that cannot be reached
+  bool w_workers_after_chain = false;   // W worker grid in plain stream order after the chain grid
   std::vector<cudaEvent_t> ev;          // fork / join events of the W update
   // A (caller-owned) and its transpose (context-owned, CSR only).
   const float* dense = nullptr;
@@ -241,7 +242,9 @@ cudaError_t enq_update(nmf_ctx* c, float* X, const float* G, const float* B, int
   }
   if (c->w_persistent) {
     c->launch_count += 1;
-    return w_persistent_run(X, B, G, c->Yc, N, K, Kp, c->eps, c->d_sync, c->d_status, c->wp, c->stream,
+    WPersistConfig wc = c->wp;
+    wc.workers_after_chain = c->w_workers_after_chain;
+    return w_persistent_run(X, B, G, c->Yc, N, K, Kp, c->eps, c->d_sync, c->d_status, wc, c->stream,
                             pre0 ? w_chain_order(c->Yc, N, c->wp).comp : nullptr, c->wait_ns, c->extra_arrivals,
                             with_s && c->ws_gram ? c->gramW.d_part : nullptr, after_chain);
   }
@@ -1597,6 +1600,14 @@ nmf_status nmf_query_form(nmf_ctx* c, int32_t* w_single_launch, int32_t* s_in_w_
   if (w_single_launch) *w_single_launch = c->w_persistent ? 1 : 0;
   if (s_in_w_update) *s_in_w_update = c->ws_gram ? 1 : 0;
   if (s_chunks) *s_chunks = c->ws_gram ? c->gramW.n_chunks : 0;
+  return NMF_OK;
+}
+
+nmf_status nmf_set_w_workers_after_chain(nmf_ctx* c, int32_t on) {
+  if (!c || (on != 0 && on != 1)) return NMF_EINVAL;
+  if (!c->w_persistent) return NMF_EUNSUPPORTED;
+  c->w_workers_after_chain = on != 0;
+  drop_graph(c);
   return NMF_OK;
 }
 

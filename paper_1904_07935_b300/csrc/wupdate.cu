@@ -1273,7 +1273,8 @@ cudaError_t launch_chain_t(const WParams& p, size_t smem, cudaStream_t s) {
 }
 
 template <int WR, bool TCW>
-cudaError_t launch_workers_t(const WParams& p, const CUtensorMap& map, int n_workers, size_t smem, cudaStream_t s) {
+cudaError_t launch_workers_t(const WParams& p, const CUtensorMap& map, int n_workers, size_t smem, cudaStream_t s,
+                             bool after_chain) {
   auto kern = w_workers_kernel<WR, TCW>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
@@ -1283,12 +1284,13 @@ cudaError_t launch_workers_t(const WParams& p, const CUtensorMap& map, int n_wor
   cfg.dynamicSmemBytes = smem;
   cfg.stream = s;
   // A programmatic dependent of the chain grid: it may begin while the
-  // chain runs (it does not wait for the chain grid's completion).
+  // chain runs (it does not wait for the chain grid's completion).  With
+  // after_chain, plain stream order instead.
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
   attr[0].val.programmaticStreamSerializationAllowed = 1;
   cfg.attrs = attr;
-  cfg.numAttrs = 1;
+  cfg.numAttrs = after_chain ? 0 : 1;
   return cudaLaunchKernelEx(&cfg, kern, p, map);
 }
 
@@ -1435,9 +1437,10 @@ cudaError_t w_persistent_run(float* X, const float* P, const float* Q, float* Yc
   }
   if (e != cudaSuccess) return e;
   if (after_chain && (e = cudaEventRecord(after_chain, s)) != cudaSuccess) return e;
-  if (cfg.tc) return launch_workers_t<1, true>(p, map, cfg.n_workers, cfg.worker_smem, s);
-  return cfg.worker_wr == 2 ? launch_workers_t<2, false>(p, map, cfg.n_workers, cfg.worker_smem, s)
-                            : launch_workers_t<1, false>(p, map, cfg.n_workers, cfg.worker_smem, s);
+  const bool ac = cfg.workers_after_chain;
+  if (cfg.tc) return launch_workers_t<1, true>(p, map, cfg.n_workers, cfg.worker_smem, s, ac);
+  return cfg.worker_wr == 2 ? launch_workers_t<2, false>(p, map, cfg.n_workers, cfg.worker_smem, s, ac)
+                            : launch_workers_t<1, false>(p, map, cfg.n_workers, cfg.worker_smem, s, ac);
 }
 
 }  // namespace plnmf

@@ -65,6 +65,7 @@ _SIGS = {
     "nmf_set_buffer": ([_vp, _i32, _vp, _i64], _i32),
     "nmf_query": ([_vp, ctypes.POINTER(_i32), ctypes.POINTER(_i32), ctypes.POINTER(_i32)], _i32),
     "nmf_set_wait_limits": ([_vp, _i64, _i32], _i32),
+    "nmf_set_w_workers_after_chain": ([_vp, _i32], _i32),
     "nmf_query_form": ([_vp, ctypes.POINTER(_i32), ctypes.POINTER(_i32), ctypes.POINTER(_i32)], _i32),
     "nmf_profile": ([_vp, _i32, _vp], _i32),
     "nmf_iterate_alg1": ([_vp, _i32, _vp], _i32),
@@ -279,6 +280,11 @@ class Nmf:
         tests of the failure path, extra chain arrivals the base-forming CTAs
         wait for (include/nmf.h, nmf_set_wait_limits)."""
         check(lib.nmf_set_wait_limits(self.h, int(wait_ns), int(extra_arrivals)), "nmf_set_wait_limits")
+
+    def set_w_workers_after_chain(self, on=True):
+        """Run the W update's worker grid after its chain grid instead of
+        beside it (include/nmf.h, nmf_set_w_workers_after_chain)."""
+        check(lib.nmf_set_w_workers_after_chain(self.h, 1 if on else 0), "nmf_set_w_workers_after_chain")
 
 
 def gemm(A, B, C, *, transA=False, prec=PREC_FP32, stream=None):

@@ -8,6 +8,11 @@ arrival than will ever come, with a 2 ms limit: their waits run out, the
 status word reports the timeout once (NMF_ETIMEOUT), the chain computes the
 bases those CTAs left with the same arithmetic, and the context stays usable.
 Nothing traps, faults or hangs: the waits are short and bounded.
+
+The other schedule the protocol must survive is the one a launch-serialising
+tool imposes: the worker grid started only after the chain grid has finished.
+The chain then forms every tile base itself, and the update must come out
+bit-identical.
 """
 
 import numpy as np
@@ -86,4 +91,43 @@ def test_wait_limits_rejects_bad_arguments(nmf):
     multi = nmf.from_sparse(sp, 32, flags=nmf.FLAG_MULTI_LAUNCH_W)
     with pytest.raises(nmf.NmfError) as e:
         multi.set_wait_limits(wait_ns=1000)
+    assert e.value.status == nmf.NMF_EUNSUPPORTED
+
+
+@pytest.mark.parametrize("V,D,K,terms", [(1500, 900, 24, 30), (6000, 2500, 160, 60), (26214, 11314, 160, 100)])
+def test_workers_after_chain_give_the_same_update(nmf, V, D, K, terms):
+    """The worker grid started only after the chain grid has finished, as a
+    tool that serialises launches runs the two: every worker is absent while
+    the chain runs, so after each tile's hand-off window the chain claims and
+    forms every tile base itself, with the workers' arithmetic in their
+    order; the workers then find every base formed and only form the Gram
+    partials of the new W.  Factors and objective bit-identical, no timeout."""
+    sp = synth.sparse_termdoc(V, D, 47, mean_terms=terms)
+    W0, H0 = synth.init_factors(48, V, D, K)
+    ref = _ctx(nmf, sp, K, W0, H0)
+    ref.iterate(2)
+    f_ref, _ = ref.error()
+    Wr, Hr = ref.get_factors()
+    ctx = _ctx(nmf, sp, K, W0, H0)
+    ctx.set_w_workers_after_chain(True)
+    ctx.iterate(2)
+    f, _ = ctx.error()
+    W, H = ctx.get_factors()
+    assert np.array_equal(W, Wr) and np.array_equal(H, Hr)
+    assert f == f_ref
+    # And back: the programmatic-dependent schedule again.
+    ctx.set_w_workers_after_chain(False)
+    ref.iterate(1)
+    ctx.iterate(1)
+    ctx.error()
+    assert np.array_equal(ctx.get_factors()[0], ref.get_factors()[0])
+
+
+def test_workers_after_chain_rejects_bad_arguments(nmf):
+    sp = synth.sparse_termdoc(3000, 1200, 49, mean_terms=40)
+    ctx = nmf.from_sparse(sp, 32)
+    assert nmf.lib.nmf_set_w_workers_after_chain(ctx.h, 2) == nmf.NMF_EINVAL
+    multi = nmf.from_sparse(sp, 32, flags=nmf.FLAG_MULTI_LAUNCH_W)
+    with pytest.raises(nmf.NmfError) as e:
+        multi.set_w_workers_after_chain(True)
     assert e.value.status == nmf.NMF_EUNSUPPORTED
