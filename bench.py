@@ -319,6 +319,18 @@ def step_bounds(ab, prof, V, D, K, peak, fpeak, s_in_w=False, s_chunks=0):
     return out
 
 
+# DRAM bytes per launch of the dominant step, from one ncu capture each
+# (dram__bytes_read.sum + dram__bytes_write.sum; summaries under profiles/).
+# Only for the kernels as captured: a change to their device code voids them.
+MEASURED_TRAFFIC = {
+    ("text20ng", 160, "fp32", "tiled", "update_W"): (
+        35_475_968 + 15_616_000,
+        "ncu, one pass, profiles/w_update_dram_text20ng_k160.md: the chain cluster grid with the worker grid "
+        "held back (ncu serialises them), so the chain formed every tile base; the worker grid's read of the "
+        "new W for S's partials is the S step's"),
+}
+
+
 def alg_bytes(V, D, nnz, K):
     """Algorithmic bytes of one iteration (each operand moved once):
     SpMM: nnz*8 + (rows+1)*4 + 4*cols*K + 4*rows*K, twice; column updates:
@@ -448,10 +460,13 @@ def run_gpu(args):
                     "alg_bytes_definition": "2|A| + 16 (V + D) K, |A| = CSR bytes (nnz * 8 + (V + 1) * 4)",
                     "iteration_frac_of_hbm": round(it_bytes / (ms * 1e-3) / 1e9 / peak, 5),
                     "step_bytes_sum": int(sum(ab.values()))}
-        if dom == "update_W":
-            roofline["traffic_source"] = ("cuda events only: the W update (chain cluster grid + worker grid) is not "
-                                          "run under ncu by this project (an earlier single-launch form faulted "
-                                          "under a profiler)")
+        meas = MEASURED_TRAFFIC.get((args.workload, K, args.prec, args.algo, dom))
+        if meas and not args.w_multi_launch and not args.tc_updates:
+            roofline["traffic"] = meas[0]
+            roofline["traffic_source"] = meas[1]
+        elif dom == "update_W":
+            roofline["traffic_source"] = ("cuda events only: no ncu capture of the W update's grids for this "
+                                          "workload, K and form")
 
     # Latency floor of the W update (K sequential cluster-wide column norms):
     # the same update on a 512 x 512 problem at the same K, where the rows'
