@@ -376,6 +376,16 @@ def run_gpu(args):
         ctx = nmf.Nmf(V, D, K, row_ptr=rp, col_idx=ci, val=va,
                       W0=torch.from_numpy(W0).to(dev), H0=torch.from_numpy(H0).to(dev),
                       stream=stream, tile_T=args.tile, flags=flags, prec=prec)
+        # The sparse products' split length of long rows: the library's
+        # default, timed per product at setup (outside every timed region),
+        # or as given.
+        spmm_split = {"P": 512, "R": 512, "chosen_by": "library default"}
+        if args.spmm_seg == -1:
+            segs = ctx.tune_spmm()
+            spmm_split = {"P": segs[0], "R": segs[1], "chosen_by": "nmf_tune_spmm at setup (untimed)"}
+        elif args.spmm_seg >= 0:
+            ctx.set_spmm_split(args.spmm_seg, args.spmm_seg)
+            spmm_split = {"P": args.spmm_seg, "R": args.spmm_seg, "chosen_by": "--spmm-seg"}
     flush = torch.empty(256 * 2 ** 20 // 4, dtype=torch.float32, device=dev)   # 256 MB > L2
 
     alg1 = args.algo != "tiled"
@@ -519,6 +529,7 @@ def run_gpu(args):
                    "l2": "flushed between steps (256 MB write)", "parallelism": "replicas" if world > 1 else "single",
                    "ms_per_step_warm_l2": round(ms_warm, 5), "rel_err_final": rel,
                    "algorithm": ALGOS[args.algo],
+                   **({"spmm_split": spmm_split} if not dense else {}),
                    "update_off_tile_sums": "tensor cores (TF32 pairs)" if args.tc_updates else "SIMT FP32"},
         "e2e": {"value": round(1.0 / t_e2e, 3), "unit": "iter/s", "h2d_bytes_per_step": fac_bytes,
                 "d2h_bytes_per_step": fac_bytes + 16},
@@ -903,6 +914,9 @@ def main():
     ap.add_argument("--workload", default="text20ng", choices=sorted(WORKLOADS))
     ap.add_argument("--prec", default="fp32", choices=["fp32", "bf16"])
     ap.add_argument("--tile", type=int, default=0)
+    ap.add_argument("--spmm-seg", type=int, default=-2,
+                    help="sparse products: split length of long rows (0: no split; -1: timed at setup; "
+                         "default: the library's 512)")
     ap.add_argument("--algo", default="tiled", choices=sorted(ALGOS),
                     help="comparators of the tiled form: alg1 (the updates column by column as Alg. 1 is "
                          "written), mu (multiplicative updates)")

@@ -283,6 +283,30 @@ nmf_status nmf_query_form(nmf_ctx* c, int32_t* w_single_launch, int32_t* s_in_w_
  * context runs the per-tile W launches, which have no such waits. */
 nmf_status nmf_set_wait_limits(nmf_ctx* c, int64_t wait_ns, int32_t extra_arrivals);
 
+/* Work schedule of the two sparse products of Alg. 1, P = A H^T (over the
+ * CSR rows of A) and R = A^T W (over those of A^T), for CSR contexts (the
+ * library CSR products of Sec. 4.2).  A row with more than seg non-zeros is
+ * cut into seg-long pieces that separate warps gather; the piece that
+ * finishes last adds the pieces' partial rows in piece order, so a product
+ * is bit-reproducible for a given seg, while another seg changes the
+ * rounding of long rows' sums (the words of the Zipf head, and long
+ * documents).  Default 512 for both.
+ * nmf_set_spmm_split: seg_P and seg_R >= 16, or 0 for no split (one piece per
+ *   row).  NMF_EINVAL for other values.
+ * nmf_tune_spmm: times each product with seg in {128, 256, 512, 1024, no
+ *   split} (CUDA events on the context stream, one warm-up and three timed
+ *   runs each, the current factors) and keeps the fastest; seg_P / seg_R
+ *   (may be NULL) return the choices (0: no split).  P's buffer is
+ *   overwritten (it is recomputed by every iteration) and R is recomputed for
+ *   the current W.  The choice depends on the timings, so two contexts tuned
+ *   separately can choose differently; nmf_set_spmm_split with the returned
+ *   values reproduces a tuned context's schedule exactly.
+ * Both: synchronous; NMF_EUNSUPPORTED for dense A; take effect at the next
+ * nmf_iterate (the iteration graph is re-captured).  Not while the context is
+ * a member of a batch (destroy the batch first). */
+nmf_status nmf_set_spmm_split(nmf_ctx* c, int32_t seg_P, int32_t seg_R);
+nmf_status nmf_tune_spmm(nmf_ctx* c, int32_t* seg_P, int32_t* seg_R);
+
 /* Launch order of the two grids of the W update (contexts that run it as
  * the column-chain cluster grid plus the tile-base worker grid, the form that
  * replaces Alg. 3's two host synchronisations per column, Sec. 4.2):

@@ -749,6 +749,63 @@ void drop_graph(nmf_ctx* c) {
   c->graph_io = nullptr;
 }
 
+// SpMM schedule of one product (which = 0: P = A H^T over the CSR of A,
+// 1: R = A^T W over the CSR of A^T): its plan rebuilt with rows longer than
+// seg non-zeros split into seg-long items (seg = kNoSplit: one item per row).
+constexpr int kNoSplit = 1 << 30;
+cudaError_t set_spmm_seg(nmf_ctx* c, int which, int seg) {
+  SpmmPlan& plan = which == 0 ? c->planA : c->planAt;
+  spmm_plan_free(plan);
+  cudaError_t e = which == 0 ? spmm_plan_build(plan, c->h_rp, c->V, c->D, c->Kp, seg)
+                             : spmm_plan_build(plan, c->h_rpT, c->D, c->V, c->Kp, seg);
+  if (e != cudaSuccess) return e;
+  (which == 0 ? c->segA : c->segAt) = seg;
+  return cudaSuccess;
+}
+
+// Times each product with seg in {128, 256, 512, 1024, no split} (CUDA
+// events on the context's stream, the current factors; one warm-up and
+// three timed runs each) and keeps the fastest.  The products' outputs are
+// overwritten (P with A H^T of the current H, R with A^T W of the current
+// W, the last one with the chosen plan).
+cudaError_t tune_spmm_segs(nmf_ctx* c) {
+  if (c->fmt != NMF_CSR_F32_I32) return cudaSuccess;
+  cudaEvent_t t0 = nullptr, t1 = nullptr;
+  cudaError_t e = cudaEventCreate(&t0);
+  if (e == cudaSuccess) e = cudaEventCreate(&t1);
+  const int segs[] = {128, 256, 512, 1024, kNoSplit};
+  for (int which = 0; which < 2 && e == cudaSuccess; ++which) {
+    const int* ci = which == 0 ? c->ci : c->ciT;
+    const float* va = which == 0 ? c->va : c->vaT;
+    const float* X = which == 0 ? c->Ht : c->W;
+    float* Y = which == 0 ? c->P : c->R;
+    int best_seg = which == 0 ? c->segA : c->segAt;
+    float best = INFINITY;
+    for (int seg : segs) {
+      if ((e = set_spmm_seg(c, which, seg)) != cudaSuccess) break;
+      const SpmmPlan& plan = which == 0 ? c->planA : c->planAt;
+      for (int rep = 0; rep < 4 && e == cudaSuccess; ++rep) {
+        if (rep == 1) e = cudaEventRecord(t0, c->stream);
+        if (e == cudaSuccess) e = spmm_run(plan, ci, va, X, Y, c->Kp, c->stream);
+      }
+      if (e == cudaSuccess) e = cudaEventRecord(t1, c->stream);
+      if (e == cudaSuccess) e = cudaEventSynchronize(t1);
+      float ms = 0.f;
+      if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, t0, t1);
+      if (e != cudaSuccess) break;
+      if (ms < best) {
+        best = ms;
+        best_seg = seg;
+      }
+    }
+    if (e == cudaSuccess) e = set_spmm_seg(c, which, best_seg);
+  }
+  if (e == cudaSuccess) e = enq_product_R(c);          // R of the current W with the chosen plan
+  if (t0) cudaEventDestroy(t0);
+  if (t1) cudaEventDestroy(t1);
+  return e;
+}
+
 // Autotuner for a batch member (Sec. 1's repeated factorisation: many small
 // problems of uneven shape, each with its own best schedule).  Three choices
 // are timed per member with CUDA events, each from the same start:
@@ -787,37 +844,7 @@ cudaError_t autotune_member(nmf_ctx* c, float* w_us_out) {
     return cudaSuccess;
   };
   // SpMM schedules (sparse A only).
-  if (c->fmt == NMF_CSR_F32_I32) {
-    const int segs[] = {128, 256, 512, 1024, 1 << 30};
-    for (int which = 0; which < 2; ++which) {
-      SpmmPlan& plan = which == 0 ? c->planA : c->planAt;
-      const std::vector<int>& rp = which == 0 ? c->h_rp : c->h_rpT;
-      const int rows = which == 0 ? c->V : c->D, cols = which == 0 ? c->D : c->V;
-      const int* ci = which == 0 ? c->ci : c->ciT;
-      const float* va = which == 0 ? c->va : c->vaT;
-      const float* X = which == 0 ? c->Ht : c->W;
-      float* Y = which == 0 ? c->P : c->R;
-      int best_seg = which == 0 ? c->segA : c->segAt;
-      float best = INFINITY;
-      for (int seg : segs) {
-        spmm_plan_free(plan);
-        if ((e = spmm_plan_build(plan, rp, rows, cols, c->Kp, seg)) != cudaSuccess) return fail(e);
-        for (int rep = 0; rep < 4; ++rep) {
-          if (rep == 1 && (e = cudaEventRecord(t0, c->stream)) != cudaSuccess) return fail(e);
-          if ((e = spmm_run(plan, ci, va, X, Y, c->Kp, c->stream)) != cudaSuccess) return fail(e);
-        }
-        float us = 0.f;
-        if ((e = elapsed_us(3, &us)) != cudaSuccess) return fail(e);
-        if (us < best) {
-          best = us;
-          best_seg = seg;
-        }
-      }
-      spmm_plan_free(plan);
-      if ((e = spmm_plan_build(plan, rp, rows, cols, c->Kp, best_seg)) != cudaSuccess) return fail(e);
-      (which == 0 ? c->segA : c->segAt) = best_seg;
-    }
-  }
+  if ((e = tune_spmm_segs(c)) != cudaSuccess) return fail(e);
   if ((e = cudaMemcpyAsync(saved, c->W, bytes, cudaMemcpyDeviceToDevice, c->stream)) != cudaSuccess) return fail(e);
   // P and Q of the current H: the W update's inputs.
   if ((e = enq_product_P(c)) != cudaSuccess) return fail(e);
@@ -1600,6 +1627,31 @@ nmf_status nmf_query_form(nmf_ctx* c, int32_t* w_single_launch, int32_t* s_in_w_
   if (w_single_launch) *w_single_launch = c->w_persistent ? 1 : 0;
   if (s_in_w_update) *s_in_w_update = c->ws_gram ? 1 : 0;
   if (s_chunks) *s_chunks = c->ws_gram ? c->gramW.n_chunks : 0;
+  return NMF_OK;
+}
+
+nmf_status nmf_set_spmm_split(nmf_ctx* c, int32_t seg_P, int32_t seg_R) {
+  if (!c || seg_P < 0 || seg_R < 0 || (seg_P > 0 && seg_P < 16) || (seg_R > 0 && seg_R < 16)) return NMF_EINVAL;
+  if (c->fmt != NMF_CSR_F32_I32) return NMF_EUNSUPPORTED;
+  CK(cudaStreamSynchronize(c->stream));
+  drop_graph(c);                       // the captured launches name the old plans' arrays
+  CK(set_spmm_seg(c, 0, seg_P ? seg_P : kNoSplit));
+  CK(set_spmm_seg(c, 1, seg_R ? seg_R : kNoSplit));
+  c->r_valid = false;                  // R of the old plan: recomputed with the new one
+  return NMF_OK;
+}
+
+nmf_status nmf_tune_spmm(nmf_ctx* c, int32_t* seg_P, int32_t* seg_R) {
+  if (!c) return NMF_EINVAL;
+  if (c->fmt != NMF_CSR_F32_I32) return NMF_EUNSUPPORTED;
+  CK(cudaStreamSynchronize(c->stream));
+  drop_graph(c);
+  c->r_valid = false;
+  CK(tune_spmm_segs(c));
+  CK(cudaStreamSynchronize(c->stream));
+  c->r_valid = true;                   // formed with the chosen plan for the current W
+  if (seg_P) *seg_P = c->segA == kNoSplit ? 0 : c->segA;
+  if (seg_R) *seg_R = c->segAt == kNoSplit ? 0 : c->segAt;
   return NMF_OK;
 }
 

@@ -66,6 +66,8 @@ _SIGS = {
     "nmf_query": ([_vp, ctypes.POINTER(_i32), ctypes.POINTER(_i32), ctypes.POINTER(_i32)], _i32),
     "nmf_set_wait_limits": ([_vp, _i64, _i32], _i32),
     "nmf_set_w_workers_after_chain": ([_vp, _i32], _i32),
+    "nmf_set_spmm_split": ([_vp, _i32, _i32], _i32),
+    "nmf_tune_spmm": ([_vp, ctypes.POINTER(_i32), ctypes.POINTER(_i32)], _i32),
     "nmf_query_form": ([_vp, ctypes.POINTER(_i32), ctypes.POINTER(_i32), ctypes.POINTER(_i32)], _i32),
     "nmf_profile": ([_vp, _i32, _vp], _i32),
     "nmf_iterate_alg1": ([_vp, _i32, _vp], _i32),
@@ -280,6 +282,18 @@ class Nmf:
         tests of the failure path, extra chain arrivals the base-forming CTAs
         wait for (include/nmf.h, nmf_set_wait_limits)."""
         check(lib.nmf_set_wait_limits(self.h, int(wait_ns), int(extra_arrivals)), "nmf_set_wait_limits")
+
+    def set_spmm_split(self, seg_P, seg_R):
+        """Split lengths of the sparse products' long rows (0: no split;
+        include/nmf.h, nmf_set_spmm_split)."""
+        check(lib.nmf_set_spmm_split(self.h, int(seg_P), int(seg_R)), "nmf_set_spmm_split")
+
+    def tune_spmm(self):
+        """Time the sparse products' split lengths and keep the fastest;
+        returns (seg_P, seg_R), 0 meaning no split (nmf_tune_spmm)."""
+        sp, sr = _i32(0), _i32(0)
+        check(lib.nmf_tune_spmm(self.h, ctypes.byref(sp), ctypes.byref(sr)), "nmf_tune_spmm")
+        return sp.value, sr.value
 
     def set_w_workers_after_chain(self, on=True):
         """Run the W update's worker grid after its chain grid instead of

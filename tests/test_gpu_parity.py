@@ -93,6 +93,60 @@ def test_sparse_products_with_long_and_empty_rows(nmf, K):
     _check_products(ctx, nmf, sp.A.to_scipy().astype(np.float64), W0, H0, 3e-6)
 
 
+@pytest.mark.parametrize("seg", [0, 16, 100, 256, 1024])
+def test_sparse_products_at_every_split_length(nmf, seg):
+    """R and P with long rows cut into pieces of `seg` non-zeros (0: no
+    split): the same products up to rounding for every schedule."""
+    sp = synth.sparse_termdoc(3000, 1400, 23, mean_terms=40)
+    assert np.diff(sp.A.row_ptr).max() > 1024
+    W0, H0 = synth.init_factors(24, 3000, 1400, 100)
+    ctx = _sparse_ctx(nmf, sp, 100, W0, H0)
+    ctx.set_spmm_split(seg, seg)
+    _check_products(ctx, nmf, sp.A.to_scipy().astype(np.float64), W0, H0, 3e-6)
+
+
+def test_tuned_split_is_reproduced_by_setting_it(nmf):
+    """nmf_tune_spmm picks lengths from its candidate set, keeps R valid
+    for the current W, and a context given the same lengths by
+    nmf_set_spmm_split iterates bit-identically; the iteration stays within
+    the one-iteration tolerance of the oracle."""
+    K = 64
+    sp = synth.sparse_termdoc(6000, 2500, 25, mean_terms=60)
+    W0, H0 = synth.init_factors(26, 6000, 2500, K)
+    tuned = _sparse_ctx(nmf, sp, K, W0, H0)
+    segP, segR = tuned.tune_spmm()
+    assert segP in (128, 256, 512, 1024, 0) and segR in (128, 256, 512, 1024, 0)
+    tuned.iterate(2)
+    fixed = _sparse_ctx(nmf, sp, K, W0, H0)
+    fixed.set_spmm_split(segP, segR)
+    fixed.iterate(2)
+    Wt, Ht = tuned.get_factors()
+    Wf, Hf = fixed.get_factors()
+    assert np.array_equal(Wt, Wf) and np.array_equal(Ht, Hf)
+    one = _sparse_ctx(nmf, sp, K, W0, H0)
+    one.set_spmm_split(segP, segR)
+    one.iterate(1)
+    Wg, Hg = one.get_factors()
+    Wr, Hr = _oracle_start(W0, H0)
+    Wr, Hr = fh.iteration(sp.A, Wr, Hr)
+    assert rel_w(Wg, Wr) < TOL_ITER and rel_h(Hg, Hr) < TOL_ITER
+
+
+def test_spmm_split_rejects_bad_arguments(nmf):
+    sp = synth.sparse_termdoc(2000, 900, 27, mean_terms=30)
+    ctx = nmf.from_sparse(sp, 16)
+    for a, b in ((-1, 512), (512, 8), (1, 1)):
+        with pytest.raises(nmf.NmfError) as e:
+            ctx.set_spmm_split(a, b)
+        assert e.value.status == nmf.NMF_EINVAL
+    prob = synth.planted_dense(100, 80, 4, 3)
+    dense = nmf.from_dense(prob.A, 8)
+    for call in (lambda: dense.set_spmm_split(512, 512), dense.tune_spmm):
+        with pytest.raises(nmf.NmfError) as e:
+            call()
+        assert e.value.status == nmf.NMF_EUNSUPPORTED
+
+
 # --- factor updates in isolation ----------------------------------------------
 
 @pytest.mark.parametrize("K,T", [(16, 16), (16, 1), (20, 3), (37, 16), (48, 8)])
