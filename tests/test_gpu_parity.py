@@ -346,6 +346,19 @@ def test_one_iteration_text_full_size_k160(nmf, text_full):
     assert rel_w(Wg, Wr) < TOL_ITER
 
 
+@pytest.mark.parametrize("K", [80, 240, 320, 400])
+def test_one_iteration_text_full_size_k_sweep(nmf, text_full, K):
+    """The other ranks of the text-like K sweep at the full size, in the
+    launch configurations the benchmark times there (rows per chain thread,
+    rows per worker lane group and SpMM lane layouts all change with K),
+    one iteration against the full FP64 oracle."""
+    W0, H0 = synth.init_factors(0xC2 + K, 26214, 11314, K)
+    ctx = _sparse_ctx(nmf, text_full, K, W0, H0)
+    Wg, Hg, Wr, Hr = _one_iteration(nmf, text_full.A, ctx, W0, H0)
+    assert rel_h(Hg, Hr) < TOL_ITER
+    assert rel_w(Wg, Wr) < TOL_ITER
+
+
 # --- objective ------------------------------------------------------------------
 
 def test_objective_after_50_iterations_dense_small(nmf):
