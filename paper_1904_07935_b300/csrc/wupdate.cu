@@ -1085,21 +1085,31 @@ __device__ void chain_role(const WParams& p, char* smem) {
         // in st).  (Unrolled by two: at 4 rows per thread the 4-way unroll
         // spilled 46 / 96 bytes, this 16 / 16, and the text-like K = 160 W
         // update went 298 -> 285 us.)
+        // Two columns per instruction (packed FP32 multiply-add, each half
+        // rounded as a scalar fmaf).
         const float(*Gp)[WT] = Gn[(tau - 1) & 1];
 #pragma unroll 2
         for (int j = 0; j < WT; ++j) {
-          float xv[RPT];
+          float2 nx[RPT];
 #pragma unroll
-          for (int i = 0; i < RPT; ++i) xv[i] = st[sidx(i, j, tr)];
+          for (int i = 0; i < RPT; ++i) {
+            const float x = -st[sidx(i, j, tr)];
+            nx[i] = make_float2(x, x);
+          }
 #pragma unroll
           for (int cq = 0; cq < WT / 4; ++cq) {
             const float4 g = *reinterpret_cast<const float4*>(&Gp[j][4 * cq]);
+            const float2 g01 = make_float2(g.x, g.y), g23 = make_float2(g.z, g.w);
 #pragma unroll
             for (int i = 0; i < RPT; ++i) {
-              y[i][4 * cq] = fmaf(-g.x, xv[i], y[i][4 * cq]);
-              y[i][4 * cq + 1] = fmaf(-g.y, xv[i], y[i][4 * cq + 1]);
-              y[i][4 * cq + 2] = fmaf(-g.z, xv[i], y[i][4 * cq + 2]);
-              y[i][4 * cq + 3] = fmaf(-g.w, xv[i], y[i][4 * cq + 3]);
+              float2 a = make_float2(y[i][4 * cq], y[i][4 * cq + 1]);
+              float2 b = make_float2(y[i][4 * cq + 2], y[i][4 * cq + 3]);
+              a = __ffma2_rn(g01, nx[i], a);
+              b = __ffma2_rn(g23, nx[i], b);
+              y[i][4 * cq] = a.x;
+              y[i][4 * cq + 1] = a.y;
+              y[i][4 * cq + 2] = b.x;
+              y[i][4 * cq + 3] = b.y;
             }
           }
         }
