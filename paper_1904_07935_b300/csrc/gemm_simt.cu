@@ -219,11 +219,13 @@ __global__ void __launch_bounds__(512) gram_tri_kernel(const float* __restrict__
   }
   const int tx = ty + rem;
   const int r0 = blockIdx.x * chunk, r1 = min(N, r0 + chunk);
-  float acc[8][8];
+  // acc[i][jj] holds columns 2 jj and 2 jj + 1 of tile row i (packed FP32
+  // multiply-adds, each half rounded as a scalar fmaf).
+  float2 acc[8][4];
 #pragma unroll
   for (int i = 0; i < 8; ++i)
 #pragma unroll
-    for (int j = 0; j < 8; ++j) acc[i][j] = 0.f;
+    for (int j = 0; j < 4; ++j) acc[i][j] = make_float2(0.f, 0.f);
   // Staging by 16-byte cp.async copies (L2 only; rows past the chunk and
   // columns past Kp zero-filled by the copy), the next block in flight while
   // the current one is multiplied.
@@ -262,11 +264,14 @@ __global__ void __launch_bounds__(512) gram_tri_kernel(const float* __restrict__
       const float4 b0 = *reinterpret_cast<const float4*>(row + 4 * tx);
       const float4 b1 = *reinterpret_cast<const float4*>(row + Kh + 4 * tx);
       const float av[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
-      const float bv[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+      const float2 bv[4] = {make_float2(b0.x, b0.y), make_float2(b0.z, b0.w), make_float2(b1.x, b1.y),
+                            make_float2(b1.z, b1.w)};
 #pragma unroll
-      for (int i = 0; i < 8; ++i)
+      for (int i = 0; i < 8; ++i) {
+        const float2 a = make_float2(av[i], av[i]);
 #pragma unroll
-        for (int j = 0; j < 8; ++j) acc[i][j] = fmaf(av[i], bv[j], acc[i][j]);
+        for (int j = 0; j < 4; ++j) acc[i][j] = __ffma2_rn(a, bv[j], acc[i][j]);
+      }
     }
     __syncthreads();                               // buf is free for the copies two blocks on
     buf ^= 1;
@@ -278,7 +283,7 @@ __global__ void __launch_bounds__(512) gram_tri_kernel(const float* __restrict__
 #pragma unroll
     for (int i = 0; i < 8; ++i)
 #pragma unroll
-      for (int j = 0; j < 8; ++j) xs[(i * 8 + j) * kTriStride + ul] = acc[i][j];
+      for (int j = 0; j < 8; ++j) xs[(i * 8 + j) * kTriStride + ul] = (j & 1) ? acc[i][j >> 1].y : acc[i][j >> 1].x;
   }
   __syncthreads();
   if (h == 1 || !act) return;
@@ -289,7 +294,7 @@ __global__ void __launch_bounds__(512) gram_tri_kernel(const float* __restrict__
 #pragma unroll
     for (int j = 0; j < 8; ++j) {
       const int cj = j < 4 ? 4 * tx + j : Kh + 4 * tx + j - 4;
-      const float v = acc[i][j] + xs[(i * 8 + j) * kTriStride + ul];
+      const float v = ((j & 1) ? acc[i][j >> 1].y : acc[i][j >> 1].x) + xs[(i * 8 + j) * kTriStride + ul];
       if (ri < Kp && cj < Kp) out[(int64_t)min(ri, cj) * Kp + max(ri, cj)] = v;
     }
     // One tile row at a time: keeps the compiler from hoisting all 64

@@ -209,15 +209,23 @@ __global__ void __launch_bounds__(4 * NG, 2) h_update_kernel(float* __restrict__
         const float4 x4 = *reinterpret_cast<const float4*>(xr[i] + j);
         xs[i][0] = x4.x; xs[i][1] = x4.y; xs[i][2] = x4.z; xs[i][3] = x4.w;
       }
+      // Two columns per instruction (packed FP32 multiply-add, each half
+      // rounded as a scalar fmaf).
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
         const float4 g = *reinterpret_cast<const float4*>(Gc + (j + u) * HT + 4 * sub);
+        const float2 g01 = make_float2(g.x, g.y), g23 = make_float2(g.z, g.w);
 #pragma unroll
         for (int i = 0; i < R; ++i) {
-          blk[i][0] = fmaf(g.x, xs[i][u], blk[i][0]);
-          blk[i][1] = fmaf(g.y, xs[i][u], blk[i][1]);
-          blk[i][2] = fmaf(g.z, xs[i][u], blk[i][2]);
-          blk[i][3] = fmaf(g.w, xs[i][u], blk[i][3]);
+          const float2 xx = make_float2(xs[i][u], xs[i][u]);
+          float2 a = make_float2(blk[i][0], blk[i][1]);
+          float2 b = make_float2(blk[i][2], blk[i][3]);
+          a = __ffma2_rn(g01, xx, a);
+          b = __ffma2_rn(g23, xx, b);
+          blk[i][0] = a.x;
+          blk[i][1] = a.y;
+          blk[i][2] = b.x;
+          blk[i][3] = b.y;
         }
       }
     };
