@@ -321,6 +321,23 @@ __device__ void worker_role(const WParams& p, char* smem, int wid) {
 #pragma unroll
       for (int v = 0; v < 4; ++v) sacc[u][v] = 0.f;
   };
+  // One row's products into the tile: two columns per instruction (packed
+  // FP32 multiply-add, each half rounded as a scalar fmaf).
+  auto s_acc = [&](const float4& a4, const float4& b4) {
+    const float a[4] = {a4.x, a4.y, a4.z, a4.w};
+    const float2 b01 = make_float2(b4.x, b4.y), b23 = make_float2(b4.z, b4.w);
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const float2 aa = make_float2(a[u], a[u]);
+      float2 l = make_float2(sacc[u][0], sacc[u][1]), r = make_float2(sacc[u][2], sacc[u][3]);
+      l = __ffma2_rn(aa, b01, l);
+      r = __ffma2_rn(aa, b23, r);
+      sacc[u][0] = l.x;
+      sacc[u][1] = l.y;
+      sacc[u][2] = r.x;
+      sacc[u][3] = r.y;
+    }
+  };
   auto s_rows = [&](int sc, int row0, int nrows) {
     int i0, j0;
     if (!s_tile(sc, &i0, &j0)) return;
@@ -336,22 +353,12 @@ __device__ void worker_role(const WParams& p, char* smem, int wid) {
           b4[q] = *reinterpret_cast<const float4*>(xr + q * ldx + j0);
         }
 #pragma unroll
-        for (int q = 0; q < 8; ++q) {
-          const float a[4] = {a4[q].x, a4[q].y, a4[q].z, a4[q].w}, b[4] = {b4[q].x, b4[q].y, b4[q].z, b4[q].w};
-#pragma unroll
-          for (int u = 0; u < 4; ++u)
-#pragma unroll
-            for (int v = 0; v < 4; ++v) sacc[u][v] = fmaf(a[u], b[v], sacc[u][v]);
-        }
+        for (int q = 0; q < 8; ++q) s_acc(a4[q], b4[q]);
       } else {
         for (int q = 0; 8 * g + q < nrows; ++q) {
           const float4 a4 = *reinterpret_cast<const float4*>(xr + q * ldx + i0);
           const float4 b4 = *reinterpret_cast<const float4*>(xr + q * ldx + j0);
-          const float a[4] = {a4.x, a4.y, a4.z, a4.w}, b[4] = {b4.x, b4.y, b4.z, b4.w};
-#pragma unroll
-          for (int u = 0; u < 4; ++u)
-#pragma unroll
-            for (int v = 0; v < 4; ++v) sacc[u][v] = fmaf(a[u], b[v], sacc[u][v]);
+          s_acc(a4, b4);
         }
       }
     }
@@ -479,15 +486,21 @@ __device__ void worker_role(const WParams& p, char* smem, int wid) {
             const float4 x4 = *reinterpret_cast<const float4*>(xr[u] + j);
             xs[u][0] = x4.x; xs[u][1] = x4.y; xs[u][2] = x4.z; xs[u][3] = x4.w;
           }
+          // Two columns per instruction (packed FP32 multiply-add).
 #pragma unroll
           for (int v = 0; v < 4; ++v) {
             const float4 g = *reinterpret_cast<const float4*>(Gc + (j + v) * WT + 4 * sub);
+            const float2 g01 = make_float2(g.x, g.y), g23 = make_float2(g.z, g.w);
 #pragma unroll
             for (int u = 0; u < WR; ++u) {
-              blk[u][0] = fmaf(g.x, xs[u][v], blk[u][0]);
-              blk[u][1] = fmaf(g.y, xs[u][v], blk[u][1]);
-              blk[u][2] = fmaf(g.z, xs[u][v], blk[u][2]);
-              blk[u][3] = fmaf(g.w, xs[u][v], blk[u][3]);
+              const float2 xx = make_float2(xs[u][v], xs[u][v]);
+              float2 l = make_float2(blk[u][0], blk[u][1]), r = make_float2(blk[u][2], blk[u][3]);
+              l = __ffma2_rn(g01, xx, l);
+              r = __ffma2_rn(g23, xx, r);
+              blk[u][0] = l.x;
+              blk[u][1] = l.y;
+              blk[u][2] = r.x;
+              blk[u][3] = r.y;
             }
           }
         };
