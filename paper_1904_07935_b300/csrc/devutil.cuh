@@ -135,6 +135,14 @@ __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
 // Blocked compensated subtraction for the factor updates, whose results
 // cancel most of their data term (y = b - sum of many non-negative terms):
 // terms are gathered in a short block partial t with plain multiply-adds;
+// (c0, c1) += a * b for two columns in one packed FP32 multiply-add; each
+// half is rounded as fmaf(a.x, b.x, c0) and fmaf(a.y, b.y, c1).
+__device__ __forceinline__ void fma_pair(float& c0, float& c1, const float2& a, const float2& b) {
+  const float2 r = __ffma2_rn(a, b, make_float2(c0, c1));
+  c0 = r.x;
+  c1 = r.y;
+}
+
 // comp_fold subtracts the block from the running value v with TwoSum and
 // keeps the exact rounding error in c, so that v + c carries the running
 // value to about one rounding of the block partials, not of every term.

@@ -96,11 +96,13 @@ __global__ void __launch_bounds__(256) gemm_kernel(GemmArgs g) {
         const float4 a = *reinterpret_cast<const float4*>(&As[buf][q][ty * 4]);
         const float4 b = *reinterpret_cast<const float4*>(&Bs[buf][q][tx * 4]);
         const float av[4] = {a.x, a.y, a.z, a.w};
-        const float bv[4] = {b.x, b.y, b.z, b.w};
+        const float2 b01 = make_float2(b.x, b.y), b23 = make_float2(b.z, b.w);
 #pragma unroll
-        for (int i = 0; i < 4; ++i)
-#pragma unroll
-          for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(av[i], bv[j], acc[i][j]);
+        for (int i = 0; i < 4; ++i) {
+          const float2 aa = make_float2(av[i], av[i]);
+          fma_pair(acc[i][0], acc[i][1], aa, b01);
+          fma_pair(acc[i][2], acc[i][3], aa, b23);
+        }
       }
       if (++steps == 64 / BK) {                 // running sum += block; the error restarts the block
 #pragma unroll
@@ -414,11 +416,14 @@ __global__ void __launch_bounds__(kSgemmThreads, 2) sgemm128_kernel(GemmArgs g) 
         const float4 b0 = *reinterpret_cast<const float4*>(&Bs[buf][q][tx * 4]);
         const float4 b1 = *reinterpret_cast<const float4*>(&Bs[buf][q][64 + tx * 4]);
         const float av[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
-        const float bv[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+        const float2 bv[4] = {make_float2(b0.x, b0.y), make_float2(b0.z, b0.w), make_float2(b1.x, b1.y),
+                              make_float2(b1.z, b1.w)};
 #pragma unroll
-        for (int i = 0; i < 8; ++i)
+        for (int i = 0; i < 8; ++i) {
+          const float2 aa = make_float2(av[i], av[i]);
 #pragma unroll
-          for (int j = 0; j < 8; ++j) acc[i][j] = fmaf(av[i], bv[j], acc[i][j]);
+          for (int j = 0; j < 4; ++j) fma_pair(acc[i][2 * j], acc[i][2 * j + 1], aa, bv[j]);
+        }
       }
       if (++steps == kFoldTiles) {
         fold();

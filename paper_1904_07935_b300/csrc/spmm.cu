@@ -14,16 +14,18 @@
 #include <algorithm>
 #include <numeric>
 
+#include "devutil.cuh"
 #include "internal.cuh"
 
 namespace plnmf {
 namespace {
 
+// acc += a x, two lanes per packed FP32 multiply-add (each half rounded as
+// a scalar fmaf).
 __device__ __forceinline__ void fma4(float4& acc, float a, const float4& x) {
-  acc.x = fmaf(a, x.x, acc.x);
-  acc.y = fmaf(a, x.y, acc.y);
-  acc.z = fmaf(a, x.z, acc.z);
-  acc.w = fmaf(a, x.w, acc.w);
+  const float2 aa = make_float2(a, a);
+  fma_pair(acc.x, acc.y, aa, make_float2(x.x, x.y));
+  fma_pair(acc.z, acc.w, aa, make_float2(x.z, x.w));
 }
 
 // Minimum resident CTAs per SM the compiler plans registers for.  It bounds
