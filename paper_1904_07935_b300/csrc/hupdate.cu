@@ -558,10 +558,9 @@ __global__ void __launch_bounds__(HTHREADS) w_prep_kernel(const float* __restric
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
       const float4 g = *reinterpret_cast<const float4*>(Gc + (j + u) * HT + 4 * sub);
-      blk[0] = fmaf(g.x, xs[u], blk[0]);
-      blk[1] = fmaf(g.y, xs[u], blk[1]);
-      blk[2] = fmaf(g.z, xs[u], blk[2]);
-      blk[3] = fmaf(g.w, xs[u], blk[3]);
+      const float2 xx = make_float2(xs[u], xs[u]);
+      fma_pair(blk[0], blk[1], make_float2(g.x, g.y), xx);
+      fma_pair(blk[2], blk[3], make_float2(g.z, g.w), xx);
     }
   };
   // Full blocks unrolled; a ragged last block step by step.

@@ -1152,11 +1152,19 @@ __device__ void chain_role(const WParams& p, char* smem) {
         if (lane == 0) wpart[warp] = ss;
         __syncthreads();
         if (t > 0) {
+          // Columns t+1 .. 15: an odd first one alone, then even-aligned
+          // pairs in packed FP32 multiply-adds (each half as a scalar fmaf).
+          const int s0 = t + 1;
+          if (s0 < WT && (s0 & 1)) {
+            const float g = G[t - 1][s0];
 #pragma unroll
-          for (int s2 = t + 1; s2 < WT; ++s2) {
-            const float g = G[t - 1][s2];
+            for (int i = 0; i < RPT; ++i) y[i][s0] = fmaf(-xp[i], g, y[i][s0]);
+          }
 #pragma unroll
-            for (int i = 0; i < RPT; ++i) y[i][s2] = fmaf(-xp[i], g, y[i][s2]);
+          for (int s2 = (s0 + 1) & ~1; s2 < WT; s2 += 2) {
+            const float2 g = make_float2(G[t - 1][s2], G[t - 1][s2 + 1]);
+#pragma unroll
+            for (int i = 0; i < RPT; ++i) fma_pair(y[i][s2], y[i][s2 + 1], make_float2(-xp[i], -xp[i]), g);
           }
         }
         // Every row warp waits for the column's CL partials itself and adds
