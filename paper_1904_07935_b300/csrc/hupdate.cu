@@ -435,10 +435,9 @@ __global__ void __launch_bounds__(256) h_update_warp_kernel(float* __restrict__ 
 #pragma unroll
         for (int q = 0; q < HT / 4; ++q) {
           const float4 g = g4[q];
-          p[4 * q] = fmaf(g.x, hj[m], p[4 * q]);
-          p[4 * q + 1] = fmaf(g.y, hj[m], p[4 * q + 1]);
-          p[4 * q + 2] = fmaf(g.z, hj[m], p[4 * q + 2]);
-          p[4 * q + 3] = fmaf(g.w, hj[m], p[4 * q + 3]);
+          const float2 hh = make_float2(hj[m], hj[m]);
+          fma_pair(p[4 * q], p[4 * q + 1], make_float2(g.x, g.y), hh);
+          fma_pair(p[4 * q + 2], p[4 * q + 3], make_float2(g.z, g.w), hh);
         }
       }
     }
