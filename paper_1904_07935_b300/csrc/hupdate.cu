@@ -114,6 +114,7 @@ __device__ __forceinline__ void prefetch_gcols(float* Gc, const float* __restric
 constexpr int HL = 4;             // lanes per row
 constexpr int HROWS = 64;         // rows per CTA
 constexpr int HTHREADS = HROWS * HL;
+constexpr int W_PREP_R = 2;       // rows per lane group in w_prep_kernel
 
 // R rows per lane group: each group of 4 lanes owns R rows (4 tile columns per
 // lane), so a 16-byte load of S's column block serves R rows.  The grid
@@ -520,12 +521,17 @@ __global__ void __launch_bounds__(256) h_update_warp_kernel(float* __restrict__ 
 // (Y = -sums; the caller adds P later); with Ylo given, the compensation of
 // the sum goes to Ylo (N x HT) instead of being rounded into Y, since P and
 // the sum cancel when the caller adds them.
-__global__ void __launch_bounds__(HTHREADS) w_prep_kernel(const float* __restrict__ X, const float* __restrict__ B,
-                                                          const float* __restrict__ G, float* __restrict__ Y,
-                                                          float* __restrict__ Ylo, int N, int K, int Kp, int lo,
-                                                          int new_end, int T, int* status, ChainOrder co) {
+template <int R>
+__global__ void __launch_bounds__(HTHREADS / R) w_prep_kernel(const float* __restrict__ X, const float* __restrict__ B,
+                                                              const float* __restrict__ G, float* __restrict__ Y,
+                                                              float* __restrict__ Ylo, int N, int K, int Kp, int lo,
+                                                              int new_end, int T, int* status, ChainOrder co) {
   // Shared memory: Gc (Kr x HT) = G[j][lo + c], zero beyond K; Xs = the CTA's
-  // rows of X (row stride Kp + 4, see h_update_kernel).
+  // rows of X (row stride Kp + 4, see h_update_kernel).  A lane group of
+  // four lanes takes R of the CTA's HROWS rows (rows g, g + HROWS / R, ...),
+  // so one 16-byte load of Gc serves R rows.
+  constexpr int NT = HTHREADS / R;
+  constexpr int NGR = NT / HL;                            // lane groups
   extern __shared__ __align__(16) float smem[];
   __shared__ __align__(8) unsigned long long bar;
   const int Kr = (Kp + HT - 1) / HT * HT;
@@ -537,30 +543,55 @@ __global__ void __launch_bounds__(HTHREADS) w_prep_kernel(const float* __restric
   const int sub = tid & (HL - 1);
   const int row0 = blockIdx.x * HROWS;
   const int nrows = min(HROWS, N - row0);
-  const int row = row0 + (tid >> 2);
-  const bool valid = (tid >> 2) < nrows;
-  stage_gcols<HTHREADS>(Gc, G, Kp, K, lo, Kr);
+  stage_gcols<NT>(Gc, G, Kp, K, lo, Kr);
   stage_rows_bulk(Xs, ldx, X, row0, nrows, Kp, &bar, status);
-  if (!valid) return;
-  const float* xr = Xs + (tid >> 2) * ldx;
-  float acc[4];
+  if ((tid >> 2) >= nrows) return;                        // (its later rows are out too)
+  int lrow[R];
+  bool valid[R];
+  const float* xr[R];
 #pragma unroll
-  for (int q = 0; q < 4; ++q) {
-    const int c = lo + 4 * sub + q;
-    acc[q] = (c < hi && B) ? __ldg(B + (int64_t)row * Kp + c) : 0.f;
+  for (int i = 0; i < R; ++i) {
+    lrow[i] = (tid >> 2) + i * NGR;
+    valid[i] = lrow[i] < nrows;
+    xr[i] = Xs + lrow[i] * ldx;                           // within the HROWS staged rows
   }
+  float acc[R][4];
+#pragma unroll
+  for (int i = 0; i < R; ++i)
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int c = lo + 4 * sub + q;
+      acc[i][q] = (valid[i] && c < hi && B) ? __ldg(B + (int64_t)(row0 + lrow[i]) * Kp + c) : 0.f;
+    }
   // Blocks of HT terms folded into acc with compensation (comp_fold).
-  float cmp[4] = {0.f, 0.f, 0.f, 0.f}, blk[4] = {0.f, 0.f, 0.f, 0.f};
+  float cmp[R][4], blk[R][4];
+#pragma unroll
+  for (int i = 0; i < R; ++i)
+#pragma unroll
+    for (int q = 0; q < 4; ++q) cmp[i][q] = blk[i][q] = 0.f;
   auto step = [&](int j) {
-    const float4 x4 = *reinterpret_cast<const float4*>(xr + j);
-    const float xs[4] = {x4.x, x4.y, x4.z, x4.w};
+    float xs[R][4];
+#pragma unroll
+    for (int i = 0; i < R; ++i) {
+      const float4 x4 = *reinterpret_cast<const float4*>(xr[i] + j);
+      xs[i][0] = x4.x; xs[i][1] = x4.y; xs[i][2] = x4.z; xs[i][3] = x4.w;
+    }
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
       const float4 g = *reinterpret_cast<const float4*>(Gc + (j + u) * HT + 4 * sub);
-      const float2 xx = make_float2(xs[u], xs[u]);
-      fma_pair(blk[0], blk[1], make_float2(g.x, g.y), xx);
-      fma_pair(blk[2], blk[3], make_float2(g.z, g.w), xx);
+#pragma unroll
+      for (int i = 0; i < R; ++i) {
+        const float2 xx = make_float2(xs[i][u], xs[i][u]);
+        fma_pair(blk[i][0], blk[i][1], make_float2(g.x, g.y), xx);
+        fma_pair(blk[i][2], blk[i][3], make_float2(g.z, g.w), xx);
+      }
     }
+  };
+  auto fold = [&]() {
+#pragma unroll
+    for (int i = 0; i < R; ++i)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) comp_fold(acc[i][q], cmp[i][q], blk[i][q]);
   };
   // Full blocks unrolled; a ragged last block step by step.
   auto outside = [&](int j0, int j1) {
@@ -569,56 +600,61 @@ __global__ void __launch_bounds__(HTHREADS) w_prep_kernel(const float* __restric
     for (; jb + HT <= j1; jb += HT) {
 #pragma unroll
       for (int jj = 0; jj < HT; jj += 4) step(jb + jj);
-#pragma unroll
-      for (int q = 0; q < 4; ++q) comp_fold(acc[q], cmp[q], blk[q]);
+      fold();
     }
     if (jb < j1) {
 #pragma unroll 1
       for (int j = jb; j < j1; j += 4) step(j);
-#pragma unroll
-      for (int q = 0; q < 4; ++q) comp_fold(acc[q], cmp[q], blk[q]);
+      fold();
     }
   };
   outside(0, new_end);
   outside(lo + T < Kp ? lo + T : Kp, Kp);
   // Old in-tile columns j > c: one more block.
-  float xo[HT];
 #pragma unroll
-  for (int q = 0; q < HT / 4; ++q) {
-    float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-    if (lo + 4 * q < Kp) v = *reinterpret_cast<const float4*>(xr + lo + 4 * q);
-    xo[4 * q] = v.x; xo[4 * q + 1] = v.y; xo[4 * q + 2] = v.z; xo[4 * q + 3] = v.w;
-  }
+  for (int i = 0; i < R; ++i) {
+    float xo[HT];
 #pragma unroll
-  for (int j = 1; j < HT; ++j) {
-    const float4 g4 = *reinterpret_cast<const float4*>(Gc + (lo + j) * HT + 4 * sub);
-    const float gv[4] = {g4.x, g4.y, g4.z, g4.w};
+    for (int q = 0; q < HT / 4; ++q) {
+      float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (lo + 4 * q < Kp) v = *reinterpret_cast<const float4*>(xr[i] + lo + 4 * q);
+      xo[4 * q] = v.x; xo[4 * q + 1] = v.y; xo[4 * q + 2] = v.z; xo[4 * q + 3] = v.w;
+    }
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const int cl = 4 * sub + q;
-      if (j > cl && j < T) blk[q] = fmaf(gv[q], xo[j], blk[q]);
+    for (int j = 1; j < HT; ++j) {
+      const float4 g4 = *reinterpret_cast<const float4*>(Gc + (lo + j) * HT + 4 * sub);
+      const float gv[4] = {g4.x, g4.y, g4.z, g4.w};
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int cl = 4 * sub + q;
+        if (j > cl && j < T) blk[i][q] = fmaf(gv[q], xo[j], blk[i][q]);
+      }
     }
   }
+  fold();
 #pragma unroll
-  for (int q = 0; q < 4; ++q) comp_fold(acc[q], cmp[q], blk[q]);
-  if (co.base) {
-    // In the W chain's register order (lo = 0, T = 16: this lane's quad;
-    // zero past K, where every G factor is).
-    const long long qi = chain_quad(row, sub, co.chain_rows, co.rpt);
-    reinterpret_cast<float4*>(co.base)[qi] = make_float4(acc[0], acc[1], acc[2], acc[3]);
-    reinterpret_cast<float4*>(co.comp)[qi] = make_float4(cmp[0], cmp[1], cmp[2], cmp[3]);
-    return;
-  }
-  float* yr = Y + (int64_t)row * Kp;
+  for (int i = 0; i < R; ++i) {
+    if (!valid[i]) continue;
+    const int row = row0 + lrow[i];
+    if (co.base) {
+      // In the W chain's register order (lo = 0, T = 16: this lane's quad;
+      // zero past K, where every G factor is).
+      const long long qi = chain_quad(row, sub, co.chain_rows, co.rpt);
+      reinterpret_cast<float4*>(co.base)[qi] = make_float4(acc[i][0], acc[i][1], acc[i][2], acc[i][3]);
+      reinterpret_cast<float4*>(co.comp)[qi] = make_float4(cmp[i][0], cmp[i][1], cmp[i][2], cmp[i][3]);
+      continue;
+    }
+    float* yr = Y + (int64_t)row * Kp;
 #pragma unroll
-  for (int q = 0; q < 4; ++q) {
-    const int c = lo + 4 * sub + q;
-    if (c >= hi) continue;
-    if (Ylo) {
-      yr[c] = acc[q];
-      Ylo[(int64_t)row * HT + c - lo] = cmp[q];
-    } else {
-      yr[c] = acc[q] + cmp[q];
+    for (int q = 0; q < 4; ++q) {
+      const int c = lo + 4 * sub + q;
+      if (c >= hi) continue;
+      if (Ylo) {
+        yr[c] = acc[i][q];
+        Ylo[(int64_t)row * HT + c - lo] = cmp[i][q];
+      } else {
+        yr[c] = acc[i][q] + cmp[i][q];
+      }
     }
   }
 }
@@ -631,11 +667,12 @@ cudaError_t w_prep_run(const float* X, const float* B, const float* G, float* Y,
   if (co && (B || lo != 0 || new_end != 0 || T != HT || !co->base || !co->comp || co->chain_rows < 1 || co->rpt < 1))
     return cudaErrorInvalidValue;
   const size_t smem = sizeof(float) * ((size_t)((Kp + HT - 1) / HT * HT) * HT + (size_t)HROWS * (Kp + 4));
-  cudaError_t e = cudaFuncSetAttribute(w_prep_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return e;
   const int blocks = (N + HROWS - 1) / HROWS;
-  w_prep_kernel<<<blocks, HTHREADS, smem, s>>>(X, B, G, Y, B ? nullptr : Ylo, N, K, Kp, lo, new_end, T, status,
-                                                co ? *co : ChainOrder{});
+  auto kern = w_prep_kernel<W_PREP_R>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  kern<<<blocks, HTHREADS / W_PREP_R, smem, s>>>(X, B, G, Y, B ? nullptr : Ylo, N, K, Kp, lo, new_end, T, status,
+                                                  co ? *co : ChainOrder{});
   return cudaGetLastError();
 }
 
