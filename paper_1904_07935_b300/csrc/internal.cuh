@@ -240,7 +240,7 @@ struct WPersistConfig {
   int rpt = 1;
   int n_workers = 0;      // worker CTAs (one per SM outside the chain)
   int worker_rows = 128;
-  int worker_wr = 1;      // rows per worker lane group (2 for Kp >= 192)
+  int worker_wr = 1;      // rows per worker lane group (2 for Kp >= 128)
   int chain_rows = 0;     // rows per chain CTA
   int stage_rows = 128;   // rows a worker stages at once (its whole block where it fits)
   size_t chain_smem = 0;

@@ -248,9 +248,10 @@ __device__ __forceinline__ void base_row_global(const WParams& p, int v, int lo,
 // Worker role: tile bases.
 // --------------------------------------------------------------------------
 // WR rows per lane group: group g takes rows g and (WR = 2) g + RB / 2 of
-// the pass, so that one 16-byte load of Q's block serves WR rows (long rows,
-// Kp >= 192, where the shared-memory loads bound the workers); each row's
-// arithmetic is the same either way.
+// the pass, so that one 16-byte load of Q's block serves WR rows (Kp >= 128,
+// where the shared-memory loads bound the workers: text-like K = 160 W update
+// 198 -> 194 us; neutral at K = 80); each row's arithmetic is the same
+// either way.
 template <int WR>
 __device__ void worker_role(const WParams& p, char* smem, int wid) {
   const int nt = (p.K + WT - 1) / WT;
@@ -1421,7 +1422,7 @@ bool w_persistent_config(int N, int Kp, WPersistConfig* cfg, bool tc) {
         wsmem = std::max(wsmem, whole);
       }
     }
-    cfg->worker_wr = Kp >= 192 ? 2 : 1;
+    cfg->worker_wr = Kp >= 128 ? 2 : 1;
     cfg->chain_smem = csmem;
     cfg->worker_smem = wsmem;
     cfg->tc = tc;
