@@ -746,10 +746,10 @@ cudaError_t h_update_dispatch(float* X, const float* B, const float* G, int N, i
   // 16-group CTAs spread more evenly over the SMs than 32-group ones (11,314
   // rows, one row per group: 708 CTAs, 4.8 per SM, against 354 at 2.4 per
   // SM: 66.6 -> 64.1 us at K = 160).  Two rows per group where that still
-  // leaves two CTAs per SM: a 16-byte load of S's block then serves both rows,
+  // leaves a CTA per SM: a 16-byte load of S's block then serves both rows,
   // and the kernel is bound by its shared-memory wavefronts (11,314 rows at
-  // K = 160: 60.3 -> 56.2 us, one row per group against two).
-  if ((long long)(N + 31) / 32 >= 2LL * sms)
+  // K = 160: 60.3 -> 56.2 us; 8,000 rows at K = 128: 37.5 -> 33.3 us).
+  if ((long long)(N + 31) / 32 >= sms)
     return h_update_launch<2, 16>(X, B, G, N, K, Kp, eps, status, s, skip, dref, dpart, nblk);
   return h_update_launch<1, 16>(X, B, G, N, K, Kp, eps, status, s, skip, dref, dpart, nblk);
 }
