@@ -344,8 +344,10 @@ nmf_status nmf_gemm(int32_t M, int32_t N, int32_t K, const float* A, int64_t lda
  *   and `stream` (the batch's launch stream; NULL = a new one owned by the
  *   batch) must differ from all of them (NMF_EINVAL otherwise, and for
  *   n < 1).  Members switch to the per-tile W launches (the two-grid W
- *   update holds every SM); a member's own single-problem graph is
- *   re-captured on its next nmf_iterate.  autotune != 0: for each member,
+ *   update holds every SM) and to H-update CTAs of two rows per lane group
+ *   (fewer, fuller CTAs for SMs that the members share; the same
+ *   arithmetic); a member's own single-problem graph is re-captured on its
+ *   next nmf_iterate.  autotune != 0: for each member,
  *   timed with CUDA events from the same start: (1) sparse A: the SpMM
  *   schedule of each product, rows longer than seg non-zeros split into
  *   seg-long items (seg in 128, 256, 512, 1024) or no split, fastest of

@@ -704,7 +704,7 @@ cudaError_t h_update_warp_launch(float* X, const float* B, const float* G, int N
 namespace {
 cudaError_t h_update_dispatch(float* X, const float* B, const float* G, int N, int K, int Kp, float eps,
                               int* status, cudaStream_t s, const int* skip, const float* dref, double* dpart,
-                              int* nblk) {
+                              int* nblk, bool pack_rows = false) {
   // One warp per row for short rows (Kp <= 32): the row is one register per
   // lane and the warp kernel's per-row column chain is short.  For longer
   // rows the four-lanes-per-row kernel is faster: its chain runs for eight
@@ -749,16 +749,16 @@ cudaError_t h_update_dispatch(float* X, const float* B, const float* G, int N, i
   // leaves a CTA per SM: a 16-byte load of S's block then serves both rows,
   // and the kernel is bound by its shared-memory wavefronts (11,314 rows at
   // K = 160: 60.3 -> 56.2 us; 8,000 rows at K = 128: 37.5 -> 33.3 us).
-  if ((long long)(N + 31) / 32 >= sms)
+  if (pack_rows || (long long)(N + 31) / 32 >= sms)
     return h_update_launch<2, 16>(X, B, G, N, K, Kp, eps, status, s, skip, dref, dpart, nblk);
   return h_update_launch<1, 16>(X, B, G, N, K, Kp, eps, status, s, skip, dref, dpart, nblk);
 }
 }  // namespace
 
 cudaError_t h_update_run(float* X, const float* B, const float* G, int N, int K, int Kp, float eps,
-                         int* status, cudaStream_t s, const int* skip) {
+                         int* status, cudaStream_t s, const int* skip, bool pack_rows) {
   if (N <= 0 || K <= 0) return cudaSuccess;
-  return h_update_dispatch(X, B, G, N, K, Kp, eps, status, s, skip, nullptr, nullptr, nullptr);
+  return h_update_dispatch(X, B, G, N, K, Kp, eps, status, s, skip, nullptr, nullptr, nullptr, pack_rows);
 }
 
 size_t h_sweep_partials(int N) { return 2 * (size_t)((N + 15) / 16); }

@@ -175,8 +175,11 @@ bool chain_config_cluster(int N, int T, int cl, ChainConfig* cfg);
 // Whole H update in one launch (rows independent): X (N x Kp) old -> new in
 // place, B = R, G = S.  skip (device int, optional): when nonzero at launch
 // the kernel leaves X as it is (the converged part of a sweep loop).
+// pack_rows: two rows per lane group at every row count (fewer CTAs and
+// shared-memory loads for the same arithmetic; for problems that share the
+// GPU with others, as batch members do).
 cudaError_t h_update_run(float* X, const float* B, const float* G, int N, int K, int Kp, float eps,
-                         int* status, cudaStream_t s, const int* skip = nullptr);
+                         int* status, cudaStream_t s, const int* skip = nullptr, bool pack_rows = false);
 // The same update with the off-tile sums on the tensor cores (3xTF32 with
 // per-plane compensated folds); supported for 16 <= Kp <= 512.
 bool h_update_tc_supported(int Kp);

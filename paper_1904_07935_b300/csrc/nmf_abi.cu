@@ -49,6 +49,7 @@ struct nmf_ctx {
   unsigned long long wait_ns = 0;       // limit of the W update's device waits (0: library default)
   int extra_arrivals = 0;               // tests of the timeout path: a hand-off count that cannot be reached
   bool w_workers_after_chain = false;   // W worker grid in plain stream order after the chain grid
+  bool h_pack_rows = false;             // H update: two rows per lane group at any row count (batch members)
   std::vector<cudaEvent_t> ev;          // fork / join events of the W update
   // A (caller-owned) and its transpose (context-owned, CSR only).
   const float* dense = nullptr;
@@ -238,7 +239,7 @@ cudaError_t enq_update(nmf_ctx* c, float* X, const float* G, const float* B, int
   if (!is_w) {
     c->launch_count += 1;
     if (c->tc_updates) return h_update_tc_run(X, B, G, N, K, Kp, c->eps, c->d_status, c->stream);
-    return h_update_run(X, B, G, N, K, Kp, c->eps, c->d_status, c->stream);
+    return h_update_run(X, B, G, N, K, Kp, c->eps, c->d_status, c->stream, nullptr, c->h_pack_rows);
   }
   if (c->w_persistent) {
     c->launch_count += 1;
@@ -937,6 +938,7 @@ nmf_status nmf_batch_create(nmf_ctx* const* ctxs, int32_t n, int32_t autotune, v
   for (int i = 0; i < n; ++i) {
     nmf_ctx* c = b->m[i];
     c->w_persistent = false;
+    c->h_pack_rows = true;        // the members share the SMs: fewer, fuller CTAs (same arithmetic)
     if (c->ws_gram) {
       // The per-tile W update forms no Gram partials; S is formed again with
       // the Gram's own chunking, so that a member computes exactly what a
